@@ -1,0 +1,477 @@
+/*
+ * FP64 CPU oracle for symmetric sparse kernels (SySTeC, arXiv 2406.09266).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is compiled into liboracle.so and is
+ * loaded by the tests, by the smoke check and by the CPU-baseline leg of the
+ * benchmark.  The product library never links, loads or calls it, and it shares
+ * no code, header, table or constant with the CUDA path.
+ *
+ * Everything here is the plain definition written out, in double precision:
+ *   - canonical coordinates: the upper triangle, i_1 <= i_2 <= ... <= i_N
+ *     (Sec. 2.1, Def. "Canonical"; full symmetry, Def. "Symmetry");
+ *   - each stored canonical entry stands for every DISTINCT permutation of its
+ *     indices (Sec. 3.1: n!/m! assignments when m indices are equal; Sec. 4.1,
+ *     Def. "Unique Symmetry Group" S_P|E and the symmetrised-kernel pseudocode
+ *     figure: for every equivalence group E, for every sigma in S_P|E, apply the
+ *     assignment with permuted indices).  The oracle enumerates those
+ *     permutations literally with a next-permutation step on the sorted tuple,
+ *     which visits each distinct arrangement exactly once;
+ *   - MTTKRP  C[i,r] = sum A[i,k,l,..] B[k,r] B[l,r] ..        (Sec. 5.2.6)
+ *   - SSYMV   y[i]   = sum_j A[i,j] x[j]                        (Sec. 5.2.1)
+ *   - SYPRD   y      = sum x[i] A[i,j] x[j]                      (Sec. 5.2.3)
+ *   - CP fit  ||X - sum_r b_r (x) ... (x) b_r||^2, unit weights, over the full
+ *     tensor (the symmetric CPD that MTTKRP serves, Sec. 5.2.6).
+ * A second, independent MTTKRP form uses per-run integer weights (the
+ * diagonal-splitting / simplicial-lookup-table result of Sec. 4.2.5, 4.2.9 and
+ * the split loop nests of Sec. 4.3) so the two can be checked against each other.
+ *
+ * Pins (tests/test_oracle_*.py): dense brute force on tiny tensors (expand the
+ * canonical triangle over all N! position permutations, then a dense einsum),
+ * the paper's printed multiplicities 6/3/3/1 and per-row update counts for the
+ * 3-way MTTKRP, the lookup-table values [2,0,1,1,0,0,1/3], closed forms
+ * N!/prod(m!) for the counts, x^T(Ax) = SYPRD, relabel and input-permutation
+ * invariance.  No function here is "parity unpinned".
+ *
+ * Conventions: 0-based indices; coordinate arrays are (order x nnz) row-major,
+ * idx[q*nnz + e]; dense factors are row-major n x R.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define ORC_OK 0
+#define ORC_INVALID (-1)
+#define ORC_NONCANONICAL (-2)
+#define ORC_RANGE (-3)
+#define ORC_DUPLICATE (-4)
+#define ORC_NOMEM (-5)
+
+#define ORC_MAX_ORDER 5
+
+/* ------------------------------------------------------------------------ */
+/* small helpers                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* In-place ascending sort of a short tuple (insertion sort). */
+static void sort_tuple(int32_t* c, int order) {
+    for (int a = 1; a < order; ++a) {
+        int32_t t = c[a];
+        int b = a - 1;
+        while (b >= 0 && c[b] > t) { c[b + 1] = c[b]; --b; }
+        c[b + 1] = t;
+    }
+}
+
+/* Next lexicographic permutation of a[0..k); returns 0 after the last one.
+ * Starting from the ascending tuple this visits every distinct arrangement
+ * of the multiset exactly once. */
+static int next_perm(int32_t* a, int k) {
+    int i = k - 2;
+    while (i >= 0 && a[i] >= a[i + 1]) --i;
+    if (i < 0) return 0;
+    int j = k - 1;
+    while (a[j] <= a[i]) --j;
+    int32_t t = a[i]; a[i] = a[j]; a[j] = t;
+    for (int l = i + 1, r = k - 1; l < r; ++l, --r) { t = a[l]; a[l] = a[r]; a[r] = t; }
+    return 1;
+}
+
+typedef struct {
+    int32_t c[ORC_MAX_ORDER];
+    float v;
+    int64_t pos;
+} rec_t;
+
+static int g_order_for_cmp = 0;
+
+static int cmp_rec(const void* pa, const void* pb) {
+    const rec_t* a = (const rec_t*)pa;
+    const rec_t* b = (const rec_t*)pb;
+    for (int q = 0; q < g_order_for_cmp; ++q) {
+        if (a->c[q] < b->c[q]) return -1;
+        if (a->c[q] > b->c[q]) return 1;
+    }
+    /* equal coordinates: keep input order so the surviving duplicate is the first */
+    if (a->pos < b->pos) return -1;
+    if (a->pos > b->pos) return 1;
+    return 0;
+}
+
+static void load_tuple(const int32_t* idx, int order, int64_t nnz, int64_t e, int32_t* c) {
+    for (int q = 0; q < order; ++q) c[q] = idx[(int64_t)q * nnz + e];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Canonicalisation (Sec. 2.1 Def. Canonical, upper triangle)                 */
+/* ------------------------------------------------------------------------ */
+
+/* Sort every tuple ascending, check 0 <= c < n, sort the entries
+ * lexicographically and resolve duplicates: policy 0 rejects any repeated
+ * multiset; policy 1 keeps the first copy and rejects copies whose value bits
+ * differ.  Output arrays have room for nnz entries. */
+int orc_canonicalize(int order, int64_t n, int64_t nnz, const int32_t* idx, const float* val,
+                     int dup_policy, int32_t* cidx, float* cval, int64_t* nnz_out) {
+    if (order < 1 || order > ORC_MAX_ORDER || n <= 0 || nnz < 0) return ORC_INVALID;
+    *nnz_out = 0;
+    if (nnz == 0) return ORC_OK;
+    rec_t* r = (rec_t*)malloc(sizeof(rec_t) * (size_t)nnz);
+    if (!r) return ORC_NOMEM;
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(idx, order, nnz, e, r[e].c);
+        for (int q = 0; q < order; ++q)
+            if (r[e].c[q] < 0 || r[e].c[q] >= n) { free(r); return ORC_RANGE; }
+        sort_tuple(r[e].c, order);
+        r[e].v = val[e];
+        r[e].pos = e;
+    }
+    g_order_for_cmp = order;
+    qsort(r, (size_t)nnz, sizeof(rec_t), cmp_rec);
+    int64_t m = 0;
+    for (int64_t e = 0; e < nnz; ++e) {
+        if (m > 0) {
+            int same = 1;
+            for (int q = 0; q < order; ++q)
+                if (r[e].c[q] != cidx[(int64_t)q * nnz + (m - 1)]) { same = 0; break; }
+            if (same) {
+                if (dup_policy != 1) { free(r); return ORC_DUPLICATE; }
+                uint32_t ba, bb;
+                memcpy(&ba, &r[e].v, 4);
+                memcpy(&bb, &cval[m - 1], 4);
+                if (ba != bb) { free(r); return ORC_DUPLICATE; }
+                continue;
+            }
+        }
+        for (int q = 0; q < order; ++q) cidx[(int64_t)q * nnz + m] = r[e].c[q];
+        cval[m] = r[e].v;
+        ++m;
+    }
+    free(r);
+    /* compact the rows if duplicates were dropped (rows are nnz apart) */
+    if (m != nnz)
+        for (int q = 1; q < order; ++q)
+            memmove(cidx + (int64_t)q * m, cidx + (int64_t)q * nnz, sizeof(int32_t) * (size_t)m);
+    *nnz_out = m;
+    return ORC_OK;
+}
+
+/* Checks that a coordinate list is canonical, sorted and duplicate free. */
+int orc_check_canonical(int order, int64_t n, int64_t nnz, const int32_t* cidx) {
+    int32_t prev[ORC_MAX_ORDER], c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        for (int q = 0; q < order; ++q) {
+            if (c[q] < 0 || c[q] >= n) return ORC_RANGE;
+            if (q > 0 && c[q - 1] > c[q]) return ORC_NONCANONICAL;
+        }
+        if (e > 0) {
+            int cmp = 0;
+            for (int q = 0; q < order && !cmp; ++q) cmp = (c[q] > prev[q]) - (c[q] < prev[q]);
+            if (cmp == 0) return ORC_DUPLICATE;
+            if (cmp < 0) return ORC_NONCANONICAL;
+        }
+        memcpy(prev, c, sizeof(c));
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Counts (integers, compared bit-exactly)                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Number of distinct permutations of a canonical tuple, by enumeration. */
+int64_t orc_distinct_perms(int order, const int32_t* c_in) {
+    int32_t c[ORC_MAX_ORDER];
+    memcpy(c, c_in, sizeof(int32_t) * (size_t)order);
+    sort_tuple(c, order);
+    int64_t k = 0;
+    do { ++k; } while (next_perm(c, order));
+    return k;
+}
+
+/* Equality pattern of a canonical tuple: bit q set when c_q == c_{q+1}. */
+static int pattern_of(const int32_t* c, int order) {
+    int p = 0;
+    for (int q = 0; q + 1 < order; ++q)
+        if (c[q] == c[q + 1]) p |= 1 << q;
+    return p;
+}
+
+/* counts[p] = entries with equality pattern p (p < 16); *expanded = sum of the
+ * distinct-permutation counts (nonzeros of the full tensor); *root_fibers =
+ * distinct c_1; *l2_fibers = distinct (c_1, c_2); *normsq = ||X||^2 over the
+ * full tensor = sum over entries of (#perms) * v^2. */
+int orc_counts(int order, int64_t nnz, const int32_t* cidx, const float* cval, int64_t* counts,
+               int64_t* expanded, int64_t* root_fibers, int64_t* l2_fibers, double* normsq) {
+    if (order < 1 || order > ORC_MAX_ORDER) return ORC_INVALID;
+    for (int p = 0; p < 16; ++p) counts[p] = 0;
+    *expanded = 0; *root_fibers = 0; *l2_fibers = 0; *normsq = 0.0;
+    int32_t c[ORC_MAX_ORDER], prev[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        counts[pattern_of(c, order)] += 1;
+        int64_t k = orc_distinct_perms(order, c);
+        *expanded += k;
+        *normsq += (double)k * (double)cval[e] * (double)cval[e];
+        if (e == 0 || c[0] != prev[0]) *root_fibers += 1;
+        if (order >= 2 && (e == 0 || c[0] != prev[0] || c[1] != prev[1])) *l2_fibers += 1;
+        memcpy(prev, c, sizeof(c));
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* MTTKRP, definitional form                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* M[pi_1, r] += v * prod_{q >= 2} B[pi_q, r] for every distinct permutation pi
+ * of every canonical entry; this is the full-tensor MTTKRP restricted to its
+ * nonzeros.  Mabs (nullable) receives sum |terms| per output element.
+ * row_mask (nullable, length n) limits the work to selected output rows. */
+int orc_mttkrp_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval,
+                    const double* B, int R, double* M, double* Mabs, const uint8_t* row_mask) {
+    if (order < 2 || order > ORC_MAX_ORDER || R <= 0) return ORC_INVALID;
+    memset(M, 0, sizeof(double) * (size_t)n * (size_t)R);
+    if (Mabs) memset(Mabs, 0, sizeof(double) * (size_t)n * (size_t)R);
+    int32_t c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_tuple(c, order);
+        double v = (double)cval[e];
+        do {
+            int64_t i = c[0];
+            if (row_mask && !row_mask[i]) continue;
+            for (int r = 0; r < R; ++r) {
+                double t = v;
+                for (int q = 1; q < order; ++q) t *= B[(int64_t)c[q] * R + r];
+                M[i * R + r] += t;
+                if (Mabs) Mabs[i * R + r] += fabs(t);
+            }
+        } while (next_perm(c, order));
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* MTTKRP, per-run weight form                                                */
+/* ------------------------------------------------------------------------ */
+
+static int64_t fact(int k) { int64_t f = 1; for (int a = 2; a <= k; ++a) f *= a; return f; }
+
+/* For a canonical entry with distinct values u_1 < .. < u_d of multiplicities
+ * m_1..m_d, the permutations whose first index is u_t number
+ * W_t = (N-1)! / ((m_t - 1)! prod_{s != t} m_s!), and each contributes
+ * v * prod_s B[u_s]^(m_s - [s == t]).  Written from the run structure, not by
+ * enumeration. */
+int orc_mttkrp_runs(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval,
+                    const double* B, int R, double* M) {
+    if (order < 2 || order > ORC_MAX_ORDER || R <= 0) return ORC_INVALID;
+    memset(M, 0, sizeof(double) * (size_t)n * (size_t)R);
+    int32_t c[ORC_MAX_ORDER], u[ORC_MAX_ORDER];
+    int m[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_tuple(c, order);
+        int d = 0;
+        for (int q = 0; q < order; ++q) {
+            if (d > 0 && u[d - 1] == c[q]) m[d - 1] += 1;
+            else { u[d] = c[q]; m[d] = 1; ++d; }
+        }
+        double v = (double)cval[e];
+        for (int t = 0; t < d; ++t) {
+            int64_t den = fact(m[t] - 1);
+            for (int s = 0; s < d; ++s) if (s != t) den *= fact(m[s]);
+            double W = (double)(fact(order - 1) / den);
+            for (int r = 0; r < R; ++r) {
+                double p = W * v;
+                for (int s = 0; s < d; ++s) {
+                    int ex = m[s] - (s == t ? 1 : 0);
+                    for (int a = 0; a < ex; ++a) p *= B[(int64_t)u[s] * R + r];
+                }
+                M[(int64_t)u[t] * R + r] += p;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SSYMV and SYPRD over an upper-triangle CSR                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Validates the upper CSR: rowptr monotone from 0, cols in [row, n) strictly
+ * increasing within a row. */
+int orc_check_upper_csr(int64_t n, const int32_t* rowptr, const int32_t* col) {
+    if (n < 0 || rowptr[0] != 0) return ORC_INVALID;
+    for (int64_t i = 0; i < n; ++i) {
+        if (rowptr[i + 1] < rowptr[i]) return ORC_INVALID;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            if (col[p] < 0 || col[p] >= n) return ORC_RANGE;
+            if (col[p] < i) return ORC_NONCANONICAL;
+            if (p > rowptr[i] && col[p] <= col[p - 1]) return ORC_NONCANONICAL;
+        }
+    }
+    return ORC_OK;
+}
+
+/* y[pi_1] += a * x[pi_2] for each distinct permutation pi of each stored (i, j). */
+int orc_ssymv_enum(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val,
+                   const double* x, double* y, double* yabs) {
+    int rc = orc_check_upper_csr(n, rowptr, col);
+    if (rc) return rc;
+    memset(y, 0, sizeof(double) * (size_t)n);
+    if (yabs) memset(yabs, 0, sizeof(double) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int32_t c[2] = {(int32_t)i, col[p]};
+            double a = (double)val[p];
+            do {
+                double t = a * x[c[1]];
+                y[c[0]] += t;
+                if (yabs) yabs[c[0]] += fabs(t);
+            } while (next_perm(c, 2));
+        }
+    return ORC_OK;
+}
+
+/* s = sum over distinct permutations pi of stored (i, j) of x[pi_1] a x[pi_2]. */
+int orc_syprd_enum(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val,
+                   const double* x, double* s, double* sabs) {
+    int rc = orc_check_upper_csr(n, rowptr, col);
+    if (rc) return rc;
+    double acc = 0.0, aabs = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int32_t c[2] = {(int32_t)i, col[p]};
+            double a = (double)val[p];
+            do {
+                double t = x[c[0]] * a * x[c[1]];
+                acc += t;
+                aabs += fabs(t);
+            } while (next_perm(c, 2));
+        }
+    *s = acc;
+    if (sabs) *sabs = aabs;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bellman-Ford relaxation step over the symmetric matrix (Sec. 5.2.2)        */
+/* ------------------------------------------------------------------------ */
+
+/* y[pi_1] = min(y[pi_1], a + d[pi_2]) over distinct permutations; y starts at d. */
+int orc_bellman_enum(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val,
+                     const double* d, double* y) {
+    int rc = orc_check_upper_csr(n, rowptr, col);
+    if (rc) return rc;
+    for (int64_t i = 0; i < n; ++i) y[i] = d[i];
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int32_t c[2] = {(int32_t)i, col[p]};
+            double a = (double)val[p];
+            do {
+                double t = a + d[c[1]];
+                if (t < y[c[0]]) y[c[0]] = t;
+            } while (next_perm(c, 2));
+        }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CP-fit residual                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* res = ||X||^2 - 2 <X, Mcp> + ||Mcp||^2 where X is the full symmetric tensor
+ * and Mcp = sum_r b_r (x) ... (x) b_r (unit weights).  Each inner product is
+ * summed over the distinct permutations of every stored entry; ||Mcp||^2 =
+ * sum_{r,s} (b_r . b_s)^N.  abs_terms (nullable) receives the sum of absolute
+ * values of all terms, the denominator of the componentwise error. */
+int orc_cpfit(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval,
+              const double* B, int R, double* res, double* abs_terms, double* parts) {
+    if (order < 2 || order > ORC_MAX_ORDER || R <= 0) return ORC_INVALID;
+    double xx = 0.0, xm = 0.0, xm_abs = 0.0;
+    int32_t c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_tuple(c, order);
+        double v = (double)cval[e];
+        do {
+            xx += v * v;
+            for (int r = 0; r < R; ++r) {
+                double t = v;
+                for (int q = 0; q < order; ++q) t *= B[(int64_t)c[q] * R + r];
+                xm += t;
+                xm_abs += fabs(t);
+            }
+        } while (next_perm(c, order));
+    }
+    double mm = 0.0, mm_abs = 0.0;
+    for (int r = 0; r < R; ++r)
+        for (int s = 0; s < R; ++s) {
+            double g = 0.0, ga = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                g += B[i * R + r] * B[i * R + s];
+                ga += fabs(B[i * R + r] * B[i * R + s]);
+            }
+            double gp = 1.0, gap = 1.0;
+            for (int q = 0; q < order; ++q) { gp *= g; gap *= ga; }
+            mm += gp;
+            mm_abs += gap;
+        }
+    *res = xx - 2.0 * xm + mm;
+    if (abs_terms) *abs_terms = xx + 2.0 * xm_abs + mm_abs;
+    if (parts) { parts[0] = xx; parts[1] = xm; parts[2] = mm; }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Expanded (non-symmetric) tensor                                            */
+/* ------------------------------------------------------------------------ */
+
+static int g_exp_order = 0;
+static int cmp_exp(const void* pa, const void* pb) {
+    const rec_t* a = (const rec_t*)pa;
+    const rec_t* b = (const rec_t*)pb;
+    for (int q = 0; q < g_exp_order; ++q) {
+        if (a->c[q] < b->c[q]) return -1;
+        if (a->c[q] > b->c[q]) return 1;
+    }
+    return 0;
+}
+
+/* Writes every distinct permutation of every canonical entry (the nonzeros of
+ * the full tensor), sorted lexicographically.  eidx is (order x cap). */
+int orc_expand(int order, int64_t nnz, const int32_t* cidx, const float* cval, int64_t cap,
+               int32_t* eidx, float* evals, int64_t* count) {
+    if (order < 1 || order > ORC_MAX_ORDER) return ORC_INVALID;
+    int64_t k = 0;
+    int32_t c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_tuple(c, order);
+        do { ++k; } while (next_perm(c, order));
+    }
+    *count = k;
+    if (k > cap) return ORC_NOMEM;
+    rec_t* r = (rec_t*)malloc(sizeof(rec_t) * (size_t)(k > 0 ? k : 1));
+    if (!r) return ORC_NOMEM;
+    int64_t w = 0;
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_tuple(c, order);
+        do {
+            memcpy(r[w].c, c, sizeof(c));
+            r[w].v = cval[e];
+            r[w].pos = w;
+            ++w;
+        } while (next_perm(c, order));
+    }
+    g_exp_order = order;
+    qsort(r, (size_t)k, sizeof(rec_t), cmp_exp);
+    for (int64_t e = 0; e < k; ++e) {
+        for (int q = 0; q < order; ++q) eidx[(int64_t)q * cap + e] = r[e].c[q];
+        evals[e] = r[e].v;
+    }
+    free(r);
+    return ORC_OK;
+}

@@ -1,0 +1,67 @@
+"""The pins have teeth: plausible mistakes planted in a copy of the oracle must fail them.
+
+Each mutant is oracle.c with one textual change (a dropped term, a wrong index,
+a transposed operand, a wrong weight), compiled to a temporary library and
+swapped in for the duration of the check.  Everything runs on the CPU.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+# (function whose body is edited, old text, new text, pin that must fail)
+MUTANTS = {
+    "enum_identity_only": ("orc_mttkrp_enum", "} while (next_perm(c, order));", "} while (0);",
+                           lambda: pins.test_mttkrp_vs_dense_bruteforce(3, 6, 0)),
+    "enum_dropped_factor": ("orc_mttkrp_enum", "for (int q = 1; q < order; ++q)", "for (int q = 2; q < order; ++q)",
+                            lambda: pins.test_mttkrp_vs_dense_bruteforce(4, 5, 0)),
+    "runs_wrong_weight": ("orc_mttkrp_runs", "int64_t den = fact(m[t] - 1);", "int64_t den = fact(m[t]);",
+                          lambda: pins.test_paper_normalized_update_counts("runs")),
+    "runs_wrong_exponent": ("orc_mttkrp_runs", "int ex = m[s] - (s == t ? 1 : 0);", "int ex = m[s];",
+                            lambda: pins.test_mttkrp_vs_dense_bruteforce(3, 6, 1)),
+    "ssymv_transposed": ("orc_ssymv_enum", "double t = a * x[c[1]];", "double t = a * x[c[0]];",
+                         lambda: pins.test_ssymv_syprd_vs_dense(0)),
+    "syprd_no_mirror": ("orc_syprd_enum", "} while (next_perm(c, 2));", "} while (0);",
+                        lambda: pins.test_paper_ssymv_syprd_assignments()),
+    "canon_unsorted_tuple": ("orc_canonicalize", "sort_tuple(r[e].c, order);", "",
+                             lambda: pins.test_canonicalize_properties()),
+    "cpfit_sign": ("orc_cpfit", "*res = xx - 2.0 * xm + mm;", "*res = xx + 2.0 * xm + mm;",
+                   lambda: pins.test_cpfit_vs_dense(3, 5)),
+    "counts_wrong_fibers": ("orc_counts", "if (e == 0 || c[0] != prev[0]) *root_fibers += 1;",
+                            "*root_fibers += 1;", lambda: pins.test_counts_closed_forms(3)),
+}
+
+
+def build_mutant(tmp_path, func, old, new):
+    src = open(SRC).read()
+    start = src.index(func + "(")
+    body_at = src.index(old, start)
+    mut = src[:body_at] + new + src[body_at + len(old):]
+    c = tmp_path / "mut.c"
+    c.write_text(mut)
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                           str(c), "-lm"])
+    return str(so)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path, monkeypatch):
+    func, old, new, pin = MUTANTS[name]
+    so = build_mutant(tmp_path, func, old, new)
+    real = oracle.lib()
+    import ctypes
+    mut = ctypes.CDLL(so)
+    # copy the argument/return types of the real bindings onto the mutant
+    for attr in dir(real):
+        if attr.startswith("orc_"):
+            f, g = getattr(real, attr), getattr(mut, attr)
+            g.argtypes, g.restype = f.argtypes, f.restype
+    monkeypatch.setattr(oracle, "_lib", mut)
+    with pytest.raises((AssertionError, oracle.OracleError)):
+        pin()

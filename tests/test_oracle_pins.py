@@ -1,0 +1,352 @@
+"""Pins for the FP64 oracle: what the paper and plain mathematics fix, independent of the oracle.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/), closed forms, dense brute force on tiny tensors
+(the canonical triangle expanded over all N! position permutations, then a
+dense contraction), invariants, and textbook special cases.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ----------------------------------------------------------------------------- brute force
+
+def dense_full(order, n, cidx, cval):
+    """Full symmetric dense tensor: every position permutation of every stored tuple."""
+    X = np.zeros((n,) * order, dtype=np.float64)
+    for e in range(cidx.shape[1]):
+        c = tuple(int(x) for x in cidx[:, e])
+        for p in itertools.permutations(range(order)):
+            X[tuple(c[q] for q in p)] = float(cval[e])
+    return X
+
+
+def dense_mttkrp(X, B):
+    order = X.ndim
+    n, R = B.shape
+    M = np.zeros((n, R))
+    for r in range(R):
+        T = X
+        for _ in range(order - 1):
+            T = T @ B[:, r]
+        M[:, r] = T
+    return M
+
+
+def dense_mttkrp_abs(X, B):
+    return dense_mttkrp(np.abs(X), np.abs(B))
+
+
+def canon(T):
+    return oracle.canonicalize(T.order, T.n, T.idx, T.val)
+
+
+# ----------------------------------------------------------------------------- multiplicities
+
+def compositions(order):
+    """All run-length structures (m_1..m_d) of a canonical tuple of the given order."""
+    for d in range(1, order + 1):
+        for cut in itertools.combinations(range(1, order), d - 1):
+            b = (0,) + cut + (order,)
+            yield tuple(b[t + 1] - b[t] for t in range(d))
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
+def test_distinct_perms_closed_form_and_bruteforce(order):
+    for ms in compositions(order):
+        tup = []
+        for t, m in enumerate(ms):
+            tup += [10 * t + 3] * m
+        closed = math.factorial(order) // math.prod(math.factorial(m) for m in ms)
+        brute = len(set(itertools.permutations(tup)))
+        assert oracle.distinct_perms(np.array(tup)) == closed == brute
+
+
+def test_paper_3way_unique_symmetry_groups():
+    g = golden("paper_mttkrp3_multiplicities.json")
+    cases = {"i<k<l": [0, 1, 2], "i=k<l": [0, 0, 2], "i<k=l": [0, 2, 2], "i=k=l": [1, 1, 1]}
+    for name, tup in cases.items():
+        assert oracle.distinct_perms(np.array(tup)) == g["unique_symmetry_groups"][name]
+    # The listed members of S_P|E for i=k<l, applied to (i, k, l), are the distinct arrangements.
+    i, k, l = 0, 0, 2
+    got = {tuple((i, k, l)[s - 1] for s in sig) for sig in g["unique_symmetry_group_members_i=k<l"]}
+    assert got == set(itertools.permutations((i, k, l)))
+
+
+def _one_entry_counts(tup, form):
+    """Row sums of the oracle's MTTKRP for a single entry with v=1 and B=1 (update counts)."""
+    order = len(tup)
+    n = 16
+    cidx = np.array(tup, dtype=np.int32).reshape(order, 1)
+    cval = np.ones(1, dtype=np.float32)
+    B = np.ones((n, 1))
+    if form == "enum":
+        M = oracle.mttkrp_enum(order, n, cidx, cval, B, want_abs=False)
+    else:
+        M = oracle.mttkrp_runs(order, n, cidx, cval, B)
+    return M[:, 0]
+
+
+@pytest.mark.parametrize("form", ["enum", "runs"])
+def test_paper_normalized_update_counts(form):
+    g = golden("paper_mttkrp3_multiplicities.json")["normalized_update_counts"]
+    i, k, l = 1, 4, 7
+    cases = {"i<k<l": (i, k, l), "i=k<l": (i, i, l), "i<k=l": (i, k, k), "i=k=l": (i, i, i)}
+    for name, tup in cases.items():
+        M = _one_entry_counts(tup, form)
+        names = {"i": tup[0], "k": tup[1], "l": tup[2]}
+        want = np.zeros_like(M)
+        for lab, cnt in g[name].items():
+            want[names[lab]] = cnt
+        assert np.array_equal(M, want), name
+
+
+@pytest.mark.parametrize("form", ["enum", "runs"])
+def test_paper_lookup_table(form):
+    g = golden("paper_mttkrp3_multiplicities.json")
+    lut = g["lookup_table"]
+    for tup in [(1, 4, 7), (1, 1, 7), (1, 4, 4), (1, 1, 1)]:
+        i, k, l = tup
+        # printed index, with the all-equal case read as entry 7 (see the fixture)
+        idx = 2 * (i == k) + 3 * (k == l) + 1 + (i == k and k == l)
+        name = {1: "i<k<l", 3: "i=k<l", 4: "i<k=l", 7: "i=k=l"}[idx]
+        assert g["lookup_index_used"][name] == idx
+        factor = lut[idx - 1]
+        # The table factor applies once per position; positions sharing a row add up.
+        want = np.zeros(16)
+        for pos in tup:
+            want[pos] += factor
+        M = _one_entry_counts(tup, form)
+        assert np.allclose(M, want, rtol=0, atol=1e-15), tup
+
+
+def test_paper_split_loop_weights():
+    g = golden("paper_mttkrp3_multiplicities.json")["split_loop_weights"]
+    assert np.array_equal(_one_entry_counts((0, 3, 5), "runs")[[0, 3, 5]],
+                          [g["strict_weight_per_position"]] * 3)
+    m = _one_entry_counts((2, 2, 5), "runs")
+    assert m[2] == 2 * g["mixed_diagonal_weight_per_position"] and m[5] == 1
+    assert _one_entry_counts((4, 4, 4), "runs")[4] == g["all_equal_updates"]
+
+
+def test_paper_savings_ratios():
+    """Sec. 5.2.6: reads shrink by N!, operations by (N-1)! for the 3/4/5-way MTTKRP."""
+    g = golden("paper_mttkrp3_multiplicities.json")["savings_Sec_5_2_6"]
+    for order in (3, 4, 5):
+        strict = np.arange(order, dtype=np.int32) * 3 + 1
+        assert oracle.distinct_perms(strict) == g[str(order)]["reads"]
+        # Updates per canonical read equal N! (one per permutation), grouped into N rows.
+        M = _one_entry_counts(tuple(strict), "enum")
+        assert M.sum() == g[str(order)]["reads"]
+        assert set(M[strict]) == {g[str(order)]["ops"]}
+
+
+def test_paper_ssymv_syprd_assignments():
+    g = golden("paper_ssymv_syprd.json")
+    rowptr = np.array([0, 2, 2, 2], np.int32)
+    col = np.array([0, 2], np.int32)
+    val = np.array([1.0, 1.0], np.float32)
+    y, _ = oracle.ssymv(3, rowptr, col, val, np.ones(3))
+    # (0,0) diagonal: one assignment to y[0]; (0,2): one to y[0], one to y[2].
+    assert y.tolist() == [g["ssymv_assignments"]["i=j"] + 1, 0.0, 1.0]
+    s, _ = oracle.syprd(3, rowptr, col, val, np.ones(3))
+    assert s == g["syprd_factor"]["i=j"] + g["syprd_factor"]["i<j"]
+
+
+# ----------------------------------------------------------------------------- brute force vs oracle
+
+@pytest.mark.parametrize("order,n", [(2, 6), (3, 6), (4, 5), (5, 4)])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_mttkrp_vs_dense_bruteforce(order, n, seed):
+    T = synth.tensor_small_all_patterns(order, n, seed)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(n, 5, seed).astype(np.float64)
+    X = dense_full(order, n, cidx, cval)
+    want = dense_mttkrp(X, B)
+    M, Ma = oracle.mttkrp_enum(order, n, cidx, cval, B)
+    Mr = oracle.mttkrp_runs(order, n, cidx, cval, B)
+    assert np.allclose(M, want, rtol=1e-12, atol=1e-12)
+    assert np.allclose(Mr, want, rtol=1e-12, atol=1e-12)
+    assert np.allclose(Ma, dense_mttkrp_abs(X, B), rtol=1e-12, atol=1e-12)
+
+
+def test_mttkrp_row_mask_matches_full():
+    T = synth.tensor_small_all_patterns(4, 6, 3)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(6, 4, 3).astype(np.float64)
+    M, _ = oracle.mttkrp_enum(4, 6, cidx, cval, B)
+    rows = [0, 3, 5]
+    Ms, _ = oracle.mttkrp_enum(4, 6, cidx, cval, B, rows=rows)
+    assert np.array_equal(Ms[rows], M[rows])
+    assert not Ms[[1, 2, 4]].any()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ssymv_syprd_vs_dense(seed):
+    A = synth.upper_csr_uniform(40, 300, seed)
+    x = synth.vector_uniform(40, seed).astype(np.float64)
+    D = np.zeros((40, 40))
+    rows = np.repeat(np.arange(40), np.diff(A.rowptr))
+    D[rows, A.col] = A.val
+    full = D + D.T - np.diag(np.diag(D))     # textbook (U + U^T - diag U)
+    y, ya = oracle.ssymv(40, A.rowptr, A.col, A.val, x)
+    assert np.allclose(y, full @ x, rtol=1e-13, atol=1e-13)
+    assert np.allclose(ya, np.abs(full) @ np.abs(x), rtol=1e-13, atol=1e-13)
+    s, sa = oracle.syprd(40, A.rowptr, A.col, A.val, x)
+    assert np.isclose(s, x @ full @ x, rtol=1e-12, atol=1e-12)
+    # invariant: x^T (A x) = SYPRD
+    assert np.isclose(x @ y, s, rtol=1e-12, atol=1e-12)
+
+
+def test_bellman_vs_dense():
+    A = synth.upper_csr_uniform(30, 120, 5)
+    d = synth.vector_uniform(30, 5).astype(np.float64) + 2.0
+    val = np.abs(A.val)
+    D = np.full((30, 30), np.inf)
+    rows = np.repeat(np.arange(30), np.diff(A.rowptr))
+    D[rows, A.col] = val
+    D[A.col, rows] = val
+    want = np.minimum(d, (D + d[None, :]).min(axis=1))
+    got = oracle.bellman(30, A.rowptr, A.col, val, d)
+    assert np.allclose(got, want, rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("order,n", [(3, 5), (4, 4), (5, 3)])
+def test_cpfit_vs_dense(order, n):
+    T = synth.tensor_small_all_patterns(order, n, 7)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(n, 3, 7).astype(np.float64)
+    X = dense_full(order, n, cidx, cval)
+    Mcp = np.zeros_like(X)
+    for r in range(B.shape[1]):
+        t = B[:, r]
+        for _ in range(order - 1):
+            t = np.multiply.outer(t, B[:, r])
+        Mcp += t
+    want = float(((X - Mcp) ** 2).sum())
+    res, ab, parts = oracle.cpfit(order, n, cidx, cval, B)
+    assert np.isclose(res, want, rtol=1e-11, atol=1e-11)
+    assert np.isclose(parts[0], (X ** 2).sum(), rtol=1e-12)
+    assert ab >= abs(res)
+
+
+# ----------------------------------------------------------------------------- canonical form / counts
+
+def test_canonicalize_properties():
+    T = synth.tensor_uniform(4, 30, 3000, 9)
+    cidx, cval = canon(T)
+    assert cidx.shape == (4, 3000)
+    assert oracle.check_canonical(4, 30, cidx) == oracle.OK
+    # same multisets as the input (independent check with numpy sorting)
+    a = np.sort(T.idx.T, axis=1)
+    o = np.lexsort(a.T[::-1])
+    assert np.array_equal(a[o].T, cidx)
+    assert np.array_equal(T.val[o], cval)
+
+
+def test_canonicalize_input_permutation_invariance():
+    T = synth.tensor_uniform(5, 12, 800, 4)
+    c1, v1 = canon(T)
+    st = synth.Stream(99)
+    perm = np.argsort(st.uniform(5 * 800).reshape(800, 5), axis=1)
+    idx2 = np.take_along_axis(T.idx.T, perm, axis=1).T
+    shuf = np.argsort(st.u64(800))
+    c2, v2 = oracle.canonicalize(5, 12, idx2[:, shuf], T.val[shuf])
+    assert np.array_equal(c1, c2) and np.array_equal(v1, v2)
+
+
+def test_canonicalize_duplicates_and_range():
+    idx = np.array([[0, 2, 1], [2, 0, 1], [1, 1, 3]], dtype=np.int32)  # (0,2,1) and (2,0,1) same multiset
+    val = np.array([1.5, 1.5, 2.0], np.float32)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.canonicalize(3, 4, idx, val, dup_policy=0)
+    assert e.value.code == oracle.DUPLICATE
+    c, v = oracle.canonicalize(3, 4, idx, val, dup_policy=1)
+    assert c.T.tolist() == [[0, 1, 2], [1, 1, 3]] and v.tolist() == [1.5, 2.0]
+    val2 = np.array([1.5, -1.5, 2.0], np.float32)
+    with pytest.raises(oracle.OracleError):
+        oracle.canonicalize(3, 4, idx, val2, dup_policy=1)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.canonicalize(3, 3, idx, val, dup_policy=1)
+    assert e.value.code == oracle.RANGE
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5])
+def test_counts_closed_forms(order):
+    T = synth.tensor_small_all_patterns(order, 7, 11, density=0.7)
+    cidx, cval = canon(T)
+    cnt = oracle.counts(order, cidx, cval)
+    rows = cidx.T
+    eq = rows[:, 1:] == rows[:, :-1]
+    pat = (eq * (1 << np.arange(order - 1))).sum(axis=1)
+    assert np.array_equal(cnt["by_pattern"][: 1 << (order - 1)], np.bincount(pat, minlength=1 << (order - 1)))
+    closed = 0
+    nsq = 0.0
+    for e, row in enumerate(rows):
+        _, m = np.unique(row, return_counts=True)
+        k = math.factorial(order) // math.prod(math.factorial(int(x)) for x in m)
+        closed += k
+        nsq += k * float(cval[e]) ** 2
+    assert cnt["expanded"] == closed
+    X = dense_full(order, 7, cidx, cval)
+    assert cnt["expanded"] == int(np.count_nonzero(X))
+    assert np.isclose(cnt["normsq"], (X ** 2).sum(), rtol=1e-12)
+    assert cnt["root_fibers"] == len(np.unique(rows[:, 0]))
+    assert cnt["l2_fibers"] == len({(a, b) for a, b in rows[:, :2]})
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_expand_matches_dense(order):
+    T = synth.tensor_small_all_patterns(order, 5, 13)
+    cidx, cval = canon(T)
+    eidx, ev = oracle.expand(order, cidx, cval)
+    X = dense_full(order, 5, cidx, cval)
+    nz = np.argwhere(X != 0)               # lexicographic order from argwhere
+    assert np.array_equal(eidx.T, nz)
+    assert np.array_equal(ev.astype(np.float64), X[tuple(nz.T)])
+
+
+# ----------------------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("order", [3, 4, 5])
+def test_mttkrp_relabel_invariance(order):
+    n = 12
+    T = synth.tensor_uniform(order, n, 150, 21)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(n, 4, 21).astype(np.float64)
+    M, _ = oracle.mttkrp_enum(order, n, cidx, cval, B)
+    pi = np.argsort(synth.Stream(5).uniform(n))     # new label of old index a is pi[a]
+    c2, v2 = oracle.canonicalize(order, n, pi[cidx], cval)
+    B2 = np.empty_like(B)
+    B2[pi] = B
+    M2, _ = oracle.mttkrp_enum(order, n, c2, v2, B2)
+    assert np.allclose(M2[pi], M, rtol=1e-12, atol=1e-12)
+
+
+def test_enum_equals_runs_on_zipf():
+    T = synth.tensor3_zipf(500, 20000, 3)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(500, 8, 3).astype(np.float64)
+    M, Ma = oracle.mttkrp_enum(3, 500, cidx, cval, B)
+    Mr = oracle.mttkrp_runs(3, 500, cidx, cval, B)
+    assert oracle.componentwise_error(Mr, M, Ma) < 1e-14
+    cnt = oracle.counts(3, cidx, cval)
+    assert cnt["by_pattern"][0] == T.meta["strict"]
+    assert cnt["by_pattern"][1] == T.meta["i=j<k"]
+    assert cnt["by_pattern"][2] == T.meta["i<j=k"]
+    assert cnt["by_pattern"][3] == T.meta["i=j=k"]
