@@ -1,0 +1,447 @@
+"""Benchmark of the symmetric sparse kernels on one GB300 (or N replicas under torchrun).
+
+Headline workload: 3-way symmetric sparse MTTKRP, n = 100,000, 20,000,000
+canonical nonzeros (i <= j <= k), Zipf(1.2) indices with an exact 1% share of
+repeated indices, values N(0,1), shared factor B of 100,000 x 64 FP32, N(0,1/64).
+A step is one sym_mttkrp call (strict stream + diagonal stream) on the resident
+canonicalised tensor; the metric is canonical nonzeros per second.  L2 is
+flushed (256 MB write) between timed steps and each step is timed with its own
+CUDA event pair on the launching stream.
+
+Also reported: the dominant kernel's roofline fraction from live per-kernel CUDA
+events, an end-to-end figure through the public API with host buffers
+(copies of the coordinate list and factor in, the result out, canonicalisation
+included), the FP64 CPU oracle on a bounded sample, the expanded non-symmetric
+baseline, the CP-fit residual cost, the 4-/5-way and SSYMV workloads, and the
+SM clocks sampled during the timed region.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--rows main|all]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+MAIN = dict(order=3, n=100_000, nnz=20_000_000, rank=64, seed=1, recipe="zipf")
+WORKLOAD_NAME = "sym_mttkrp3_zipf1.2_n100k_nnz20M_r64_f32"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- helpers
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("mttkrp.cuh", "common.cuh", "tensor.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_09266_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch recorded in profiles/ for this kernel source, else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    want = kernel_source_hash()
+    with open(p) as f:
+        for ln in f:
+            m = re.match(r"\s*(\S+)\s+(\S+)\s+src=(\w+)\s+dram_bytes_per_launch=(\d+)", ln)
+            if m and m.group(1) == kernel and m.group(2) == workload and m.group(3) == want:
+                return int(m.group(4))
+    return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Dist:
+    def __init__(self):
+        self.ws, self.rank, self.local = dist_env()
+        self.pg = None
+        if self.ws > 1:
+            import torch.distributed as td
+            td.init_process_group("gloo")
+            self.td = td
+
+    def barrier(self):
+        if self.ws > 1:
+            self.td.barrier()
+
+    def max(self, v: float) -> float:
+        if self.ws == 1:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64)
+        self.td.all_reduce(t, op=self.td.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.ws > 1:
+            self.td.destroy_process_group()
+
+
+def make_main_tensor():
+    return synth.make_tensor(MAIN["order"], MAIN["n"], MAIN["nnz"], MAIN["seed"], MAIN["recipe"])
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample_rate(T, rank, target_s=12.0):
+    """Times the FP64 oracle MTTKRP (definitional form) on a bounded sample of the workload."""
+    import oracle
+    B = synth.factor_normal(T.n, rank, MAIN["seed"]).astype(np.float64)
+    # the coordinate list is in random order, so a prefix is a uniform sample
+    probe = min(T.nnz, 100_000)
+    cidx, cval = oracle.canonicalize(T.order, T.n, T.idx[:, :probe], T.val[:probe])
+    t0 = time.perf_counter()
+    oracle.mttkrp_enum(T.order, T.n, cidx, cval, B, want_abs=False)
+    rate = probe / max(time.perf_counter() - t0, 1e-9)
+    size = int(min(T.nnz, max(probe, rate * target_s)))
+    cidx, cval = oracle.canonicalize(T.order, T.n, T.idx[:, :size], T.val[:size])
+    t0 = time.perf_counter()
+    oracle.mttkrp_enum(T.order, T.n, cidx, cval, B, want_abs=False)
+    dt = time.perf_counter() - t0
+    return cidx.shape[1] / dt, {"kind": "oracle", "cores": 1,
+                                "sample": f"first {size} of {T.nnz} entries of the shuffled coordinate list "
+                                          f"({cidx.shape[1]} canonical), FP64 definitional MTTKRP, "
+                                          f"rank {rank}, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    T = make_main_tensor()
+    import oracle
+    B = synth.factor_normal(T.n, MAIN["rank"], MAIN["seed"]).astype(np.float64)
+    sample = min(T.nnz, int(os.environ.get("SYMGPU_REF_SAMPLE", "400000")))
+    cidx, cval = oracle.canonicalize(T.order, T.n, T.idx[:, :sample], T.val[:sample])
+    for _ in range(args.warmup):
+        oracle.mttkrp_enum(T.order, T.n, cidx, cval, B, want_abs=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mttkrp_enum(T.order, T.n, cidx, cval, B, want_abs=False)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = cidx.shape[1] / dt
+    out = {"impl": "reference", "metric": "canonical_nnz_per_s", "value": v, "unit": "canonical nnz/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAME, "sample_canonical_nnz": int(cidx.shape[1])},
+           "cpu_baseline": {"value": v, "unit": "canonical nnz/s", "cores": 1, "kind": "oracle",
+                            "sample": f"first {sample} entries of the shuffled coordinate list, FP64 definitional "
+                                      f"MTTKRP per step"},
+           "e2e": {"value": v, "unit": "canonical nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def timed_steps(torch, step, K, flush_buf, stream):
+    """Runs K steps, each between its own CUDA events; L2 flushed before each step."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush_buf.fill_(k & 0xff)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2406_09266_gb300 as sg
+
+    D = Dist()
+    torch.cuda.set_device(D.local)
+    dev = torch.device("cuda", D.local)
+    sg.load()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    hbm_peak, peak_kind = peaks()
+
+    # ---- workload (host), resident copy (device), canonicalisation
+    T = make_main_tensor()
+    Bh = synth.factor_normal(T.n, MAIN["rank"], MAIN["seed"])
+    idx_d = torch.from_numpy(T.idx).to(dev)
+    val_d = torch.from_numpy(T.val).to(dev)
+    B = torch.from_numpy(Bh).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X = sg.SymTensor(idx_d, val_d, T.n)
+    torch.cuda.synchronize()
+    create_ms = (time.perf_counter() - t0) * 1e3
+    info = X.info()
+    M = torch.empty((T.n, MAIN["rank"]), dtype=torch.float32, device=dev)
+    ws_res = X.mttkrp_workspace(MAIN["rank"])
+
+    step = lambda: X.mttkrp(B, M=M)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device value)
+    sg.profile_reset()
+    sg.profile_enable(True)
+    D.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(D.local) as clk:
+        t_wall = time.perf_counter()
+        times = timed_steps(torch, step, args.steps, flush, stream)
+        t_wall = time.perf_counter() - t_wall
+    D.barrier()
+    sg.profile_enable(False)
+    prof = sg.profile_read()
+    ms = D.max(float(np.mean(times)))
+    value = info["nnz"] * D.ws / (ms * 1e-3)
+    launches = sum(v[0] for v in prof.values())
+
+    # ---- roofline of the dominant kernel (strict stream)
+    strict_launches, strict_ms = prof.get("mttkrp_strict", (0, 0.0))
+    per_launch_ms = strict_ms / max(strict_launches, 1)
+    kw_bytes = 8 * (2 if info["key_bits"] * 3 > 64 else 1)
+    alg_bytes = info["nnz_strict"] * (kw_bytes + 4) + T.n * MAIN["rank"] * 4 * 3   # stream + B read + M rmw
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_mttkrp_strict<3,1,16,f32>", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+            "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_kind,
+            "traffic": recorded_traffic("mttkrp_strict", WORKLOAD_NAME),
+            "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": per_launch_ms,
+            "share_of_step": strict_ms / max(sum(v[1] for v in prof.values()), 1e-12)}
+
+    extras = {"per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
+              "canonicalise_ms": create_ms, "tensor": {k: info[k] for k in (
+                  "nnz", "nnz_strict", "nnz_diag", "expanded_nnz", "root_fibers", "l2_fibers")}}
+
+    # ---- CP-fit residual cost (FP64), same tensor
+    Mr, res = X.mttkrp(B, residual=True, ws=ws_res)
+    torch.cuda.synchronize()
+    rt = timed_steps(torch, lambda: X.mttkrp(B, M=M, residual=True, ws=ws_res), 5, flush, stream)
+    extras["mttkrp_plus_residual_ms"] = float(np.mean(rt))
+    extras["residual"] = float(res.item())
+
+    # ---- expanded non-symmetric baseline on the same tensor
+    if args.rows == "all" and D.rank == 0:
+        try:
+            E = X.expanded()
+            Me = torch.empty_like(M)
+            for _ in range(2):
+                E.mttkrp(B, M=Me)
+            et = timed_steps(torch, lambda: E.mttkrp(B, M=Me), 5, flush, stream)
+            extras["expanded_baseline"] = {"expanded_nnz": E.nnz, "ms": float(np.mean(et)),
+                                           "speedup_sym_over_expanded": float(np.mean(et)) / ms,
+                                           "read_reduction": E.nnz / info["nnz"],
+                                           "max_abs_diff_vs_sym": float((Me - M).abs().max())}
+            E.close()
+            del Me
+        except Exception as e:  # report, do not hide
+            extras["expanded_baseline"] = {"error": str(e)}
+
+    # ---- end to end through the public API with host buffers
+    idx_h = torch.from_numpy(T.idx).pin_memory()
+    val_h = torch.from_numpy(T.val).pin_memory()
+    B_h = torch.from_numpy(Bh).pin_memory()
+    M_h = torch.empty((T.n, MAIN["rank"]), dtype=torch.float32).pin_memory()
+    ws_create = torch.empty(sg.SymTensor.create_ws_bytes(3, T.n, T.nnz), dtype=torch.uint8, device=dev)
+    del X
+    torch.cuda.empty_cache()
+
+    def e2e_step():
+        i_d = idx_h.to(dev, non_blocking=True)
+        v_d = val_h.to(dev, non_blocking=True)
+        b_d = B_h.to(dev, non_blocking=True)
+        Xe = sg.SymTensor(i_d, v_d, T.n, ws=ws_create)
+        Xe.mttkrp(b_d, M=M)
+        M_h.copy_(M, non_blocking=True)
+        torch.cuda.synchronize()
+        Xe.close()
+
+    e2e_step()
+    e2e_k = max(3, min(args.steps, 10))
+    D.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_k):
+        e2e_step()
+    e2e_s = D.max((time.perf_counter() - t0) / e2e_k)
+    h2d = idx_h.numel() * 4 + val_h.numel() * 4 + B_h.numel() * 4
+    d2h = M_h.numel() * 4
+
+    # ---- secondary rows
+    if args.rows == "all" and D.rank == 0:
+        extras["rows"] = secondary_rows(torch, sg, dev, flush, stream, hbm_peak)
+
+    out = {"metric": "canonical_nnz_per_s", "value": value, "unit": "canonical nnz/s", "n_gpus": D.ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAME, "order": 3, "n": T.n, "canonical_nnz": info["nnz"],
+                      "rank": MAIN["rank"], "factor_dtype": "f32", "indices": "zipf(1.2), 1% repeated",
+                      "l2": "flushed between steps (256 MB write); each step timed by its own event pair",
+                      "parallelism": f"replicas{D.ws}"},
+           "effective_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+           "roofline": roof,
+           "e2e": {"value": info["nnz"] * D.ws / e2e_s, "unit": "canonical nnz/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+                   "includes": "H2D of coordinate list + values + factor, canonicalisation, MTTKRP, D2H of M"},
+           "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed": t_wall, "extras": extras}
+    if D.rank == 0 and not args.no_cpu:
+        rate, meta = oracle_sample_rate(T, MAIN["rank"])
+        meta["value"] = rate
+        meta["unit"] = "canonical nnz/s"
+        out["cpu_baseline"] = meta
+    if D.rank == 0:
+        print(json.dumps(out))
+    D.close()
+
+
+def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
+    rows = {}
+    # 4-way and 5-way symmetric MTTKRP, FP32 and BF16 factors
+    for name, order, n, nnz, rank in [("mttkrp4_unif_n20k_nnz10M_r32", 4, 20_000, 10_000_000, 32),
+                                      ("mttkrp5_unif_n2k_nnz5M_r16", 5, 2_000, 5_000_000, 16)]:
+        T = synth.make_tensor(order, n, nnz, 2, "uniform")
+        X = sg.SymTensor(torch.from_numpy(T.idx).to(dev), torch.from_numpy(T.val).to(dev), n)
+        info = X.info()
+        B32 = synth.factor_normal(n, rank, 2)
+        r = {"canonical_nnz": info["nnz"], "nnz_diag": info["nnz_diag"]}
+        for tag, Bt in (("f32", torch.from_numpy(B32).to(dev)),
+                        ("bf16", torch.from_numpy(synth.bf16_rne(B32).view(np.int16)).to(dev).view(torch.bfloat16))):
+            M = torch.empty((n, rank), dtype=torch.float32, device=dev)
+            for _ in range(3):
+                X.mttkrp(Bt, M=M)
+            t = timed_steps(torch, lambda: X.mttkrp(Bt, M=M), 10, flush, stream)
+            ms = float(np.mean(t))
+            r[tag] = {"ms": ms, "canonical_nnz_per_s": info["nnz"] / (ms * 1e-3)}
+        try:
+            E = X.expanded()
+            Me = torch.empty((n, rank), dtype=torch.float32, device=dev)
+            Bt = torch.from_numpy(B32).to(dev)
+            E.mttkrp(Bt, M=Me)
+            t = timed_steps(torch, lambda: E.mttkrp(Bt, M=Me), 5, flush, stream)
+            r["expanded_ms"] = float(np.mean(t))
+            r["speedup_sym_over_expanded"] = r["expanded_ms"] / r["f32"]["ms"]
+            r["read_reduction"] = E.nnz / info["nnz"]
+            E.close()
+        except Exception as e:
+            r["expanded_error"] = str(e)
+        rows[name] = r
+        X.close()
+    # SSYMV + SYPRD, n = 2000, 20k upper nonzeros (launch-latency bound)
+    A = synth.upper_csr_uniform(2000, 20000, 0)
+    x = synth.vector_uniform(2000, 0)
+    t_ = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rp, cl, vl, xd = t_(A.rowptr), t_(A.col), t_(A.val), t_(x)
+    y = torch.empty(2000, dtype=torch.float32, device=dev)
+    ws = sg.spmv_workspace(2000, rp, cl, vl)
+    for _ in range(5):
+        sg.spmv(2000, rp, cl, vl, xd, y=y, syprd=True, ws=ws)
+    t = timed_steps(torch, lambda: sg.spmv(2000, rp, cl, vl, xd, y=y, syprd=True, ws=ws), 50, flush, stream)
+    ms = float(np.mean(t))
+    rows["ssymv_n2000_nnz20k"] = {"ms": ms, "canonical_nnz_per_s": A.nnz / (ms * 1e-3)}
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rows", default="all", choices=["main", "all"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,368 @@
+/*
+ * symgpu.h — C ABI of the GB300 symmetric sparse kernels (SySTeC hot path).
+ *
+ * The paper: "SySTeC: A Symmetric Sparse Tensor Compiler", arXiv 2406.09266.
+ * A fully symmetric tensor X (Sec. 2.1, Def. "Symmetry") is stored by its
+ * canonical triangle only: coordinates with i_1 <= i_2 <= ... <= i_N (Sec. 2.1,
+ * Def. "Canonical", upper triangle).  Each stored entry stands for every
+ * DISTINCT permutation of its indices (Sec. 3.1: n!/m! assignments when m
+ * indices are equal; Sec. 4.1, unique symmetry group S_P|E), and the kernels
+ * apply it once per such permutation.
+ *
+ * Conventions for every call:
+ *   - Indices are 0-based.  Dense matrices are row-major with an explicit row
+ *     stride (ld*) in elements.
+ *   - Pointers marked [device] are CUDA device pointers; [host] are host
+ *     pointers.  All device memory is owned by the caller (the library never
+ *     calls cudaMalloc/cudaFree): handles and scratch are carved out of
+ *     caller-given arenas and workspaces whose sizes come from the *_bytes
+ *     queries.  Arenas and workspaces must be 256-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Compute calls are asynchronous on that stream unless documented otherwise.
+ *   - Every call returns a sym_status.  Argument errors are detected on the host
+ *     before anything is enqueued and leave outputs untouched.  No C++
+ *     exception and no abort crosses this boundary.
+ *   - Handles are thread-compatible: concurrent calls on one handle need
+ *     external synchronisation; distinct handles are independent.
+ */
+#ifndef SYMGPU_H
+#define SYMGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Every entry point below is exported from libsymgpu.so even when the library
+ * is compiled with hidden default visibility. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+#define SYMGPU_VERSION 1
+
+typedef void* sym_stream_t; /* cudaStream_t */
+
+typedef enum {
+    SYM_OK = 0,
+    SYM_E_INVALID = -1,      /* bad argument (null pointer, size, alignment, unsupported shape) */
+    SYM_E_NONCANONICAL = -2, /* input claimed canonical is not (CSR column below the diagonal, unsorted) */
+    SYM_E_RANGE = -3,        /* an index outside [0, n) */
+    SYM_E_DUPLICATE = -4,    /* two stored entries with the same index multiset */
+    SYM_E_NOMEM = -5,        /* arena or workspace smaller than the *_bytes query */
+    SYM_E_BUDGET = -6,       /* request larger than the serving HBM budget */
+    SYM_E_TIMEOUT = -7,      /* a bounded wait ran out */
+    SYM_E_CUDA = -8,         /* a CUDA runtime call failed (see sym_last_cuda_error) */
+    SYM_E_BADREQ = -9,       /* malformed serving request */
+    SYM_E_UNSUPPORTED = -10, /* valid but not implemented here (e.g. order > 5) */
+    SYM_E_NOTFOUND = -11,    /* unknown ticket */
+    SYM_PENDING = 1          /* serving request not finished yet */
+} sym_status;
+
+typedef enum { SYM_F32 = 0, SYM_BF16 = 1 } sym_dtype;
+
+typedef enum {
+    SYM_DUP_ERROR = 0,      /* any repeated index multiset is an error */
+    SYM_DUP_KEEP_EQUAL = 1  /* keep the first copy; copies must carry bit-identical values */
+} sym_dup_policy;
+
+const char* sym_status_string(sym_status s);
+/* Last CUDA error code seen by the library in this thread (cudaError_t as int). */
+int sym_last_cuda_error(void);
+int sym_version(void);
+
+/* Optional per-kernel timing: when enabled, the library records a CUDA event
+ * pair on the launching stream around each of its kernel launches.
+ * sym_profile_read synchronises on the recorded events and returns, per kernel
+ * name, the launch count and the summed event time. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} sym_profile_entry;
+sym_status sym_profile_enable(int on);
+/* Returns the number of entries written (at most max_entries). */
+int sym_profile_read(sym_profile_entry* out, int max_entries);
+sym_status sym_profile_reset(void);
+
+/* ===================================================================== */
+/* SSYMV / SYPRD over an upper-triangle CSR (Sec. 3.1 figure "spmv_code",  */
+/* Sec. 5.2.1 SSYMV y[i] = A[i,j] x[j], Sec. 5.2.3 SYPRD y = x[i]A[i,j]x[j]) */
+/* ===================================================================== */
+
+/* Upper triangle of a symmetric n x n matrix in CSR: row i holds columns
+ * j >= i, strictly increasing.  All arrays [device]; rowptr has n+1 entries. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const float* val;
+} sym_csr_upper;
+
+/* Workspace for sym_spmv when SYPRD is requested (per-block FP64 partials). */
+size_t sym_spmv_workspace_bytes(const sym_csr_upper* A);
+
+/* y = A x with A symmetric (both triangles), reading each stored entry once:
+ * an off-diagonal entry a_ij (i < j) adds a x_j to y_i and a x_i to y_j; a
+ * diagonal entry adds a x_i to y_i once.  y [device, n floats] is overwritten.
+ * If syprd [device, 1 double] is not NULL it receives x^T A x, with the
+ * off-diagonal terms weighted 2 (invisible output symmetry, Sec. 3.2.2), per-
+ * block partials formed in FP32 and the cross-block sum in FP64.  x, y: n
+ * floats [device], 16-byte aligned not required.  ws may be NULL when syprd is
+ * NULL.  The CSR is trusted (use sym_csr_upper_check to validate). */
+sym_status sym_spmv(const sym_csr_upper* A, const float* x, float* y, double* syprd, void* ws,
+                    size_t ws_bytes, sym_stream_t stream);
+
+/* Validates an upper CSR on the device; *bad [device, 1 int64] receives the
+ * number of offending rows (0 = valid).  ws >= sym_spmv_workspace_bytes(A). */
+sym_status sym_csr_upper_check(const sym_csr_upper* A, int64_t* bad, sym_stream_t stream);
+
+/* Bellman-Ford relaxation over the same storage (Sec. 5.2.2):
+ * y[i] = min(d[i], min over stored (i,j) and (j,i) of a + d[other]).  y, d: n floats. */
+sym_status sym_bellman_step(const sym_csr_upper* A, const float* d, float* y, sym_stream_t stream);
+
+/* Baseline: the same product from a full (both-triangle) CSR built by
+ * sym_csr_expand_upper; plain row-per-warp SpMV. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const float* val;
+} sym_csr_full;
+/* Bytes of the full CSR (rowptr + col + val) and of the build workspace. */
+size_t sym_csr_expand_bytes(const sym_csr_upper* A, size_t* ws_bytes);
+/* Writes the full CSR of A into arena [device] (rowptr | col | val, each
+ * 256-byte aligned) and fills *out.  Synchronises `stream`. */
+sym_status sym_csr_expand_upper(const sym_csr_upper* A, void* arena, size_t arena_bytes, void* ws,
+                                size_t ws_bytes, sym_stream_t stream, sym_csr_full* out);
+sym_status sym_spmv_full(const sym_csr_full* A, const float* x, float* y, sym_stream_t stream);
+
+/* ===================================================================== */
+/* Batched SSYMV + SYPRD: many independent matrices in one persistent launch */
+/* ===================================================================== */
+
+/* Instance b owns global rows [row_off[b], row_off[b+1]) of x and y; rowptr is
+ * global (nnz offsets, int64, total_rows+1 entries); col holds columns LOCAL to
+ * the instance.  All arrays [device]. */
+typedef struct {
+    int64_t count;
+    int64_t total_rows;
+    int64_t total_nnz;
+    const int64_t* row_off;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const float* val;
+} sym_csr_batch;
+
+/* Work decomposition of the persistent kernel. */
+typedef struct {
+    int32_t rows_per_tile;    /* rows in one work tile (tiles never straddle instances) */
+    int32_t lanes_per_row;    /* 1..32, power of two: lanes cooperating on one row */
+    int32_t threads_per_cta;  /* 128..1024, multiple of 32 */
+    int32_t ctas_per_sm;      /* persistent CTAs per SM */
+} sym_tile_cfg;
+
+/* A plan: the tile list and the FP64 partial buffers, carved from `arena`. */
+typedef struct sym_batch_plan_s* sym_batch_plan;
+/* host_row_off: [host] copy of row_off (count+1 entries), used to size tiles. */
+size_t sym_spmv_batch_plan_bytes(const sym_csr_batch* A, const int64_t* host_row_off, const sym_tile_cfg* cfg);
+sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const int64_t* host_row_off,
+                                      const sym_tile_cfg* cfg, void* arena, size_t arena_bytes,
+                                      sym_stream_t stream, sym_batch_plan* out);
+/* y = A_b x_b for every instance; syprd [device, count doubles] (nullable)
+ * receives x_b^T A_b x_b (FP64 cross-tile sums).  One persistent launch plus
+ * the reset and finalise steps, all on `stream`. */
+sym_status sym_spmv_batch_run(sym_batch_plan plan, const float* x, float* y, double* syprd,
+                              sym_stream_t stream);
+/* Captures sym_spmv_batch_run into a CUDA graph (fixed pointers) and replays
+ * it with sym_spmv_batch_graph_launch.  The graph lives in the plan. */
+sym_status sym_spmv_batch_capture(sym_batch_plan plan, const float* x, float* y, double* syprd,
+                                  sym_stream_t stream);
+sym_status sym_spmv_batch_graph_launch(sym_batch_plan plan, sym_stream_t stream);
+sym_status sym_spmv_batch_plan_destroy(sym_batch_plan plan);
+
+/* Autotuner: times candidate sym_tile_cfg shapes on this batch (each as a
+ * plan built in `arena`, so arena must hold the largest candidate plan:
+ * sym_spmv_batch_plan_bytes with rows_per_tile = 1 bounds them all), keeps the
+ * fastest, and records it in the text cache file `cache_path` (nullable) keyed
+ * by device name and batch shape.  A cache hit skips the timing.  Synchronous. */
+sym_status sym_autotune_spmv_batch(const sym_csr_batch* A, const int64_t* host_row_off, const float* x,
+                                   float* y, double* syprd, void* arena, size_t arena_bytes,
+                                   const char* cache_path, sym_stream_t stream, sym_tile_cfg* best,
+                                   float* best_ms);
+
+/* ===================================================================== */
+/* Fully symmetric sparse tensors of order 2..5                            */
+/* ===================================================================== */
+
+typedef struct sym_tensor_s* sym_tensor;
+
+/* Sizes for sym_tensor_create: *arena_bytes stays owned by the tensor,
+ * *ws_bytes is scratch needed only during the call. */
+sym_status sym_tensor_create_bytes(int order, int64_t n, int64_t nnz, size_t* arena_bytes,
+                                   size_t* ws_bytes);
+
+/* Canonicalises a coordinate list into the tensor's device layout (Sec. 2.1
+ * canonical triangle; Sec. 4.2.9 diagonal splitting):
+ *   1. every coordinate tuple is sorted ascending and range checked;
+ *   2. entries are sorted lexicographically (radix sort of packed keys);
+ *   3. repeated multisets follow `dup` (never summed);
+ *   4. entries are split, order preserved, into the STRICT stream (all
+ *      indices distinct) and the DIAGONAL stream (some index repeated);
+ *   5. exact counts are taken (per equality pattern, full-tensor nonzeros,
+ *      fibers) and ||X||^2 over the full tensor is summed in FP64.
+ * idx [device]: order rows of nnz int32, row q at idx + q*ld_idx, any position
+ * order per tuple.  val [device]: nnz floats.  Order 2..5, 1 <= n < 2^31,
+ * order * ceil(log2 n) <= 128.  Synchronises `stream` (it reads back counts).
+ * On error no tensor is created. */
+sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const int32_t* idx, int64_t ld_idx,
+                             const float* val, sym_dup_policy dup, void* arena, size_t arena_bytes,
+                             void* ws, size_t ws_bytes, sym_stream_t stream, sym_tensor* out);
+
+typedef struct {
+    int32_t order;
+    int32_t key_bits;          /* bits per index in the packed keys */
+    int64_t n;
+    int64_t nnz;               /* canonical entries kept */
+    int64_t nnz_strict;
+    int64_t nnz_diag;
+    int64_t duplicates_dropped;
+    int64_t counts_by_pattern[16]; /* bit q of the pattern: c_q == c_{q+1} */
+    int64_t expanded_nnz;      /* sum over entries of the distinct-permutation count */
+    int64_t root_fibers;       /* distinct c_1 */
+    int64_t l2_fibers;         /* distinct (c_1, c_2) */
+    double normsq;             /* ||X||^2 of the full tensor, FP64 */
+    size_t arena_used;
+} sym_tensor_info_t;
+
+sym_status sym_tensor_info(sym_tensor X, sym_tensor_info_t* out);
+
+/* Writes the canonical entries [device]: first the strict stream, then the
+ * diagonal stream, each in lexicographic order.  cidx has order rows of
+ * ld_out int32 (ld_out >= nnz), cval nnz floats. */
+sym_status sym_tensor_export(sym_tensor X, int32_t* cidx, int64_t ld_out, float* cval, sym_stream_t stream);
+
+sym_status sym_tensor_destroy(sym_tensor X);
+
+/* Counter-based SplitMix64 coordinate generator for large on-device pools:
+ * draw q of entry e is word e*order+q of the stream with `seed`; index =
+ * high 32 bits * n >> 32; value = the entry's multiset hash mapped to a 24-bit
+ * uniform in [-1, 1) (equal multisets get equal values, so the keep-equal
+ * duplicate policy merges repeats).  idx: order rows of ld_idx int32 [device]. */
+sym_status sym_gen_coords(int order, int64_t n, int64_t count, uint64_t seed, int32_t* idx, int64_t ld_idx,
+                          float* val, sym_stream_t stream);
+
+/* ===================================================================== */
+/* Symmetric MTTKRP (Sec. 4.3, Sec. 5.2.6):                                */
+/*   M[i, r] = sum over the full tensor X[i, k, l, ..] B[k, r] B[l, r] ..  */
+/* with one shared factor B (the symmetric CPD update).                     */
+/* ===================================================================== */
+
+/* Workspace for sym_mttkrp (needed when residual != NULL; 0 otherwise). */
+size_t sym_mttkrp_workspace_bytes(sym_tensor X, int rank, sym_dtype bdt, int want_residual);
+
+/* M [device, n x rank floats, row stride ldm, overwritten] = MTTKRP of X with
+ * B [device, n x rank, row stride ldb, FP32 or BF16 per bdt; BF16 values are
+ * widened to FP32 on load and all accumulation is FP32].
+ * The strict stream applies weight (N-1)! per position; the diagonal stream
+ * applies per-run integer weights (N-1)!/((m_t-1)! prod_{s!=t} m_s!).
+ * rank: 4..128, multiple of 4; ldb, ldm multiples of 4 (8 for BF16 ldb is not
+ * required); B and M 16-byte aligned.
+ * residual [device, 1 double] (nullable): the CP-fit residual
+ * ||X - sum_r b_r^(x)N||^2 = ||X||^2 - 2<X,Mcp> + ||Mcp||^2 with unit weights,
+ * evaluated in FP64 (exact FP32 products, double-float partials, FP64 sums). */
+sym_status sym_mttkrp(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
+                      int64_t ldm, double* residual, void* ws, size_t ws_bytes, sym_stream_t stream);
+
+/* Kernel shape for MTTKRP (entries per warp-chunk); 0 = library default. */
+sym_status sym_mttkrp_set_chunk(sym_tensor X, int entries_per_warp);
+
+/* ===================================================================== */
+/* Baseline: MTTKRP over the fully expanded (non-symmetric) tensor          */
+/* ===================================================================== */
+
+typedef struct sym_expanded_s* sym_expanded;
+/* Sizes for the expanded tensor (all distinct permutations of every entry). */
+sym_status sym_expanded_bytes(sym_tensor X, size_t* arena_bytes, size_t* ws_bytes);
+/* Writes every distinct permutation of every canonical entry, sorted
+ * lexicographically (mode-1 major).  Synchronises `stream`. */
+sym_status sym_expanded_create(sym_tensor X, void* arena, size_t arena_bytes, void* ws, size_t ws_bytes,
+                               sym_stream_t stream, sym_expanded* out);
+sym_status sym_expanded_info(sym_expanded E, int64_t* nnz);
+sym_status sym_expanded_export(sym_expanded E, int32_t* eidx, int64_t ld_out, float* evals, sym_stream_t stream);
+/* Plain mode-1 MTTKRP over the expanded tensor: no symmetry used, no atomics
+ * except at chunk seams (entries are sorted by mode 1). */
+sym_status sym_mttkrp_expanded(sym_expanded E, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
+                               int64_t ldm, sym_stream_t stream);
+sym_status sym_expanded_destroy(sym_expanded E);
+
+/* ===================================================================== */
+/* Serving: continuous batching of MTTKRP requests                          */
+/* ===================================================================== */
+
+typedef struct sym_server_s* sym_server;
+
+typedef struct {
+    sym_tensor X;        /* a resident tensor */
+    const void* B;       /* [device] factor, n x rank, row stride ldb */
+    sym_dtype bdt;
+    int32_t rank;
+    int64_t ldb;
+    float* M;            /* [device] output, n x rank, row stride ldm; caller keeps it alive until done */
+    int64_t ldm;
+    int32_t want_residual;
+    uint64_t user_tag;
+} sym_request;
+
+typedef struct {
+    sym_status status;   /* SYM_OK, an error, or SYM_PENDING */
+    double residual;     /* CP-fit residual when requested */
+    uint64_t user_tag;
+    uint64_t t_submit_ns; /* host steady clock */
+    uint64_t t_admit_ns;
+    uint64_t t_done_ns;
+} sym_result;
+
+typedef struct {
+    int32_t max_slots;         /* requests in flight at once (device streams) */
+    int32_t max_rank;          /* largest rank accepted */
+    size_t hbm_budget_bytes;   /* bound on the bytes touched by requests in flight */
+    int32_t coalesce_small;    /* launch small admitted requests as one grouped launch */
+    int64_t small_nnz;         /* "small" threshold for coalescing */
+    int64_t wait_limit_ns;     /* bound used by sym_server_destroy's drain */
+} sym_server_cfg;
+
+/* Device scratch the server needs (per-slot residual workspaces). */
+size_t sym_server_arena_bytes(const sym_server_cfg* cfg);
+/* Starts the scheduler thread.  arena [device] holds per-slot scratch. */
+sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, size_t arena_bytes, int device,
+                             sym_server* out);
+/* Queues a request (non-blocking); *ticket identifies it.  The request is
+ * validated on the host first: a bad one fails here with SYM_E_BADREQ or
+ * SYM_E_BUDGET and gets no ticket. */
+sym_status sym_batch_submit(sym_server S, const sym_request* req, uint64_t* ticket);
+/* SYM_PENDING until the request finishes; then its result (once). */
+sym_status sym_batch_poll(sym_server S, uint64_t ticket, sym_result* out);
+/* Blocks up to timeout_ns for the result (SYM_E_TIMEOUT if it runs out). */
+sym_status sym_batch_wait(sym_server S, uint64_t ticket, int64_t timeout_ns, sym_result* out);
+typedef struct {
+    int64_t submitted, admitted, completed, rejected;
+    int64_t launches, grouped_launches;
+    int64_t peak_inflight, peak_bytes;
+} sym_server_stats;
+sym_status sym_server_stats_get(sym_server S, sym_server_stats* out);
+/* Drains in-flight work (bounded by cfg.wait_limit_ns) and stops the thread. */
+sym_status sym_server_destroy(sym_server S);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYMGPU_H */

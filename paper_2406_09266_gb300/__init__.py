@@ -1,0 +1,438 @@
+"""Python binding of libsymgpu (the C ABI in include/symgpu.h).
+
+Argument marshalling only: PyTorch supplies device memory (arenas and
+workspaces sized by the library's *_bytes queries) and streams; every step of
+the symmetric kernels runs in libsymgpu's CUDA code.  There is no CPU fallback:
+if the shared library is missing or cannot load, every call raises.
+
+Names follow the C ABI: sym_tensor_create -> SymTensor, sym_mttkrp ->
+SymTensor.mttkrp, sym_spmv -> spmv, sym_batch_submit/poll -> Server.submit/poll.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsymgpu.so")
+
+SYM_OK, SYM_PENDING = 0, 1
+STATUS = {0: "SYM_OK", -1: "SYM_E_INVALID", -2: "SYM_E_NONCANONICAL", -3: "SYM_E_RANGE", -4: "SYM_E_DUPLICATE",
+          -5: "SYM_E_NOMEM", -6: "SYM_E_BUDGET", -7: "SYM_E_TIMEOUT", -8: "SYM_E_CUDA", -9: "SYM_E_BADREQ",
+          -10: "SYM_E_UNSUPPORTED", -11: "SYM_E_NOTFOUND", 1: "SYM_PENDING"}
+F32, BF16 = 0, 1
+DUP_ERROR, DUP_KEEP_EQUAL = 0, 1
+
+
+class SymError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+# ------------------------------------------------------------------ C structs
+
+class CsrUpper(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+CsrFull = CsrUpper
+
+
+class CsrBatch(C.Structure):
+    _fields_ = [("count", C.c_int64), ("total_rows", C.c_int64), ("total_nnz", C.c_int64),
+                ("row_off", C.c_void_p), ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class TileCfg(C.Structure):
+    _fields_ = [("rows_per_tile", C.c_int32), ("lanes_per_row", C.c_int32), ("threads_per_cta", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TensorInfo(C.Structure):
+    _fields_ = [("order", C.c_int32), ("key_bits", C.c_int32), ("n", C.c_int64), ("nnz", C.c_int64),
+                ("nnz_strict", C.c_int64), ("nnz_diag", C.c_int64), ("duplicates_dropped", C.c_int64),
+                ("counts_by_pattern", C.c_int64 * 16), ("expanded_nnz", C.c_int64), ("root_fibers", C.c_int64),
+                ("l2_fibers", C.c_int64), ("normsq", C.c_double), ("arena_used", C.c_size_t)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["counts_by_pattern"] = list(self.counts_by_pattern)
+        return d
+
+
+class Request(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("B", C.c_void_p), ("bdt", C.c_int), ("rank", C.c_int32), ("ldb", C.c_int64),
+                ("M", C.c_void_p), ("ldm", C.c_int64), ("want_residual", C.c_int32), ("user_tag", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("residual", C.c_double), ("user_tag", C.c_uint64),
+                ("t_submit_ns", C.c_uint64), ("t_admit_ns", C.c_uint64), ("t_done_ns", C.c_uint64)]
+
+
+class ServerCfg(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("max_rank", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
+                ("coalesce_small", C.c_int32), ("small_nnz", C.c_int64), ("wait_limit_ns", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("launches", C.c_int64), ("grouped_launches", C.c_int64),
+                ("peak_inflight", C.c_int64), ("peak_bytes", C.c_int64)]
+
+
+class ProfileEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+# ------------------------------------------------------------------ loading
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "sym_status_string": ([C.c_int], C.c_char_p),
+    "sym_last_cuda_error": ([], C.c_int),
+    "sym_version": ([], C.c_int),
+    "sym_profile_enable": ([C.c_int], C.c_int),
+    "sym_profile_read": ([C.c_void_p, C.c_int], C.c_int),
+    "sym_profile_reset": ([], C.c_int),
+    "sym_spmv_workspace_bytes": ([C.c_void_p], C.c_size_t),
+    "sym_spmv": ([C.c_void_p] * 5 + [C.c_size_t, C.c_void_p], C.c_int),
+    "sym_csr_upper_check": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_bellman_step": ([C.c_void_p] * 4, C.c_int),
+    "sym_csr_expand_bytes": ([C.c_void_p, C.c_void_p], C.c_size_t),
+    "sym_csr_expand_upper": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p,
+                              C.c_void_p], C.c_int),
+    "sym_spmv_full": ([C.c_void_p] * 4, C.c_int),
+    "sym_spmv_batch_plan_bytes": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_size_t),
+    "sym_spmv_batch_plan_create": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
+                                    C.c_void_p], C.c_int),
+    "sym_spmv_batch_run": ([C.c_void_p] * 5, C.c_int),
+    "sym_spmv_batch_capture": ([C.c_void_p] * 5, C.c_int),
+    "sym_spmv_batch_graph_launch": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_spmv_batch_plan_destroy": ([C.c_void_p], C.c_int),
+    "sym_autotune_spmv_batch": ([C.c_void_p] * 6 + [C.c_size_t, C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p],
+                                C.c_int),
+    "sym_tensor_create_bytes": ([C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_tensor_create": ([C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
+                           C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_tensor_info": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_tensor_export": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_tensor_destroy": ([C.c_void_p], C.c_int),
+    "sym_gen_coords": ([C.c_int, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p,
+                        C.c_void_p], C.c_int),
+    "sym_mttkrp_workspace_bytes": ([C.c_void_p, C.c_int, C.c_int, C.c_int], C.c_size_t),
+    "sym_mttkrp": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                    C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "sym_mttkrp_set_chunk": ([C.c_void_p, C.c_int], C.c_int),
+    "sym_expanded_bytes": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_expanded_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p,
+                             C.c_void_p], C.c_int),
+    "sym_expanded_info": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_expanded_export": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_mttkrp_expanded": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64,
+                             C.c_void_p], C.c_int),
+    "sym_expanded_destroy": ([C.c_void_p], C.c_int),
+    "sym_server_arena_bytes": ([C.c_void_p], C.c_size_t),
+    "sym_server_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p], C.c_int),
+    "sym_batch_submit": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_batch_poll": ([C.c_void_p, C.c_uint64, C.c_void_p], C.c_int),
+    "sym_batch_wait": ([C.c_void_p, C.c_uint64, C.c_int64, C.c_void_p], C.c_int),
+    "sym_server_stats_get": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_server_destroy": ([C.c_void_p], C.c_int),
+}
+
+
+def exported_symbols():
+    """Names the C ABI declares (include/symgpu.h) and this binding wires up."""
+    return sorted(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Loads libsymgpu.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsymgpu.so is not built ({path}); run __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes, f.restype = args, res
+        _lib = L
+        return L
+
+
+def lib():
+    return _lib if _lib is not None else load()
+
+
+def check(code: int, what: str):
+    if code != SYM_OK:
+        raise SymError(code, what)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _scratch(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _dtype_code(B: torch.Tensor) -> int:
+    if B.dtype == torch.float32:
+        return F32
+    if B.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError("factor must be float32 or bfloat16")
+
+
+# ------------------------------------------------------------------ profiling
+
+def profile_enable(on: bool = True):
+    check(lib().sym_profile_enable(int(on)), "sym_profile_enable")
+
+
+def profile_reset():
+    check(lib().sym_profile_reset(), "sym_profile_reset")
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total event ms)} since the last reset."""
+    buf = (ProfileEntry * 64)()
+    k = lib().sym_profile_read(buf, 64)
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(k)}
+
+
+# ------------------------------------------------------------------ SSYMV / SYPRD
+
+def csr_upper(n, rowptr, col, val) -> CsrUpper:
+    return CsrUpper(int(n), int(col.numel()), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+
+
+def spmv_workspace(n, rowptr, col, val, device=None) -> torch.Tensor:
+    A = csr_upper(n, rowptr, col, val)
+    return _scratch(lib().sym_spmv_workspace_bytes(C.byref(A)), device or rowptr.device)
+
+
+def spmv(n, rowptr, col, val, x, y=None, syprd=False, ws=None, stream=None):
+    """y = A x for the symmetric A given by its upper-triangle CSR; optionally SYPRD x^T A x (FP64)."""
+    A = csr_upper(n, rowptr, col, val)
+    if y is None:
+        y = torch.empty(n, dtype=torch.float32, device=x.device)
+    s_out = torch.empty(1, dtype=torch.float64, device=x.device) if syprd else None
+    if syprd and ws is None:
+        ws = _scratch(lib().sym_spmv_workspace_bytes(C.byref(A)), x.device)
+    check(lib().sym_spmv(C.byref(A), _ptr(x), _ptr(y), _ptr(s_out), _ptr(ws), ws.numel() if ws is not None else 0,
+                         _stream(stream)), "sym_spmv")
+    return (y, s_out) if syprd else y
+
+
+def csr_upper_check(n, rowptr, col, val, stream=None) -> int:
+    A = csr_upper(n, rowptr, col, val)
+    bad = torch.zeros(1, dtype=torch.int64, device=rowptr.device)
+    check(lib().sym_csr_upper_check(C.byref(A), _ptr(bad), _stream(stream)), "sym_csr_upper_check")
+    return int(bad.item())
+
+
+def bellman_step(n, rowptr, col, val, d, y=None, stream=None):
+    A = csr_upper(n, rowptr, col, val)
+    if y is None:
+        y = torch.empty_like(d)
+    check(lib().sym_bellman_step(C.byref(A), _ptr(d), _ptr(y), _stream(stream)), "sym_bellman_step")
+    return y
+
+
+class FullCSR:
+    """Both-triangle CSR built on the device from an upper CSR (the non-symmetric baseline)."""
+
+    def __init__(self, n, rowptr, col, val, stream=None):
+        A = csr_upper(n, rowptr, col, val)
+        wsb = C.c_size_t(0)
+        ab = lib().sym_csr_expand_bytes(C.byref(A), C.byref(wsb))
+        self.arena = _scratch(ab, rowptr.device)
+        ws = _scratch(wsb.value, rowptr.device)
+        self.desc = CsrFull()
+        check(lib().sym_csr_expand_upper(C.byref(A), _ptr(self.arena), self.arena.numel(), _ptr(ws), ws.numel(),
+                                         _stream(stream), C.byref(self.desc)), "sym_csr_expand_upper")
+        self.n, self.nnz = self.desc.n, self.desc.nnz
+
+    def spmv(self, x, y=None, stream=None):
+        if y is None:
+            y = torch.empty_like(x)
+        check(lib().sym_spmv_full(C.byref(self.desc), _ptr(x), _ptr(y), _stream(stream)), "sym_spmv_full")
+        return y
+
+    def arrays(self):
+        """(rowptr, col, val) as torch views of the arena."""
+        base = self.arena.data_ptr()
+        n, nnz = self.n, self.nnz
+
+        def view(ptr, count, dtype):
+            off = ptr - base
+            es = torch.tensor([], dtype=dtype).element_size()
+            return self.arena[off: off + count * es].view(dtype)
+        return (view(self.desc.rowptr, n + 1, torch.int32), view(self.desc.col, nnz, torch.int32),
+                view(self.desc.val, nnz, torch.float32))
+
+
+# ------------------------------------------------------------------ tensors
+
+class SymTensor:
+    """A canonicalised fully symmetric sparse tensor resident on the device."""
+
+    def __init__(self, idx: torch.Tensor, val: torch.Tensor, n: int, dup: int = DUP_ERROR, stream=None,
+                 ws: torch.Tensor | None = None):
+        if idx.dim() != 2 or idx.dtype != torch.int32 or not idx.is_cuda:
+            raise TypeError("idx must be a (order, nnz) int32 CUDA tensor")
+        if val.dtype != torch.float32 or not val.is_cuda:
+            raise TypeError("val must be a float32 CUDA tensor")
+        order, nnz = idx.shape
+        idx = idx.contiguous()
+        ab, wb = C.c_size_t(0), C.c_size_t(0)
+        check(lib().sym_tensor_create_bytes(order, n, nnz, C.byref(ab), C.byref(wb)), "sym_tensor_create_bytes")
+        self.arena = _scratch(ab.value, idx.device)
+        if ws is None or ws.numel() < wb.value:
+            ws = _scratch(wb.value, idx.device)
+        h = C.c_void_p()
+        check(lib().sym_tensor_create(order, n, nnz, _ptr(idx), max(nnz, 1), _ptr(val.contiguous()), dup,
+                                      _ptr(self.arena), self.arena.numel(), _ptr(ws), ws.numel(), _stream(stream),
+                                      C.byref(h)), "sym_tensor_create")
+        self.handle = h
+        self.order, self.n = order, n
+        self.device = idx.device
+        self._info = None
+
+    @staticmethod
+    def create_ws_bytes(order, n, nnz) -> int:
+        ab, wb = C.c_size_t(0), C.c_size_t(0)
+        check(lib().sym_tensor_create_bytes(order, n, nnz, C.byref(ab), C.byref(wb)), "sym_tensor_create_bytes")
+        return wb.value
+
+    def info(self) -> dict:
+        if self._info is None:
+            inf = TensorInfo()
+            check(lib().sym_tensor_info(self.handle, C.byref(inf)), "sym_tensor_info")
+            self._info = inf.as_dict()
+        return self._info
+
+    @property
+    def nnz(self) -> int:
+        return self.info()["nnz"]
+
+    def export(self, stream=None):
+        """(cidx (order x nnz) int32, cval) on the device: strict stream, then diagonal stream."""
+        nnz = self.nnz
+        cidx = torch.empty((self.order, max(nnz, 1)), dtype=torch.int32, device=self.device)
+        cval = torch.empty(max(nnz, 1), dtype=torch.float32, device=self.device)
+        check(lib().sym_tensor_export(self.handle, _ptr(cidx), max(nnz, 1), _ptr(cval), _stream(stream)),
+              "sym_tensor_export")
+        return cidx[:, :nnz], cval[:nnz]
+
+    def set_chunk(self, entries_per_warp: int):
+        check(lib().sym_mttkrp_set_chunk(self.handle, entries_per_warp), "sym_mttkrp_set_chunk")
+
+    def mttkrp_workspace(self, rank: int, bdt: int = F32, residual: bool = True) -> torch.Tensor:
+        return _scratch(lib().sym_mttkrp_workspace_bytes(self.handle, rank, bdt, int(residual)), self.device)
+
+    def mttkrp(self, B: torch.Tensor, M: torch.Tensor | None = None, residual: bool = False,
+               ws: torch.Tensor | None = None, stream=None):
+        """Symmetric MTTKRP M = X_(1) (B kr ... kr B); optional FP64 CP-fit residual (device scalar)."""
+        rank = B.shape[1]
+        bdt = _dtype_code(B)
+        if M is None:
+            M = torch.empty((self.n, rank), dtype=torch.float32, device=B.device)
+        res = torch.empty(1, dtype=torch.float64, device=B.device) if residual else None
+        if residual and ws is None:
+            ws = self.mttkrp_workspace(rank, bdt, True)
+        check(lib().sym_mttkrp(self.handle, _ptr(B), bdt, rank, B.stride(0), _ptr(M), M.stride(0), _ptr(res),
+                               _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream)), "sym_mttkrp")
+        return (M, res) if residual else M
+
+    def expanded(self, stream=None) -> "Expanded":
+        return Expanded(self, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sym_tensor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gen_coords(order, n, count, seed, device="cuda", stream=None):
+    """On-device counter-based coordinate pool (same definition as synth.coord_pool)."""
+    idx = torch.empty((order, max(count, 1)), dtype=torch.int32, device=device)
+    val = torch.empty(max(count, 1), dtype=torch.float32, device=device)
+    check(lib().sym_gen_coords(order, n, count, C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _ptr(idx), max(count, 1),
+                               _ptr(val), _stream(stream)), "sym_gen_coords")
+    return idx[:, :count], val[:count]
+
+
+class Expanded:
+    """The fully expanded (non-symmetric) tensor: every distinct permutation of every entry."""
+
+    def __init__(self, X: SymTensor, stream=None):
+        ab, wb = C.c_size_t(0), C.c_size_t(0)
+        check(lib().sym_expanded_bytes(X.handle, C.byref(ab), C.byref(wb)), "sym_expanded_bytes")
+        self.arena = _scratch(ab.value, X.device)
+        ws = _scratch(wb.value, X.device)
+        h = C.c_void_p()
+        check(lib().sym_expanded_create(X.handle, _ptr(self.arena), self.arena.numel(), _ptr(ws), ws.numel(),
+                                        _stream(stream), C.byref(h)), "sym_expanded_create")
+        del ws
+        self.handle, self.order, self.n, self.device = h, X.order, X.n, X.device
+
+    @property
+    def nnz(self) -> int:
+        v = C.c_int64(0)
+        check(lib().sym_expanded_info(self.handle, C.byref(v)), "sym_expanded_info")
+        return v.value
+
+    def export(self, stream=None):
+        nnz = self.nnz
+        eidx = torch.empty((self.order, max(nnz, 1)), dtype=torch.int32, device=self.device)
+        ev = torch.empty(max(nnz, 1), dtype=torch.float32, device=self.device)
+        check(lib().sym_expanded_export(self.handle, _ptr(eidx), max(nnz, 1), _ptr(ev), _stream(stream)),
+              "sym_expanded_export")
+        return eidx[:, :nnz], ev[:nnz]
+
+    def mttkrp(self, B, M=None, stream=None):
+        rank = B.shape[1]
+        if M is None:
+            M = torch.empty((self.n, rank), dtype=torch.float32, device=B.device)
+        check(lib().sym_mttkrp_expanded(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(M),
+                                        M.stride(0), _stream(stream)), "sym_mttkrp_expanded")
+        return M
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sym_expanded_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

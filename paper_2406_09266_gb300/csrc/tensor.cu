@@ -1,0 +1,446 @@
+// Symmetric tensor handles: canonicalisation of a coordinate list into the
+// device layout used by the MTTKRP kernels.
+//
+// Canonical triangle (Sec. 2.1, Def. "Canonical", upper triangle): every tuple
+// is stored sorted, i_1 <= ... <= i_N, and entries are kept in lexicographic
+// order, which is the traversal order of a CSF tree rooted at i_1 (Sec. 2.2).
+// Diagonal splitting (Sec. 4.2.9): entries with all indices distinct form the
+// STRICT stream; entries with a repeated index form the DIAGONAL stream.  Both
+// live in one array, strict first, each in lexicographic order.
+//
+// Layout per entry: the sorted tuple packed into a key of ORDER * bits bits
+// (c_1 most significant), 64-bit words (a second word when ORDER*bits > 64),
+// plus a float value.  Keys are what the radix sort orders and what the
+// kernels decode.
+#include <new>
+#include <string.h>
+
+#include "common.cuh"
+#include "tensor.cuh"
+
+namespace symgpu {
+
+namespace {
+
+constexpr int CT = 256;
+
+struct DevCounters {
+    unsigned long long range_bad;
+    unsigned long long dup_seen;       // entries equal to their predecessor
+    unsigned long long dup_mismatch;   // ... whose value bits differ
+    unsigned long long by_pattern[16];
+    unsigned long long expanded;
+    unsigned long long root_fibers;
+    unsigned long long l2_fibers;
+    unsigned long long nnz_strict;
+    unsigned long long nnz_kept;
+    double normsq;
+};
+
+template <int N>
+__device__ __forceinline__ void sort_small(int32_t* c) {
+#pragma unroll
+    for (int a = 1; a < N; ++a)
+#pragma unroll
+        for (int b = a; b > 0; --b) {
+            int32_t x = c[b - 1], y = c[b];
+            c[b - 1] = min(x, y);
+            c[b] = max(x, y);
+        }
+}
+
+// Number of distinct permutations N!/prod(m_t!) from a sorted tuple's runs.
+template <int N>
+__device__ __forceinline__ int distinct_perms(const int32_t* c) {
+    const int fact[6] = {1, 1, 2, 6, 24, 120};
+    int den = 1, run = 1;
+#pragma unroll
+    for (int q = 1; q < N; ++q) {
+        if (c[q] == c[q - 1]) {
+            ++run;
+        } else {
+            den *= fact[run];
+            run = 1;
+        }
+    }
+    den *= fact[run];
+    return fact[N] / den;
+}
+
+template <int N, int KW>
+__global__ void k_pack(const int32_t* __restrict__ idx, int64_t ld, const float* __restrict__ val, int64_t nnz,
+                       int64_t n, int bits, uint64_t* __restrict__ klo, uint64_t* __restrict__ khi,
+                       uint32_t* __restrict__ pay, DevCounters* cnt) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (e < nnz) {
+        int32_t c[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            c[q] = idx[(int64_t)q * ld + e];
+            if (c[q] < 0 || c[q] >= n) {
+                bad = true;
+                c[q] = 0;
+            }
+        }
+        sort_small<N>(c);
+        KeyWords k = pack_key<N, KW>(c, bits);
+        klo[e] = k.lo;
+        if (KW == 2) khi[e] = k.hi;
+        pay[e] = (uint32_t)e;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, bad);
+    if (m && (threadIdx.x & 31) == 0) atomicAdd(&cnt->range_bad, (unsigned long long)__popc(m));
+    (void)val;
+}
+
+// Marks kept entries (first of each equal-key run), classifies them and takes
+// the exact counts.  flag_s / flag_d: 1 when the entry goes to that stream.
+template <int N, int KW>
+__global__ void __launch_bounds__(CT) k_mark(const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi,
+                                             const uint32_t* __restrict__ pay, const float* __restrict__ val,
+                                             int64_t nnz, int bits, int policy, uint32_t* __restrict__ flag_s,
+                                             uint32_t* __restrict__ flag_d, DevCounters* cnt) {
+    __shared__ unsigned long long s_pat[16];
+    __shared__ unsigned long long s_misc[6];  // expanded, root, l2, strict, kept, dups
+    __shared__ unsigned long long s_mis;
+    __shared__ double s_norm[CT / 32];
+    if (threadIdx.x < 16) s_pat[threadIdx.x] = 0;
+    if (threadIdx.x < 6) s_misc[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_mis = 0;
+    __syncthreads();
+    int64_t p = (int64_t)blockIdx.x * CT + threadIdx.x;
+    double nrm = 0.0;
+    if (p < nnz) {
+        KeyWords k{klo[p], KW == 2 ? khi[p] : 0ull};
+        bool dup = false, mismatch = false;
+        int32_t c[N], pc[N];
+        unpack_key<N, KW>(k, bits, c);
+        if (p > 0) {
+            KeyWords kp{klo[p - 1], KW == 2 ? khi[p - 1] : 0ull};
+            dup = (kp.lo == k.lo) && (kp.hi == k.hi);
+            unpack_key<N, KW>(kp, bits, pc);
+            if (dup && policy == SYM_DUP_KEEP_EQUAL)
+                mismatch = __float_as_uint(val[pay[p]]) != __float_as_uint(val[pay[p - 1]]);
+        }
+        bool keep = !dup;
+        int pat = 0;
+#pragma unroll
+        for (int q = 0; q + 1 < N; ++q) pat |= (c[q] == c[q + 1]) ? (1 << q) : 0;
+        flag_s[p] = (keep && pat == 0) ? 1u : 0u;
+        flag_d[p] = (keep && pat != 0) ? 1u : 0u;
+        if (dup) atomicAdd(&s_misc[5], 1ull);
+        if (mismatch) atomicAdd(&s_mis, 1ull);
+        if (keep) {
+            int ex = distinct_perms<N>(c);
+            atomicAdd(&s_pat[pat], 1ull);
+            atomicAdd(&s_misc[0], (unsigned long long)ex);
+            if (p == 0 || pc[0] != c[0]) atomicAdd(&s_misc[1], 1ull);
+            if (p == 0 || pc[0] != c[0] || pc[1] != c[1]) atomicAdd(&s_misc[2], 1ull);
+            if (pat == 0) atomicAdd(&s_misc[3], 1ull);
+            atomicAdd(&s_misc[4], 1ull);
+            double v = (double)val[pay[p]];
+            nrm = (double)ex * v * v;
+        }
+    }
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) s_norm[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x < 16 && s_pat[threadIdx.x]) atomicAdd(&cnt->by_pattern[threadIdx.x], s_pat[threadIdx.x]);
+    if (threadIdx.x == 16) {
+        atomicAdd(&cnt->expanded, s_misc[0]);
+        atomicAdd(&cnt->root_fibers, s_misc[1]);
+        atomicAdd(&cnt->l2_fibers, s_misc[2]);
+        atomicAdd(&cnt->nnz_strict, s_misc[3]);
+        atomicAdd(&cnt->nnz_kept, s_misc[4]);
+        atomicAdd(&cnt->dup_seen, s_misc[5]);
+        atomicAdd(&cnt->dup_mismatch, s_mis);
+    }
+    if (threadIdx.x == 32) {
+        double t = 0.0;
+        for (int w = 0; w < CT / 32; ++w) t += s_norm[w];
+        atomicAdd(&cnt->normsq, t);
+    }
+}
+
+template <int KW>
+__global__ void k_compact(const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi,
+                          const uint32_t* __restrict__ pay, const float* __restrict__ val, int64_t nnz,
+                          const uint32_t* __restrict__ flag_s, const uint32_t* __restrict__ flag_d,
+                          const uint32_t* __restrict__ pos_s, const uint32_t* __restrict__ pos_d,
+                          const DevCounters* cnt, uint64_t* __restrict__ out_lo, uint64_t* __restrict__ out_hi,
+                          float* __restrict__ out_val) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    int64_t dst = -1;
+    if (flag_s[p]) dst = pos_s[p];
+    else if (flag_d[p]) dst = (int64_t)cnt->nnz_strict + pos_d[p];
+    if (dst < 0) return;
+    out_lo[dst] = klo[p];
+    if (KW == 2) out_hi[dst] = khi[p];
+    out_val[dst] = val[pay[p]];
+}
+
+template <int N, int KW>
+__global__ void k_export(const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi,
+                         const float* __restrict__ val, int64_t nnz, int bits, int32_t* __restrict__ cidx,
+                         int64_t ld, float* __restrict__ cval) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    int32_t c[N];
+    unpack_key<N, KW>(KeyWords{klo[p], KW == 2 ? khi[p] : 0ull}, bits, c);
+#pragma unroll
+    for (int q = 0; q < N; ++q) cidx[(int64_t)q * ld + p] = c[q];
+    cval[p] = val[p];
+}
+
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_gen_coords(int order, int64_t n, int64_t count, uint64_t seed, int32_t* __restrict__ idx,
+                             int64_t ld, float* __restrict__ val) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+    uint64_t s1 = 0, s2 = 0;
+    for (int q = 0; q < order; ++q) {
+        uint64_t k = (uint64_t)e * order + q + 1;
+        uint64_t z = sm64_mix(seed + k * gamma);
+        uint64_t r = ((z >> 32) * (uint64_t)n) >> 32;
+        idx[(int64_t)q * ld + e] = (int32_t)r;
+        s1 += r;
+        s2 += sm64_mix(r + seed);
+    }
+    uint64_t h = sm64_mix(s1 * gamma + s2);
+    int32_t m = (int32_t)(h >> 40);
+    val[e] = (float)(m - (1 << 23)) * (1.0f / 8388608.0f);
+}
+
+int bits_for(int64_t n) {
+    int b = 0;
+    while ((1ll << b) < n) ++b;
+    return b < 1 ? 1 : b;
+}
+
+struct CreatePlan {
+    int kw;
+    int bits;
+};
+
+// Workspace layout of sym_tensor_create (shared by the size query and the call).
+template <typename C>
+void layout_ws(C& c, int64_t nnz, int kw, uint64_t** lo0, uint64_t** hi0, uint32_t** p0, uint64_t** lo1,
+               uint64_t** hi1, uint32_t** p1, uint32_t** fs, uint32_t** fd, uint32_t** ps, uint32_t** pd,
+               DevCounters** cnt, void** radix, void** scan) {
+    size_t m = nnz > 0 ? (size_t)nnz : 1;
+    *lo0 = c.template take<uint64_t>(m);
+    *hi0 = kw == 2 ? c.template take<uint64_t>(m) : nullptr;
+    *p0 = c.template take<uint32_t>(m);
+    *lo1 = c.template take<uint64_t>(m);
+    *hi1 = kw == 2 ? c.template take<uint64_t>(m) : nullptr;
+    *p1 = c.template take<uint32_t>(m);
+    *fs = c.template take<uint32_t>(m);
+    *fd = c.template take<uint32_t>(m);
+    *ps = c.template take<uint32_t>(m);
+    *pd = c.template take<uint32_t>(m);
+    *cnt = c.template take<DevCounters>(1);
+    *radix = c.template take<char>(radix_ws_bytes((int64_t)m, kw));
+    *scan = c.template take<char>(scan_ws_bytes((int64_t)m));
+}
+
+struct NullCarver {
+    Sizer s;
+    template <typename T>
+    T* take(size_t n) {
+        s.take<T>(n);
+        return nullptr;
+    }
+};
+
+template <typename C>
+void layout_arena(C& c, int64_t nnz, int kw, uint64_t** lo, uint64_t** hi, float** val) {
+    size_t m = nnz > 0 ? (size_t)nnz : 1;
+    *lo = c.template take<uint64_t>(m);
+    *hi = kw == 2 ? c.template take<uint64_t>(m) : nullptr;
+    *val = c.template take<float>(m);
+}
+
+template <int N>
+sym_status launch_create_kernels(int kw, const int32_t* idx, int64_t ld, const float* val, int64_t nnz, int64_t n,
+                                 int bits, int policy, uint64_t* lo0, uint64_t* hi0, uint32_t* p0, uint64_t* lo1,
+                                 uint64_t* hi1, uint32_t* p1, uint32_t* fs, uint32_t* fd, uint32_t* ps,
+                                 uint32_t* pd, DevCounters* cnt, void* radix, void* scan, uint64_t* out_lo,
+                                 uint64_t* out_hi, float* out_val, cudaStream_t s) {
+    unsigned g = (unsigned)((nnz + CT - 1) / CT);
+    if (kw == 1)
+        k_pack<N, 1><<<g, CT, 0, s>>>(idx, ld, val, nnz, n, bits, lo0, hi0, p0, cnt);
+    else
+        k_pack<N, 2><<<g, CT, 0, s>>>(idx, ld, val, nnz, n, bits, lo0, hi0, p0, cnt);
+    SYM_CHECK_LAUNCH();
+    uint64_t *slo, *shi;
+    uint32_t* sp;
+    sym_status st = radix_sort_pairs(kw, lo0, hi0, p0, lo1, hi1, p1, nnz, N * bits, radix, s, &slo, &shi, &sp);
+    if (st != SYM_OK) return st;
+    if (kw == 1)
+        k_mark<N, 1><<<g, CT, 0, s>>>(slo, shi, sp, val, nnz, bits, policy, fs, fd, cnt);
+    else
+        k_mark<N, 2><<<g, CT, 0, s>>>(slo, shi, sp, val, nnz, bits, policy, fs, fd, cnt);
+    SYM_CHECK_LAUNCH();
+    st = exclusive_scan_u32(fs, ps, nnz, scan, s);
+    if (st != SYM_OK) return st;
+    st = exclusive_scan_u32(fd, pd, nnz, scan, s);
+    if (st != SYM_OK) return st;
+    if (kw == 1)
+        k_compact<1><<<g, CT, 0, s>>>(slo, shi, sp, val, nnz, fs, fd, ps, pd, cnt, out_lo, out_hi, out_val);
+    else
+        k_compact<2><<<g, CT, 0, s>>>(slo, shi, sp, val, nnz, fs, fd, ps, pd, cnt, out_lo, out_hi, out_val);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+}  // namespace
+
+}  // namespace symgpu
+
+using namespace symgpu;
+
+extern "C" sym_status sym_tensor_create_bytes(int order, int64_t n, int64_t nnz, size_t* arena_bytes,
+                                              size_t* ws_bytes) {
+    if (order < 2 || order > 5 || n < 1 || n > 0x7fffffffLL || nnz < 0 || nnz > 0xffffffffLL) return SYM_E_INVALID;
+    int bits = bits_for(n);
+    if (order * bits > 128) return SYM_E_UNSUPPORTED;
+    int kw = order * bits > 64 ? 2 : 1;
+    NullCarver a, w;
+    uint64_t *lo, *hi;
+    float* v;
+    layout_arena(a, nnz, kw, &lo, &hi, &v);
+    uint64_t *l0, *h0, *l1, *h1;
+    uint32_t *p0, *p1, *fs, *fd, *ps, *pd;
+    DevCounters* c;
+    void *r, *sc;
+    layout_ws(w, nnz, kw, &l0, &h0, &p0, &l1, &h1, &p1, &fs, &fd, &ps, &pd, &c, &r, &sc);
+    if (arena_bytes) *arena_bytes = a.s.used;
+    if (ws_bytes) *ws_bytes = w.s.used;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const int32_t* idx, int64_t ld_idx,
+                                        const float* val, sym_dup_policy dup, void* arena, size_t arena_bytes,
+                                        void* ws, size_t ws_bytes, sym_stream_t stream, sym_tensor* out) {
+    if (!out) return SYM_E_INVALID;
+    *out = nullptr;
+    size_t need_a = 0, need_w = 0;
+    sym_status st = sym_tensor_create_bytes(order, n, nnz, &need_a, &need_w);
+    if (st != SYM_OK) return st;
+    if (nnz > 0 && (!idx || !val || ld_idx < nnz)) return SYM_E_INVALID;
+    if (dup != SYM_DUP_ERROR && dup != SYM_DUP_KEEP_EQUAL) return SYM_E_INVALID;
+    if (!arena || !ws || !aligned(arena, 256) || !aligned(ws, 256)) return SYM_E_INVALID;
+    if (arena_bytes < need_a || ws_bytes < need_w) return SYM_E_NOMEM;
+    const int bits = bits_for(n);
+    const int kw = order * bits > 64 ? 2 : 1;
+    cudaStream_t s = as_stream(stream);
+
+    Carver A(arena, arena_bytes), W(ws, ws_bytes);
+    uint64_t *out_lo, *out_hi;
+    float* out_val;
+    layout_arena(A, nnz, kw, &out_lo, &out_hi, &out_val);
+    uint64_t *l0, *h0, *l1, *h1;
+    uint32_t *p0, *p1, *fs, *fd, *ps, *pd;
+    DevCounters* cnt;
+    void *radix, *scan;
+    layout_ws(W, nnz, kw, &l0, &h0, &p0, &l1, &h1, &p1, &fs, &fd, &ps, &pd, &cnt, &radix, &scan);
+    SYM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(DevCounters), s));
+    if (nnz > 0) {
+        switch (order) {
+            case 2: st = launch_create_kernels<2>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, s); break;
+            case 3: st = launch_create_kernels<3>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, s); break;
+            case 4: st = launch_create_kernels<4>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, s); break;
+            default: st = launch_create_kernels<5>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, s); break;
+        }
+        if (st != SYM_OK) return st;
+    }
+    DevCounters h;
+    SYM_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SYM_CUDA(cudaStreamSynchronize(s));
+    if (h.range_bad) return SYM_E_RANGE;
+    if (dup == SYM_DUP_ERROR && h.dup_seen) return SYM_E_DUPLICATE;
+    if (dup == SYM_DUP_KEEP_EQUAL && h.dup_mismatch) return SYM_E_DUPLICATE;
+
+    sym_tensor_s* t = new (std::nothrow) sym_tensor_s();
+    if (!t) return SYM_E_NOMEM;
+    t->order = order;
+    t->bits = bits;
+    t->kw = kw;
+    t->n = n;
+    t->nnz = (int64_t)h.nnz_kept;
+    t->nnz_strict = (int64_t)h.nnz_strict;
+    t->klo = out_lo;
+    t->khi = out_hi;
+    t->val = out_val;
+    t->chunk = 0;
+    t->device = current_device();
+    sym_tensor_info_t& I = t->info;
+    memset(&I, 0, sizeof(I));
+    I.order = order;
+    I.key_bits = bits;
+    I.n = n;
+    I.nnz = t->nnz;
+    I.nnz_strict = t->nnz_strict;
+    I.nnz_diag = t->nnz - t->nnz_strict;
+    I.duplicates_dropped = (int64_t)h.dup_seen;
+    for (int p = 0; p < 16; ++p) I.counts_by_pattern[p] = (int64_t)h.by_pattern[p];
+    I.expanded_nnz = (int64_t)h.expanded;
+    I.root_fibers = (int64_t)h.root_fibers;
+    I.l2_fibers = (int64_t)h.l2_fibers;
+    I.normsq = h.normsq;
+    I.arena_used = A.used;
+    *out = t;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_tensor_info(sym_tensor X, sym_tensor_info_t* out) {
+    if (!X || !out) return SYM_E_INVALID;
+    *out = X->info;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_tensor_export(sym_tensor X, int32_t* cidx, int64_t ld_out, float* cval,
+                                        sym_stream_t stream) {
+    if (!X || (X->nnz > 0 && (!cidx || !cval)) || ld_out < X->nnz) return SYM_E_INVALID;
+    if (X->nnz == 0) return SYM_OK;
+    cudaStream_t s = as_stream(stream);
+    unsigned g = (unsigned)((X->nnz + 255) / 256);
+#define SYM_EXPORT_CASE(N)                                                                                    \
+    if (X->kw == 1)                                                                                           \
+        k_export<N, 1><<<g, 256, 0, s>>>(X->klo, X->khi, X->val, X->nnz, X->bits, cidx, ld_out, cval);      \
+    else                                                                                                      \
+        k_export<N, 2><<<g, 256, 0, s>>>(X->klo, X->khi, X->val, X->nnz, X->bits, cidx, ld_out, cval);
+    switch (X->order) {
+        case 2: SYM_EXPORT_CASE(2) break;
+        case 3: SYM_EXPORT_CASE(3) break;
+        case 4: SYM_EXPORT_CASE(4) break;
+        default: SYM_EXPORT_CASE(5) break;
+    }
+#undef SYM_EXPORT_CASE
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_tensor_destroy(sym_tensor X) {
+    delete X;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_gen_coords(int order, int64_t n, int64_t count, uint64_t seed, int32_t* idx,
+                                     int64_t ld_idx, float* val, sym_stream_t stream) {
+    if (order < 1 || order > 5 || n < 1 || n > 0x7fffffffLL || count < 0 || ld_idx < count) return SYM_E_INVALID;
+    if (count == 0) return SYM_OK;
+    if (!idx || !val) return SYM_E_INVALID;
+    k_gen_coords<<<(unsigned)((count + 255) / 256), 256, 0, as_stream(stream)>>>(order, n, count, seed, idx, ld_idx,
+                                                                                 val);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}

@@ -1,0 +1,156 @@
+"""Symmetric MTTKRP on the GPU vs the FP64 oracle (componentwise error gate)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_helpers import TOL_BF16, TOL_F32, dev, factor, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def run_case(sg, T, rank, bf16=False, chunk=0, seed=1):
+    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
+    if chunk:
+        X.set_chunk(chunk)
+    Bt, B32, Bused = factor(T.n, rank, seed, bf16)
+    M = host(X.mttkrp(Bt))
+    cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
+    ref, ref_abs = oracle.mttkrp_enum(T.order, T.n, cidx, cval, B32.astype(np.float64))
+    e32 = oracle.componentwise_error(M, ref, ref_abs)
+    if bf16:
+        refb, refb_abs = oracle.mttkrp_enum(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+        eb = oracle.componentwise_error(M, refb, refb_abs)
+        return e32, eb
+    return e32, None
+
+
+@pytest.mark.parametrize("order,n,nnz", [(2, 300, 3000), (3, 500, 20000), (4, 60, 12000), (5, 25, 8000)])
+@pytest.mark.parametrize("rank", [4, 8, 16, 32, 64, 128])
+def test_mttkrp_f32(order, n, nnz, rank):
+    sg = need_gpu()
+    T = synth.tensor_uniform(order, n, nnz, 10 + order)
+    e, _ = run_case(sg, T, rank)
+    assert e <= TOL_F32, e
+
+
+@pytest.mark.parametrize("order,n,nnz,rank", [(3, 500, 20000, 64), (4, 60, 12000, 32), (5, 25, 8000, 16),
+                                              (3, 400, 5000, 8)])
+def test_mttkrp_bf16(order, n, nnz, rank):
+    sg = need_gpu()
+    T = synth.tensor_uniform(order, n, nnz, 20 + order)
+    e32, eb = run_case(sg, T, rank, bf16=True)
+    assert e32 <= TOL_BF16, e32
+    assert eb <= TOL_F32, eb
+
+
+@pytest.mark.parametrize("chunk", [-1, 32, 64, 1024])
+def test_mttkrp_chunk_shapes(chunk):
+    """Factorised kernel at several chunk sizes, and the unfactorised per-entry form (-1)."""
+    sg = need_gpu()
+    T = synth.tensor3_zipf(2000, 60000, 4)
+    e, _ = run_case(sg, T, 32, chunk=chunk)
+    assert e <= TOL_F32, e
+
+
+def test_mttkrp_zipf_hot_rows():
+    sg = need_gpu()
+    T = synth.tensor3_zipf(5000, 200_000, 8)
+    e, _ = run_case(sg, T, 64)
+    assert e <= TOL_F32, e
+
+
+@pytest.mark.parametrize("order", [3, 4, 5])
+def test_mttkrp_all_diagonal(order):
+    """Every entry has a repeated index: only the diagonal stream runs."""
+    sg = need_gpu()
+    T = synth.tensor_small_all_patterns(order, 9, 2, density=1.0)
+    keep = np.array([len(set(T.idx[:, e])) < order for e in range(T.nnz)])
+    T2 = synth.SymCOO(order, 9, np.ascontiguousarray(T.idx[:, keep]), T.val[keep])
+    e, _ = run_case(sg, T2, 16)
+    assert e <= TOL_F32, e
+
+
+def test_mttkrp_single_entry_and_long_fiber():
+    sg = need_gpu()
+    # one strict entry
+    T = synth.SymCOO(3, 10, np.array([[7], [2], [5]], np.int32), np.array([1.25], np.float32))
+    e, _ = run_case(sg, T, 8)
+    assert e <= TOL_F32
+    # one root fiber of 50k entries: (0, j, k) for many (j, k)
+    j, k = np.triu_indices(320, 1)
+    j, k = j[:50_000] + 1, k[:50_000] + 1
+    idx = np.stack([np.zeros_like(j), j, k]).astype(np.int32)
+    val = synth.Stream(3).normal(idx.shape[1]).astype(np.float32)
+    e, _ = run_case(sg, synth.SymCOO(3, 330, idx, val), 16)
+    assert e <= TOL_F32, e
+
+
+def test_mttkrp_strided_output_and_factor():
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    T = synth.tensor_uniform(4, 40, 4000, 31)
+    X = sg.SymTensor(dev(T.idx), dev(T.val), 40)
+    B = synth.factor_normal(40, 16, 31)
+    Bp = torch.zeros((40, 24), device="cuda")
+    Bp[:, :16] = dev(B)
+    Mp = torch.full((40, 20), 7.0, device="cuda")
+    X.mttkrp(Bp[:, :16], M=Mp[:, :16])
+    cidx, cval = oracle.canonicalize(4, 40, T.idx, T.val)
+    ref, ra = oracle.mttkrp_enum(4, 40, cidx, cval, B.astype(np.float64))
+    assert oracle.componentwise_error(host(Mp[:, :16]), ref, ra) <= TOL_F32
+    assert float((Mp[:, 16:] - 7.0).abs().max()) == 0.0   # padding untouched
+
+
+def test_mttkrp_rejects_bad_arguments():
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    T = synth.tensor_uniform(3, 20, 100, 1)
+    X = sg.SymTensor(dev(T.idx), dev(T.val), 20)
+    for r in (3, 6, 132):
+        with pytest.raises(sg.SymError) as e:
+            X.mttkrp(torch.zeros((20, r), device="cuda"))
+        assert e.value.code == -1
+
+
+def test_relabel_invariance_on_gpu():
+    sg = need_gpu()
+    T = synth.tensor_uniform(4, 50, 6000, 12)
+    pi = np.argsort(synth.Stream(1).uniform(50)).astype(np.int32)
+    B = synth.factor_normal(50, 16, 12)
+    X1 = sg.SymTensor(dev(T.idx), dev(T.val), 50)
+    X2 = sg.SymTensor(dev(pi[T.idx]), dev(T.val), 50)
+    B2 = np.empty_like(B)
+    B2[pi] = B
+    M1, M2 = host(X1.mttkrp(dev(B))), host(X2.mttkrp(dev(B2)))
+    cidx, cval = oracle.canonicalize(4, 50, T.idx, T.val)
+    _, ra = oracle.mttkrp_enum(4, 50, cidx, cval, B.astype(np.float64))
+    assert oracle.componentwise_error(M2[pi], M1, 2 * ra + 1e-300) <= TOL_F32
+
+
+@pytest.mark.parametrize("order,rank", [(3, 16), (4, 8), (5, 8)])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_cpfit_residual(order, rank, bf16):
+    sg = need_gpu()
+    T = synth.tensor_uniform(order, 30, 3000, 40 + order)
+    X = sg.SymTensor(dev(T.idx), dev(T.val), 30)
+    Bt, B32, Bused = factor(30, rank, 3, bf16)
+    M, res = X.mttkrp(Bt, residual=True)
+    cidx, cval = oracle.canonicalize(order, 30, T.idx, T.val)
+    want, ab, _ = oracle.cpfit(order, 30, cidx, cval, Bused.astype(np.float64))
+    err = abs(float(res.item()) - want) / ab
+    assert err <= TOL_F32, err
+
+
+def test_cpfit_good_fit_cancellation():
+    """A tensor that is exactly sum_r b_r^(x)3 (dense, tiny): the residual must be ~0."""
+    sg = need_gpu()
+    import itertools
+    n, R = 8, 4
+    B = synth.factor_normal(n, R, 9)
+    rows = np.array(list(itertools.combinations_with_replacement(range(n), 3)), np.int32)
+    vals = np.array([sum(np.prod(B[list(t), r].astype(np.float64)) for r in range(R)) for t in rows], np.float32)
+    X = sg.SymTensor(dev(rows.T.copy()), dev(vals), n)
+    M, res = X.mttkrp(dev(B), residual=True)
+    want, ab, _ = oracle.cpfit(3, n, rows.T.copy(), vals, B.astype(np.float64))
+    assert abs(float(res.item()) - want) <= TOL_F32 * ab
