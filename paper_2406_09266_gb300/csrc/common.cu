@@ -88,6 +88,8 @@ void drain_locked() {
 
 ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), stream(s), start(nullptr) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     cudaEvent_t e = take_event();
     if (e && cudaEventRecord(e, s) == cudaSuccess) start = e;

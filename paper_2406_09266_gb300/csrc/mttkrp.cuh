@@ -254,3 +254,15 @@ sym_status launch_mttkrp_order(const sym_tensor_s* X, const void* B, bool bf16, 
                                int64_t ldm, int chunk, bool factorised, cudaStream_t s);
 
 }  // namespace symgpu
+
+namespace symgpu {
+// Entry points shared with the serving runtime (defined in mttkrp.cu).
+sym_status mttkrp_core(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, float* M, int64_t ldm,
+                       int chunk, bool factorised, cudaStream_t s);
+sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, const float* M,
+                           int64_t ldm, double* residual, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t residual_ws_bytes(int R);
+sym_status validate_mttkrp_args(const sym_tensor_s* X, const void* B, sym_dtype bdt, int rank, int64_t ldb,
+                                const float* M, int64_t ldm);
+int default_chunk(const sym_tensor_s* X);
+}  // namespace symgpu

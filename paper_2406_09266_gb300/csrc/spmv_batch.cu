@@ -1,17 +1,456 @@
-// Batched SSYMV/SYPRD (placeholder entry points; implemented next).
+// Batched SSYMV + SYPRD: thousands of independent symmetric matrices (upper
+// CSR each, concatenated) in one persistent launch.
+//
+// Work unit = a tile of consecutive rows of one instance (tiles never straddle
+// instances).  Persistent CTAs take tiles from a device counter in list order,
+// so CTAs that run at the same time work on neighbouring tiles of the same few
+// instances and those instances' x and y stay in L2.  Inside a tile, groups of
+// L lanes take rows; each group keeps the row partial of y[i] in registers
+// (workspace transformation, Sec. 4.2.8) and reduces the mirrored updates
+// y[j] += a x_i (Sec. 3.1, reusing each canonical read) into global memory.
+// SYPRD (Sec. 3.2.2, off-diagonal terms weighted 2) is formed per tile in FP32,
+// written as one FP64 partial per tile, and summed per instance in FP64 in a
+// fixed order (deterministic).
+//
+// The launch sequence (reset counter, zero y, persistent kernel, FP64
+// finaliser) can be captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 
-extern "C" size_t sym_spmv_batch_plan_bytes(const sym_csr_batch*, const int64_t*, const sym_tile_cfg*) { return 0; }
-extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch*, const int64_t*, const sym_tile_cfg*, void*,
-                                                 size_t, sym_stream_t, sym_batch_plan* out) {
-    if (out) *out = nullptr;
-    return SYM_E_UNSUPPORTED;
+struct Tile {
+    int64_t row0;      // first global row
+    int32_t rows;      // rows in the tile
+    int32_t inst;      // instance id
+};
+
+struct sym_batch_plan_s {
+    sym_csr_batch A;
+    sym_tile_cfg cfg;
+    int64_t ntiles;
+    Tile* tiles;              // [device] tile list
+    int64_t* tile_first;      // [device] first tile of each instance (count + 1)
+    double* tile_partials;    // [device] FP64 SYPRD partial per tile
+    unsigned long long* counter;  // [device] next tile
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int device;
+};
+
+namespace symgpu {
+
+namespace {
+
+template <int L>
+__device__ __forceinline__ float gsum(float v) {
+#pragma unroll
+    for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
-extern "C" sym_status sym_spmv_batch_run(sym_batch_plan, const float*, float*, double*, sym_stream_t) { return SYM_E_UNSUPPORTED; }
-extern "C" sym_status sym_spmv_batch_capture(sym_batch_plan, const float*, float*, double*, sym_stream_t) { return SYM_E_UNSUPPORTED; }
-extern "C" sym_status sym_spmv_batch_graph_launch(sym_batch_plan, sym_stream_t) { return SYM_E_UNSUPPORTED; }
-extern "C" sym_status sym_spmv_batch_plan_destroy(sym_batch_plan) { return SYM_OK; }
-extern "C" sym_status sym_autotune_spmv_batch(const sym_csr_batch*, const int64_t*, const float*, float*, double*,
-                                              void*, size_t, const char*, sym_stream_t, sym_tile_cfg*, float*) {
-    return SYM_E_UNSUPPORTED;
+
+template <int L, bool SYPRD>
+__global__ void k_ssymv_batch(const Tile* __restrict__ tiles, int64_t ntiles, const int64_t* __restrict__ row_off,
+                              const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const float* __restrict__ val, const float* __restrict__ x, float* __restrict__ y,
+                              double* __restrict__ tile_partials, unsigned long long* __restrict__ counter) {
+    __shared__ int64_t s_tile;
+    __shared__ float s_red[32];
+    const int lane = threadIdx.x & 31;
+    const int s = lane % L;
+    const int groups = blockDim.x / L;
+    const int g = threadIdx.x / L;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t t = s_tile;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const Tile tile = tiles[t];
+        const int64_t base = row_off[tile.inst];   // global row of local index 0
+        float syp = 0.f;
+        // uniform trip count across the block, so the group shuffles see full warps
+        for (int r0 = 0; r0 < tile.rows; r0 += groups) {
+            const int r = r0 + g;
+            const bool act = r < tile.rows;
+            const int64_t i = tile.row0 + (act ? r : 0);  // global row
+            float rowsum = 0.f, rs = 0.f, xi = 0.f;
+            if (act) {
+                const int32_t li = (int32_t)(i - base);
+                xi = x[i];
+                const int64_t p1 = rowptr[i + 1];
+                for (int64_t p = rowptr[i] + s; p < p1; p += L) {
+                    const int32_t j = col[p];
+                    const float a = val[p];
+                    const float tt = a * x[base + j];
+                    rowsum += tt;
+                    if (j != li) {
+                        atomicAdd(&y[base + j], a * xi);
+                        if (SYPRD) rs += 2.f * tt;
+                    } else if (SYPRD) {
+                        rs += tt;
+                    }
+                }
+            }
+            rowsum = gsum<L>(rowsum);
+            if (act && s == 0 && rowsum != 0.f) atomicAdd(&y[i], rowsum);
+            if (SYPRD) syp += rs * xi;
+        }
+        if (SYPRD) {
+            float w = syp;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (lane == 0) s_red[threadIdx.x >> 5] = w;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float tot = 0.f;
+                for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += s_red[k];
+                tile_partials[t] = (double)tot;
+            }
+        }
+    }
+}
+
+// syprd[b] = sum of instance b's tile partials, FP64, fixed order.
+__global__ void k_batch_syprd(const double* __restrict__ tile_partials, const int64_t* __restrict__ tile_first,
+                              int64_t count, double* __restrict__ syprd) {
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= count) return;
+    double acc = 0.0;
+    for (int64_t t = tile_first[b] + lane; t < tile_first[b + 1]; t += 32) acc += tile_partials[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) syprd[b] = acc;
+}
+
+int64_t count_tiles(const int64_t* host_row_off, int64_t count, int rows_per_tile) {
+    int64_t nt = 0;
+    for (int64_t b = 0; b < count; ++b) {
+        const int64_t n = host_row_off[b + 1] - host_row_off[b];
+        nt += (n + rows_per_tile - 1) / rows_per_tile;
+    }
+    return nt;
+}
+
+template <typename C>
+void layout_plan(C& c, int64_t ntiles, int64_t count, Tile** tiles, int64_t** first, double** parts,
+                 unsigned long long** counter) {
+    *tiles = c.template take<Tile>((size_t)std::max<int64_t>(ntiles, 1));
+    *first = c.template take<int64_t>((size_t)count + 1);
+    *parts = c.template take<double>((size_t)std::max<int64_t>(ntiles, 1));
+    *counter = c.template take<unsigned long long>(1);
+}
+
+struct NullCarver {
+    Sizer s;
+    template <typename T>
+    T* take(size_t n) {
+        s.take<T>(n);
+        return nullptr;
+    }
+};
+
+bool cfg_ok(const sym_tile_cfg* c) {
+    if (!c) return false;
+    const int L = c->lanes_per_row;
+    if (L < 1 || L > 32 || (L & (L - 1))) return false;
+    if (c->threads_per_cta < 64 || c->threads_per_cta > 1024 || c->threads_per_cta % 32) return false;
+    if (c->rows_per_tile < 1 || c->rows_per_tile > (1 << 20)) return false;
+    if (c->ctas_per_sm < 1 || c->ctas_per_sm > 32) return false;
+    return true;
+}
+
+sym_status batch_enqueue(sym_batch_plan_s* P, const float* x, float* y, double* syprd, cudaStream_t s) {
+    SYM_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(unsigned long long), s));
+    SYM_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)P->A.total_rows, s));
+    if (P->ntiles == 0) {
+        if (syprd && P->A.count > 0) SYM_CUDA(cudaMemsetAsync(syprd, 0, sizeof(double) * P->A.count, s));
+        return SYM_OK;
+    }
+    const int threads = P->cfg.threads_per_cta;
+    int dev = 0;
+    SYM_CUDA(cudaGetDevice(&dev));
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)sm_count() * P->cfg.ctas_per_sm, P->ntiles);
+    {
+        SYM_PROF("ssymv_batch", s);
+#define SYM_BATCH_L(LL)                                                                                         \
+    case LL:                                                                                                    \
+        if (syprd)                                                                                              \
+            k_ssymv_batch<LL, true><<<grid, threads, 0, s>>>(P->tiles, P->ntiles, P->A.row_off, P->A.rowptr,   \
+                                                             P->A.col, P->A.val, x, y, P->tile_partials,       \
+                                                             P->counter);                                      \
+        else                                                                                                    \
+            k_ssymv_batch<LL, false><<<grid, threads, 0, s>>>(P->tiles, P->ntiles, P->A.row_off, P->A.rowptr,  \
+                                                              P->A.col, P->A.val, x, y, P->tile_partials,      \
+                                                              P->counter);                                     \
+        break;
+        switch (P->cfg.lanes_per_row) {
+            SYM_BATCH_L(1)
+            SYM_BATCH_L(2)
+            SYM_BATCH_L(4)
+            SYM_BATCH_L(8)
+            SYM_BATCH_L(16)
+            SYM_BATCH_L(32)
+            default: return SYM_E_INVALID;
+        }
+#undef SYM_BATCH_L
+        SYM_CHECK_LAUNCH();
+    }
+    if (syprd) {
+        const unsigned g2 = (unsigned)((P->A.count + 7) / 8);
+        k_batch_syprd<<<g2, 256, 0, s>>>(P->tile_partials, P->tile_first, P->A.count, syprd);
+        SYM_CHECK_LAUNCH();
+    }
+    return SYM_OK;
+}
+
+sym_status validate_batch(const sym_csr_batch* A, const int64_t* host_row_off) {
+    if (!A || !host_row_off || A->count < 0 || A->total_rows < 0 || A->total_nnz < 0) return SYM_E_INVALID;
+    if (A->count > 0 && (!A->row_off || !A->rowptr)) return SYM_E_INVALID;
+    if (A->total_nnz > 0 && (!A->col || !A->val)) return SYM_E_INVALID;
+    if (host_row_off[0] != 0 || host_row_off[A->count] != A->total_rows) return SYM_E_INVALID;
+    for (int64_t b = 0; b < A->count; ++b)
+        if (host_row_off[b + 1] < host_row_off[b] || host_row_off[b + 1] - host_row_off[b] > 0x7fffffffLL)
+            return SYM_E_INVALID;
+    return SYM_OK;
+}
+
+}  // namespace
+
+}  // namespace symgpu
+
+using namespace symgpu;
+
+extern "C" size_t sym_spmv_batch_plan_bytes(const sym_csr_batch* A, const int64_t* host_row_off,
+                                            const sym_tile_cfg* cfg) {
+    if (validate_batch(A, host_row_off) != SYM_OK || !cfg_ok(cfg)) return 0;
+    NullCarver c;
+    Tile* t;
+    int64_t* f;
+    double* p;
+    unsigned long long* k;
+    layout_plan(c, count_tiles(host_row_off, A->count, cfg->rows_per_tile), A->count, &t, &f, &p, &k);
+    return c.s.used;
+}
+
+extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const int64_t* host_row_off,
+                                                 const sym_tile_cfg* cfg, void* arena, size_t arena_bytes,
+                                                 sym_stream_t stream, sym_batch_plan* out) {
+    if (!out) return SYM_E_INVALID;
+    *out = nullptr;
+    sym_status st = validate_batch(A, host_row_off);
+    if (st != SYM_OK) return st;
+    if (!cfg_ok(cfg) || !arena || !aligned(arena, 256)) return SYM_E_INVALID;
+    if (arena_bytes < sym_spmv_batch_plan_bytes(A, host_row_off, cfg)) return SYM_E_NOMEM;
+    const int64_t ntiles = count_tiles(host_row_off, A->count, cfg->rows_per_tile);
+    std::vector<Tile> tiles;
+    std::vector<int64_t> first((size_t)A->count + 1);
+    try {
+        tiles.reserve((size_t)ntiles);
+    } catch (...) {
+        return SYM_E_NOMEM;
+    }
+    for (int64_t b = 0; b < A->count; ++b) {
+        first[(size_t)b] = (int64_t)tiles.size();
+        for (int64_t r = host_row_off[b]; r < host_row_off[b + 1]; r += cfg->rows_per_tile)
+            tiles.push_back(Tile{r, (int32_t)std::min<int64_t>(cfg->rows_per_tile, host_row_off[b + 1] - r),
+                                 (int32_t)b});
+    }
+    first[(size_t)A->count] = (int64_t)tiles.size();
+    sym_batch_plan_s* P = new (std::nothrow) sym_batch_plan_s();
+    if (!P) return SYM_E_NOMEM;
+    P->A = *A;
+    P->cfg = *cfg;
+    P->ntiles = ntiles;
+    P->graph = nullptr;
+    P->exec = nullptr;
+    P->device = current_device();
+    Carver c(arena, arena_bytes);
+    layout_plan(c, ntiles, A->count, &P->tiles, &P->tile_first, &P->tile_partials, &P->counter);
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaSuccess;
+    if (ntiles > 0) e = cudaMemcpyAsync(P->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->tile_first, first.data(), sizeof(int64_t) * first.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_status(e);
+    }
+    *out = P;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_spmv_batch_run(sym_batch_plan P, const float* x, float* y, double* syprd,
+                                         sym_stream_t stream) {
+    if (!P || (P->A.total_rows > 0 && (!x || !y))) return SYM_E_INVALID;
+    return batch_enqueue(P, x, y, syprd, as_stream(stream));
+}
+
+extern "C" sym_status sym_spmv_batch_capture(sym_batch_plan P, const float* x, float* y, double* syprd,
+                                             sym_stream_t stream) {
+    if (!P || (P->A.total_rows > 0 && (!x || !y))) return SYM_E_INVALID;
+    cudaStream_t s = as_stream(stream);
+    if (P->exec) {
+        cudaGraphExecDestroy(P->exec);
+        P->exec = nullptr;
+    }
+    if (P->graph) {
+        cudaGraphDestroy(P->graph);
+        P->graph = nullptr;
+    }
+    // capture on a private stream so the caller's stream may be the legacy default
+    cudaStream_t cs;
+    SYM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    sym_status st = SYM_OK;
+    if (e == cudaSuccess) {
+        st = batch_enqueue(P, x, y, syprd, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (st == SYM_OK && e2 == cudaSuccess) {
+            P->graph = g;
+            e = cudaGraphInstantiate(&P->exec, g, 0);
+        } else {
+            if (g) cudaGraphDestroy(g);
+            if (st == SYM_OK) e = e2;
+        }
+    }
+    cudaStreamDestroy(cs);
+    (void)s;
+    if (st != SYM_OK) return st;
+    return cuda_status(e);
+}
+
+extern "C" sym_status sym_spmv_batch_graph_launch(sym_batch_plan P, sym_stream_t stream) {
+    if (!P || !P->exec) return SYM_E_INVALID;
+    {
+        SYM_PROF("ssymv_batch_graph", as_stream(stream));
+        SYM_CUDA(cudaGraphLaunch(P->exec, as_stream(stream)));
+    }
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_spmv_batch_plan_destroy(sym_batch_plan P) {
+    if (!P) return SYM_OK;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    delete P;
+    return SYM_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+namespace {
+
+std::string cache_key(const sym_csr_batch* A) {
+    cudaDeviceProp prop;
+    int dev = current_device();
+    std::string name = "unknown";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (auto& ch : name)
+        if (ch == ' ') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "ssymv_batch|%s|%lld|%lld|%lld", name.c_str(), (long long)A->count,
+             (long long)A->total_rows, (long long)A->total_nnz);
+    return buf;
+}
+
+bool cache_lookup(const char* path, const std::string& key, sym_tile_cfg* cfg, float* ms) {
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        char k[300];
+        sym_tile_cfg c;
+        float t;
+        if (sscanf(line, "%299s %d %d %d %d %f", k, &c.rows_per_tile, &c.lanes_per_row, &c.threads_per_cta,
+                   &c.ctas_per_sm, &t) == 6 &&
+            key == k && cfg_ok(&c)) {
+            *cfg = c;
+            *ms = t;
+            found = true;  // the last matching line wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const char* path, const std::string& key, const sym_tile_cfg& c, float ms) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), c.rows_per_tile, c.lanes_per_row, c.threads_per_cta,
+            c.ctas_per_sm, ms);
+    fclose(f);
+}
+
+}  // namespace
+
+extern "C" sym_status sym_autotune_spmv_batch(const sym_csr_batch* A, const int64_t* host_row_off, const float* x,
+                                              float* y, double* syprd, void* arena, size_t arena_bytes,
+                                              const char* cache_path, sym_stream_t stream, sym_tile_cfg* best,
+                                              float* best_ms) {
+    sym_status st = validate_batch(A, host_row_off);
+    if (st != SYM_OK || !best) return SYM_E_INVALID;
+    const std::string key = cache_key(A);
+    float cached_ms = 0.f;
+    if (cache_lookup(cache_path, key, best, &cached_ms)) {
+        if (best_ms) *best_ms = cached_ms;
+        return SYM_OK;
+    }
+    cudaStream_t s = as_stream(stream);
+    const int lanes[] = {4, 8, 16, 32};
+    const int rows[] = {16, 64, 256};
+    const int threads[] = {256, 512};
+    const int ctas[] = {2, 4, 8};
+    cudaEvent_t e0, e1;
+    SYM_CUDA(cudaEventCreate(&e0));
+    SYM_CUDA(cudaEventCreate(&e1));
+    float best_t = 1e30f;
+    sym_tile_cfg bc{64, 16, 256, 4};
+    bool any = false;
+    for (int L : lanes)
+        for (int R : rows)
+            for (int T : threads)
+                for (int K : ctas) {
+                    if (T * K > 2048) continue;  // at most 2048 resident threads per SM
+                    sym_tile_cfg c{R, L, T, K};
+                    if (sym_spmv_batch_plan_bytes(A, host_row_off, &c) > arena_bytes) continue;
+                    sym_batch_plan P = nullptr;
+                    if (sym_spmv_batch_plan_create(A, host_row_off, &c, arena, arena_bytes, stream, &P) != SYM_OK)
+                        continue;
+                    float tot = 0.f;
+                    bool ok = batch_enqueue(P, x, y, syprd, s) == SYM_OK;  // warm-up
+                    for (int rep = 0; ok && rep < 3; ++rep) {
+                        cudaEventRecord(e0, s);
+                        ok = batch_enqueue(P, x, y, syprd, s) == SYM_OK;
+                        cudaEventRecord(e1, s);
+                        float t = 0.f;
+                        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+                            ok = false;
+                        tot += t;
+                    }
+                    sym_spmv_batch_plan_destroy(P);
+                    if (ok && tot / 3 < best_t) {
+                        best_t = tot / 3;
+                        bc = c;
+                        any = true;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!any) return SYM_E_NOMEM;
+    *best = bc;
+    if (best_ms) *best_ms = best_t;
+    cache_store(cache_path, key, bc, best_t);
+    return SYM_OK;
 }
