@@ -295,6 +295,13 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": per_launch_ms,
             "share_of_step": strict_ms / max(sum(v[1] for v in prof.values()), 1e-12)}
 
+    if args.kernel_only:
+        if D.rank == 0:
+            print(json.dumps({"metric": "canonical_nnz_per_s", "value": value, "ms_per_step": ms,
+                              "mode": "kernel-only (profiling)", "per_kernel": prof}))
+        D.close()
+        return
+
     extras = {"per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
               "canonicalise_ms": create_ms, "tensor": {k: info[k] for k in (
                   "nnz", "nnz_strict", "nnz_diag", "expanded_nnz", "root_fibers", "l2_fibers")}}
@@ -434,6 +441,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rows", default="all", choices=["main", "all"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="profiling mode: setup, warm-up and the timed steps only (no e2e or extra rows)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -146,8 +146,9 @@ sym_status sym_spmv_full(const sym_csr_full* A, const float* x, float* y, sym_st
 /* ===================================================================== */
 
 /* Instance b owns global rows [row_off[b], row_off[b+1]) of x and y; rowptr is
- * global (nnz offsets, int64, total_rows+1 entries); col holds columns LOCAL to
- * the instance.  All arrays [device]. */
+ * global (nnz offsets, int64, total_rows+1 entries); col holds GLOBAL column
+ * indices, each inside its own instance's row range and >= its row.  All
+ * arrays [device]. */
 typedef struct {
     int64_t count;
     int64_t total_rows;
@@ -248,6 +249,13 @@ sym_status sym_tensor_export(sym_tensor X, int32_t* cidx, int64_t ld_out, float*
 
 sym_status sym_tensor_destroy(sym_tensor X);
 
+/* Order-2 tensors: the canonical entries as an upper-triangle CSR (row i holds
+ * columns j >= i, ascending).  rowptr: n+1 int64, col: nnz int32, val: nnz
+ * floats, all [device]; ws >= sym_tensor_upper_csr_ws_bytes(X). */
+size_t sym_tensor_upper_csr_ws_bytes(sym_tensor X);
+sym_status sym_tensor_upper_csr(sym_tensor X, int64_t* rowptr, int32_t* col, float* val, void* ws, size_t ws_bytes,
+                                sym_stream_t stream);
+
 /* Counter-based SplitMix64 coordinate generator for large on-device pools:
  * draw q of entry e is word e*order+q of the stream with `seed`; index =
  * high 32 bits * n >> 32; value = the entry's multiset hash mapped to a 24-bit
@@ -255,6 +263,16 @@ sym_status sym_tensor_destroy(sym_tensor X);
  * duplicate policy merges repeats).  idx: order rows of ld_idx int32 [device]. */
 sym_status sym_gen_coords(int order, int64_t n, int64_t count, uint64_t seed, int32_t* idx, int64_t ld_idx,
                           float* val, sym_stream_t stream);
+
+/* Counter-based generator of batched symmetric matrices: instance b (global
+ * rows [row_off[b], row_off[b+1]), n_b rows) receives draws
+ * [draw_off[b], draw_off[b+1]); draw d is word d of the SplitMix64 stream with
+ * `seed`, u = (word >> 11) * 2^-53, slot s = floor(u * n_b(n_b+1)/2) of the
+ * row-major upper triangle, mapped to (i, j), i <= j, written as GLOBAL indices
+ * idx[0][d], idx[1][d] with value = the pair's multiset hash in [-1, 1)
+ * (repeats carry equal values).  row_off, draw_off: count+1 int64 [device]. */
+sym_status sym_gen_batch_coords(int64_t count, const int64_t* row_off, const int64_t* draw_off, int64_t total_draws,
+                                uint64_t seed, int32_t* idx, int64_t ld_idx, float* val, sym_stream_t stream);
 
 /* ===================================================================== */
 /* Symmetric MTTKRP (Sec. 4.3, Sec. 5.2.6):                                */

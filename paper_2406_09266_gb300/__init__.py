@@ -128,6 +128,10 @@ _SIGS = {
     "sym_tensor_info": ([C.c_void_p, C.c_void_p], C.c_int),
     "sym_tensor_export": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "sym_tensor_destroy": ([C.c_void_p], C.c_int),
+    "sym_tensor_upper_csr_ws_bytes": ([C.c_void_p], C.c_size_t),
+    "sym_tensor_upper_csr": ([C.c_void_p] * 5 + [C.c_size_t, C.c_void_p], C.c_int),
+    "sym_gen_batch_coords": ([C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_int64,
+                              C.c_void_p, C.c_void_p], C.c_int),
     "sym_gen_coords": ([C.c_int, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p,
                         C.c_void_p], C.c_int),
     "sym_mttkrp_workspace_bytes": ([C.c_void_p, C.c_int, C.c_int, C.c_int], C.c_size_t),
@@ -366,6 +370,19 @@ class SymTensor:
                                _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream)), "sym_mttkrp")
         return (M, res) if residual else M
 
+    def upper_csr(self, stream=None):
+        """Order-2 tensors: (rowptr int64, col int32, val) of the canonical entries as an upper CSR."""
+        if self.order != 2:
+            raise ValueError("upper CSR needs an order-2 tensor")
+        nnz = self.nnz
+        rowptr = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.device)
+        val = torch.empty(max(nnz, 1), dtype=torch.float32, device=self.device)
+        ws = _scratch(lib().sym_tensor_upper_csr_ws_bytes(self.handle), self.device)
+        check(lib().sym_tensor_upper_csr(self.handle, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(ws), ws.numel(),
+                                         _stream(stream)), "sym_tensor_upper_csr")
+        return rowptr, col[:nnz], val[:nnz]
+
     def expanded(self, stream=None) -> "Expanded":
         return Expanded(self, stream)
 
@@ -388,6 +405,39 @@ def gen_coords(order, n, count, seed, device="cuda", stream=None):
     check(lib().sym_gen_coords(order, n, count, C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _ptr(idx), max(count, 1),
                                _ptr(val), _stream(stream)), "sym_gen_coords")
     return idx[:, :count], val[:count]
+
+
+def gen_batch_coords(row_off: torch.Tensor, draw_off: torch.Tensor, seed: int, stream=None):
+    """On-device draws for batched symmetric matrices (same definition as synth.batch_coords)."""
+    total = int(draw_off[-1].item())
+    idx = torch.empty((2, max(total, 1)), dtype=torch.int32, device=row_off.device)
+    val = torch.empty(max(total, 1), dtype=torch.float32, device=row_off.device)
+    check(lib().sym_gen_batch_coords(row_off.numel() - 1, _ptr(row_off), _ptr(draw_off), total,
+                                     C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _ptr(idx), max(total, 1), _ptr(val),
+                                     _stream(stream)), "sym_gen_batch_coords")
+    return idx[:, :total], val[:total]
+
+
+def make_batch(sizes, per_row: float, seed: int, device="cuda", stream=None):
+    """Builds a BatchCSR on the device: counter-based draws, canonicalisation, upper CSR.
+
+    Instance b has sizes[b] rows and round(per_row * sizes[b]) draws over its
+    upper triangle; repeated positions merge (keep-equal), so rows hold on
+    average slightly fewer than per_row entries.
+    """
+    import numpy as _np
+    sizes = _np.asarray(sizes, dtype=_np.int64)
+    row_off = _np.concatenate([[0], _np.cumsum(sizes)]).astype(_np.int64)
+    draws = _np.rint(per_row * sizes).astype(_np.int64)
+    draw_off = _np.concatenate([[0], _np.cumsum(draws)]).astype(_np.int64)
+    ro = torch.from_numpy(row_off).to(device)
+    do = torch.from_numpy(draw_off).to(device)
+    idx, val = gen_batch_coords(ro, do, seed, stream)
+    X = SymTensor(idx, val, int(row_off[-1]), dup=DUP_KEEP_EQUAL, stream=stream)
+    del idx, val
+    rowptr, col, v = X.upper_csr(stream)
+    X.close()
+    return BatchCSR(ro, rowptr, col.clone(), v.clone())
 
 
 class Expanded:
@@ -430,6 +480,134 @@ class Expanded:
         if getattr(self, "handle", None):
             lib().sym_expanded_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batched SSYMV / SYPRD
+
+class BatchCSR:
+    """Concatenated upper CSRs of many independent symmetric matrices (device arrays)."""
+
+    def __init__(self, row_off, rowptr, col, val):
+        self.row_off, self.rowptr, self.col, self.val = row_off, rowptr, col, val
+        self.host_row_off = row_off.cpu().numpy().astype("int64")
+        self.desc = CsrBatch(len(self.host_row_off) - 1, int(self.host_row_off[-1]), int(col.numel()),
+                             row_off.data_ptr(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+
+    def _hro(self):
+        return self.host_row_off.ctypes.data_as(C.c_void_p)
+
+
+class BatchPlan:
+    """Tile list + FP64 partial buffers for one batch and one tile shape (sym_spmv_batch_plan_*)."""
+
+    def __init__(self, batch: BatchCSR, cfg: TileCfg, stream=None):
+        self.batch, self.cfg = batch, cfg
+        nb = lib().sym_spmv_batch_plan_bytes(C.byref(batch.desc), batch._hro(), C.byref(cfg))
+        if nb == 0:
+            raise SymError(-1, "sym_spmv_batch_plan_bytes")
+        self.arena = _scratch(nb, batch.rowptr.device)
+        h = C.c_void_p()
+        check(lib().sym_spmv_batch_plan_create(C.byref(batch.desc), batch._hro(), C.byref(cfg), _ptr(self.arena),
+                                               self.arena.numel(), _stream(stream), C.byref(h)),
+              "sym_spmv_batch_plan_create")
+        self.handle = h
+
+    def run(self, x, y, syprd=None, stream=None):
+        check(lib().sym_spmv_batch_run(self.handle, _ptr(x), _ptr(y), _ptr(syprd), _stream(stream)),
+              "sym_spmv_batch_run")
+
+    def capture(self, x, y, syprd=None, stream=None):
+        check(lib().sym_spmv_batch_capture(self.handle, _ptr(x), _ptr(y), _ptr(syprd), _stream(stream)),
+              "sym_spmv_batch_capture")
+
+    def launch(self, stream=None):
+        check(lib().sym_spmv_batch_graph_launch(self.handle, _stream(stream)), "sym_spmv_batch_graph_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sym_spmv_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_batch(batch: BatchCSR, x, y, syprd=None, cache_path=None, stream=None):
+    """Times candidate tile shapes on this batch; returns (TileCfg, ms). Cached by device and shape."""
+    worst = TileCfg(1, 32, 256, 1)
+    nb = lib().sym_spmv_batch_plan_bytes(C.byref(batch.desc), batch._hro(), C.byref(TileCfg(16, 32, 256, 1)))
+    arena = _scratch(nb, batch.rowptr.device)
+    best = TileCfg()
+    ms = C.c_float(0)
+    check(lib().sym_autotune_spmv_batch(C.byref(batch.desc), batch._hro(), _ptr(x), _ptr(y), _ptr(syprd),
+                                        _ptr(arena), arena.numel(),
+                                        cache_path.encode() if cache_path else None, _stream(stream),
+                                        C.byref(best), C.byref(ms)), "sym_autotune_spmv_batch")
+    del worst
+    return best, ms.value
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """Continuous-batching MTTKRP server (sym_server_create / sym_batch_submit / sym_batch_poll)."""
+
+    def __init__(self, max_slots=8, max_rank=64, hbm_budget_bytes=120 << 30, small_nnz=1_000_000,
+                 wait_limit_s=30.0, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.cfg = ServerCfg(max_slots, max_rank, hbm_budget_bytes, 0, small_nnz, int(wait_limit_s * 1e9))
+        self.arena = _scratch(lib().sym_server_arena_bytes(C.byref(self.cfg)), dev)
+        h = C.c_void_p()
+        check(lib().sym_server_create(C.byref(self.cfg), _ptr(self.arena), self.arena.numel(), dev.index,
+                                      C.byref(h)), "sym_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, X: SymTensor, B, M, residual=False, tag=0) -> int:
+        req = Request(X.handle.value, B.data_ptr(), _dtype_code(B), B.shape[1], B.stride(0), M.data_ptr(),
+                      M.stride(0), int(residual), tag)
+        t = C.c_uint64(0)
+        check(lib().sym_batch_submit(self.handle, C.byref(req), C.byref(t)), "sym_batch_submit")
+        self._keep[t.value] = (X, B, M)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending; else a dict with status, residual and timestamps."""
+        r = Result()
+        code = lib().sym_batch_poll(self.handle, ticket, C.byref(r))
+        if code == SYM_PENDING:
+            return None
+        check(code, "sym_batch_poll")
+        self._keep.pop(ticket, None)
+        return {"status": r.status, "residual": r.residual, "tag": r.user_tag, "t_submit_ns": r.t_submit_ns,
+                "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns}
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        r = Result()
+        check(lib().sym_batch_wait(self.handle, ticket, int(timeout_s * 1e9), C.byref(r)), "sym_batch_wait")
+        self._keep.pop(ticket, None)
+        return {"status": r.status, "residual": r.residual, "tag": r.user_tag, "t_submit_ns": r.t_submit_ns,
+                "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns}
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(lib().sym_server_stats_get(self.handle, C.byref(st)), "sym_server_stats_get")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            code = lib().sym_server_destroy(self.handle)
+            self.handle = None
+            check(code, "sym_server_destroy")
 
     def __del__(self):
         try:

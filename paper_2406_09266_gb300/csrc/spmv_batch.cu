@@ -5,7 +5,7 @@
 // instances).  Persistent CTAs take tiles from a device counter in list order,
 // so CTAs that run at the same time work on neighbouring tiles of the same few
 // instances and those instances' x and y stay in L2.  Inside a tile, groups of
-// L lanes take rows; each group keeps the row partial of y[i] in registers
+// L lanes take rows (column indices are global); each group keeps the row partial of y[i] in registers
 // (workspace transformation, Sec. 4.2.8) and reduces the mirrored updates
 // y[j] += a x_i (Sec. 3.1, reusing each canonical read) into global memory.
 // SYPRD (Sec. 3.2.2, off-diagonal terms weighted 2) is formed per tile in FP32,
@@ -72,7 +72,6 @@ __global__ void k_ssymv_batch(const Tile* __restrict__ tiles, int64_t ntiles, co
         __syncthreads();
         if (t >= ntiles) break;
         const Tile tile = tiles[t];
-        const int64_t base = row_off[tile.inst];   // global row of local index 0
         float syp = 0.f;
         // uniform trip count across the block, so the group shuffles see full warps
         for (int r0 = 0; r0 < tile.rows; r0 += groups) {
@@ -81,16 +80,15 @@ __global__ void k_ssymv_batch(const Tile* __restrict__ tiles, int64_t ntiles, co
             const int64_t i = tile.row0 + (act ? r : 0);  // global row
             float rowsum = 0.f, rs = 0.f, xi = 0.f;
             if (act) {
-                const int32_t li = (int32_t)(i - base);
                 xi = x[i];
                 const int64_t p1 = rowptr[i + 1];
                 for (int64_t p = rowptr[i] + s; p < p1; p += L) {
-                    const int32_t j = col[p];
+                    const int64_t j = col[p];
                     const float a = val[p];
-                    const float tt = a * x[base + j];
+                    const float tt = a * x[j];
                     rowsum += tt;
-                    if (j != li) {
-                        atomicAdd(&y[base + j], a * xi);
+                    if (j != i) {
+                        atomicAdd(&y[j], a * xi);
                         if (SYPRD) rs += 2.f * tt;
                     } else if (SYPRD) {
                         rs += tt;

@@ -219,6 +219,78 @@ __global__ void k_gen_coords(int order, int64_t n, int64_t count, uint64_t seed,
     val[e] = (float)(m - (1 << 23)) * (1.0f / 8388608.0f);
 }
 
+// ---------------------------------------------------------------- order-2 -> upper CSR
+
+__global__ void k_csr_counts(const uint64_t* __restrict__ klo, int64_t nnz, int64_t nnz_strict, int bits,
+                             unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ scnt,
+                             int* __restrict__ has_diag) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    int32_t c[2];
+    unpack_key<2, 1>(KeyWords{klo[p], 0ull}, bits, c);
+    atomicAdd(&cnt[c[0]], 1ull);
+    if (p < nnz_strict)
+        atomicAdd(&scnt[c[0]], 1ull);
+    else
+        has_diag[c[0]] = 1;
+}
+
+__global__ void k_csr_fill(const uint64_t* __restrict__ klo, const float* __restrict__ val, int64_t nnz,
+                           int64_t nnz_strict, int bits, const int64_t* __restrict__ rowptr,
+                           const int64_t* __restrict__ sstart, const int* __restrict__ has_diag,
+                           int32_t* __restrict__ col, float* __restrict__ oval) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    int32_t c[2];
+    unpack_key<2, 1>(KeyWords{klo[p], 0ull}, bits, c);
+    const int64_t dst = (p < nnz_strict) ? rowptr[c[0]] + has_diag[c[0]] + (p - sstart[c[0]]) : rowptr[c[0]];
+    col[dst] = c[1];
+    oval[dst] = val[p];
+}
+
+__global__ void k_u64_to_i64(const unsigned long long* __restrict__ a, int64_t n, int64_t* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (int64_t)a[i];
+}
+
+// ---------------------------------------------------------------- batched matrix generator
+
+__global__ void k_gen_batch(int64_t count, const int64_t* __restrict__ row_off, const int64_t* __restrict__ draw_off,
+                            int64_t total, uint64_t seed, int32_t* __restrict__ idx, int64_t ld,
+                            float* __restrict__ val) {
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= total) return;
+    int64_t lo = 0, hi = count;  // instance b with draw_off[b] <= d < draw_off[b+1]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (draw_off[mid] <= d) lo = mid; else hi = mid;
+    }
+    const int64_t b = lo;
+    const int64_t n = row_off[b + 1] - row_off[b];
+    const int64_t slots = n * (n + 1) / 2;
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+    const uint64_t z = sm64_mix(seed + (uint64_t)(d + 1) * gamma);
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    int64_t sl = (int64_t)floor(u * (double)slots);
+    if (sl >= slots) sl = slots - 1;
+    const double t = (double)(2 * n + 1);
+    int64_t i = (int64_t)floor((t - sqrt(t * t - 8.0 * (double)sl)) * 0.5);
+    if (i < 0) i = 0;
+    if (i > n - 1) i = n - 1;
+    auto start = [n](int64_t r) { return r * (2 * n - r + 1) / 2; };
+    while (i > 0 && start(i) > sl) --i;
+    while (i + 1 < n && start(i + 1) <= sl) ++i;
+    const int64_t j = i + (sl - start(i));
+    const uint64_t gi = (uint64_t)(row_off[b] + i), gj = (uint64_t)(row_off[b] + j);
+    idx[d] = (int32_t)gi;
+    idx[ld + d] = (int32_t)gj;
+    const uint64_t s1 = gi + gj;
+    const uint64_t s2 = sm64_mix(gi + seed) + sm64_mix(gj + seed);
+    const uint64_t h = sm64_mix(s1 * gamma + s2);
+    const int32_t m = (int32_t)(h >> 40);
+    val[d] = (float)(m - (1 << 23)) * (1.0f / 8388608.0f);
+}
+
 int bits_for(int64_t n) {
     int b = 0;
     while ((1ll << b) < n) ++b;
@@ -441,6 +513,67 @@ extern "C" sym_status sym_gen_coords(int order, int64_t n, int64_t count, uint64
     if (!idx || !val) return SYM_E_INVALID;
     k_gen_coords<<<(unsigned)((count + 255) / 256), 256, 0, as_stream(stream)>>>(order, n, count, seed, idx, ld_idx,
                                                                                  val);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+extern "C" size_t sym_tensor_upper_csr_ws_bytes(sym_tensor X) {
+    if (!X || X->order != 2) return 0;
+    Sizer z;
+    z.take<unsigned long long>((size_t)X->n + 1);
+    z.take<unsigned long long>((size_t)X->n + 1);
+    z.take<int64_t>((size_t)X->n + 1);
+    z.take<int>((size_t)X->n + 1);
+    z.take<char>(scan_ws_bytes(X->n + 1));
+    return z.used;
+}
+
+extern "C" sym_status sym_tensor_upper_csr(sym_tensor X, int64_t* rowptr, int32_t* col, float* val, void* ws,
+                                           size_t ws_bytes, sym_stream_t stream) {
+    if (!X || X->order != 2 || X->kw != 1 || !rowptr || (X->nnz > 0 && (!col || !val)) || !ws) return SYM_E_INVALID;
+    if (ws_bytes < sym_tensor_upper_csr_ws_bytes(X)) return SYM_E_NOMEM;
+    cudaStream_t s = as_stream(stream);
+    const int64_t n = X->n;
+    Carver W(ws, ws_bytes);
+    unsigned long long* cnt = W.take<unsigned long long>((size_t)n + 1);
+    unsigned long long* scnt = W.take<unsigned long long>((size_t)n + 1);
+    int64_t* sstart = W.take<int64_t>((size_t)n + 1);
+    int* hd = W.take<int>((size_t)n + 1);
+    void* scan = W.take<char>(scan_ws_bytes(n + 1));
+    SYM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (n + 1), s));
+    SYM_CUDA(cudaMemsetAsync(scnt, 0, sizeof(unsigned long long) * (n + 1), s));
+    SYM_CUDA(cudaMemsetAsync(hd, 0, sizeof(int) * (n + 1), s));
+    if (X->nnz > 0) {
+        k_csr_counts<<<(unsigned)((X->nnz + 255) / 256), 256, 0, s>>>(X->klo, X->nnz, X->nnz_strict, X->bits, cnt, scnt,
+                                                                      hd);
+        SYM_CHECK_LAUNCH();
+    }
+    const unsigned gn = (unsigned)((n + 1 + 255) / 256);
+    k_u64_to_i64<<<gn, 256, 0, s>>>(cnt, n + 1, rowptr);
+    SYM_CHECK_LAUNCH();
+    sym_status st = exclusive_scan_i64(rowptr, rowptr, n + 1, scan, s);
+    if (st != SYM_OK) return st;
+    k_u64_to_i64<<<gn, 256, 0, s>>>(scnt, n + 1, sstart);
+    SYM_CHECK_LAUNCH();
+    st = exclusive_scan_i64(sstart, sstart, n + 1, scan, s);
+    if (st != SYM_OK) return st;
+    if (X->nnz > 0) {
+        k_csr_fill<<<(unsigned)((X->nnz + 255) / 256), 256, 0, s>>>(X->klo, X->val, X->nnz, X->nnz_strict, X->bits,
+                                                                    rowptr, sstart, hd, col, val);
+        SYM_CHECK_LAUNCH();
+    }
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_gen_batch_coords(int64_t count, const int64_t* row_off, const int64_t* draw_off,
+                                           int64_t total_draws, uint64_t seed, int32_t* idx, int64_t ld_idx,
+                                           float* val, sym_stream_t stream) {
+    if (count < 1 || !row_off || !draw_off || total_draws < 0 || ld_idx < total_draws) return SYM_E_INVALID;
+    if (total_draws == 0) return SYM_OK;
+    if (!idx || !val) return SYM_E_INVALID;
+    k_gen_batch<<<(unsigned)((total_draws + 255) / 256), 256, 0, as_stream(stream)>>>(count, row_off, draw_off,
+                                                                                     total_draws, seed, idx, ld_idx,
+                                                                                     val);
     SYM_CHECK_LAUNCH();
     return SYM_OK;
 }

@@ -314,6 +314,54 @@ def coord_value(rows: np.ndarray, seed: int) -> np.ndarray:
     return ((m.astype(np.float64) * (2.0 ** -23)) - 1.0).astype(np.float32)
 
 
+def batch_coords(row_off: np.ndarray, draw_off: np.ndarray, seed: int):
+    """Counter-based draws for batched symmetric matrices (same definition as sym_gen_batch_coords).
+
+    Instance b owns global rows [row_off[b], row_off[b+1]) and draws
+    [draw_off[b], draw_off[b+1]).  Draw d: u = (word_d >> 11) * 2^-53 of the
+    SplitMix64 stream, slot s = floor(u * n_b (n_b + 1) / 2) of the row-major
+    upper triangle, mapped to (i, j) with i <= j; returned as global indices,
+    value from the pair's multiset (`coord_value`).
+    """
+    row_off = np.asarray(row_off, dtype=np.int64)
+    draw_off = np.asarray(draw_off, dtype=np.int64)
+    total = int(draw_off[-1])
+    d = np.arange(total, dtype=np.int64)
+    b = np.searchsorted(draw_off, d, side="right") - 1
+    n = row_off[b + 1] - row_off[b]
+    slots = n * (n + 1) // 2
+    z = splitmix64(seed, 0, total)
+    u = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    sl = np.floor(u * slots.astype(np.float64)).astype(np.int64)
+    sl = np.minimum(sl, slots - 1)
+    t = (2 * n + 1).astype(np.float64)
+    i = np.floor((t - np.sqrt(t * t - 8.0 * sl.astype(np.float64))) * 0.5).astype(np.int64)
+    i = np.clip(i, 0, n - 1)
+    start = lambda r: r * (2 * n - r + 1) // 2
+    for _ in range(4):  # integer fix-up of the floating-point row estimate
+        down = (i > 0) & (start(i) > sl)
+        i = i - down
+        up = (i + 1 < n) & (start(i + 1) <= sl)
+        i = i + up
+    j = i + (sl - start(i))
+    gi, gj = row_off[b] + i, row_off[b] + j
+    idx = np.stack([gi, gj]).astype(np.int32)
+    return idx, coord_value(np.stack([gi, gj], axis=1), seed)
+
+
+def batch_upper_csr_host(row_off, idx, val):
+    """Upper CSR (global rows and columns) of deduplicated draws; host-side, for small batches."""
+    total_rows = int(row_off[-1])
+    key = idx[0].astype(np.int64) * total_rows + idx[1]
+    _, first = np.unique(key, return_index=True)
+    i, j, v = idx[0][first], idx[1][first], val[first]
+    o = np.lexsort((j, i))
+    i, j, v = i[o], j[o], v[o]
+    rowptr = np.zeros(total_rows + 1, dtype=np.int64)
+    np.add.at(rowptr, i.astype(np.int64) + 1, 1)
+    return np.cumsum(rowptr), j.astype(np.int32), v.astype(np.float32)
+
+
 # ----------------------------------------------------------------------------
 # Symmetric matrices (upper-triangle CSR) and dense operands
 # ----------------------------------------------------------------------------
