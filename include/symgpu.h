@@ -249,6 +249,15 @@ sym_status sym_tensor_export(sym_tensor X, int32_t* cidx, int64_t ld_out, float*
 
 sym_status sym_tensor_destroy(sym_tensor X);
 
+/* Leaf index (orders >= 3): the strict stream a second time, each tuple
+ * reversed (c_N first) and sorted, so that the MTTKRP can treat the last
+ * position as the root of a second CSF traversal and accumulate its rows in
+ * registers instead of reducing into M once per entry.  It costs one more copy
+ * of the strict stream (arena) and a sort (workspace).  Synchronises `stream`. */
+sym_status sym_tensor_leaf_index_bytes(sym_tensor X, size_t* arena_bytes, size_t* ws_bytes);
+sym_status sym_tensor_add_leaf_index(sym_tensor X, void* arena, size_t arena_bytes, void* ws, size_t ws_bytes,
+                                     sym_stream_t stream);
+
 /* Order-2 tensors: the canonical entries as an upper-triangle CSR (row i holds
  * columns j >= i, ascending).  rowptr: n+1 int64, col: nnz int32, val: nnz
  * floats, all [device]; ws >= sym_tensor_upper_csr_ws_bytes(X). */
@@ -296,8 +305,40 @@ size_t sym_mttkrp_workspace_bytes(sym_tensor X, int rank, sym_dtype bdt, int wan
 sym_status sym_mttkrp(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
                       int64_t ldm, double* residual, void* ws, size_t ws_bytes, sym_stream_t stream);
 
-/* Kernel shape for MTTKRP (entries per warp-chunk); 0 = library default. */
+/* Kernel configuration of one tensor's MTTKRP calls (all variants compute the
+ * same result; they differ in speed).  The autotuner below picks one. */
+typedef enum {
+    SYM_MTTKRP_PLAIN = 0,        /* CSF-factorised, chunked warps, reductions to global memory */
+    SYM_MTTKRP_PIPELINED = 1,    /* the same with the next leaf gather issued early; chunked or persistent;
+                                    optional shared-memory hot rows */
+    SYM_MTTKRP_UNFACTORISED = 2  /* one entry per lane group, every position updated separately */
+} sym_mttkrp_kernel;
+typedef struct {
+    int32_t strict_kernel;     /* sym_mttkrp_kernel for the strict stream */
+    int32_t entries_per_warp;  /* work chunk per warp, a multiple of 32; 0 = persistent contiguous slices
+                                  (pipelined kernel only) */
+    int32_t threads_per_cta;   /* pipelined / unfactorised kernels: 64..512 */
+    int32_t ctas_per_sm;       /* persistent grids: CTAs per SM */
+    int32_t strict_smem_kb;    /* pipelined kernel: shared memory per CTA for hot (low-index) rows, 0 = none */
+    int32_t diag_smem_kb;      /* diagonal stream: the same, 0 = none */
+    int32_t b_share_pct;       /* share of that shared memory holding rows of B (the rest holds rows of M) */
+    int32_t leaf_index;        /* plain kernel: 1 = take the leaf position from the tensor's leaf index (see
+                                  sym_tensor_add_leaf_index) instead of one reduction per entry */
+    int32_t vec_per_lane;      /* plain kernel: float4 column groups per lane, 1 or 2 (2 needs rank >= 8) */
+} sym_mttkrp_cfg;
+sym_status sym_mttkrp_default_config(sym_mttkrp_cfg* out);
+sym_status sym_mttkrp_set_config(sym_tensor X, const sym_mttkrp_cfg* cfg);
+sym_status sym_mttkrp_get_config(sym_tensor X, sym_mttkrp_cfg* out);
+/* Shorthand: > 0 selects the plain kernel with that many entries per warp,
+ * 0 restores the default configuration, -1 selects the unfactorised kernel. */
 sym_status sym_mttkrp_set_chunk(sym_tensor X, int entries_per_warp);
+/* Times candidate configurations on this tensor with these operands (M is
+ * overwritten), stores the fastest in the tensor and appends it to the text
+ * cache `cache_path` (nullable) keyed by device and problem shape; a cache hit
+ * skips the timing.  Synchronous. */
+sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
+                               int64_t ldm, const char* cache_path, sym_stream_t stream, sym_mttkrp_cfg* best,
+                               float* best_ms);
 
 /* ===================================================================== */
 /* Baseline: MTTKRP over the fully expanded (non-symmetric) tensor          */

@@ -89,6 +89,18 @@ class ServerStats(C.Structure):
                 ("peak_inflight", C.c_int64), ("peak_bytes", C.c_int64)]
 
 
+class MttkrpCfg(C.Structure):
+    _fields_ = [("strict_kernel", C.c_int32), ("entries_per_warp", C.c_int32), ("threads_per_cta", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("strict_smem_kb", C.c_int32), ("diag_smem_kb", C.c_int32),
+                ("b_share_pct", C.c_int32), ("leaf_index", C.c_int32), ("vec_per_lane", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+MTTKRP_PLAIN, MTTKRP_PIPELINED, MTTKRP_UNFACTORISED = 0, 1, 2
+
+
 class ProfileEntry(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -129,6 +141,9 @@ _SIGS = {
     "sym_tensor_export": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "sym_tensor_destroy": ([C.c_void_p], C.c_int),
     "sym_tensor_upper_csr_ws_bytes": ([C.c_void_p], C.c_size_t),
+    "sym_tensor_leaf_index_bytes": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_tensor_add_leaf_index": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p],
+                                  C.c_int),
     "sym_tensor_upper_csr": ([C.c_void_p] * 5 + [C.c_size_t, C.c_void_p], C.c_int),
     "sym_gen_batch_coords": ([C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_int64,
                               C.c_void_p, C.c_void_p], C.c_int),
@@ -138,6 +153,11 @@ _SIGS = {
     "sym_mttkrp": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                     C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "sym_mttkrp_set_chunk": ([C.c_void_p, C.c_int], C.c_int),
+    "sym_mttkrp_default_config": ([C.c_void_p], C.c_int),
+    "sym_mttkrp_set_config": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_mttkrp_get_config": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_mttkrp_autotune": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_char_p,
+                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_expanded_bytes": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_expanded_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p,
                              C.c_void_p], C.c_int),
@@ -352,6 +372,38 @@ class SymTensor:
 
     def set_chunk(self, entries_per_warp: int):
         check(lib().sym_mttkrp_set_chunk(self.handle, entries_per_warp), "sym_mttkrp_set_chunk")
+
+    def set_config(self, strict_kernel=MTTKRP_PLAIN, entries_per_warp=256, threads_per_cta=256, ctas_per_sm=2,
+                   strict_smem_kb=0, diag_smem_kb=96, b_share_pct=0, leaf_index=1, vec_per_lane=1):
+        cfg = MttkrpCfg(strict_kernel, entries_per_warp, threads_per_cta, ctas_per_sm, strict_smem_kb, diag_smem_kb,
+                        b_share_pct, leaf_index, vec_per_lane)
+        check(lib().sym_mttkrp_set_config(self.handle, C.byref(cfg)), "sym_mttkrp_set_config")
+
+    def add_leaf_index(self, stream=None):
+        """Builds the leaf index (strict stream sorted by its last coordinate); MTTKRP then uses it."""
+        ab, wb = C.c_size_t(0), C.c_size_t(0)
+        check(lib().sym_tensor_leaf_index_bytes(self.handle, C.byref(ab), C.byref(wb)), "sym_tensor_leaf_index_bytes")
+        self.leaf_arena = _scratch(ab.value, self.device)
+        ws = _scratch(wb.value, self.device)
+        check(lib().sym_tensor_add_leaf_index(self.handle, _ptr(self.leaf_arena), self.leaf_arena.numel(), _ptr(ws),
+                                              ws.numel(), _stream(stream)), "sym_tensor_add_leaf_index")
+        self._info = None
+
+    def get_config(self) -> dict:
+        cfg = MttkrpCfg()
+        check(lib().sym_mttkrp_get_config(self.handle, C.byref(cfg)), "sym_mttkrp_get_config")
+        return cfg.as_dict()
+
+    def autotune(self, B: torch.Tensor, M: torch.Tensor | None = None, cache_path: str | None = None, stream=None):
+        """Times kernel configurations for these operands; keeps the fastest. Returns (config dict, ms)."""
+        rank = B.shape[1]
+        if M is None:
+            M = torch.empty((self.n, rank), dtype=torch.float32, device=B.device)
+        best, ms = MttkrpCfg(), C.c_float(0)
+        check(lib().sym_mttkrp_autotune(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(M), M.stride(0),
+                                        cache_path.encode() if cache_path else None, _stream(stream), C.byref(best),
+                                        C.byref(ms)), "sym_mttkrp_autotune")
+        return best.as_dict(), ms.value
 
     def mttkrp_workspace(self, rank: int, bdt: int = F32, residual: bool = True) -> torch.Tensor:
         return _scratch(lib().sym_mttkrp_workspace_bytes(self.handle, rank, bdt, int(residual)), self.device)

@@ -13,6 +13,9 @@
 // product of two floats is exact in FP64).  ||X||^2 was summed in FP64 when the
 // tensor was created.
 #include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "mttkrp.cuh"
@@ -196,26 +199,92 @@ sym_status validate_mttkrp_args(const sym_tensor_s* X, const void* B, sym_dtype 
     return SYM_OK;
 }
 
-sym_status mttkrp_core(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, float* M, int64_t ldm,
-                       int chunk, bool factorised, cudaStream_t s) {
+sym_status mttkrp_core_cfg(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, float* M,
+                           int64_t ldm, const sym_mttkrp_cfg& cfg, cudaStream_t s) {
     if (ldm == R)
         SYM_CUDA(cudaMemsetAsync(M, 0, sizeof(float) * (size_t)X->n * R, s));
     else
         SYM_CUDA(cudaMemset2DAsync(M, sizeof(float) * ldm, 0, sizeof(float) * R, X->n, s));
     if (X->nnz == 0) return SYM_OK;
     switch (X->order) {
-        case 2: return launch_mttkrp_order<2>(X, B, bf16, R, ldb, M, ldm, chunk, factorised, s);
-        case 3: return launch_mttkrp_order<3>(X, B, bf16, R, ldb, M, ldm, chunk, factorised, s);
-        case 4: return launch_mttkrp_order<4>(X, B, bf16, R, ldb, M, ldm, chunk, factorised, s);
-        case 5: return launch_mttkrp_order<5>(X, B, bf16, R, ldb, M, ldm, chunk, factorised, s);
+        case 2: return launch_mttkrp_order<2>(X, B, bf16, R, ldb, M, ldm, cfg, s);
+        case 3: return launch_mttkrp_order<3>(X, B, bf16, R, ldb, M, ldm, cfg, s);
+        case 4: return launch_mttkrp_order<4>(X, B, bf16, R, ldb, M, ldm, cfg, s);
+        case 5: return launch_mttkrp_order<5>(X, B, bf16, R, ldb, M, ldm, cfg, s);
         default: return SYM_E_UNSUPPORTED;
     }
 }
 
-int default_chunk(const sym_tensor_s* X) {
-    if (X->chunk > 0) return X->chunk;
-    return 256;
+sym_status mttkrp_core(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, float* M, int64_t ldm,
+                       cudaStream_t s) {
+    return mttkrp_core_cfg(X, B, bf16, R, ldb, M, ldm, X->cfg, s);
 }
+
+sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
+    if (!c) return SYM_E_INVALID;
+    if (c->strict_kernel < 0 || c->strict_kernel > 2) return SYM_E_INVALID;
+    if (c->entries_per_warp < 0 || c->entries_per_warp % 32 != 0 || c->entries_per_warp > (1 << 24))
+        return SYM_E_INVALID;
+    if (c->entries_per_warp == 0 && c->strict_kernel != SYM_MTTKRP_PIPELINED) return SYM_E_INVALID;
+    if (c->threads_per_cta < 64 || c->threads_per_cta > 512 || c->threads_per_cta % 32) return SYM_E_INVALID;
+    if (c->ctas_per_sm < 1 || c->ctas_per_sm > 8) return SYM_E_INVALID;
+    if (c->strict_smem_kb < 0 || c->strict_smem_kb > 220 || c->diag_smem_kb < 0 || c->diag_smem_kb > 220)
+        return SYM_E_INVALID;
+    if (c->b_share_pct < 0 || c->b_share_pct > 100) return SYM_E_INVALID;
+    if (c->leaf_index != 0 && c->leaf_index != 1) return SYM_E_INVALID;
+    if (c->vec_per_lane != 1 && c->vec_per_lane != 2) return SYM_E_INVALID;
+    return SYM_OK;
+}
+
+namespace {
+
+std::string tune_key(const sym_tensor_s* X, int rank, sym_dtype bdt) {
+    cudaDeviceProp prop;
+    std::string name = "unknown";
+    if (cudaGetDeviceProperties(&prop, current_device()) == cudaSuccess) name = prop.name;
+    for (auto& ch : name)
+        if (ch == ' ') ch = '_';
+    char buf[320];
+    snprintf(buf, sizeof(buf), "mttkrp|%s|N%d|n%lld|nnz%lld|strict%lld|R%d|%s|leaf%d", name.c_str(), X->order,
+             (long long)X->n, (long long)X->nnz, (long long)X->nnz_strict, rank, bdt == SYM_BF16 ? "bf16" : "f32",
+             X->rklo ? 1 : 0);
+    return buf;
+}
+
+bool tune_lookup(const char* path, const std::string& key, sym_mttkrp_cfg* cfg, float* ms) {
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[640];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        char k[400];
+        sym_mttkrp_cfg c;
+        float t;
+        if (sscanf(line, "%399s %d %d %d %d %d %d %d %d %d %f", k, &c.strict_kernel, &c.entries_per_warp,
+                   &c.threads_per_cta, &c.ctas_per_sm, &c.strict_smem_kb, &c.diag_smem_kb, &c.b_share_pct,
+                   &c.leaf_index, &c.vec_per_lane, &t) == 11 &&
+            key == k && validate_mttkrp_cfg(&c) == SYM_OK) {
+            *cfg = c;
+            *ms = t;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void tune_store(const char* path, const std::string& key, const sym_mttkrp_cfg& c, float ms) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %.6f\n", key.c_str(), c.strict_kernel, c.entries_per_warp,
+            c.threads_per_cta, c.ctas_per_sm, c.strict_smem_kb, c.diag_smem_kb, c.b_share_pct, c.leaf_index,
+            c.vec_per_lane, ms);
+    fclose(f);
+}
+
+}  // namespace
 
 }  // namespace symgpu
 
@@ -238,18 +307,125 @@ extern "C" sym_status sym_mttkrp(sym_tensor X, const void* B, sym_dtype bdt, int
     }
     cudaStream_t s = as_stream(stream);
     const bool bf16 = bdt == SYM_BF16;
-    const int chunk = default_chunk(X);
-    st = mttkrp_core(X, B, bf16, rank, ldb, M, ldm, chunk > 0 ? chunk : 256, X->chunk >= 0, s);
+    st = mttkrp_core(X, B, bf16, rank, ldb, M, ldm, s);
     if (st != SYM_OK) return st;
     if (residual) return residual_launch(X, B, bf16, rank, ldb, M, ldm, residual, ws, ws_bytes, s);
     return SYM_OK;
 }
 
+extern "C" sym_status sym_mttkrp_default_config(sym_mttkrp_cfg* out) {
+    if (!out) return SYM_E_INVALID;
+    *out = sym_mttkrp_cfg{SYM_MTTKRP_PLAIN, 256, 256, 2, 0, 96, 0, 1, 1};
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_mttkrp_set_config(sym_tensor X, const sym_mttkrp_cfg* cfg) {
+    if (!X) return SYM_E_INVALID;
+    sym_status st = validate_mttkrp_cfg(cfg);
+    if (st != SYM_OK) return st;
+    X->cfg = *cfg;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_mttkrp_get_config(sym_tensor X, sym_mttkrp_cfg* out) {
+    if (!X || !out) return SYM_E_INVALID;
+    *out = X->cfg;
+    return SYM_OK;
+}
+
 extern "C" sym_status sym_mttkrp_set_chunk(sym_tensor X, int entries_per_warp) {
     if (!X) return SYM_E_INVALID;
-    // > 0: entries per warp (multiple of 32); 0: default; -1: unfactorised per-entry kernel
-    if (entries_per_warp > 0 && entries_per_warp % 32 != 0) return SYM_E_INVALID;
-    if (entries_per_warp < -1) return SYM_E_INVALID;
-    X->chunk = entries_per_warp;
+    sym_mttkrp_cfg c;
+    sym_mttkrp_default_config(&c);
+    if (entries_per_warp > 0) {
+        if (entries_per_warp % 32 != 0) return SYM_E_INVALID;
+        c.strict_kernel = SYM_MTTKRP_PLAIN;
+        c.entries_per_warp = entries_per_warp;
+    } else if (entries_per_warp == -1) {
+        c.strict_kernel = SYM_MTTKRP_UNFACTORISED;
+    } else if (entries_per_warp != 0) {
+        return SYM_E_INVALID;
+    }
+    X->cfg = c;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb,
+                                          float* M, int64_t ldm, const char* cache_path, sym_stream_t stream,
+                                          sym_mttkrp_cfg* best, float* best_ms) {
+    sym_status st = validate_mttkrp_args(X, B, bdt, rank, ldb, M, ldm);
+    if (st != SYM_OK) return st;
+    const std::string key = tune_key(X, rank, bdt);
+    sym_mttkrp_cfg found;
+    float found_ms = 0.f;
+    if (tune_lookup(cache_path, key, &found, &found_ms)) {
+        X->cfg = found;
+        if (best) *best = found;
+        if (best_ms) *best_ms = found_ms;
+        return SYM_OK;
+    }
+    cudaStream_t s = as_stream(stream);
+    const bool bf16 = bdt == SYM_BF16;
+    std::vector<sym_mttkrp_cfg> cands;
+    for (int leaf : {0, 1}) {
+        if (leaf && !X->rklo) continue;
+        for (int chunk : {128, 256, 512}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, leaf, 1});
+    }
+    if (rank >= 8)
+        for (int chunk : {128, 256, 512}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, 0, 2});
+    for (int chunk : {128, 256}) cands.push_back({SYM_MTTKRP_PIPELINED, chunk, 256, 2, 0, 0, 0, 0, 1});
+    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 0, 0, 0, 0, 1});
+    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 96, 0, 50, 0, 1});
+    cands.push_back({SYM_MTTKRP_UNFACTORISED, 256, 256, 2, 0, 0, 0, 0, 1});
+    cudaEvent_t e0, e1;
+    SYM_CUDA(cudaEventCreate(&e0));
+    SYM_CUDA(cudaEventCreate(&e1));
+    auto time_cfg = [&](const sym_mttkrp_cfg& c, float* out) -> bool {
+        if (mttkrp_core_cfg(X, B, bf16, rank, ldb, M, ldm, c, s) != SYM_OK) return false;  // warm-up
+        float tot = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, s);
+            if (mttkrp_core_cfg(X, B, bf16, rank, ldb, M, ldm, c, s) != SYM_OK) return false;
+            cudaEventRecord(e1, s);
+            float t = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+                return false;
+            tot += t;
+        }
+        *out = tot / 3;
+        return true;
+    };
+    // strict-stream kernel first (diagonal stream at the default), then the diagonal option
+    sym_mttkrp_cfg bc;
+    sym_mttkrp_default_config(&bc);
+    float bt = 1e30f;
+    bool any = false;
+    for (auto c : cands) {
+        c.diag_smem_kb = bc.diag_smem_kb;
+        float t;
+        if (time_cfg(c, &t) && t < bt) {
+            bt = t;
+            bc = c;
+            any = true;
+        }
+    }
+    if (any && X->nnz > X->nnz_strict) {
+        for (int kb : {0, 48, 96}) {
+            sym_mttkrp_cfg c = bc;
+            c.diag_smem_kb = kb;
+            float t;
+            if (time_cfg(c, &t) && t < bt) {
+                bt = t;
+                bc = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!any) return SYM_E_CUDA;
+    X->cfg = bc;
+    if (best) *best = bc;
+    if (best_ms) *best_ms = bt;
+    tune_store(cache_path, key, bc, bt);
     return SYM_OK;
 }

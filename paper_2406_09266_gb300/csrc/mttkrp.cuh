@@ -6,8 +6,8 @@
 // entry c_1 < ... < c_N with value v stands for N! full-tensor entries, and
 // the N!/N = (N-1)! of them that start with c_p all add the same term
 // v * prod_{q != p} B[c_q] to row c_p (distributive assignment grouping,
-// Sec. 4.2.7: the factor 2 of the 3-way split loop nest).  The kernel walks the
-// sorted entries as a CSF tree (Sec. 2.2) and factorises the sums level by
+// Sec. 4.2.7: the factor 2 of the 3-way split loop nest).  The kernels walk the
+// sorted entries as a CSF tree (Sec. 2.2) and factorise the sums level by
 // level (workspace transformation, Sec. 4.2.8, applied at every level):
 //   P_q  = B[c_1] * ... * B[c_q]                    (prefix products, cached)
 //   T_q  = sum over the subtree below (c_1..c_q) of v * prod_{t > q} B[c_t]
@@ -28,10 +28,11 @@
 // reductions).  A warp loads 32 consecutive entries with coalesced 64-bit key
 // and 32-bit value loads; group g processes the L entries held by its own
 // lanes, so each group walks a strided but ordered subsequence of the warp's
-// contiguous chunk and keeps its fiber state in registers across batches.
+// contiguous range and keeps its fiber state in registers across batches.
 #pragma once
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "tensor.cuh"
@@ -45,7 +46,99 @@ __device__ __forceinline__ void decode_entry(uint64_t lo, uint64_t hi, int bits,
     unpack_key<N, KW>(KeyWords{lo, hi}, bits, c);
 }
 
-template <int N, int KW, int L, bool BF16>
+__device__ __forceinline__ float f4_get(const float4& v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// Output rows below H accumulate in a shared-memory copy of M (flushed once per
+// CTA); the other rows take one 16-byte vector reduction in global memory.
+// The four shared-memory adds of a lane start at a lane-dependent column so
+// that the lanes of a group hit different banks.
+struct RowSink {
+    float* smem;  // H x R floats
+    int H;
+    int R;
+    float* M;
+    int64_t ldm;
+    __device__ __forceinline__ void add(int64_t row, int col, float4 v) const {
+        if (row < H) {
+            float* p = smem + row * R + col;
+            const int rot = (col >> 2) & 3;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = (k + rot) & 3;
+                atomicAdd(p + j, f4_get(v, j));
+            }
+        } else {
+            red_add_f4(M + row * ldm + col, v);
+        }
+    }
+};
+
+__device__ __forceinline__ void sink_zero(float* smem, int count) {
+    float4* s4 = reinterpret_cast<float4*>(smem);
+    for (int k = threadIdx.x; k < count / 4; k += blockDim.x) s4[k] = f4_zero();
+}
+
+__device__ __forceinline__ void sink_flush(const float* smem, int H, int R, float* M, int64_t ldm) {
+    const float4* s4 = reinterpret_cast<const float4*>(smem);
+    const int per_row = R / 4;
+    for (int k = threadIdx.x; k < H * per_row; k += blockDim.x) {
+        const float4 v = s4[k];
+        if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+            red_add_f4(M + (int64_t)(k / per_row) * ldm + 4 * (k % per_row), v);
+    }
+}
+
+// Factor rows below HB come from a shared-memory copy of B (loaded once per CTA,
+// BF16 widened to FP32), the others from global memory.
+template <bool BF16>
+struct RowSource {
+    const float* smem;  // HB x R floats
+    int HB;
+    int R;
+    const void* B;
+    int64_t ldb;
+    __device__ __forceinline__ float4 get(int64_t row, int col) const {
+        if (row < HB) return *reinterpret_cast<const float4*>(smem + row * R + col);
+        return load_row4<BF16>(B, row, ldb, col);
+    }
+};
+
+template <bool BF16>
+__device__ __forceinline__ void source_fill(float* smem, int HB, int R, const void* B, int64_t ldb) {
+    const int per_row = R / 4;
+    for (int k = threadIdx.x; k < HB * per_row; k += blockDim.x) {
+        const int row = k / per_row, c4 = 4 * (k % per_row);
+        *reinterpret_cast<float4*>(smem + row * R + c4) = load_row4<BF16>(B, row, ldb, c4);
+    }
+}
+
+// Range of the strict stream owned by the calling warp: fixed chunks of
+// `chunk` entries (chunk > 0), or, for chunk == 0, CTA c owns the contiguous
+// slice [nnz*c/G, nnz*(c+1)/G) and each warp a contiguous part of it.
+__device__ __forceinline__ void warp_range(int64_t nnz, int64_t chunk, int64_t* start, int64_t* end) {
+    if (chunk > 0) {
+        const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        *start = warp * chunk;
+        *end = min(*start + chunk, nnz);
+    } else {
+        const int nw = blockDim.x >> 5, wi = threadIdx.x >> 5;
+        const int64_t c0 = nnz * blockIdx.x / gridDim.x, c1 = nnz * (blockIdx.x + 1) / gridDim.x;
+        *start = c0 + (c1 - c0) * wi / nw;
+        *end = c0 + (c1 - c0) * (wi + 1) / nw;
+    }
+}
+
+// CSF-factorised strict-stream kernel, no shared memory, one entry at a time
+// per lane group (the simplest form).
+//   MODE 0: every position (fiber flushes for c_1..c_{N-1}, a reduction per
+//           entry for the leaf c_N);
+//   MODE 1: the same without the leaf reductions (the leaf index covers them);
+//   MODE 2: run over the leaf index (tuples reversed, c_N first) and flush the
+//           root level only: row c_N receives (N-1)! * sum over its subtree of
+//           v * prod_{q<N} B[c_q], accumulated in registers.
+template <int N, int KW, int L, bool BF16, int MODE>
 __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
@@ -56,10 +149,9 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict(
     const int g = lane / L;
     const int col = 4 * (lane % L);
     const bool on = col < R;
-    const int64_t warp = ((int64_t)blockIdx.x * MT_THREADS + threadIdx.x) >> 5;
-    const int64_t start = warp * chunk;
-    if (start >= nnz) return;
-    const int64_t end = min(start + chunk, nnz);
+    int64_t start, end;
+    warp_range(nnz, chunk, &start, &end);
+    if (start >= end) return;
 
     int32_t cur[LV];
     float4 Brow[LV], P[LV], T[LV];
@@ -100,8 +192,10 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict(
 #pragma unroll
                     for (int q = LV - 1; q >= 0; --q) {
                         if (q >= d) {
-                            float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
-                            if (on) red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+                            if (MODE != 2 || q == 0) {
+                                float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+                                if (on) red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+                            }
                             if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
                             T[q] = f4_zero();
                         }
@@ -111,48 +205,288 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict(
                 for (int q = 0; q < LV; ++q) {
                     if (q >= d) {
                         cur[q] = c[q];
-                        Brow[q] = on ? load_row4<BF16>(B, c[q], ldb, col) : f4_zero();
-                        P[q] = (q > 0) ? f4_mul(P[q - 1], Brow[q]) : Brow[q];
+                        // the root row's own factor is not needed when only the root is flushed
+                        Brow[q] = (on && (MODE != 2 || q > 0)) ? load_row4<BF16>(B, c[q], ldb, col) : f4_zero();
+                        if (MODE != 2) P[q] = (q > 0) ? f4_mul(P[q - 1], Brow[q]) : Brow[q];
                     }
                 }
                 have = true;
             }
             const float4 bl = on ? load_row4<BF16>(B, c[N - 1], ldb, col) : f4_zero();
             T[LV - 1] = f4_fmas(bl, v, T[LV - 1]);
-            if (on) red_add_f4(M + (int64_t)c[N - 1] * ldm + col, f4_scale(P[LV - 1], w * v));
+            if (MODE == 0 && on) red_add_f4(M + (int64_t)c[N - 1] * ldm + col, f4_scale(P[LV - 1], w * v));
         }
     }
-    if (have) {
+    if (have && on) {
 #pragma unroll
         for (int q = LV - 1; q >= 0; --q) {
-            float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
-            if (on) red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+            if (MODE != 2 || q == 0) {
+                float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+                red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+            }
             if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
         }
     }
 }
 
-// One entry per lane group, any equality pattern (used for the diagonal
-// stream; with all-distinct entries it is the unfactorised per-entry form).
+// The plain kernel with VPL float4 column groups per lane (L = R / (4 VPL) lanes
+// per entry), so one warp instruction serves more entries and the per-entry
+// scalar work (shuffles, key decode, fiber tests, addressing) is spread over
+// fewer lanes.  Every position is handled in this one pass.
+template <int N, int KW, int L, int VPL, bool BF16>
+__global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict_wide(
+    const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
+    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
+    int64_t chunk) {
+    constexpr int LV = N - 1;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L;
+    const int col0 = 4 * VPL * (lane % L);
+    int64_t start, end;
+    warp_range(nnz, chunk, &start, &end);
+    if (start >= end || col0 >= R) {
+        // lanes without columns still take part in the shuffles below
+        if (start >= end) return;
+    }
+    int32_t cur[LV];
+    float4 Brow[LV][VPL], P[LV][VPL], T[LV][VPL];
+#pragma unroll
+    for (int q = 0; q < LV; ++q) {
+        cur[q] = -1;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            Brow[q][v] = f4_zero();
+            P[q][v] = f4_zero();
+            T[q][v] = f4_zero();
+        }
+    }
+    bool have = false;
+    bool on[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) on[v] = col0 + 4 * v < R;
+    for (int64_t b0 = start; b0 < end; b0 += 32) {
+        const int64_t e = b0 + lane;
+        uint64_t mlo = 0, mhi = 0;
+        float mv = 0.f;
+        if (e < end) {
+            mlo = klo[e];
+            if (KW == 2) mhi = khi[e];
+            mv = val[e];
+        }
+#pragma unroll 1
+        for (int t = 0; t < L; ++t) {
+            const int src = g * L + t;
+            const uint64_t lo = __shfl_sync(0xffffffffu, mlo, src);
+            const uint64_t hi = (KW == 2) ? __shfl_sync(0xffffffffu, mhi, src) : 0ull;
+            const float x = __shfl_sync(0xffffffffu, mv, src);
+            if (b0 + src >= end || !on[0]) continue;
+            int32_t c[N];
+            decode_entry<N, KW>(lo, hi, bits, c);
+            int d = LV;
+#pragma unroll
+            for (int q = LV - 1; q >= 0; --q)
+                if (!have || c[q] != cur[q]) d = q;
+            if (d < LV) {
+                if (have) {
+#pragma unroll
+                    for (int q = LV - 1; q >= 0; --q) {
+                        if (q >= d) {
+#pragma unroll
+                            for (int v = 0; v < VPL; ++v) {
+                                float4 out = (q > 0) ? f4_mul(P[q - 1][v], T[q][v]) : T[q][v];
+                                if (on[v]) red_add_f4(M + (int64_t)cur[q] * ldm + col0 + 4 * v, f4_scale(out, w));
+                                if (q > 0) T[q - 1][v] = f4_fma(Brow[q][v], T[q][v], T[q - 1][v]);
+                                T[q][v] = f4_zero();
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < LV; ++q) {
+                    if (q >= d) {
+                        cur[q] = c[q];
+#pragma unroll
+                        for (int v = 0; v < VPL; ++v) {
+                            Brow[q][v] = on[v] ? load_row4<BF16>(B, c[q], ldb, col0 + 4 * v) : f4_zero();
+                            P[q][v] = (q > 0) ? f4_mul(P[q - 1][v], Brow[q][v]) : Brow[q][v];
+                        }
+                    }
+                }
+                have = true;
+            }
+            float4 bl[VPL];
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) bl[v] = on[v] ? load_row4<BF16>(B, c[N - 1], ldb, col0 + 4 * v) : f4_zero();
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                T[LV - 1][v] = f4_fmas(bl[v], x, T[LV - 1][v]);
+                if (on[v]) red_add_f4(M + (int64_t)c[N - 1] * ldm + col0 + 4 * v, f4_scale(P[LV - 1][v], w * x));
+            }
+        }
+    }
+    if (have) {
+#pragma unroll
+        for (int q = LV - 1; q >= 0; --q) {
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                float4 out = (q > 0) ? f4_mul(P[q - 1][v], T[q][v]) : T[q][v];
+                if (on[v]) red_add_f4(M + (int64_t)cur[q] * ldm + col0 + 4 * v, f4_scale(out, w));
+                if (q > 0) T[q - 1][v] = f4_fma(Brow[q][v], T[q][v], T[q - 1][v]);
+            }
+        }
+    }
+}
+
+// Same computation with a one-deep software pipeline (the next entry's leaf
+// factor row is requested before the current entry is processed), a choice of
+// chunked or persistent work ranges, and optional shared-memory hot rows for M
+// (H rows) and B (HB rows).
 template <int N, int KW, int L, bool BF16>
-__global__ void __launch_bounds__(MT_THREADS) k_mttkrp_entries(
+__global__ void __launch_bounds__(512) k_mttkrp_strict_pipe(
+    const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
+    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
+    int64_t chunk, int H, int HB) {
+    extern __shared__ float4 sink_mem[];
+    constexpr int LV = N - 1;
+    float* sm_m = reinterpret_cast<float*>(sink_mem);
+    float* sm_b = sm_m + (size_t)H * R;
+    const RowSink sink{sm_m, H, R, M, ldm};
+    const RowSource<BF16> src_b{sm_b, HB, R, B, ldb};
+    if (H + HB > 0) {
+        sink_zero(sm_m, H * R);
+        source_fill<BF16>(sm_b, HB, R, B, ldb);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L;
+    const int col = 4 * (lane % L);
+    const bool on = col < R;
+    int64_t start, end;
+    warp_range(nnz, chunk, &start, &end);
+
+    int32_t cur[LV];
+    float4 Brow[LV], P[LV], T[LV];
+#pragma unroll
+    for (int q = 0; q < LV; ++q) {
+        cur[q] = -1;
+        Brow[q] = f4_zero();
+        P[q] = f4_zero();
+        T[q] = f4_zero();
+    }
+    bool have = false;
+    for (int64_t b0 = start; b0 < end; b0 += 32) {
+        const int64_t e = b0 + lane;
+        uint64_t mlo = 0, mhi = 0;
+        float mv = 0.f;
+        if (e < end) {
+            mlo = klo[e];
+            if (KW == 2) mhi = khi[e];
+            mv = val[e];
+        }
+        // entries of this group in this batch: b0 + g*L + t, valid while t < nval
+        const int64_t left = end - (b0 + g * L);
+        const int nval = left <= 0 ? 0 : (left >= L ? L : (int)left);
+        int32_t cn[N];
+        float vn = 0.f;
+        float4 bn = f4_zero();
+        {
+            const uint64_t lo = __shfl_sync(0xffffffffu, mlo, g * L);
+            const uint64_t hi = (KW == 2) ? __shfl_sync(0xffffffffu, mhi, g * L) : 0ull;
+            vn = __shfl_sync(0xffffffffu, mv, g * L);
+            decode_entry<N, KW>(lo, hi, bits, cn);
+            if (nval > 0 && on) bn = src_b.get(cn[N - 1], col);
+        }
+#pragma unroll 1
+        for (int t = 0; t < L; ++t) {
+            int32_t c[N];
+#pragma unroll
+            for (int q = 0; q < N; ++q) c[q] = cn[q];
+            const float v = vn;
+            const float4 bl = bn;
+            if (t + 1 < L) {  // issue the next entry's leaf gather first
+                const int srcl = g * L + t + 1;
+                const uint64_t lo = __shfl_sync(0xffffffffu, mlo, srcl);
+                const uint64_t hi = (KW == 2) ? __shfl_sync(0xffffffffu, mhi, srcl) : 0ull;
+                vn = __shfl_sync(0xffffffffu, mv, srcl);
+                decode_entry<N, KW>(lo, hi, bits, cn);
+                if (t + 1 < nval && on) bn = src_b.get(cn[N - 1], col);
+            }
+            if (t >= nval || !on) continue;
+            int d = LV;
+#pragma unroll
+            for (int q = LV - 1; q >= 0; --q)
+                if (!have || c[q] != cur[q]) d = q;
+            if (d < LV) {
+                if (have) {
+#pragma unroll
+                    for (int q = LV - 1; q >= 0; --q) {
+                        if (q >= d) {
+                            float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+                            sink.add(cur[q], col, f4_scale(out, w));
+                            if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+                            T[q] = f4_zero();
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < LV; ++q) {
+                    if (q >= d) {
+                        cur[q] = c[q];
+                        Brow[q] = src_b.get(c[q], col);
+                        P[q] = (q > 0) ? f4_mul(P[q - 1], Brow[q]) : Brow[q];
+                    }
+                }
+                have = true;
+            }
+            T[LV - 1] = f4_fmas(bl, v, T[LV - 1]);
+            sink.add(c[N - 1], col, f4_scale(P[LV - 1], w * v));
+        }
+    }
+    if (have && on) {
+#pragma unroll
+        for (int q = LV - 1; q >= 0; --q) {
+            float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+            sink.add(cur[q], col, f4_scale(out, w));
+            if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+        }
+    }
+    if (H > 0) {
+        __syncthreads();
+        sink_flush(sm_m, H, R, M, ldm);
+    }
+}
+
+// One entry per lane group, any equality pattern (the diagonal stream; with
+// all-distinct entries it is the unfactorised per-entry form).  Grid-stride
+// over entries; optional shared-memory hot rows as above.
+template <int N, int KW, int L, bool BF16>
+__global__ void __launch_bounds__(512) k_mttkrp_entries(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t cnt,
-    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm) {
+    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, int H, int HB) {
+    extern __shared__ float4 sink_mem[];
+    float* sm_m = reinterpret_cast<float*>(sink_mem);
+    float* sm_b = sm_m + (size_t)H * R;
+    const RowSink sink{sm_m, H, R, M, ldm};
+    const RowSource<BF16> src_b{sm_b, HB, R, B, ldb};
+    if (H + HB > 0) {
+        sink_zero(sm_m, H * R);
+        source_fill<BF16>(sm_b, HB, R, B, ldb);
+        __syncthreads();
+    }
     constexpr int GPW = 32 / L;
     const int lane = threadIdx.x & 31;
     const int col = 4 * (lane % L);
     const bool on = col < R;
-    const int64_t group = (((int64_t)blockIdx.x * MT_THREADS + threadIdx.x) >> 5) * GPW + lane / L;
-    const int64_t ngroups = ((int64_t)gridDim.x * MT_THREADS >> 5) * GPW;
+    const int64_t group = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * GPW + lane / L;
+    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x >> 5) * GPW;
     const int fact[6] = {1, 1, 2, 6, 24, 120};
-    for (int64_t e = group; e < cnt; e += ngroups) {
+    for (int64_t e = group; e < cnt && on; e += ngroups) {
         int32_t c[N];
         decode_entry<N, KW>(klo[e], KW == 2 ? khi[e] : 0ull, bits, c);
         const float v = val[e];
-        if (!on) continue;
         float4 b[N];
 #pragma unroll
-        for (int q = 0; q < N; ++q) b[q] = load_row4<BF16>(B, c[q], ldb, col);
+        for (int q = 0; q < N; ++q) b[q] = src_b.get(c[q], col);
         // prefix / suffix products over positions
         float4 pre[N + 1], suf[N + 1];
         pre[0] = make_float4(1.f, 1.f, 1.f, 1.f);
@@ -181,39 +515,106 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_entries(
             for (int q = p + 1; q < N; ++q)
                 if (c[q] == c[p]) ++m;
             const float W = (float)(fact[N - 1] * m / den);
-            red_add_f4(M + (int64_t)c[p] * ldm + col, f4_scale(f4_mul(pre[p], suf[p + 1]), W * v));
+            sink.add(c[p], col, f4_scale(f4_mul(pre[p], suf[p + 1]), W * v));
         }
+    }
+    if (H > 0) {
+        __syncthreads();
+        sink_flush(sm_m, H, R, M, ldm);
     }
 }
 
-// Per-order launchers (one translation unit per order instantiates its kernels).
+// ---------------------------------------------------------------- launch
+
+// Hot-row sizing within a shared-memory budget: rows of M (H) and of B (HB).
+struct SinkPlan {
+    int H;
+    int HB;
+    size_t bytes;
+};
+inline SinkPlan plan_sink(int64_t n, int R, int kb, int b_share_pct) {
+    if (kb <= 0) return SinkPlan{0, 0, 0};
+    const size_t row = (size_t)R * sizeof(float);
+    const size_t budget = (size_t)kb * 1024;
+    int HB = (int)std::min<int64_t>(n, (int64_t)(budget * (size_t)b_share_pct / 100 / row));
+    int H = (int)std::min<int64_t>(n, (int64_t)((budget - (size_t)HB * row) / row));
+    return SinkPlan{H, HB, (size_t)(H + HB) * row};
+}
+
 template <int N, int KW, int L, bool BF16>
 sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int64_t ldb, float* M, int64_t ldm,
-                               int chunk, bool factorised, cudaStream_t s) {
+                               const sym_mttkrp_cfg& cfg, cudaStream_t s) {
     const int64_t ns = X->nnz_strict, nd = X->nnz - X->nnz_strict;
     const int fact[6] = {1, 1, 2, 6, 24, 120};
-    const int64_t groups_per_cta = (MT_THREADS / 32) * (32 / L);
-    const int64_t max_ctas = (int64_t)sm_count() * 16;
+    const int sms = sm_count();
+    const int threads = std::max(64, std::min(512, (int)cfg.threads_per_cta)) / 32 * 32;
     if (ns > 0) {
-        if (factorised) {
+        if (cfg.strict_kernel == SYM_MTTKRP_PLAIN) {
+            const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
             const int64_t warps = (ns + chunk - 1) / chunk;
             const unsigned grid = (unsigned)((warps * 32 + MT_THREADS - 1) / MT_THREADS);
+            const bool leaf_pass = cfg.leaf_index != 0 && X->rklo != nullptr;
+            constexpr int L2 = L / 2;   // lanes per entry with 8 columns per lane
+            if (!leaf_pass && cfg.vec_per_lane == 2 && L2 >= 1) {
+                SYM_PROF("mttkrp_strict", s);
+                k_mttkrp_strict_wide<N, KW, (L2 >= 1 ? L2 : 1), 2, BF16><<<grid, MT_THREADS, 0, s>>>(
+                    X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
+            } else if (!leaf_pass) {
+                SYM_PROF("mttkrp_strict", s);
+                k_mttkrp_strict<N, KW, L, BF16, 0><<<grid, MT_THREADS, 0, s>>>(
+                    X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
+            } else {
+                {
+                    SYM_PROF("mttkrp_strict", s);
+                    k_mttkrp_strict<N, KW, L, BF16, 1><<<grid, MT_THREADS, 0, s>>>(
+                        X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
+                }
+                SYM_CHECK_LAUNCH();
+                SYM_PROF("mttkrp_strict_leaf", s);
+                k_mttkrp_strict<N, KW, L, BF16, 2><<<grid, MT_THREADS, 0, s>>>(
+                    X->rklo, X->rkhi, X->rval, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
+            }
+        } else if (cfg.strict_kernel == SYM_MTTKRP_PIPELINED) {
+            const SinkPlan sp = plan_sink(X->n, R, cfg.strict_smem_kb, cfg.b_share_pct);
+            if (sp.bytes > 48 * 1024)
+                SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_strict_pipe<N, KW, L, BF16>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.bytes));
+            unsigned grid;
+            if (cfg.entries_per_warp > 0) {
+                const int64_t warps = (ns + cfg.entries_per_warp - 1) / cfg.entries_per_warp;
+                grid = (unsigned)((warps * 32 + threads - 1) / threads);
+            } else {
+                grid = (unsigned)std::max<int64_t>(
+                    1, std::min<int64_t>((int64_t)sms * std::max(1, (int)cfg.ctas_per_sm), (ns + 255) / 256));
+            }
             SYM_PROF("mttkrp_strict", s);
-            k_mttkrp_strict<N, KW, L, BF16><<<grid, MT_THREADS, 0, s>>>(X->klo, X->khi, X->val, ns, X->bits, B, ldb,
-                                                                        R, M, ldm, (float)fact[N - 1], chunk);
+            k_mttkrp_strict_pipe<N, KW, L, BF16><<<grid, threads, sp.bytes, s>>>(
+                X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
+                std::max<int64_t>(0, cfg.entries_per_warp), sp.H, sp.HB);
         } else {
-            const unsigned grid = (unsigned)std::min<int64_t>((ns + groups_per_cta - 1) / groups_per_cta, max_ctas);
-            SYM_PROF("mttkrp_strict_entries", s);
-            k_mttkrp_entries<N, KW, L, BF16><<<grid, MT_THREADS, 0, s>>>(X->klo, X->khi, X->val, ns, X->bits, B, ldb,
-                                                                         R, M, ldm);
+            const int64_t gpc = (threads / 32) * (32 / L);
+            const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ns + gpc - 1) / gpc,
+                                                                                     (int64_t)sms * 16));
+            SYM_PROF("mttkrp_strict", s);
+            k_mttkrp_entries<N, KW, L, BF16><<<grid, threads, 0, s>>>(X->klo, X->khi, X->val, ns, X->bits, B, ldb, R,
+                                                                      M, ldm, 0, 0);
         }
         SYM_CHECK_LAUNCH();
     }
     if (nd > 0) {
-        const unsigned grid = (unsigned)std::min<int64_t>((nd + groups_per_cta - 1) / groups_per_cta, max_ctas);
+        const uint64_t* dlo = X->klo + ns;
+        const uint64_t* dhi = X->khi ? X->khi + ns : nullptr;
+        const SinkPlan sp = plan_sink(X->n, R, cfg.diag_smem_kb, cfg.b_share_pct);
+        if (sp.bytes > 48 * 1024)
+            SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_entries<N, KW, L, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sp.bytes));
+        const int dthreads = sp.bytes > 0 ? 512 : 256;
+        const int64_t gpc = (dthreads / 32) * (32 / L);
+        const int64_t cap = sp.bytes > 0 ? (int64_t)sms * (sp.bytes > 100 * 1024 ? 1 : 2) : (int64_t)sms * 16;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nd + gpc - 1) / gpc, cap));
         SYM_PROF("mttkrp_diag", s);
-        k_mttkrp_entries<N, KW, L, BF16><<<grid, MT_THREADS, 0, s>>>(
-            X->klo + ns, X->khi ? X->khi + ns : nullptr, X->val + ns, nd, X->bits, B, ldb, R, M, ldm);
+        k_mttkrp_entries<N, KW, L, BF16><<<grid, dthreads, sp.bytes, s>>>(dlo, dhi, X->val + ns, nd, X->bits, B, ldb,
+                                                                          R, M, ldm, sp.H, sp.HB);
         SYM_CHECK_LAUNCH();
     }
     return SYM_OK;
@@ -227,42 +628,40 @@ inline int lanes_for_rank(int R) {
 
 template <int N, int KW, bool BF16>
 sym_status launch_mttkrp_kw(const sym_tensor_s* X, const void* B, int R, int64_t ldb, float* M, int64_t ldm,
-                            int chunk, bool factorised, cudaStream_t s) {
+                            const sym_mttkrp_cfg& cfg, cudaStream_t s) {
     switch (lanes_for_rank(R)) {
-        case 1: return launch_mttkrp_shape<N, KW, 1, BF16>(X, B, R, ldb, M, ldm, chunk, factorised, s);
-        case 2: return launch_mttkrp_shape<N, KW, 2, BF16>(X, B, R, ldb, M, ldm, chunk, factorised, s);
-        case 4: return launch_mttkrp_shape<N, KW, 4, BF16>(X, B, R, ldb, M, ldm, chunk, factorised, s);
-        case 8: return launch_mttkrp_shape<N, KW, 8, BF16>(X, B, R, ldb, M, ldm, chunk, factorised, s);
-        case 16: return launch_mttkrp_shape<N, KW, 16, BF16>(X, B, R, ldb, M, ldm, chunk, factorised, s);
-        case 32: return launch_mttkrp_shape<N, KW, 32, BF16>(X, B, R, ldb, M, ldm, chunk, factorised, s);
+        case 1: return launch_mttkrp_shape<N, KW, 1, BF16>(X, B, R, ldb, M, ldm, cfg, s);
+        case 2: return launch_mttkrp_shape<N, KW, 2, BF16>(X, B, R, ldb, M, ldm, cfg, s);
+        case 4: return launch_mttkrp_shape<N, KW, 4, BF16>(X, B, R, ldb, M, ldm, cfg, s);
+        case 8: return launch_mttkrp_shape<N, KW, 8, BF16>(X, B, R, ldb, M, ldm, cfg, s);
+        case 16: return launch_mttkrp_shape<N, KW, 16, BF16>(X, B, R, ldb, M, ldm, cfg, s);
+        case 32: return launch_mttkrp_shape<N, KW, 32, BF16>(X, B, R, ldb, M, ldm, cfg, s);
         default: return SYM_E_UNSUPPORTED;
     }
 }
 
 template <int N>
 sym_status launch_mttkrp_impl(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, float* M,
-                              int64_t ldm, int chunk, bool factorised, cudaStream_t s) {
+                              int64_t ldm, const sym_mttkrp_cfg& cfg, cudaStream_t s) {
     if (X->kw == 1)
-        return bf16 ? launch_mttkrp_kw<N, 1, true>(X, B, R, ldb, M, ldm, chunk, factorised, s)
-                    : launch_mttkrp_kw<N, 1, false>(X, B, R, ldb, M, ldm, chunk, factorised, s);
-    return bf16 ? launch_mttkrp_kw<N, 2, true>(X, B, R, ldb, M, ldm, chunk, factorised, s)
-                : launch_mttkrp_kw<N, 2, false>(X, B, R, ldb, M, ldm, chunk, factorised, s);
+        return bf16 ? launch_mttkrp_kw<N, 1, true>(X, B, R, ldb, M, ldm, cfg, s)
+                    : launch_mttkrp_kw<N, 1, false>(X, B, R, ldb, M, ldm, cfg, s);
+    return bf16 ? launch_mttkrp_kw<N, 2, true>(X, B, R, ldb, M, ldm, cfg, s)
+                : launch_mttkrp_kw<N, 2, false>(X, B, R, ldb, M, ldm, cfg, s);
 }
 
 template <int N>
 sym_status launch_mttkrp_order(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, float* M,
-                               int64_t ldm, int chunk, bool factorised, cudaStream_t s);
+                               int64_t ldm, const sym_mttkrp_cfg& cfg, cudaStream_t s);
 
-}  // namespace symgpu
-
-namespace symgpu {
 // Entry points shared with the serving runtime (defined in mttkrp.cu).
 sym_status mttkrp_core(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, float* M, int64_t ldm,
-                       int chunk, bool factorised, cudaStream_t s);
+                       cudaStream_t s);
 sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, const float* M,
                            int64_t ldm, double* residual, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t residual_ws_bytes(int R);
 sym_status validate_mttkrp_args(const sym_tensor_s* X, const void* B, sym_dtype bdt, int rank, int64_t ldb,
                                 const float* M, int64_t ldm);
-int default_chunk(const sym_tensor_s* X);
+sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c);
+
 }  // namespace symgpu

@@ -108,8 +108,7 @@ void sym_server_s::launch(Slot& s) {
     using namespace symgpu;
     const sym_request& r = s.req.r;
     const bool bf16 = r.bdt == SYM_BF16;
-    sym_status st = mttkrp_core(r.X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, default_chunk(r.X), r.X->chunk >= 0,
-                                s.stream);
+    sym_status st = mttkrp_core(r.X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.stream);
     if (st == SYM_OK && r.want_residual) {
         st = residual_launch(r.X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.res_dev, s.ws, s.ws_bytes, s.stream);
         if (st == SYM_OK)

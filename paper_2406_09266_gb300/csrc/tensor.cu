@@ -111,9 +111,11 @@ __global__ void __launch_bounds__(CT) k_mark(const uint64_t* __restrict__ klo, c
     __syncthreads();
     int64_t p = (int64_t)blockIdx.x * CT + threadIdx.x;
     double nrm = 0.0;
+    bool dup = false, mismatch = false, keep = false, new_root = false, new_l2 = false;
+    int pat = -1;
+    unsigned ex = 0;
     if (p < nnz) {
         KeyWords k{klo[p], KW == 2 ? khi[p] : 0ull};
-        bool dup = false, mismatch = false;
         int32_t c[N], pc[N];
         unpack_key<N, KW>(k, bits, c);
         if (p > 0) {
@@ -123,25 +125,43 @@ __global__ void __launch_bounds__(CT) k_mark(const uint64_t* __restrict__ klo, c
             if (dup && policy == SYM_DUP_KEEP_EQUAL)
                 mismatch = __float_as_uint(val[pay[p]]) != __float_as_uint(val[pay[p - 1]]);
         }
-        bool keep = !dup;
-        int pat = 0;
+        keep = !dup;
+        pat = 0;
 #pragma unroll
         for (int q = 0; q + 1 < N; ++q) pat |= (c[q] == c[q + 1]) ? (1 << q) : 0;
         flag_s[p] = (keep && pat == 0) ? 1u : 0u;
         flag_d[p] = (keep && pat != 0) ? 1u : 0u;
-        if (dup) atomicAdd(&s_misc[5], 1ull);
-        if (mismatch) atomicAdd(&s_mis, 1ull);
         if (keep) {
-            int ex = distinct_perms<N>(c);
-            atomicAdd(&s_pat[pat], 1ull);
-            atomicAdd(&s_misc[0], (unsigned long long)ex);
-            if (p == 0 || pc[0] != c[0]) atomicAdd(&s_misc[1], 1ull);
-            if (p == 0 || pc[0] != c[0] || pc[1] != c[1]) atomicAdd(&s_misc[2], 1ull);
-            if (pat == 0) atomicAdd(&s_misc[3], 1ull);
-            atomicAdd(&s_misc[4], 1ull);
+            ex = (unsigned)distinct_perms<N>(c);
+            new_root = (p == 0 || pc[0] != c[0]);
+            new_l2 = (p == 0 || pc[0] != c[0] || pc[1] != c[1]);
             double v = (double)val[pay[p]];
             nrm = (double)ex * v * v;
         }
+    }
+    // warp-aggregated counts, one shared-memory update per warp and counter
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned ex_sum = __reduce_add_sync(full, ex);
+    const int n_root = __popc(__ballot_sync(full, new_root));
+    const int n_l2 = __popc(__ballot_sync(full, new_l2));
+    const int n_strict = __popc(__ballot_sync(full, keep && pat == 0));
+    const int n_keep = __popc(__ballot_sync(full, keep));
+    const int n_dup = __popc(__ballot_sync(full, dup));
+    const int n_mis = __popc(__ballot_sync(full, mismatch));
+#pragma unroll
+    for (int q = 0; q < (1 << (N - 1)); ++q) {
+        const int cq = __popc(__ballot_sync(full, keep && pat == q));
+        if (lane == 0 && cq) atomicAdd(&s_pat[q], (unsigned long long)cq);
+    }
+    if (lane == 0) {
+        if (ex_sum) atomicAdd(&s_misc[0], (unsigned long long)ex_sum);
+        if (n_root) atomicAdd(&s_misc[1], (unsigned long long)n_root);
+        if (n_l2) atomicAdd(&s_misc[2], (unsigned long long)n_l2);
+        if (n_strict) atomicAdd(&s_misc[3], (unsigned long long)n_strict);
+        if (n_keep) atomicAdd(&s_misc[4], (unsigned long long)n_keep);
+        if (n_dup) atomicAdd(&s_misc[5], (unsigned long long)n_dup);
+        if (n_mis) atomicAdd(&s_mis, (unsigned long long)n_mis);
     }
     nrm = warp_sum(nrm);
     if ((threadIdx.x & 31) == 0) s_norm[threadIdx.x >> 5] = nrm;
@@ -289,6 +309,30 @@ __global__ void k_gen_batch(int64_t count, const int64_t* __restrict__ row_off, 
     const uint64_t h = sm64_mix(s1 * gamma + s2);
     const int32_t m = (int32_t)(h >> 40);
     val[d] = (float)(m - (1 << 23)) * (1.0f / 8388608.0f);
+}
+
+// ---------------------------------------------------------------- leaf index
+
+template <int N, int KW>
+__global__ void k_reverse_pack(const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, int64_t ns,
+                               int bits, uint64_t* __restrict__ olo, uint64_t* __restrict__ ohi,
+                               uint32_t* __restrict__ pay) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= ns) return;
+    int32_t c[N], r[N];
+    unpack_key<N, KW>(KeyWords{klo[p], KW == 2 ? khi[p] : 0ull}, bits, c);
+#pragma unroll
+    for (int q = 0; q < N; ++q) r[q] = c[N - 1 - q];
+    const KeyWords k = pack_key<N, KW>(r, bits);
+    olo[p] = k.lo;
+    if (KW == 2) ohi[p] = k.hi;
+    pay[p] = (uint32_t)p;
+}
+
+__global__ void k_gather_f32(const float* __restrict__ src, const uint32_t* __restrict__ pay, int64_t m,
+                             float* __restrict__ dst) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) dst[k] = src[pay[k]];
 }
 
 int bits_for(int64_t n) {
@@ -452,7 +496,10 @@ extern "C" sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const
     t->klo = out_lo;
     t->khi = out_hi;
     t->val = out_val;
-    t->chunk = 0;
+    t->rklo = nullptr;
+    t->rkhi = nullptr;
+    t->rval = nullptr;
+    sym_mttkrp_default_config(&t->cfg);
     t->device = current_device();
     sym_tensor_info_t& I = t->info;
     memset(&I, 0, sizeof(I));
@@ -575,5 +622,89 @@ extern "C" sym_status sym_gen_batch_coords(int64_t count, const int64_t* row_off
                                                                                      total_draws, seed, idx, ld_idx,
                                                                                      val);
     SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+namespace {
+
+template <typename C>
+void layout_leaf(C& a, C& w, int64_t ns, int kw, uint64_t** rlo, uint64_t** rhi, float** rval, uint64_t** l0,
+                 uint64_t** h0, uint32_t** p0, uint64_t** l1, uint64_t** h1, uint32_t** p1, void** radix) {
+    const size_t m = ns > 0 ? (size_t)ns : 1;
+    *rlo = a.template take<uint64_t>(m);
+    *rhi = kw == 2 ? a.template take<uint64_t>(m) : nullptr;
+    *rval = a.template take<float>(m);
+    *l0 = w.template take<uint64_t>(m);
+    *h0 = kw == 2 ? w.template take<uint64_t>(m) : nullptr;
+    *p0 = w.template take<uint32_t>(m);
+    *l1 = w.template take<uint64_t>(m);
+    *h1 = kw == 2 ? w.template take<uint64_t>(m) : nullptr;
+    *p1 = w.template take<uint32_t>(m);
+    *radix = w.template take<char>(radix_ws_bytes((int64_t)m, kw));
+}
+
+template <int N>
+sym_status build_leaf(sym_tensor_s* X, uint64_t* rlo, uint64_t* rhi, float* rval, uint64_t* l0, uint64_t* h0,
+                      uint32_t* p0, uint64_t* l1, uint64_t* h1, uint32_t* p1, void* radix, cudaStream_t s) {
+    const int64_t ns = X->nnz_strict;
+    const unsigned g = (unsigned)((ns + 255) / 256);
+    if (X->kw == 1)
+        k_reverse_pack<N, 1><<<g, 256, 0, s>>>(X->klo, X->khi, ns, X->bits, l0, h0, p0);
+    else
+        k_reverse_pack<N, 2><<<g, 256, 0, s>>>(X->klo, X->khi, ns, X->bits, l0, h0, p0);
+    SYM_CHECK_LAUNCH();
+    uint64_t *slo, *shi;
+    uint32_t* sp;
+    sym_status st = radix_sort_pairs(X->kw, l0, h0, p0, l1, h1, p1, ns, N * X->bits, radix, s, &slo, &shi, &sp);
+    if (st != SYM_OK) return st;
+    SYM_CUDA(cudaMemcpyAsync(rlo, slo, sizeof(uint64_t) * ns, cudaMemcpyDeviceToDevice, s));
+    if (X->kw == 2) SYM_CUDA(cudaMemcpyAsync(rhi, shi, sizeof(uint64_t) * ns, cudaMemcpyDeviceToDevice, s));
+    k_gather_f32<<<g, 256, 0, s>>>(X->val, sp, ns, rval);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+}  // namespace
+
+extern "C" sym_status sym_tensor_leaf_index_bytes(sym_tensor X, size_t* arena_bytes, size_t* ws_bytes) {
+    if (!X || X->order < 3) return SYM_E_INVALID;
+    NullCarver a, w;
+    uint64_t *rlo, *rhi, *l0, *h0, *l1, *h1;
+    float* rv;
+    uint32_t *p0, *p1;
+    void* radix;
+    layout_leaf(a, w, X->nnz_strict, X->kw, &rlo, &rhi, &rv, &l0, &h0, &p0, &l1, &h1, &p1, &radix);
+    if (arena_bytes) *arena_bytes = a.s.used;
+    if (ws_bytes) *ws_bytes = w.s.used;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_tensor_add_leaf_index(sym_tensor X, void* arena, size_t arena_bytes, void* ws,
+                                                size_t ws_bytes, sym_stream_t stream) {
+    size_t na = 0, nw = 0;
+    sym_status st = sym_tensor_leaf_index_bytes(X, &na, &nw);
+    if (st != SYM_OK) return st;
+    if (!arena || !ws || !aligned(arena, 256) || !aligned(ws, 256)) return SYM_E_INVALID;
+    if (arena_bytes < na || ws_bytes < nw) return SYM_E_NOMEM;
+    Carver A(arena, arena_bytes), W(ws, ws_bytes);
+    uint64_t *rlo, *rhi, *l0, *h0, *l1, *h1;
+    float* rv;
+    uint32_t *p0, *p1;
+    void* radix;
+    layout_leaf(A, W, X->nnz_strict, X->kw, &rlo, &rhi, &rv, &l0, &h0, &p0, &l1, &h1, &p1, &radix);
+    cudaStream_t s = as_stream(stream);
+    if (X->nnz_strict > 0) {
+        switch (X->order) {
+            case 3: st = build_leaf<3>(X, rlo, rhi, rv, l0, h0, p0, l1, h1, p1, radix, s); break;
+            case 4: st = build_leaf<4>(X, rlo, rhi, rv, l0, h0, p0, l1, h1, p1, radix, s); break;
+            default: st = build_leaf<5>(X, rlo, rhi, rv, l0, h0, p0, l1, h1, p1, radix, s); break;
+        }
+        if (st != SYM_OK) return st;
+    }
+    SYM_CUDA(cudaStreamSynchronize(s));
+    X->rklo = rlo;
+    X->rkhi = rhi;
+    X->rval = rv;
+    X->info.arena_used += A.used;
     return SYM_OK;
 }

@@ -63,7 +63,10 @@ struct sym_tensor_s {
     uint64_t* klo;
     uint64_t* khi;
     float* val;
-    int chunk;   // entries per warp for the strict MTTKRP kernel (0 = default)
+    uint64_t* rklo;  // leaf index: strict entries with reversed tuples (c_N first), sorted; null if absent
+    uint64_t* rkhi;
+    float* rval;
+    sym_mttkrp_cfg cfg;  // MTTKRP kernel configuration
     int device;
     sym_tensor_info_t info;
 };

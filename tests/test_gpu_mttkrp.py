@@ -9,10 +9,12 @@ from tests.gpu_helpers import TOL_BF16, TOL_F32, dev, factor, host, need_gpu
 pytestmark = pytest.mark.gpu
 
 
-def run_case(sg, T, rank, bf16=False, chunk=0, seed=1):
+def run_case(sg, T, rank, bf16=False, chunk=0, seed=1, cfg=None):
     X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
     if chunk:
         X.set_chunk(chunk)
+    if cfg is not None:
+        X.set_config(**cfg)
     Bt, B32, Bused = factor(T.n, rank, seed, bf16)
     M = host(X.mttkrp(Bt))
     cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
@@ -26,11 +28,12 @@ def run_case(sg, T, rank, bf16=False, chunk=0, seed=1):
 
 
 @pytest.mark.parametrize("order,n,nnz", [(2, 300, 3000), (3, 500, 20000), (4, 60, 12000), (5, 25, 8000)])
-@pytest.mark.parametrize("rank", [4, 8, 16, 32, 64, 128])
-def test_mttkrp_f32(order, n, nnz, rank):
+@pytest.mark.parametrize("rank", [4, 8, 12, 16, 32, 64, 128])
+@pytest.mark.parametrize("vpl", [1, 2])
+def test_mttkrp_f32(order, n, nnz, rank, vpl):
     sg = need_gpu()
     T = synth.tensor_uniform(order, n, nnz, 10 + order)
-    e, _ = run_case(sg, T, rank)
+    e, _ = run_case(sg, T, rank, cfg=dict(vec_per_lane=vpl, leaf_index=0))
     assert e <= TOL_F32, e
 
 
@@ -51,6 +54,67 @@ def test_mttkrp_chunk_shapes(chunk):
     T = synth.tensor3_zipf(2000, 60000, 4)
     e, _ = run_case(sg, T, 32, chunk=chunk)
     assert e <= TOL_F32, e
+
+
+CONFIGS = [
+    dict(strict_kernel=1, entries_per_warp=128, diag_smem_kb=0),
+    dict(strict_kernel=1, entries_per_warp=0, threads_per_cta=512, ctas_per_sm=2),
+    dict(strict_kernel=1, entries_per_warp=0, threads_per_cta=512, strict_smem_kb=96, b_share_pct=50),
+    dict(strict_kernel=1, entries_per_warp=0, threads_per_cta=256, strict_smem_kb=200, b_share_pct=0, ctas_per_sm=1),
+    dict(strict_kernel=0, entries_per_warp=512, diag_smem_kb=48, b_share_pct=50),
+    dict(strict_kernel=2, entries_per_warp=32, threads_per_cta=128, diag_smem_kb=0),
+    dict(strict_kernel=0, entries_per_warp=256, vec_per_lane=2, leaf_index=0),
+    dict(strict_kernel=0, entries_per_warp=64, vec_per_lane=2, leaf_index=0, diag_smem_kb=0),
+]
+
+
+@pytest.mark.parametrize("k", range(len(CONFIGS)))
+@pytest.mark.parametrize("case", ["zipf3", "unif4", "unif5_small_n"])
+def test_mttkrp_kernel_configs(k, case):
+    """Every kernel configuration (plain / pipelined / unfactorised, chunked / persistent, shared-memory rows)."""
+    sg = need_gpu()
+    if case == "zipf3":
+        T, R = synth.tensor3_zipf(3000, 80000, 4), 64
+    elif case == "unif4":
+        T, R = synth.tensor_uniform(4, 80, 30000, 5), 32
+    else:
+        T, R = synth.tensor_uniform(5, 20, 8000, 6), 16   # all of M and B fit in shared memory
+    e, _ = run_case(sg, T, R, cfg=CONFIGS[k])
+    assert e <= TOL_F32, e
+
+
+@pytest.mark.parametrize("order,n,nnz,rank", [(3, 3000, 80000, 64), (4, 80, 30000, 32), (5, 20, 8000, 16),
+                                              (5, 200_000, 20000, 8), (3, 2_000_000, 30000, 16)])
+@pytest.mark.parametrize("chunk", [32, 256])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_mttkrp_leaf_index(order, n, nnz, rank, chunk, bf16):
+    """The leaf position taken from the reversed, sorted copy of the strict stream (two-word keys included)."""
+    sg = need_gpu()
+    T = synth.tensor3_zipf(n, nnz, 12) if (order == 3 and n == 3000) else synth.tensor_uniform(order, n, nnz, 12)
+    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
+    X.add_leaf_index()
+    X.set_config(strict_kernel=0, entries_per_warp=chunk, leaf_index=1)
+    Bt, B32, Bused = factor(T.n, rank, 3, bf16)
+    M = host(X.mttkrp(Bt))
+    cidx, cval = oracle.canonicalize(order, T.n, T.idx, T.val)
+    ref, ra = oracle.mttkrp_enum(order, T.n, cidx, cval, Bused.astype(np.float64))
+    assert oracle.componentwise_error(M, ref, ra) <= TOL_F32
+
+
+def test_mttkrp_autotune_and_cache(tmp_path):
+    sg = need_gpu()
+    T = synth.tensor3_zipf(3000, 80000, 9)
+    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
+    B = dev(synth.factor_normal(T.n, 32, 9))
+    cache = str(tmp_path / "mt.txt")
+    cfg, ms = X.autotune(B, cache_path=cache)
+    assert ms > 0 and X.get_config() == cfg
+    X2 = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
+    cfg2, ms2 = X2.autotune(B, cache_path=cache)    # cache hit: same choice, no timing
+    assert cfg2 == cfg and abs(ms2 - ms) < 1e-3
+    cidx, cval = oracle.canonicalize(3, T.n, T.idx, T.val)
+    ref, ra = oracle.mttkrp_enum(3, T.n, cidx, cval, synth.factor_normal(T.n, 32, 9).astype(np.float64))
+    assert oracle.componentwise_error(host(X2.mttkrp(B)), ref, ra) <= TOL_F32
 
 
 def test_mttkrp_zipf_hot_rows():
