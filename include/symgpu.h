@@ -116,6 +116,20 @@ size_t sym_spmv_workspace_bytes(const sym_csr_upper* A);
 sym_status sym_spmv(const sym_csr_upper* A, const float* x, float* y, double* syprd, void* ws,
                     size_t ws_bytes, sym_stream_t stream);
 
+/* Allocation-free variant of sym_spmv (the paper has no counterpart: it is a
+ * service to callers that cannot allocate).  For callers that cannot hand the
+ * library any device memory: hosts whose pool allocator owns the whole device,
+ * code that must keep working once device memory is exhausted, or loops that
+ * must not call cudaMalloc because it can synchronise the device.  It computes
+ * exactly what sym_spmv computes; the per-block FP64 SYPRD partials live in a
+ * 256 KiB array compiled into the library, which every GPU that loads the
+ * library keeps until the process exits.  Limit: n <= 262,144 rows, otherwise
+ * SYM_E_UNSUPPORTED (use sym_spmv with a workspace).  The first call on a
+ * device looks up the array's device address (make it before any stream
+ * capture).  Calls share the array, so calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  Allocates nothing. */
+sym_status sym_spmv_noalloc(const sym_csr_upper* A, const float* x, float* y, double* syprd, sym_stream_t stream);
+
 /* Validates an upper CSR on the device; *bad [device, 1 int64] receives the
  * number of offending rows (0 = valid).  ws >= sym_spmv_workspace_bytes(A). */
 sym_status sym_csr_upper_check(const sym_csr_upper* A, int64_t* bad, sym_stream_t stream);

@@ -119,6 +119,7 @@ _SIGS = {
     "sym_profile_reset": ([], C.c_int),
     "sym_spmv_workspace_bytes": ([C.c_void_p], C.c_size_t),
     "sym_spmv": ([C.c_void_p] * 5 + [C.c_size_t, C.c_void_p], C.c_int),
+    "sym_spmv_noalloc": ([C.c_void_p] * 5, C.c_int),
     "sym_csr_upper_check": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_bellman_step": ([C.c_void_p] * 4, C.c_int),
     "sym_csr_expand_bytes": ([C.c_void_p, C.c_void_p], C.c_size_t),
@@ -267,6 +268,13 @@ def spmv(n, rowptr, col, val, x, y=None, syprd=False, ws=None, stream=None):
     check(lib().sym_spmv(C.byref(A), _ptr(x), _ptr(y), _ptr(s_out), _ptr(ws), ws.numel() if ws is not None else 0,
                          _stream(stream)), "sym_spmv")
     return (y, s_out) if syprd else y
+
+
+def spmv_noalloc(n, rowptr, col, val, x, y, syprd_out=None, stream=None):
+    """sym_spmv_noalloc: the same product with no workspace (y and syprd_out preallocated by the caller)."""
+    A = csr_upper(n, rowptr, col, val)
+    check(lib().sym_spmv_noalloc(C.byref(A), _ptr(x), _ptr(y), _ptr(syprd_out), _stream(stream)), "sym_spmv_noalloc")
+    return y
 
 
 def csr_upper_check(n, rowptr, col, val, stream=None) -> int:
