@@ -261,6 +261,10 @@ def run_ours(args):
     info = X.info()
     M = torch.empty((T.n, MAIN["rank"]), dtype=torch.float32, device=dev)
     ws_res = X.mttkrp_workspace(MAIN["rank"])
+    import tempfile
+    t0 = time.perf_counter()
+    tuned_cfg, tuned_ms = X.autotune(B, M=M, cache_path=os.path.join(tempfile.gettempdir(), "symgpu_tune.txt"))
+    tune_s = time.perf_counter() - t0
 
     step = lambda: X.mttkrp(B, M=M)
     for _ in range(args.warmup):
@@ -303,6 +307,7 @@ def run_ours(args):
         return
 
     extras = {"per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
+              "mttkrp_config": tuned_cfg, "autotune_s": tune_s,
               "canonicalise_ms": create_ms, "tensor": {k: info[k] for k in (
                   "nnz", "nnz_strict", "nnz_diag", "expanded_nnz", "root_fibers", "l2_fibers")}}
 
@@ -362,6 +367,14 @@ def run_ours(args):
     # ---- secondary rows
     if args.rows == "all" and D.rank == 0:
         extras["rows"] = secondary_rows(torch, sg, dev, flush, stream, hbm_peak)
+        try:
+            extras["rows"]["batched_ssymv_syprd_4096"] = batch_row(torch, sg, dev, flush, stream, hbm_peak)
+        except Exception as e:
+            extras["rows"]["batched_ssymv_syprd_4096"] = {"error": repr(e)}
+        try:
+            extras["rows"]["serving_poisson_2000rps"] = serving_row(torch, sg, dev)
+        except Exception as e:
+            extras["rows"]["serving_poisson_2000rps"] = {"error": repr(e)}
 
     out = {"metric": "canonical_nnz_per_s", "value": value, "unit": "canonical nnz/s", "n_gpus": D.ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -431,6 +444,173 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
     ms = float(np.mean(t))
     rows["ssymv_n2000_nnz20k"] = {"ms": ms, "canonical_nnz_per_s": A.nnz / (ms * 1e-3)}
     return rows
+
+
+def batch_row(torch, sg, dev, flush, stream, hbm_peak, count=4096, per_row=16, seed=3):
+    """4,096 independent symmetric matrices, n log-uniform on [256, 65536], 16 draws per row."""
+    import tempfile
+    sizes = synth.batch_sizes(count, 256, 65536, seed)
+    t0 = time.perf_counter()
+    batch = sg.make_batch(sizes, per_row, seed)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    rows = int(batch.host_row_off[-1])
+    nnz = int(batch.col.numel())
+    x = torch.from_numpy(synth.vector_uniform(rows, seed)).to(dev)
+    y = torch.empty_like(x)
+    sy = torch.empty(count, dtype=torch.float64, device=dev)
+    cache = os.path.join(tempfile.gettempdir(), "symgpu_tune.txt")
+    t0 = time.perf_counter()
+    cfg, tuned_ms = sg.autotune_batch(batch, x, y, sy, cache_path=cache)
+    tune_s = time.perf_counter() - t0
+    plan = sg.BatchPlan(batch, cfg)
+    plan.capture(x, y, sy)
+    for _ in range(3):
+        plan.launch()
+    sg.profile_reset()
+    sg.profile_enable(True)
+    t = timed_steps(torch, plan.launch, 10, flush, stream)
+    sg.profile_enable(False)
+    prof = sg.profile_read()
+    ms = float(np.mean(t))
+    kern_ms = prof.get("ssymv_batch", (1, 0.0))
+    alg = nnz * 8 + (rows + count) * 8 + rows * 4 * 3 + count * 8   # col+val, rowptr, x + y rmw, syprd
+    out = {"instances": count, "rows": rows, "upper_nnz": nnz, "generate_s": gen_s, "autotune_s": tune_s,
+           "tile_cfg": cfg.as_dict(), "graph_ms": ms, "canonical_nnz_per_s": nnz / (ms * 1e-3),
+           "effective_gbs": alg / (ms * 1e-3) / 1e9, "hbm_frac": alg / (ms * 1e-3) / 1e9 / hbm_peak}
+    # plain form: one sym_spmv launch per instance (each with its own upper CSR, local indices)
+    ro = batch.host_row_off
+    rp_h = batch.rowptr.cpu()
+    views = []
+    for b in range(count):
+        r0, r1 = int(ro[b]), int(ro[b + 1])
+        p0, p1 = int(rp_h[r0]), int(rp_h[r1])
+        rp = (batch.rowptr[r0:r1 + 1] - p0).to(torch.int32)
+        cl = batch.col[p0:p1] - r0
+        views.append((r1 - r0, rp, cl, batch.val[p0:p1], x[r0:r1], y[r0:r1]))
+    sy2 = torch.empty(count, dtype=torch.float64, device=dev)
+    wss = [sg.spmv_workspace(v[0], v[1], v[2], v[3]) for v in views]
+
+    def plain():
+        for b, (n_b, rp, cl, vl, xb, yb) in enumerate(views):
+            sg.spmv(n_b, rp, cl, vl, xb, y=yb, syprd=False, ws=wss[b])
+    plain()
+    tp = timed_steps(torch, plain, 3, flush, stream)
+    out["one_launch_per_instance_ms"] = float(np.mean(tp))
+    out["speedup_over_one_launch_per_instance"] = float(np.mean(tp)) / ms
+    # full-size parity on sampled instances (the oracle computes them one by one)
+    import oracle
+    plan.launch()
+    torch.cuda.synchronize()
+    yh, sh = y.cpu().numpy(), sy.cpu().numpy()
+    xh = x.cpu().numpy()
+    worst_y, worst_s = 0.0, 0.0
+    for b in list(range(0, count, max(1, count // 12)))[:12]:
+        r0, r1 = int(ro[b]), int(ro[b + 1])
+        p0, p1 = int(rp_h[r0]), int(rp_h[r1])
+        rp = (rp_h[r0:r1 + 1] - p0).numpy().astype(np.int32)
+        cl = (batch.col[p0:p1] - r0).cpu().numpy().astype(np.int32)
+        vl = batch.val[p0:p1].cpu().numpy()
+        yr, ya = oracle.ssymv(r1 - r0, rp, cl, vl, xh[r0:r1].astype(np.float64))
+        sr, sa = oracle.syprd(r1 - r0, rp, cl, vl, xh[r0:r1].astype(np.float64))
+        worst_y = max(worst_y, oracle.componentwise_error(yh[r0:r1], yr, ya))
+        worst_s = max(worst_s, abs(sh[b] - sr) / sa if sa > 0 else 0.0)
+    out["sampled_parity"] = {"instances": 12, "ssymv_componentwise": worst_y, "syprd_componentwise": worst_s}
+    plan.close()
+    return out
+
+
+def serving_row(torch, sg, dev, requests=1500, rate=2000.0, pool_size=32, seed=4):
+    """Poisson arrivals of MTTKRP requests; continuous batching vs one launch per request (FP32)."""
+    import threading
+    st = synth.Stream(seed, tag=77)
+    orders = np.where(st.uniform(pool_size) < 0.6, 3, np.where(st.uniform(pool_size) < 0.75, 4, 5))
+    ns = np.rint(np.exp(math.log(1e3) + st.uniform(pool_size) * math.log(200.0))).astype(np.int64)
+    nnzs = np.rint(np.exp(math.log(1e4) + st.uniform(pool_size) * math.log(5000.0))).astype(np.int64)
+    pool = []
+    t0 = time.perf_counter()
+    for k in range(pool_size):
+        idx, val = sg.gen_coords(int(orders[k]), int(ns[k]), int(nnzs[k]), seed * 1000 + k)
+        X = sg.SymTensor(idx, val, int(ns[k]), dup=sg.DUP_KEEP_EQUAL)
+        del idx, val
+        pool.append(X)
+    torch.cuda.synchronize()
+    pool_s = time.perf_counter() - t0
+    ranks = [8, 16, 32, 64]
+    facs = {}
+    for k, X in enumerate(pool):
+        for R in ranks:
+            B = torch.randn((X.n, R), device=dev, generator=torch.Generator(device=dev).manual_seed(k * 7 + R))
+            B /= math.sqrt(R)
+            facs[(k, R, "f32")] = B
+            facs[(k, R, "bf16")] = B.to(torch.bfloat16)
+    # trace
+    gaps = -np.log(st.uniform_open0(requests)) / rate
+    arrive = np.cumsum(gaps)
+    which = (st.uniform(requests) * pool_size).astype(np.int64)
+    rsel = np.array(ranks)[(st.uniform(requests) * 4).astype(np.int64)]
+    dts = np.where(st.uniform(requests) < 0.5, "bf16", "f32")
+    work_nnz = float(sum(pool[w].nnz for w in which))
+
+    def summarize(lat, span):
+        lat = np.sort(np.asarray(lat))
+        return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "throughput_req_per_s": requests / span, "canonical_nnz_per_s": work_nnz / span}
+
+    # continuous batching server
+    S = sg.Server(max_slots=8, max_rank=64, hbm_budget_bytes=120 << 30, small_nnz=1_000_000)
+    outs = [None] * requests
+    tickets = [None] * requests
+    base = time.perf_counter() + 0.05
+    clock_off = None
+
+    def submitter():
+        for i in range(requests):
+            while time.perf_counter() < base + arrive[i]:
+                pass
+            B = facs[(int(which[i]), int(rsel[i]), dts[i])]
+            M = torch.empty((pool[which[i]].n, int(rsel[i])), device=dev)
+            outs[i] = M
+            tickets[i] = S.submit(pool[which[i]], B, M, residual=True, tag=i)
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    done_ns = []
+    for i in range(requests):
+        r = S.wait(tickets[i], 120.0)
+        assert r["status"] == 0
+        done_ns.append(r["t_done_ns"])
+    stats = S.stats()
+    S.close()
+    # host steady clock (ns) vs perf_counter: measure the offset once
+    import ctypes
+    t_ref_ns = time.monotonic_ns()
+    t_ref_pc = time.perf_counter()
+    to_pc = lambda ns_: t_ref_pc + (ns_ - t_ref_ns) * 1e-9
+    lat = [to_pc(done_ns[i]) - (base + arrive[i]) for i in range(requests)]
+    span = max(to_pc(d) for d in done_ns) - base
+    cb = summarize(lat, span)
+    cb["server_stats"] = stats
+    # plain: one launch per request on one stream, FP32 factors, in arrival order
+    torch.cuda.synchronize()
+    base = time.perf_counter() + 0.05
+    lat2 = []
+    for i in range(requests):
+        while time.perf_counter() < base + arrive[i]:
+            pass
+        X = pool[which[i]]
+        X.mttkrp(facs[(int(which[i]), int(rsel[i]), "f32")], residual=True)
+        torch.cuda.synchronize()
+        lat2.append(time.perf_counter() - (base + arrive[i]))
+    span2 = time.perf_counter() - base
+    plain = summarize(lat2, span2)
+    pool_nnz = int(sum(X_.nnz for X_ in pool))
+    for X in pool:
+        X.close()
+    return {"requests": requests, "rate_req_per_s": rate, "pool": {"tensors": pool_size, "build_s": pool_s,
+            "canonical_nnz": pool_nnz, "orders": [int(o) for o in orders]},
+            "offered_canonical_nnz_per_s": work_nnz / arrive[-1],
+            "continuous_batching": cb, "one_launch_per_request_f32": plain}
 
 
 def main():

@@ -325,13 +325,15 @@ typedef enum {
     SYM_MTTKRP_PLAIN = 0,        /* CSF-factorised, chunked warps, reductions to global memory */
     SYM_MTTKRP_PIPELINED = 1,    /* the same with the next leaf gather issued early; chunked or persistent;
                                     optional shared-memory hot rows */
-    SYM_MTTKRP_UNFACTORISED = 2  /* one entry per lane group, every position updated separately */
+    SYM_MTTKRP_UNFACTORISED = 2, /* one entry per lane group, every position updated separately */
+    SYM_MTTKRP_STAGED = 3        /* the plain kernel with the next batch's leaf factor rows copied into a
+                                    shared-memory double buffer (cp.async) while the current batch runs */
 } sym_mttkrp_kernel;
 typedef struct {
     int32_t strict_kernel;     /* sym_mttkrp_kernel for the strict stream */
     int32_t entries_per_warp;  /* work chunk per warp, a multiple of 32; 0 = persistent contiguous slices
                                   (pipelined kernel only) */
-    int32_t threads_per_cta;   /* pipelined / unfactorised kernels: 64..512 */
+    int32_t threads_per_cta;   /* pipelined / unfactorised / staged kernels: 64..512 */
     int32_t ctas_per_sm;       /* persistent grids: CTAs per SM */
     int32_t strict_smem_kb;    /* pipelined kernel: shared memory per CTA for hot (low-index) rows, 0 = none */
     int32_t diag_smem_kb;      /* diagonal stream: the same, 0 = none */

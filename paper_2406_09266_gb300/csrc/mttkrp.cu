@@ -222,7 +222,7 @@ sym_status mttkrp_core(const sym_tensor_s* X, const void* B, bool bf16, int R, i
 
 sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
     if (!c) return SYM_E_INVALID;
-    if (c->strict_kernel < 0 || c->strict_kernel > 2) return SYM_E_INVALID;
+    if (c->strict_kernel < 0 || c->strict_kernel > 3) return SYM_E_INVALID;
     if (c->entries_per_warp < 0 || c->entries_per_warp % 32 != 0 || c->entries_per_warp > (1 << 24))
         return SYM_E_INVALID;
     if (c->entries_per_warp == 0 && c->strict_kernel != SYM_MTTKRP_PIPELINED) return SYM_E_INVALID;
@@ -373,6 +373,8 @@ extern "C" sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype
     }
     if (rank >= 8)
         for (int chunk : {128, 256, 512}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, 0, 2});
+    for (int chunk : {128, 256, 512})
+        for (int thr : {128, 256}) cands.push_back({SYM_MTTKRP_STAGED, chunk, thr, 2, 0, 0, 0, 0, 1});
     for (int chunk : {128, 256}) cands.push_back({SYM_MTTKRP_PIPELINED, chunk, 256, 2, 0, 0, 0, 0, 1});
     cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 0, 0, 0, 0, 1});
     cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 96, 0, 50, 0, 1});

@@ -337,6 +337,163 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict_wide(
     }
 }
 
+// ---------------------------------------------------------------- staged leaf rows
+
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Bytes of one staged leaf row slice held by one lane (4 columns).
+template <bool BF16>
+constexpr int stage_lane_bytes() { return BF16 ? 8 : 16; }
+
+// The plain kernel with the leaf factor rows of the NEXT batch of 32 entries
+// copied into a per-warp shared-memory double buffer (cp.async) while the
+// current batch is processed, so a warp keeps up to 32 row copies in flight
+// without holding them in registers.  Each lane copies, and later reads, only
+// its own 4 columns of each row, so no synchronisation beyond the cp.async
+// group wait is needed.
+template <int N, int KW, int L, bool BF16>
+__global__ void __launch_bounds__(256) k_mttkrp_strict_staged(
+    const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
+    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
+    int64_t chunk) {
+    extern __shared__ float4 stage_mem[];
+    constexpr int LV = N - 1;
+    constexpr int LB = stage_lane_bytes<BF16>();
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L;
+    const int s_lane = lane % L;
+    const int col = 4 * s_lane;
+    const bool on = col < R;
+    // per warp: 2 buffers x 32 slots x L lane slices of LB bytes
+    char* wbuf = reinterpret_cast<char*>(stage_mem) + (size_t)(threadIdx.x >> 5) * (2 * 32 * L * LB);
+    int64_t start, end;
+    warp_range(nnz, chunk, &start, &end);
+    if (start >= end) return;
+
+    // loads the keys of the batch starting at b0 (lane e holds entry b0+e) and
+    // issues the copies of its leaf rows into buffer `buf`
+    auto fetch = [&](int64_t b0, int buf, uint64_t& mlo, uint64_t& mhi, float& mv) {
+        const int64_t e = b0 + lane;
+        mlo = 0;
+        mhi = 0;
+        mv = 0.f;
+        int32_t leaf = 0;
+        if (e < end) {
+            mlo = klo[e];
+            if (KW == 2) mhi = khi[e];
+            mv = val[e];
+            int32_t c[N];
+            decode_entry<N, KW>(mlo, mhi, bits, c);
+            leaf = c[N - 1];
+        }
+#pragma unroll 1
+        for (int t = 0; t < L; ++t) {
+            const int slot = g * L + t;
+            const int32_t row = __shfl_sync(0xffffffffu, leaf, slot);
+            if (on && b0 + slot < end) {
+                char* dst = wbuf + ((size_t)(buf * 32 + slot) * L + s_lane) * LB;
+                if (BF16)
+                    cp_async_8(dst, static_cast<const char*>(B) + ((int64_t)row * ldb + col) * 2);
+                else
+                    cp_async_16(dst, static_cast<const char*>(B) + ((int64_t)row * ldb + col) * 4);
+            }
+        }
+        cp_async_commit();
+    };
+
+    int32_t cur[LV];
+    float4 Brow[LV], P[LV], T[LV];
+#pragma unroll
+    for (int q = 0; q < LV; ++q) {
+        cur[q] = -1;
+        Brow[q] = f4_zero();
+        P[q] = f4_zero();
+        T[q] = f4_zero();
+    }
+    bool have = false;
+    uint64_t mlo, mhi;
+    float mv;
+    fetch(start, 0, mlo, mhi, mv);
+    int buf = 0;
+    for (int64_t b0 = start; b0 < end; b0 += 32, buf ^= 1) {
+        uint64_t nlo = 0, nhi = 0;
+        float nv = 0.f;
+        if (b0 + 32 < end)
+            fetch(b0 + 32, buf ^ 1, nlo, nhi, nv);
+        else
+            cp_async_commit();  // keep one group per batch so the wait below always targets this batch
+        cp_async_wait_prev();
+#pragma unroll 1
+        for (int t = 0; t < L; ++t) {
+            const int src = g * L + t;
+            const uint64_t lo = __shfl_sync(0xffffffffu, mlo, src);
+            const uint64_t hi = (KW == 2) ? __shfl_sync(0xffffffffu, mhi, src) : 0ull;
+            const float v = __shfl_sync(0xffffffffu, mv, src);
+            if (b0 + src >= end || !on) continue;
+            int32_t c[N];
+            decode_entry<N, KW>(lo, hi, bits, c);
+            int d = LV;
+#pragma unroll
+            for (int q = LV - 1; q >= 0; --q)
+                if (!have || c[q] != cur[q]) d = q;
+            if (d < LV) {
+                if (have) {
+#pragma unroll
+                    for (int q = LV - 1; q >= 0; --q) {
+                        if (q >= d) {
+                            float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+                            red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+                            if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+                            T[q] = f4_zero();
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < LV; ++q) {
+                    if (q >= d) {
+                        cur[q] = c[q];
+                        Brow[q] = load_row4<BF16>(B, c[q], ldb, col);
+                        P[q] = (q > 0) ? f4_mul(P[q - 1], Brow[q]) : Brow[q];
+                    }
+                }
+                have = true;
+            }
+            const char* sp = wbuf + ((size_t)(buf * 32 + src) * L + s_lane) * LB;
+            float4 bl;
+            if (BF16) {
+                const uint2 u = *reinterpret_cast<const uint2*>(sp);
+                bl = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                                 __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+            } else {
+                bl = *reinterpret_cast<const float4*>(sp);
+            }
+            T[LV - 1] = f4_fmas(bl, v, T[LV - 1]);
+            red_add_f4(M + (int64_t)c[N - 1] * ldm + col, f4_scale(P[LV - 1], w * v));
+        }
+        mlo = nlo;
+        mhi = nhi;
+        mv = nv;
+    }
+    if (have && on) {
+#pragma unroll
+        for (int q = LV - 1; q >= 0; --q) {
+            float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+            red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+            if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Same computation with a one-deep software pipeline (the next entry's leaf
 // factor row is requested before the current entry is processed), a choice of
 // chunked or persistent work ranges, and optional shared-memory hot rows for M
@@ -591,6 +748,20 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             k_mttkrp_strict_pipe<N, KW, L, BF16><<<grid, threads, sp.bytes, s>>>(
                 X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
                 std::max<int64_t>(0, cfg.entries_per_warp), sp.H, sp.HB);
+        } else if (cfg.strict_kernel == SYM_MTTKRP_STAGED) {
+            const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
+            const size_t per_warp = (size_t)2 * 32 * L * stage_lane_bytes<BF16>();
+            int st_threads = threads;
+            while (st_threads > 64 && per_warp * (st_threads / 32) > 96 * 1024) st_threads /= 2;
+            const size_t smem = per_warp * (st_threads / 32);
+            if (smem > 48 * 1024)
+                SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_strict_staged<N, KW, L, BF16>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int64_t warps = (ns + chunk - 1) / chunk;
+            const unsigned grid = (unsigned)((warps * 32 + st_threads - 1) / st_threads);
+            SYM_PROF("mttkrp_strict", s);
+            k_mttkrp_strict_staged<N, KW, L, BF16><<<grid, st_threads, smem, s>>>(
+                X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
         } else {
             const int64_t gpc = (threads / 32) * (32 / L);
             const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ns + gpc - 1) / gpc,

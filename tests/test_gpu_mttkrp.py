@@ -37,6 +37,20 @@ def test_mttkrp_f32(order, n, nnz, rank, vpl):
     assert e <= TOL_F32, e
 
 
+@pytest.mark.parametrize("order,n,nnz", [(2, 300, 3000), (3, 500, 20000), (4, 60, 12000), (5, 25, 8000)])
+@pytest.mark.parametrize("rank", [4, 12, 32, 64, 128])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_mttkrp_staged(order, n, nnz, rank, bf16):
+    """The cp.async-staged kernel: every rank width, both factor types, ragged batch tails."""
+    sg = need_gpu()
+    T = synth.tensor_uniform(order, n, nnz + 7, 30 + order)
+    e32, eb = run_case(sg, T, rank, bf16=bf16, cfg=dict(strict_kernel=3, entries_per_warp=96, leaf_index=0))
+    if bf16:
+        assert e32 <= TOL_BF16 and eb <= TOL_F32, (e32, eb)
+    else:
+        assert e32 <= TOL_F32, e32
+
+
 @pytest.mark.parametrize("order,n,nnz,rank", [(3, 500, 20000, 64), (4, 60, 12000, 32), (5, 25, 8000, 16),
                                               (3, 400, 5000, 8)])
 def test_mttkrp_bf16(order, n, nnz, rank):
@@ -65,6 +79,9 @@ CONFIGS = [
     dict(strict_kernel=2, entries_per_warp=32, threads_per_cta=128, diag_smem_kb=0),
     dict(strict_kernel=0, entries_per_warp=256, vec_per_lane=2, leaf_index=0),
     dict(strict_kernel=0, entries_per_warp=64, vec_per_lane=2, leaf_index=0, diag_smem_kb=0),
+    dict(strict_kernel=3, entries_per_warp=256, threads_per_cta=256, leaf_index=0),
+    dict(strict_kernel=3, entries_per_warp=32, threads_per_cta=64, leaf_index=0, diag_smem_kb=0),
+    dict(strict_kernel=3, entries_per_warp=1024, threads_per_cta=512, leaf_index=0),
 ]
 
 
