@@ -263,7 +263,12 @@ def run_ours(args):
     ws_res = X.mttkrp_workspace(MAIN["rank"])
     import tempfile
     t0 = time.perf_counter()
-    tuned_cfg, tuned_ms = X.autotune(B, M=M, cache_path=os.path.join(tempfile.gettempdir(), "symgpu_tune.txt"))
+    if args.kernel_only:
+        # profiling mode: a fixed configuration (the one the autotuner picks for this workload)
+        X.set_config(strict_kernel=0, entries_per_warp=512, diag_smem_kb=48, leaf_index=0)
+        tuned_cfg, tuned_ms = X.get_config(), 0.0
+    else:
+        tuned_cfg, tuned_ms = X.autotune(B, M=M, cache_path=os.path.join(tempfile.gettempdir(), "symgpu_tune.txt"))
     tune_s = time.perf_counter() - t0
 
     step = lambda: X.mttkrp(B, M=M)
@@ -613,6 +618,25 @@ def serving_row(torch, sg, dev, requests=1500, rate=2000.0, pool_size=32, seed=4
             "continuous_batching": cb, "one_launch_per_request_f32": plain}
 
 
+def run_batch_only(args):
+    """Profiling mode for the batched SSYMV: tile kernel, fixed shape, plain runs (no graph)."""
+    import torch
+
+    import paper_2406_09266_gb300 as sg
+    sg.load()
+    dev = torch.device("cuda")
+    sizes = synth.batch_sizes(args.batch_only, 256, 65536, 3)
+    batch = sg.make_batch(sizes, 16, 3)
+    x = torch.from_numpy(synth.vector_uniform(int(batch.host_row_off[-1]), 3)).to(dev)
+    y = torch.empty_like(x)
+    sy = torch.empty(len(sizes), dtype=torch.float64, device=dev)
+    plan = sg.BatchPlan(batch, sg.TileCfg(256, 8, 256, 8, 0, 0))
+    for _ in range(args.warmup + args.steps):
+        plan.run(x, y, sy)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "batch-only (profiling)", "instances": len(sizes), "upper_nnz": int(batch.col.numel())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -622,12 +646,17 @@ def main():
     ap.add_argument("--rows", default="all", choices=["main", "all"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--kernel-only", action="store_true",
-                    help="profiling mode: setup, warm-up and the timed steps only (no e2e or extra rows)")
+                    help="profiling mode: setup, warm-up and the timed steps only (no e2e or extra rows), with "
+                         "the MTTKRP configuration fixed instead of autotuned")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="INSTANCES",
+                    help="profiling mode: build a batch of this many instances and run the batched SSYMV a few times")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch_only:
+        run_batch_only(args)
     else:
         run_ours(args)
 

@@ -179,6 +179,10 @@ typedef struct {
     int32_t lanes_per_row;    /* 1..32, power of two: lanes cooperating on one row */
     int32_t threads_per_cta;  /* 128..1024, multiple of 32 */
     int32_t ctas_per_sm;      /* persistent CTAs per SM */
+    int32_t local_smem_kb;    /* instances whose n floats fit in this much shared memory are processed whole
+                                 by one CTA with y (and x, when 2n floats fit) on chip; 0 = all on tiles */
+    int32_t tile_order;       /* 0: tiles in instance order; 1: interleaved across instances, so CTAs that run
+                                 together reduce into different instances' y */
 } sym_tile_cfg;
 
 /* A plan: the tile list and the FP64 partial buffers, carved from `arena`. */

@@ -361,7 +361,7 @@ constexpr int stage_lane_bytes() { return BF16 ? 8 : 16; }
 // its own 4 columns of each row, so no synchronisation beyond the cp.async
 // group wait is needed.
 template <int N, int KW, int L, bool BF16>
-__global__ void __launch_bounds__(256) k_mttkrp_strict_staged(
+__global__ void __launch_bounds__(512) k_mttkrp_strict_staged(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
     int64_t chunk) {

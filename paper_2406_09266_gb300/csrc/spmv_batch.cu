@@ -28,6 +28,7 @@ struct Tile {
     int64_t row0;      // first global row
     int32_t rows;      // rows in the tile
     int32_t inst;      // instance id
+    int64_t slot;      // index of this tile's SYPRD partial (tiles of one instance are contiguous slots)
 };
 
 struct sym_batch_plan_s {
@@ -38,6 +39,10 @@ struct sym_batch_plan_s {
     int64_t* tile_first;      // [device] first tile of each instance (count + 1)
     double* tile_partials;    // [device] FP64 SYPRD partial per tile
     unsigned long long* counter;  // [device] next tile
+    int64_t n_local;              // instances processed whole by one CTA with y (and x) in shared memory
+    int64_t* local_order;         // [device] those instances, largest first
+    unsigned long long* local_counter;  // [device] next local instance
+    int local_cap;                // floats of shared memory per CTA for the local path
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int device;
@@ -108,18 +113,97 @@ __global__ void k_ssymv_batch(const Tile* __restrict__ tiles, int64_t ntiles, co
             if (threadIdx.x == 0) {
                 float tot = 0.f;
                 for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += s_red[k];
-                tile_partials[t] = (double)tot;
+                tile_partials[tile.slot] = (double)tot;
             }
         }
     }
 }
 
-// syprd[b] = sum of instance b's tile partials, FP64, fixed order.
+// Instance-resident path: one CTA owns a whole instance at a time, with its
+// y in shared memory (mirrored updates become shared-memory adds, and y is
+// written back with plain stores) and its x too when both fit.  Instances are
+// taken largest first.  SYPRD: per-row FP32 terms accumulated in FP64 per
+// thread, one FP64 block sum per instance (no cross-block partials needed).
+template <int L, bool SYPRD>
+__global__ void __launch_bounds__(1024) k_ssymv_batch_local(
+    const int64_t* __restrict__ order, int64_t n_local, const int64_t* __restrict__ row_off,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
+    const float* __restrict__ x, float* __restrict__ y, double* __restrict__ syprd,
+    unsigned long long* __restrict__ counter, int cap) {
+    extern __shared__ float sm_local[];
+    __shared__ int64_t s_item;
+    __shared__ double s_red[32];
+    const int lane = threadIdx.x & 31;
+    const int s = lane % L;
+    const int groups = blockDim.x / L;
+    const int g = threadIdx.x / L;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= n_local) break;
+        const int64_t b = order[item];
+        const int64_t r0 = row_off[b];
+        const int n = (int)(row_off[b + 1] - r0);
+        const bool xs = 2 * n <= cap;  // x staged too
+        float* ys = sm_local;
+        float* xsm = sm_local + n;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            ys[k] = 0.f;
+            if (xs) xsm[k] = x[r0 + k];
+        }
+        __syncthreads();
+        double syp = 0.0;
+        for (int rb = 0; rb < n; rb += groups) {  // uniform trip count: full warps at the shuffles
+            const int r = rb + g;
+            const bool act = r < n;
+            float rowsum = 0.f, rs = 0.f, xi = 0.f;
+            if (act) {
+                const int64_t i = r0 + r;
+                xi = xs ? xsm[r] : x[i];
+                const int64_t p1 = rowptr[i + 1];
+                for (int64_t p = rowptr[i] + s; p < p1; p += L) {
+                    const int jl = (int)(col[p] - r0);
+                    const float a = val[p];
+                    const float t = a * (xs ? xsm[jl] : x[r0 + jl]);
+                    rowsum += t;
+                    if (jl != r) {
+                        atomicAdd(&ys[jl], a * xi);
+                        if (SYPRD) rs += 2.f * t;
+                    } else if (SYPRD) {
+                        rs += t;
+                    }
+                }
+            }
+            rowsum = gsum<L>(rowsum);
+            if (act && s == 0 && rowsum != 0.f) atomicAdd(&ys[r], rowsum);
+            if (SYPRD) syp += (double)(rs * xi);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) y[r0 + k] = ys[k];
+        if (SYPRD) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) syp += __shfl_xor_sync(0xffffffffu, syp, o);
+            if (lane == 0) s_red[threadIdx.x >> 5] = syp;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += s_red[k];
+                syprd[b] = tot;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// syprd[b] = sum of instance b's tile partials, FP64, fixed order (instances
+// without tiles are handled by the instance-resident path).
 __global__ void k_batch_syprd(const double* __restrict__ tile_partials, const int64_t* __restrict__ tile_first,
                               int64_t count, double* __restrict__ syprd) {
     const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= count) return;
+    if (tile_first[b] == tile_first[b + 1]) return;
     double acc = 0.0;
     for (int64_t t = tile_first[b] + lane; t < tile_first[b + 1]; t += 32) acc += tile_partials[t];
 #pragma unroll
@@ -127,22 +211,36 @@ __global__ void k_batch_syprd(const double* __restrict__ tile_partials, const in
     if (lane == 0) syprd[b] = acc;
 }
 
-int64_t count_tiles(const int64_t* host_row_off, int64_t count, int rows_per_tile) {
+// Shared-memory capacity (floats) of the instance-resident path; 0 disables it.
+int local_capacity(const sym_tile_cfg* cfg) {
+    if (!cfg->local_smem_kb) return 0;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, current_device()) != cudaSuccess)
+        return 0;
+    const int kb = std::min(cfg->local_smem_kb, (optin - 2048) / 1024);
+    return kb > 0 ? kb * 1024 / 4 : 0;
+}
+
+bool is_local(int64_t n, int cap) { return cap > 0 && n <= cap; }
+
+int64_t count_tiles(const int64_t* host_row_off, int64_t count, int rows_per_tile, int cap) {
     int64_t nt = 0;
     for (int64_t b = 0; b < count; ++b) {
         const int64_t n = host_row_off[b + 1] - host_row_off[b];
-        nt += (n + rows_per_tile - 1) / rows_per_tile;
+        if (!is_local(n, cap)) nt += (n + rows_per_tile - 1) / rows_per_tile;
     }
     return nt;
 }
 
 template <typename C>
 void layout_plan(C& c, int64_t ntiles, int64_t count, Tile** tiles, int64_t** first, double** parts,
-                 unsigned long long** counter) {
+                 unsigned long long** counter, int64_t** local_order, unsigned long long** local_counter) {
     *tiles = c.template take<Tile>((size_t)std::max<int64_t>(ntiles, 1));
     *first = c.template take<int64_t>((size_t)count + 1);
     *parts = c.template take<double>((size_t)std::max<int64_t>(ntiles, 1));
     *counter = c.template take<unsigned long long>(1);
+    *local_order = c.template take<int64_t>((size_t)std::max<int64_t>(count, 1));
+    *local_counter = c.template take<unsigned long long>(1);
 }
 
 struct NullCarver {
@@ -161,16 +259,56 @@ bool cfg_ok(const sym_tile_cfg* c) {
     if (c->threads_per_cta < 64 || c->threads_per_cta > 1024 || c->threads_per_cta % 32) return false;
     if (c->rows_per_tile < 1 || c->rows_per_tile > (1 << 20)) return false;
     if (c->ctas_per_sm < 1 || c->ctas_per_sm > 32) return false;
+    if (c->local_smem_kb < 0 || c->local_smem_kb > 256) return false;
+    if (c->tile_order != 0 && c->tile_order != 1) return false;
     return true;
+}
+
+sym_status batch_enqueue_local(sym_batch_plan_s* P, const float* x, float* y, double* syprd, cudaStream_t s) {
+    if (P->n_local == 0) return SYM_OK;
+    SYM_CUDA(cudaMemsetAsync(P->local_counter, 0, sizeof(unsigned long long), s));
+    const int threads = P->cfg.threads_per_cta >= 1024 ? 1024 : 512;
+    const size_t smem = (size_t)P->local_cap * sizeof(float);
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)sm_count(), P->n_local);
+    SYM_PROF("ssymv_batch_local", s);
+#define SYM_LOCAL_L(LL)                                                                                          \
+    case LL:                                                                                                     \
+        if (syprd) {                                                                                             \
+            SYM_CUDA(cudaFuncSetAttribute(k_ssymv_batch_local<LL, true>,                                         \
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
+            k_ssymv_batch_local<LL, true><<<grid, threads, smem, s>>>(P->local_order, P->n_local, P->A.row_off, \
+                                                                      P->A.rowptr, P->A.col, P->A.val, x, y,   \
+                                                                      syprd, P->local_counter, P->local_cap);  \
+        } else {                                                                                                 \
+            SYM_CUDA(cudaFuncSetAttribute(k_ssymv_batch_local<LL, false>,                                        \
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
+            k_ssymv_batch_local<LL, false><<<grid, threads, smem, s>>>(P->local_order, P->n_local,              \
+                                                                       P->A.row_off, P->A.rowptr, P->A.col,    \
+                                                                       P->A.val, x, y, syprd,                  \
+                                                                       P->local_counter, P->local_cap);        \
+        }                                                                                                        \
+        break;
+    switch (P->cfg.lanes_per_row) {
+        SYM_LOCAL_L(1)
+        SYM_LOCAL_L(2)
+        SYM_LOCAL_L(4)
+        SYM_LOCAL_L(8)
+        SYM_LOCAL_L(16)
+        SYM_LOCAL_L(32)
+        default: return SYM_E_INVALID;
+    }
+#undef SYM_LOCAL_L
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
 }
 
 sym_status batch_enqueue(sym_batch_plan_s* P, const float* x, float* y, double* syprd, cudaStream_t s) {
     SYM_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(unsigned long long), s));
     SYM_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)P->A.total_rows, s));
-    if (P->ntiles == 0) {
-        if (syprd && P->A.count > 0) SYM_CUDA(cudaMemsetAsync(syprd, 0, sizeof(double) * P->A.count, s));
-        return SYM_OK;
-    }
+    if (syprd && P->A.count > 0) SYM_CUDA(cudaMemsetAsync(syprd, 0, sizeof(double) * P->A.count, s));
+    sym_status lst = batch_enqueue_local(P, x, y, syprd, s);
+    if (lst != SYM_OK) return lst;
+    if (P->ntiles == 0) return SYM_OK;
     const int threads = P->cfg.threads_per_cta;
     int dev = 0;
     SYM_CUDA(cudaGetDevice(&dev));
@@ -208,6 +346,8 @@ sym_status batch_enqueue(sym_batch_plan_s* P, const float* x, float* y, double* 
     return SYM_OK;
 }
 
+
+
 sym_status validate_batch(const sym_csr_batch* A, const int64_t* host_row_off) {
     if (!A || !host_row_off || A->count < 0 || A->total_rows < 0 || A->total_nnz < 0) return SYM_E_INVALID;
     if (A->count > 0 && (!A->row_off || !A->rowptr)) return SYM_E_INVALID;
@@ -233,7 +373,10 @@ extern "C" size_t sym_spmv_batch_plan_bytes(const sym_csr_batch* A, const int64_
     int64_t* f;
     double* p;
     unsigned long long* k;
-    layout_plan(c, count_tiles(host_row_off, A->count, cfg->rows_per_tile), A->count, &t, &f, &p, &k);
+    int64_t* lo;
+    unsigned long long* lc;
+    layout_plan(c, count_tiles(host_row_off, A->count, cfg->rows_per_tile, local_capacity(cfg)), A->count, &t, &f,
+                &p, &k, &lo, &lc);
     return c.s.used;
 }
 
@@ -246,9 +389,11 @@ extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const i
     if (st != SYM_OK) return st;
     if (!cfg_ok(cfg) || !arena || !aligned(arena, 256)) return SYM_E_INVALID;
     if (arena_bytes < sym_spmv_batch_plan_bytes(A, host_row_off, cfg)) return SYM_E_NOMEM;
-    const int64_t ntiles = count_tiles(host_row_off, A->count, cfg->rows_per_tile);
+    const int cap = local_capacity(cfg);
+    const int64_t ntiles = count_tiles(host_row_off, A->count, cfg->rows_per_tile, cap);
     std::vector<Tile> tiles;
     std::vector<int64_t> first((size_t)A->count + 1);
+    std::vector<int64_t> local;
     try {
         tiles.reserve((size_t)ntiles);
     } catch (...) {
@@ -256,11 +401,36 @@ extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const i
     }
     for (int64_t b = 0; b < A->count; ++b) {
         first[(size_t)b] = (int64_t)tiles.size();
+        if (is_local(host_row_off[b + 1] - host_row_off[b], cap)) {
+            local.push_back(b);
+            continue;
+        }
         for (int64_t r = host_row_off[b]; r < host_row_off[b + 1]; r += cfg->rows_per_tile)
             tiles.push_back(Tile{r, (int32_t)std::min<int64_t>(cfg->rows_per_tile, host_row_off[b + 1] - r),
-                                 (int32_t)b});
+                                 (int32_t)b, (int64_t)tiles.size()});
     }
     first[(size_t)A->count] = (int64_t)tiles.size();
+    if (cfg->tile_order == 1) {
+        // round-robin over instances: tile k of every instance, then tile k+1, ...
+        std::vector<Tile> inter;
+        inter.reserve(tiles.size());
+        for (int64_t k = 0;; ++k) {
+            bool any = false;
+            for (int64_t b = 0; b < A->count; ++b) {
+                const int64_t t = first[(size_t)b] + k;
+                if (t < first[(size_t)b + 1]) {
+                    inter.push_back(tiles[(size_t)t]);
+                    any = true;
+                }
+            }
+            if (!any) break;
+        }
+        tiles.swap(inter);
+    }
+    // largest instances first on the instance-resident path
+    std::stable_sort(local.begin(), local.end(), [&](int64_t a, int64_t b) {
+        return host_row_off[a + 1] - host_row_off[a] > host_row_off[b + 1] - host_row_off[b];
+    });
     sym_batch_plan_s* P = new (std::nothrow) sym_batch_plan_s();
     if (!P) return SYM_E_NOMEM;
     P->A = *A;
@@ -270,12 +440,17 @@ extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const i
     P->exec = nullptr;
     P->device = current_device();
     Carver c(arena, arena_bytes);
-    layout_plan(c, ntiles, A->count, &P->tiles, &P->tile_first, &P->tile_partials, &P->counter);
+    layout_plan(c, ntiles, A->count, &P->tiles, &P->tile_first, &P->tile_partials, &P->counter, &P->local_order,
+                &P->local_counter);
+    P->n_local = (int64_t)local.size();
+    P->local_cap = cap;
     cudaStream_t s = as_stream(stream);
     cudaError_t e = cudaSuccess;
     if (ntiles > 0) e = cudaMemcpyAsync(P->tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(P->tile_first, first.data(), sizeof(int64_t) * first.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !local.empty())
+        e = cudaMemcpyAsync(P->local_order, local.data(), sizeof(int64_t) * local.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         delete P;
@@ -355,7 +530,7 @@ std::string cache_key(const sym_csr_batch* A) {
     for (auto& ch : name)
         if (ch == ' ') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof(buf), "ssymv_batch|%s|%lld|%lld|%lld", name.c_str(), (long long)A->count,
+    snprintf(buf, sizeof(buf), "ssymv_batch3|%s|%lld|%lld|%lld", name.c_str(), (long long)A->count,
              (long long)A->total_rows, (long long)A->total_nnz);
     return buf;
 }
@@ -370,8 +545,8 @@ bool cache_lookup(const char* path, const std::string& key, sym_tile_cfg* cfg, f
         char k[300];
         sym_tile_cfg c;
         float t;
-        if (sscanf(line, "%299s %d %d %d %d %f", k, &c.rows_per_tile, &c.lanes_per_row, &c.threads_per_cta,
-                   &c.ctas_per_sm, &t) == 6 &&
+        if (sscanf(line, "%299s %d %d %d %d %d %d %f", k, &c.rows_per_tile, &c.lanes_per_row, &c.threads_per_cta,
+                   &c.ctas_per_sm, &c.local_smem_kb, &c.tile_order, &t) == 8 &&
             key == k && cfg_ok(&c)) {
             *cfg = c;
             *ms = t;
@@ -386,8 +561,8 @@ void cache_store(const char* path, const std::string& key, const sym_tile_cfg& c
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), c.rows_per_tile, c.lanes_per_row, c.threads_per_cta,
-            c.ctas_per_sm, ms);
+    fprintf(f, "%s %d %d %d %d %d %d %.6f\n", key.c_str(), c.rows_per_tile, c.lanes_per_row, c.threads_per_cta,
+            c.ctas_per_sm, c.local_smem_kb, c.tile_order, ms);
     fclose(f);
 }
 
@@ -408,20 +583,26 @@ extern "C" sym_status sym_autotune_spmv_batch(const sym_csr_batch* A, const int6
     cudaStream_t s = as_stream(stream);
     const int lanes[] = {4, 8, 16, 32};
     const int rows[] = {16, 64, 256};
-    const int threads[] = {256, 512};
+    const int threads[] = {256, 512, 1024};
     const int ctas[] = {2, 4, 8};
+    const int locals[] = {0, 224};
+    const int orders[] = {0, 1};
     cudaEvent_t e0, e1;
     SYM_CUDA(cudaEventCreate(&e0));
     SYM_CUDA(cudaEventCreate(&e1));
     float best_t = 1e30f;
-    sym_tile_cfg bc{64, 16, 256, 4};
+    sym_tile_cfg bc{64, 16, 256, 4, 0, 0};
     bool any = false;
+    for (int LS : locals)
+    for (int O : orders)
     for (int L : lanes)
         for (int R : rows)
             for (int T : threads)
                 for (int K : ctas) {
                     if (T * K > 2048) continue;  // at most 2048 resident threads per SM
-                    sym_tile_cfg c{R, L, T, K};
+                    if (LS == 0 && T > 512) continue;
+                    if (LS > 0 && (T != 1024 || L > 8 || R != 256 || K != 1 || O != 0)) continue;
+                    sym_tile_cfg c{R, L, T, K, LS, O};
                     if (sym_spmv_batch_plan_bytes(A, host_row_off, &c) > arena_bytes) continue;
                     sym_batch_plan P = nullptr;
                     if (sym_spmv_batch_plan_create(A, host_row_off, &c, arena, arena_bytes, stream, &P) != SYM_OK)
