@@ -630,7 +630,7 @@ def run_batch_only(args):
     x = torch.from_numpy(synth.vector_uniform(int(batch.host_row_off[-1]), 3)).to(dev)
     y = torch.empty_like(x)
     sy = torch.empty(len(sizes), dtype=torch.float64, device=dev)
-    plan = sg.BatchPlan(batch, sg.TileCfg(256, 8, 256, 8, 0, 0))
+    plan = sg.BatchPlan(batch, sg.TileCfg(256, 8, 256, 8, 0, 0, 0))
     for _ in range(args.warmup + args.steps):
         plan.run(x, y, sy)
     torch.cuda.synchronize()

@@ -183,6 +183,9 @@ typedef struct {
                                  by one CTA with y (and x, when 2n floats fit) on chip; 0 = all on tiles */
     int32_t tile_order;       /* 0: tiles in instance order; 1: interleaved across instances, so CTAs that run
                                  together reduce into different instances' y */
+    int32_t x_smem_kb;        /* > 0: each tile copies the first x_smem_kb*256 floats of its x window
+                                 (x[row0 ..]) into shared memory and gathers from there; rows_per_tile must
+                                 not exceed that many floats */
 } sym_tile_cfg;
 
 /* A plan: the tile list and the FP64 partial buffers, carved from `arena`. */

@@ -50,7 +50,8 @@ class CsrBatch(C.Structure):
 
 class TileCfg(C.Structure):
     _fields_ = [("rows_per_tile", C.c_int32), ("lanes_per_row", C.c_int32), ("threads_per_cta", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("local_smem_kb", C.c_int32), ("tile_order", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("local_smem_kb", C.c_int32), ("tile_order", C.c_int32),
+                ("x_smem_kb", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -603,7 +604,7 @@ class BatchPlan:
 
 def autotune_batch(batch: BatchCSR, x, y, syprd=None, cache_path=None, stream=None):
     """Times candidate tile shapes on this batch; returns (TileCfg, ms). Cached by device and shape."""
-    nb = lib().sym_spmv_batch_plan_bytes(C.byref(batch.desc), batch._hro(), C.byref(TileCfg(16, 32, 256, 1, 0, 0)))
+    nb = lib().sym_spmv_batch_plan_bytes(C.byref(batch.desc), batch._hro(), C.byref(TileCfg(16, 32, 256, 1, 0, 0, 0)))
     arena = _scratch(nb, batch.rowptr.device)
     best = TileCfg()
     ms = C.c_float(0)

@@ -119,6 +119,78 @@ __global__ void k_ssymv_batch(const Tile* __restrict__ tiles, int64_t ntiles, co
     }
 }
 
+// Tile kernel with the tile's window of x staged in shared memory: columns of
+// an upper CSR row are >= the row, so a tile starting at global row row0 only
+// reads x[row0 .. end of its instance); the first S floats of that window are
+// copied in (coalesced) and gathered from shared memory, the rest from global
+// memory.  The mirrored updates still go to y with global reductions.  Large
+// tiles amortise the staging; it replaces one random L2 sector per nonzero.
+template <int L, bool SYPRD>
+__global__ void k_ssymv_batch_xs(const Tile* __restrict__ tiles, int64_t ntiles, const int64_t* __restrict__ row_off,
+                                 const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                 const float* __restrict__ val, const float* __restrict__ x, float* __restrict__ y,
+                                 double* __restrict__ tile_partials, unsigned long long* __restrict__ counter, int S) {
+    extern __shared__ float xs[];
+    __shared__ int64_t s_tile;
+    __shared__ float s_red[32];
+    const int lane = threadIdx.x & 31;
+    const int s = lane % L;
+    const int groups = blockDim.x / L;
+    const int g = threadIdx.x / L;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t t = s_tile;
+        if (t >= ntiles) break;
+        const Tile tile = tiles[t];
+        const int64_t wend = row_off[tile.inst + 1];                // end of this instance's rows
+        const int64_t wlen = wend - tile.row0;
+        const int win = (int)(wlen < (int64_t)S ? wlen : (int64_t)S);
+        for (int k = threadIdx.x; k < win; k += blockDim.x) xs[k] = x[tile.row0 + k];
+        __syncthreads();
+        float syp = 0.f;
+        for (int r0 = 0; r0 < tile.rows; r0 += groups) {
+            const int r = r0 + g;
+            const bool act = r < tile.rows;
+            const int64_t i = tile.row0 + (act ? r : 0);
+            float rowsum = 0.f, rs = 0.f, xi = 0.f;
+            if (act) {
+                xi = xs[r];  // r < rows <= window
+                const int64_t p1 = rowptr[i + 1];
+                for (int64_t p = rowptr[i] + s; p < p1; p += L) {
+                    const int64_t j = col[p];
+                    const float a = val[p];
+                    const int64_t off = j - tile.row0;
+                    const float xj = (off >= 0 && off < win) ? xs[off] : x[j];
+                    const float tt = a * xj;
+                    rowsum += tt;
+                    if (j != i) {
+                        atomicAdd(&y[j], a * xi);
+                        if (SYPRD) rs += 2.f * tt;
+                    } else if (SYPRD) {
+                        rs += tt;
+                    }
+                }
+            }
+            rowsum = gsum<L>(rowsum);
+            if (act && s == 0 && rowsum != 0.f) atomicAdd(&y[i], rowsum);
+            if (SYPRD) syp += rs * xi;
+        }
+        if (SYPRD) {
+            float w = syp;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (lane == 0) s_red[threadIdx.x >> 5] = w;
+        }
+        __syncthreads();  // xs and s_red are reused by the next tile
+        if (SYPRD && threadIdx.x == 0) {
+            float tot = 0.f;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += s_red[k];
+            tile_partials[tile.slot] = (double)tot;
+        }
+    }
+}
+
 // Instance-resident path: one CTA owns a whole instance at a time, with its
 // y in shared memory (mirrored updates become shared-memory adds, and y is
 // written back with plain stores) and its x too when both fit.  Instances are
@@ -261,6 +333,8 @@ bool cfg_ok(const sym_tile_cfg* c) {
     if (c->ctas_per_sm < 1 || c->ctas_per_sm > 32) return false;
     if (c->local_smem_kb < 0 || c->local_smem_kb > 256) return false;
     if (c->tile_order != 0 && c->tile_order != 1) return false;
+    if (c->x_smem_kb < 0 || c->x_smem_kb > 220) return false;
+    if (c->x_smem_kb > 0 && c->rows_per_tile > c->x_smem_kb * 256) return false;  // the rows' own x must fit
     return true;
 }
 
@@ -310,10 +384,39 @@ sym_status batch_enqueue(sym_batch_plan_s* P, const float* x, float* y, double* 
     if (lst != SYM_OK) return lst;
     if (P->ntiles == 0) return SYM_OK;
     const int threads = P->cfg.threads_per_cta;
-    int dev = 0;
-    SYM_CUDA(cudaGetDevice(&dev));
     const unsigned grid = (unsigned)std::min<int64_t>((int64_t)sm_count() * P->cfg.ctas_per_sm, P->ntiles);
-    {
+    if (P->cfg.x_smem_kb > 0) {
+        const int S = P->cfg.x_smem_kb * 256;  // floats
+        const size_t smem = (size_t)S * sizeof(float);
+        SYM_PROF("ssymv_batch", s);
+#define SYM_XS_L(LL)                                                                                              \
+    case LL:                                                                                                      \
+        if (syprd) {                                                                                              \
+            SYM_CUDA(cudaFuncSetAttribute(k_ssymv_batch_xs<LL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          (int)smem));                                                            \
+            k_ssymv_batch_xs<LL, true><<<grid, threads, smem, s>>>(P->tiles, P->ntiles, P->A.row_off, P->A.rowptr, \
+                                                                   P->A.col, P->A.val, x, y, P->tile_partials,    \
+                                                                   P->counter, S);                                 \
+        } else {                                                                                                  \
+            SYM_CUDA(cudaFuncSetAttribute(k_ssymv_batch_xs<LL, false>,                                            \
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));              \
+            k_ssymv_batch_xs<LL, false><<<grid, threads, smem, s>>>(P->tiles, P->ntiles, P->A.row_off,            \
+                                                                    P->A.rowptr, P->A.col, P->A.val, x, y,        \
+                                                                    P->tile_partials, P->counter, S);             \
+        }                                                                                                         \
+        break;
+        switch (P->cfg.lanes_per_row) {
+            SYM_XS_L(1)
+            SYM_XS_L(2)
+            SYM_XS_L(4)
+            SYM_XS_L(8)
+            SYM_XS_L(16)
+            SYM_XS_L(32)
+            default: return SYM_E_INVALID;
+        }
+#undef SYM_XS_L
+        SYM_CHECK_LAUNCH();
+    } else {
         SYM_PROF("ssymv_batch", s);
 #define SYM_BATCH_L(LL)                                                                                         \
     case LL:                                                                                                    \
@@ -530,7 +633,7 @@ std::string cache_key(const sym_csr_batch* A) {
     for (auto& ch : name)
         if (ch == ' ') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof(buf), "ssymv_batch3|%s|%lld|%lld|%lld", name.c_str(), (long long)A->count,
+    snprintf(buf, sizeof(buf), "ssymv_batch4|%s|%lld|%lld|%lld", name.c_str(), (long long)A->count,
              (long long)A->total_rows, (long long)A->total_nnz);
     return buf;
 }
@@ -545,8 +648,8 @@ bool cache_lookup(const char* path, const std::string& key, sym_tile_cfg* cfg, f
         char k[300];
         sym_tile_cfg c;
         float t;
-        if (sscanf(line, "%299s %d %d %d %d %d %d %f", k, &c.rows_per_tile, &c.lanes_per_row, &c.threads_per_cta,
-                   &c.ctas_per_sm, &c.local_smem_kb, &c.tile_order, &t) == 8 &&
+        if (sscanf(line, "%299s %d %d %d %d %d %d %d %f", k, &c.rows_per_tile, &c.lanes_per_row,
+                   &c.threads_per_cta, &c.ctas_per_sm, &c.local_smem_kb, &c.tile_order, &c.x_smem_kb, &t) == 9 &&
             key == k && cfg_ok(&c)) {
             *cfg = c;
             *ms = t;
@@ -561,8 +664,8 @@ void cache_store(const char* path, const std::string& key, const sym_tile_cfg& c
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %.6f\n", key.c_str(), c.rows_per_tile, c.lanes_per_row, c.threads_per_cta,
-            c.ctas_per_sm, c.local_smem_kb, c.tile_order, ms);
+    fprintf(f, "%s %d %d %d %d %d %d %d %.6f\n", key.c_str(), c.rows_per_tile, c.lanes_per_row, c.threads_per_cta,
+            c.ctas_per_sm, c.local_smem_kb, c.tile_order, c.x_smem_kb, ms);
     fclose(f);
 }
 
@@ -587,12 +690,14 @@ extern "C" sym_status sym_autotune_spmv_batch(const sym_csr_batch* A, const int6
     const int ctas[] = {2, 4, 8};
     const int locals[] = {0, 224};
     const int orders[] = {0, 1};
+    const int xsk[] = {0, 32, 96, 200};
     cudaEvent_t e0, e1;
     SYM_CUDA(cudaEventCreate(&e0));
     SYM_CUDA(cudaEventCreate(&e1));
     float best_t = 1e30f;
-    sym_tile_cfg bc{64, 16, 256, 4, 0, 0};
+    sym_tile_cfg bc{64, 16, 256, 4, 0, 0, 0};
     bool any = false;
+    for (int XS : xsk)
     for (int LS : locals)
     for (int O : orders)
     for (int L : lanes)
@@ -601,8 +706,11 @@ extern "C" sym_status sym_autotune_spmv_batch(const sym_csr_batch* A, const int6
                 for (int K : ctas) {
                     if (T * K > 2048) continue;  // at most 2048 resident threads per SM
                     if (LS == 0 && T > 512) continue;
-                    if (LS > 0 && (T != 1024 || L > 8 || R != 256 || K != 1 || O != 0)) continue;
-                    sym_tile_cfg c{R, L, T, K, LS, O};
+                    if (LS > 0 && (T != 1024 || L > 8 || R != 256 || K != 1 || O != 0 || XS)) continue;
+                    if (XS > 0 && (O != 0 || R < 256 || L > 16)) continue;
+                    if (XS >= 96 && T * K > 1024) continue;
+                    const int RR = XS > 0 ? (R == 256 ? 2048 : R) : R;
+                    sym_tile_cfg c{RR, L, T, K, LS, O, XS};
                     if (sym_spmv_batch_plan_bytes(A, host_row_off, &c) > arena_bytes) continue;
                     sym_batch_plan P = nullptr;
                     if (sym_spmv_batch_plan_create(A, host_row_off, &c, arena, arena_bytes, stream, &P) != SYM_OK)

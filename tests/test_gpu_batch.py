@@ -47,9 +47,10 @@ def test_device_batch_generator_matches_host():
     assert torch.equal(B.row_off.cpu(), torch.from_numpy(row_off))
 
 
-@pytest.mark.parametrize("cfg", [(16, 4, 256, 2, 0, 0), (64, 16, 512, 2, 0, 1), (1, 32, 128, 8, 0, 0),
-                                 (256, 8, 256, 4, 0, 1), (64, 8, 512, 2, 224, 0), (64, 16, 1024, 1, 224, 1),
-                                 (64, 4, 512, 2, 8, 0)])
+@pytest.mark.parametrize("cfg", [(16, 4, 256, 2, 0, 0, 0), (64, 16, 512, 2, 0, 1, 0), (1, 32, 128, 8, 0, 0, 0),
+                                 (256, 8, 256, 4, 0, 1, 0), (64, 8, 512, 2, 224, 0, 0), (64, 16, 1024, 1, 224, 1, 0),
+                                 (64, 4, 512, 2, 8, 0, 0), (2048, 8, 256, 4, 0, 0, 32), (256, 16, 512, 2, 0, 0, 1),
+                                 (4096, 4, 1024, 1, 0, 0, 200)])
 def test_batch_parity(cfg):
     sg = need_gpu()
     torch = pytest.importorskip("torch")
@@ -87,7 +88,7 @@ def test_batch_local_path_mixed(local_kb):
     rowptr, col, v = synth.batch_upper_csr_host(row_off, idx, val)
     x = synth.vector_uniform(int(row_off[-1]), 21)
     batch = sg.BatchCSR(dev(row_off), dev(rowptr), dev(col), dev(v))
-    plan = sg.BatchPlan(batch, sg.TileCfg(64, 8, 512, 2, local_kb, 0))
+    plan = sg.BatchPlan(batch, sg.TileCfg(64, 8, 512, 2, local_kb, 0, 0))
     y = torch.empty(int(row_off[-1]), device="cuda")
     s = torch.empty(len(sizes), dtype=torch.float64, device="cuda")
     plan.run(dev(x), y, s)
@@ -109,7 +110,7 @@ def test_batch_with_empty_and_tiny_instances():
     rowptr, col, v = synth.batch_upper_csr_host(row_off, idx, val)
     x = synth.vector_uniform(int(row_off[-1]), 9)
     batch = sg.BatchCSR(dev(row_off), dev(rowptr), dev(col), dev(v))
-    plan = sg.BatchPlan(batch, sg.TileCfg(8, 4, 128, 2, 0, 1))
+    plan = sg.BatchPlan(batch, sg.TileCfg(8, 4, 128, 2, 0, 1, 0))
     y = torch.empty(int(row_off[-1]), device="cuda")
     s = torch.empty(len(sizes), dtype=torch.float64, device="cuda")
     plan.run(dev(x), y, s)
@@ -137,7 +138,7 @@ def test_autotune_picks_valid_cfg_and_caches(tmp_path):
     plan = sg.BatchPlan(batch, cfg)
     plan.run(x, y, s)
     ref = torch.empty_like(y)
-    plan2 = sg.BatchPlan(batch, sg.TileCfg(64, 16, 256, 2, 0, 0))
+    plan2 = sg.BatchPlan(batch, sg.TileCfg(64, 16, 256, 2, 0, 0, 0))
     s2 = torch.empty_like(s)
     plan2.run(x, ref, s2)
     torch.cuda.synchronize()
