@@ -348,6 +348,9 @@ typedef struct {
     int32_t leaf_index;        /* plain kernel: 1 = take the leaf position from the tensor's leaf index (see
                                   sym_tensor_add_leaf_index) instead of one reduction per entry */
     int32_t vec_per_lane;      /* plain kernel: float4 column groups per lane, 1 or 2 (2 needs rank >= 8) */
+    int32_t stream_hint;       /* plain kernel: 1 = read the canonical stream with evict-first loads so it does not
+                                  displace factor rows from L1 / L2 */
+    int32_t l1_pref;           /* plain kernel: 1 = ask for the largest L1 (no shared-memory carveout) */
 } sym_mttkrp_cfg;
 sym_status sym_mttkrp_default_config(sym_mttkrp_cfg* out);
 sym_status sym_mttkrp_set_config(sym_tensor X, const sym_mttkrp_cfg* cfg);
@@ -362,6 +365,18 @@ sym_status sym_mttkrp_set_chunk(sym_tensor X, int entries_per_warp);
 sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
                                int64_t ldm, const char* cache_path, sym_stream_t stream, sym_mttkrp_cfg* best,
                                float* best_ms);
+
+/* One symmetric CP-ALS update of the shared factor (the decomposition the
+ * symmetric MTTKRP serves, Sec. 5.2.6):
+ *   B_out = M H^{-1},  M = MTTKRP(X, B),  H = (B^T B)^{o(N-1)} + ridge I
+ * (o(N-1): elementwise power).  H is formed, Cholesky-factorised and inverted
+ * in FP64; the n x R product runs in FP32 and is stored in B's dtype.
+ * info [device, 1 int] (nullable) receives 0, or the 1-based column of a
+ * non-positive pivot (then B_out = 0).  B_out must not alias B.  ws >=
+ * sym_cp_als_workspace_bytes (it holds M, G, L^{-1} and H^{-1}). */
+size_t sym_cp_als_workspace_bytes(sym_tensor X, int rank);
+sym_status sym_cp_als_step(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, void* B_out,
+                           int64_t ldo, double ridge, int* info, void* ws, size_t ws_bytes, sym_stream_t stream);
 
 /* ===================================================================== */
 /* Baseline: MTTKRP over the fully expanded (non-symmetric) tensor          */

@@ -66,7 +66,9 @@ def lib():
                                     f64p]
             L.orc_expand.argtypes = [C.c_int, C.c_int64, i32p, f32p, C.c_int64, i32p, f32p,
                                      C.POINTER(C.c_int64)]
-            for name in ("orc_canonicalize", "orc_check_canonical", "orc_counts", "orc_mttkrp_enum",
+            L.orc_cp_als_step.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, C.c_double,
+                                          f64p, C.POINTER(C.c_int)]
+            for name in ("orc_cp_als_step", "orc_canonicalize", "orc_check_canonical", "orc_counts", "orc_mttkrp_enum",
                          "orc_mttkrp_runs", "orc_check_upper_csr", "orc_ssymv_enum", "orc_syprd_enum",
                          "orc_bellman_enum", "orc_cpfit", "orc_expand"):
                 getattr(L, name).restype = C.c_int
@@ -202,6 +204,18 @@ def cpfit(order, n, cidx, cval, B):
     _check(lib().orc_cpfit(order, n, cval.shape[0], _p(cidx), _p(cval), _p(B), B.shape[1], C.byref(res),
                            C.byref(ab), _p(parts)), "cpfit")
     return res.value, ab.value, parts
+
+
+def cp_als_step(order, n, cidx, cval, B, ridge=0.0):
+    """One symmetric CP-ALS update B_new = M (B^T B)^{o(N-1)} + ridge I)^{-1}; returns (B_new, info)."""
+    cidx = _c(cidx, np.int32)
+    cval = _c(cval, np.float32)
+    B = _c(B, np.float64)
+    out = np.zeros_like(B)
+    info = C.c_int(0)
+    _check(lib().orc_cp_als_step(order, n, cval.shape[0], _p(cidx), _p(cval), _p(B), B.shape[1], float(ridge),
+                                 _p(out), C.byref(info)), "cp_als_step")
+    return out, info.value
 
 
 def expand(order, cidx, cval):

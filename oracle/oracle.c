@@ -475,3 +475,65 @@ int orc_expand(int order, int64_t nnz, const int32_t* cidx, const float* cval, i
     free(r);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Symmetric CP-ALS update (the shared-factor update the MTTKRP serves,      */
+/* Sec. 5.2.6: one factor for all modes)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* B_new = M H^{-1} with M the full-tensor MTTKRP of X with B (by enumeration),
+ * H = (B^T B) raised elementwise to the power N-1, plus ridge on the diagonal.
+ * H is factorised by Cholesky (H = L L^T) and every row solved by forward and
+ * back substitution.  Returns the 1-based column of a non-positive pivot in
+ * *info (0 = success). */
+int orc_cp_als_step(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval, const double* B,
+                    int R, double ridge, double* B_new, int* info) {
+    if (order < 2 || order > ORC_MAX_ORDER || R <= 0) return ORC_INVALID;
+    double* M = (double*)malloc(sizeof(double) * (size_t)n * (size_t)R);
+    double* H = (double*)malloc(sizeof(double) * (size_t)R * (size_t)R);
+    double* y = (double*)malloc(sizeof(double) * (size_t)R);
+    if (!M || !H || !y) { free(M); free(H); free(y); return ORC_NOMEM; }
+    int rc = orc_mttkrp_enum(order, n, nnz, cidx, cval, B, R, M, NULL, NULL);
+    if (rc) { free(M); free(H); free(y); return rc; }
+    for (int r = 0; r < R; ++r)
+        for (int s = 0; s < R; ++s) {
+            double g = 0.0;
+            for (int64_t i = 0; i < n; ++i) g += B[i * R + r] * B[i * R + s];
+            double h = 1.0;
+            for (int q = 0; q < order - 1; ++q) h *= g;
+            H[r * R + s] = h + (r == s ? ridge : 0.0);
+        }
+    /* Cholesky, lower triangle in place */
+    *info = 0;
+    for (int j = 0; j < R; ++j) {
+        double d = H[j * R + j];
+        for (int k = 0; k < j; ++k) d -= H[j * R + k] * H[j * R + k];
+        if (!(d > 0.0)) { *info = j + 1; break; }
+        d = sqrt(d);
+        H[j * R + j] = d;
+        for (int i = j + 1; i < R; ++i) {
+            double t = H[i * R + j];
+            for (int k = 0; k < j; ++k) t -= H[i * R + k] * H[j * R + k];
+            H[i * R + j] = t / d;
+        }
+    }
+    if (*info == 0) {
+        for (int64_t i = 0; i < n; ++i) {
+            /* solve L y = m_i, then L^T b = y */
+            for (int r = 0; r < R; ++r) {
+                double t = M[i * R + r];
+                for (int k = 0; k < r; ++k) t -= H[r * R + k] * y[k];
+                y[r] = t / H[r * R + r];
+            }
+            for (int r = R - 1; r >= 0; --r) {
+                double t = y[r];
+                for (int k = r + 1; k < R; ++k) t -= H[k * R + r] * B_new[i * R + k];
+                B_new[i * R + r] = t / H[r * R + r];
+            }
+        }
+    } else {
+        memset(B_new, 0, sizeof(double) * (size_t)n * (size_t)R);
+    }
+    free(M); free(H); free(y);
+    return ORC_OK;
+}

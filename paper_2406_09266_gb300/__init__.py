@@ -93,7 +93,8 @@ class ServerStats(C.Structure):
 class MttkrpCfg(C.Structure):
     _fields_ = [("strict_kernel", C.c_int32), ("entries_per_warp", C.c_int32), ("threads_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("strict_smem_kb", C.c_int32), ("diag_smem_kb", C.c_int32),
-                ("b_share_pct", C.c_int32), ("leaf_index", C.c_int32), ("vec_per_lane", C.c_int32)]
+                ("b_share_pct", C.c_int32), ("leaf_index", C.c_int32), ("vec_per_lane", C.c_int32),
+                ("stream_hint", C.c_int32), ("l1_pref", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -160,6 +161,9 @@ _SIGS = {
     "sym_mttkrp_get_config": ([C.c_void_p, C.c_void_p], C.c_int),
     "sym_mttkrp_autotune": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_char_p,
                              C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_cp_als_workspace_bytes": ([C.c_void_p, C.c_int], C.c_size_t),
+    "sym_cp_als_step": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
+                         C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "sym_expanded_bytes": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_expanded_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p,
                              C.c_void_p], C.c_int),
@@ -383,9 +387,10 @@ class SymTensor:
         check(lib().sym_mttkrp_set_chunk(self.handle, entries_per_warp), "sym_mttkrp_set_chunk")
 
     def set_config(self, strict_kernel=MTTKRP_PLAIN, entries_per_warp=256, threads_per_cta=256, ctas_per_sm=2,
-                   strict_smem_kb=0, diag_smem_kb=96, b_share_pct=0, leaf_index=1, vec_per_lane=1):
+                   strict_smem_kb=0, diag_smem_kb=96, b_share_pct=0, leaf_index=1, vec_per_lane=1, stream_hint=0,
+                   l1_pref=0):
         cfg = MttkrpCfg(strict_kernel, entries_per_warp, threads_per_cta, ctas_per_sm, strict_smem_kb, diag_smem_kb,
-                        b_share_pct, leaf_index, vec_per_lane)
+                        b_share_pct, leaf_index, vec_per_lane, stream_hint, l1_pref)
         check(lib().sym_mttkrp_set_config(self.handle, C.byref(cfg)), "sym_mttkrp_set_config")
 
     def add_leaf_index(self, stream=None):
@@ -443,6 +448,22 @@ class SymTensor:
         check(lib().sym_tensor_upper_csr(self.handle, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(ws), ws.numel(),
                                          _stream(stream)), "sym_tensor_upper_csr")
         return rowptr, col[:nnz], val[:nnz]
+
+    def cp_als_step(self, B: torch.Tensor, B_out: torch.Tensor | None = None, ridge: float = 0.0, ws=None,
+                    stream=None):
+        """One symmetric CP-ALS update B_out = MTTKRP(X, B) ((B^T B)^{o(N-1)} + ridge I)^{-1}.
+
+        Returns (B_out, info) with info a device int (0 = success, k = first non-positive pivot)."""
+        rank = B.shape[1]
+        if B_out is None:
+            B_out = torch.empty_like(B)
+        info = torch.zeros(1, dtype=torch.int32, device=B.device)
+        if ws is None:
+            ws = _scratch(lib().sym_cp_als_workspace_bytes(self.handle, rank), self.device)
+        check(lib().sym_cp_als_step(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(B_out),
+                                    B_out.stride(0), float(ridge), _ptr(info), _ptr(ws), ws.numel(), _stream(stream)),
+              "sym_cp_als_step")
+        return B_out, info
 
     def expanded(self, stream=None) -> "Expanded":
         return Expanded(self, stream)

@@ -26,7 +26,9 @@ namespace symgpu {
 namespace {
 
 constexpr int GRAM_ROWS = 32;
-constexpr int GRAM_PPT = 16;  // (r, s) pairs per thread
+constexpr int GRAM_PPT = 20;       // (r, s) pairs per thread
+constexpr int GRAM_THREADS = 512;  // 512 x 20 >= 8256 pairs of R = 128
+static_assert(GRAM_THREADS * GRAM_PPT >= 128 * 129 / 2, "one CTA must cover every pair of the largest rank");
 
 template <bool BF16>
 __device__ __forceinline__ float load_b(const void* B, int64_t i, int64_t ldb, int r) {
@@ -38,15 +40,36 @@ __device__ __forceinline__ float load_b(const void* B, int64_t i, int64_t ldb, i
     }
 }
 
-// G[r,s] += sum_i B[i,r] B[i,s] over this CTA's rows.
+// Triangular index p = r*R - r*(r-1)/2 + (s - r) of the pair (r, s), r <= s.
+__device__ __forceinline__ void tri_pair(int p, int R, int* r_out, int* s_out) {
+    const double t = 2.0 * R + 1.0;
+    int r = (int)((t - sqrt(t * t - 8.0 * p)) * 0.5);
+    if (r < 0) r = 0;
+    if (r > R - 1) r = R - 1;
+    auto start = [R](int q) { return q * R - q * (q - 1) / 2; };
+    while (r > 0 && start(r) > p) --r;
+    while (r + 1 < R && start(r + 1) <= p) ++r;
+    *r_out = r;
+    *s_out = r + (p - start(r));
+}
+
+// G[r,s] += sum_i B[i,r] B[i,s] over this CTA's rows, for r <= s only (G is
+// symmetric); G is stored as the packed upper triangle.
 template <bool BF16>
-__global__ void k_gram(const void* __restrict__ B, int64_t n, int64_t ldb, int R, double* __restrict__ G,
-                       int64_t rows_per_cta) {
+__global__ void __launch_bounds__(GRAM_THREADS) k_gram(const void* __restrict__ B, int64_t n, int64_t ldb, int R,
+                                                       double* __restrict__ G, int64_t rows_per_cta) {
     extern __shared__ float tile[];  // GRAM_ROWS x R
-    const int pairs = R * R;
+    const int pairs = R * (R + 1) / 2;
     double acc[GRAM_PPT];
+    int pr_rs[GRAM_PPT];  // r << 16 | s
 #pragma unroll
-    for (int k = 0; k < GRAM_PPT; ++k) acc[k] = 0.0;
+    for (int k = 0; k < GRAM_PPT; ++k) {
+        acc[k] = 0.0;
+        const int pr = threadIdx.x + k * blockDim.x;
+        int r = 0, s = 0;
+        if (pr < pairs) tri_pair(pr, R, &r, &s);
+        pr_rs[k] = (r << 16) | s;
+    }
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
     const int64_t r1 = min(n, r0 + rows_per_cta);
     for (int64_t t0 = r0; t0 < r1; t0 += GRAM_ROWS) {
@@ -61,7 +84,7 @@ __global__ void k_gram(const void* __restrict__ B, int64_t n, int64_t ldb, int R
         for (int k = 0; k < GRAM_PPT; ++k) {
             const int pr = threadIdx.x + k * blockDim.x;
             if (pr >= pairs) break;
-            const int r = pr / R, s = pr % R;
+            const int r = pr_rs[k] >> 16, s = pr_rs[k] & 0xffff;
             float hi = 0.f, lo = 0.f;
             for (int i = 0; i < rows; ++i) {
                 const float a = tile[i * R + r], b = tile[i * R + s];
@@ -109,10 +132,13 @@ __global__ void k_residual_final(const double* __restrict__ G, int R, int order,
                                  double normsq, double* __restrict__ residual) {
     __shared__ double sh[32];
     double acc = 0.0;
-    for (int k = threadIdx.x; k < R * R; k += blockDim.x) {
+    const int pairs = R * (R + 1) / 2;
+    for (int k = threadIdx.x; k < pairs; k += blockDim.x) {
+        int r, s;
+        tri_pair(k, R, &r, &s);
         double g = G[k], p = 1.0;
         for (int q = 0; q < order; ++q) p *= g;
-        acc += p;
+        acc += (r == s) ? p : 2.0 * p;  // off-diagonal pairs stand for (r,s) and (s,r)
     }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -132,7 +158,7 @@ struct ResidualWs {
 template <typename C>
 ResidualWs layout_residual(C& c, int R) {
     ResidualWs w;
-    w.G = c.template take<double>((size_t)R * R);
+    w.G = c.template take<double>((size_t)R * (R + 1) / 2);
     w.xm = c.template take<double>(1);
     return w;
 }
@@ -155,7 +181,8 @@ sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int 
     if (!w.G || !w.xm) return SYM_E_NOMEM;
     SYM_CUDA(cudaMemsetAsync(ws, 0, c.used, s));
     const int sms = sm_count();
-    const int threads = std::max(128, std::min(1024, ((R * R + GRAM_PPT - 1) / GRAM_PPT + 31) / 32 * 32));
+    const int tri = R * (R + 1) / 2;
+    const int threads = std::max(128, std::min(GRAM_THREADS, ((tri + GRAM_PPT - 1) / GRAM_PPT + 31) / 32 * 32));
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(2 * sms, (X->n + GRAM_ROWS - 1) / GRAM_ROWS));
     int64_t rows_per_cta = (X->n + ctas - 1) / ctas;
     rows_per_cta = (rows_per_cta + GRAM_ROWS - 1) / GRAM_ROWS * GRAM_ROWS;
@@ -179,6 +206,27 @@ sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int 
         SYM_CHECK_LAUNCH();
     }
     k_residual_final<<<1, 256, 0, s>>>(w.G, R, X->order, w.xm, X->info.normsq, residual);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+// G (packed upper triangle, FP64) = B^T B, exact products and FP64 sums.
+sym_status gram_launch(int64_t n, const void* B, bool bf16, int R, int64_t ldb, double* G, cudaStream_t s) {
+    SYM_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)R * (R + 1) / 2, s));
+    if (n == 0) return SYM_OK;
+    const int sms = sm_count();
+    const int tri = R * (R + 1) / 2;
+    const int threads = std::max(128, std::min(GRAM_THREADS, ((tri + GRAM_PPT - 1) / GRAM_PPT + 31) / 32 * 32));
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(2 * sms, (n + GRAM_ROWS - 1) / GRAM_ROWS));
+    int64_t rows_per_cta = (n + ctas - 1) / ctas;
+    rows_per_cta = (rows_per_cta + GRAM_ROWS - 1) / GRAM_ROWS * GRAM_ROWS;
+    const unsigned grid = (unsigned)((n + rows_per_cta - 1) / rows_per_cta);
+    const size_t smem = sizeof(float) * GRAM_ROWS * R;
+    SYM_PROF("gram", s);
+    if (bf16)
+        k_gram<true><<<grid, threads, smem, s>>>(B, n, ldb, R, G, rows_per_cta);
+    else
+        k_gram<false><<<grid, threads, smem, s>>>(B, n, ldb, R, G, rows_per_cta);
     SYM_CHECK_LAUNCH();
     return SYM_OK;
 }
@@ -233,6 +281,7 @@ sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
     if (c->b_share_pct < 0 || c->b_share_pct > 100) return SYM_E_INVALID;
     if (c->leaf_index != 0 && c->leaf_index != 1) return SYM_E_INVALID;
     if (c->vec_per_lane != 1 && c->vec_per_lane != 2) return SYM_E_INVALID;
+    if ((c->stream_hint != 0 && c->stream_hint != 1) || (c->l1_pref != 0 && c->l1_pref != 1)) return SYM_E_INVALID;
     return SYM_OK;
 }
 
@@ -245,7 +294,7 @@ std::string tune_key(const sym_tensor_s* X, int rank, sym_dtype bdt) {
     for (auto& ch : name)
         if (ch == ' ') ch = '_';
     char buf[320];
-    snprintf(buf, sizeof(buf), "mttkrp|%s|N%d|n%lld|nnz%lld|strict%lld|R%d|%s|leaf%d", name.c_str(), X->order,
+    snprintf(buf, sizeof(buf), "mttkrp2|%s|N%d|n%lld|nnz%lld|strict%lld|R%d|%s|leaf%d", name.c_str(), X->order,
              (long long)X->n, (long long)X->nnz, (long long)X->nnz_strict, rank, bdt == SYM_BF16 ? "bf16" : "f32",
              X->rklo ? 1 : 0);
     return buf;
@@ -261,9 +310,9 @@ bool tune_lookup(const char* path, const std::string& key, sym_mttkrp_cfg* cfg, 
         char k[400];
         sym_mttkrp_cfg c;
         float t;
-        if (sscanf(line, "%399s %d %d %d %d %d %d %d %d %d %f", k, &c.strict_kernel, &c.entries_per_warp,
+        if (sscanf(line, "%399s %d %d %d %d %d %d %d %d %d %d %d %f", k, &c.strict_kernel, &c.entries_per_warp,
                    &c.threads_per_cta, &c.ctas_per_sm, &c.strict_smem_kb, &c.diag_smem_kb, &c.b_share_pct,
-                   &c.leaf_index, &c.vec_per_lane, &t) == 11 &&
+                   &c.leaf_index, &c.vec_per_lane, &c.stream_hint, &c.l1_pref, &t) == 13 &&
             key == k && validate_mttkrp_cfg(&c) == SYM_OK) {
             *cfg = c;
             *ms = t;
@@ -278,9 +327,9 @@ void tune_store(const char* path, const std::string& key, const sym_mttkrp_cfg& 
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %.6f\n", key.c_str(), c.strict_kernel, c.entries_per_warp,
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %.6f\n", key.c_str(), c.strict_kernel, c.entries_per_warp,
             c.threads_per_cta, c.ctas_per_sm, c.strict_smem_kb, c.diag_smem_kb, c.b_share_pct, c.leaf_index,
-            c.vec_per_lane, ms);
+            c.vec_per_lane, c.stream_hint, c.l1_pref, ms);
     fclose(f);
 }
 
@@ -315,7 +364,7 @@ extern "C" sym_status sym_mttkrp(sym_tensor X, const void* B, sym_dtype bdt, int
 
 extern "C" sym_status sym_mttkrp_default_config(sym_mttkrp_cfg* out) {
     if (!out) return SYM_E_INVALID;
-    *out = sym_mttkrp_cfg{SYM_MTTKRP_PLAIN, 256, 256, 2, 0, 96, 0, 1, 1};
+    *out = sym_mttkrp_cfg{SYM_MTTKRP_PLAIN, 256, 256, 2, 0, 96, 0, 1, 1, 0, 0};
     return SYM_OK;
 }
 
@@ -369,16 +418,18 @@ extern "C" sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype
     std::vector<sym_mttkrp_cfg> cands;
     for (int leaf : {0, 1}) {
         if (leaf && !X->rklo) continue;
-        for (int chunk : {128, 256, 512}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, leaf, 1});
+        for (int chunk : {128, 256, 512})
+            for (int sh : {0, 1})
+                for (int l1 : {0, 1}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, leaf, 1, sh, l1});
     }
     if (rank >= 8)
-        for (int chunk : {128, 256, 512}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, 0, 2});
+        for (int chunk : {256, 512}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, 0, 2, 0, 0});
     for (int chunk : {128, 256, 512})
-        for (int thr : {128, 256}) cands.push_back({SYM_MTTKRP_STAGED, chunk, thr, 2, 0, 0, 0, 0, 1});
-    for (int chunk : {128, 256}) cands.push_back({SYM_MTTKRP_PIPELINED, chunk, 256, 2, 0, 0, 0, 0, 1});
-    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 0, 0, 0, 0, 1});
-    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 96, 0, 50, 0, 1});
-    cands.push_back({SYM_MTTKRP_UNFACTORISED, 256, 256, 2, 0, 0, 0, 0, 1});
+        for (int thr : {128, 256}) cands.push_back({SYM_MTTKRP_STAGED, chunk, thr, 2, 0, 0, 0, 0, 1, 0, 0});
+    for (int chunk : {128, 256}) cands.push_back({SYM_MTTKRP_PIPELINED, chunk, 256, 2, 0, 0, 0, 0, 1, 0, 0});
+    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 0, 0, 0, 0, 1, 0, 0});
+    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 96, 0, 50, 0, 1, 0, 0});
+    cands.push_back({SYM_MTTKRP_UNFACTORISED, 256, 256, 2, 0, 0, 0, 0, 1, 0, 0});
     cudaEvent_t e0, e1;
     SYM_CUDA(cudaEventCreate(&e0));
     SYM_CUDA(cudaEventCreate(&e1));

@@ -142,7 +142,7 @@ template <int N, int KW, int L, bool BF16, int MODE>
 __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
-    int64_t chunk) {
+    int64_t chunk, int stream_hint) {
     static_assert(N >= 2 && N <= 5, "order");
     constexpr int LV = N - 1;  // fiber levels above the leaf
     const int lane = threadIdx.x & 31;
@@ -169,9 +169,15 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict(
         uint64_t mlo = 0, mhi = 0;
         float mv = 0.f;
         if (e < end) {
-            mlo = klo[e];
-            if (KW == 2) mhi = khi[e];
-            mv = val[e];
+            if (stream_hint) {  // evict-first: the stream is read once
+                mlo = __ldcs(klo + e);
+                if (KW == 2) mhi = __ldcs(khi + e);
+                mv = __ldcs(val + e);
+            } else {
+                mlo = klo[e];
+                if (KW == 2) mhi = khi[e];
+                mv = val[e];
+            }
         }
 #pragma unroll 1
         for (int t = 0; t < L; ++t) {
@@ -712,6 +718,10 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             const unsigned grid = (unsigned)((warps * 32 + MT_THREADS - 1) / MT_THREADS);
             const bool leaf_pass = cfg.leaf_index != 0 && X->rklo != nullptr;
             constexpr int L2 = L / 2;   // lanes per entry with 8 columns per lane
+            // carveout preference: all of the unified L1 / shared memory as L1, or the driver default
+            SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_strict<N, KW, L, BF16, 0>,
+                                          cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cfg.l1_pref ? 0 : (int)cudaSharedmemCarveoutDefault));
             if (!leaf_pass && cfg.vec_per_lane == 2 && L2 >= 1) {
                 SYM_PROF("mttkrp_strict", s);
                 k_mttkrp_strict_wide<N, KW, (L2 >= 1 ? L2 : 1), 2, BF16><<<grid, MT_THREADS, 0, s>>>(
@@ -719,17 +729,20 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             } else if (!leaf_pass) {
                 SYM_PROF("mttkrp_strict", s);
                 k_mttkrp_strict<N, KW, L, BF16, 0><<<grid, MT_THREADS, 0, s>>>(
-                    X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
+                    X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
+                    cfg.stream_hint);
             } else {
                 {
                     SYM_PROF("mttkrp_strict", s);
                     k_mttkrp_strict<N, KW, L, BF16, 1><<<grid, MT_THREADS, 0, s>>>(
-                        X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
+                        X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
+                        cfg.stream_hint);
                 }
                 SYM_CHECK_LAUNCH();
                 SYM_PROF("mttkrp_strict_leaf", s);
                 k_mttkrp_strict<N, KW, L, BF16, 2><<<grid, MT_THREADS, 0, s>>>(
-                    X->rklo, X->rkhi, X->rval, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
+                    X->rklo, X->rkhi, X->rval, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
+                    cfg.stream_hint);
             }
         } else if (cfg.strict_kernel == SYM_MTTKRP_PIPELINED) {
             const SinkPlan sp = plan_sink(X->n, R, cfg.strict_smem_kb, cfg.b_share_pct);
@@ -831,6 +844,8 @@ sym_status mttkrp_core(const sym_tensor_s* X, const void* B, bool bf16, int R, i
 sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, const float* M,
                            int64_t ldm, double* residual, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t residual_ws_bytes(int R);
+// G (packed upper triangle r <= s, FP64, overwritten) = B^T B.
+sym_status gram_launch(int64_t n, const void* B, bool bf16, int R, int64_t ldb, double* G, cudaStream_t s);
 sym_status validate_mttkrp_args(const sym_tensor_s* X, const void* B, sym_dtype bdt, int rank, int64_t ldb,
                                 const float* M, int64_t ldm);
 sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c);

@@ -82,6 +82,7 @@ CONFIGS = [
     dict(strict_kernel=3, entries_per_warp=256, threads_per_cta=256, leaf_index=0),
     dict(strict_kernel=3, entries_per_warp=32, threads_per_cta=64, leaf_index=0, diag_smem_kb=0),
     dict(strict_kernel=3, entries_per_warp=1024, threads_per_cta=512, leaf_index=0),
+    dict(strict_kernel=0, entries_per_warp=512, leaf_index=0, stream_hint=1, l1_pref=1),
 ]
 
 
@@ -209,7 +210,7 @@ def test_relabel_invariance_on_gpu():
     assert oracle.componentwise_error(M2[pi], M1, 2 * ra + 1e-300) <= TOL_F32
 
 
-@pytest.mark.parametrize("order,rank", [(3, 16), (4, 8), (5, 8)])
+@pytest.mark.parametrize("order,rank", [(3, 16), (4, 8), (5, 8), (3, 128), (3, 100)])
 @pytest.mark.parametrize("bf16", [False, True])
 def test_cpfit_residual(order, rank, bf16):
     sg = need_gpu()

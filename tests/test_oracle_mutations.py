@@ -32,6 +32,12 @@ MUTANTS = {
                              lambda: pins.test_canonicalize_properties()),
     "cpfit_sign": ("orc_cpfit", "*res = xx - 2.0 * xm + mm;", "*res = xx + 2.0 * xm + mm;",
                    lambda: pins.test_cpfit_vs_dense(3, 5)),
+    "cpals_wrong_power": ("orc_cp_als_step", "for (int q = 0; q < order - 1; ++q) h *= g;",
+                          "for (int q = 0; q < order; ++q) h *= g;",
+                          lambda: pins.test_cp_als_step_vs_dense(3, 6, 2)),
+    "cpals_transposed_solve": ("orc_cp_als_step", "t -= H[k * R + r] * B_new[i * R + k];",
+                               "t -= H[r * R + k] * B_new[i * R + k];",
+                               lambda: pins.test_cp_als_step_vs_dense(4, 5, 3)),
     "counts_wrong_fibers": ("orc_counts", "if (e == 0 || c[0] != prev[0]) *root_fibers += 1;",
                             "*root_fibers += 1;", lambda: pins.test_counts_closed_forms(3)),
 }

@@ -350,3 +350,42 @@ def test_enum_equals_runs_on_zipf():
     assert cnt["by_pattern"][1] == T.meta["i=j<k"]
     assert cnt["by_pattern"][2] == T.meta["i<j=k"]
     assert cnt["by_pattern"][3] == T.meta["i=j=k"]
+
+
+# ----------------------------------------------------------------------------- symmetric CP-ALS step
+
+@pytest.mark.parametrize("order,n,R", [(3, 6, 2), (4, 5, 3), (5, 4, 2)])
+def test_cp_als_step_vs_dense(order, n, R):
+    """Independent path: dense MTTKRP by einsum, H by numpy, rows solved with numpy.linalg.solve."""
+    T = synth.tensor_small_all_patterns(order, n, 31, density=0.8)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(n, R, 31).astype(np.float64)
+    X = dense_full(order, n, cidx, cval)
+    M = dense_mttkrp(X, B)
+    H = (B.T @ B) ** (order - 1) + 0.1 * np.eye(R)
+    want = np.linalg.solve(H, M.T).T
+    got, info = oracle.cp_als_step(order, n, cidx, cval, B, ridge=0.1)
+    assert info == 0
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_cp_als_fixed_point(order):
+    """An exact symmetric CP tensor sum_r b_r^(x)N is a fixed point of the update (ridge 0)."""
+    n, R = 6, 2
+    Bs = synth.factor_normal(n, R, 77).astype(np.float64)
+    rows = np.array(list(itertools.combinations_with_replacement(range(n), order)), np.int32)
+    vals = np.array([sum(np.prod(Bs[list(t), r]) for r in range(R)) for t in rows])
+    # values in float32 carry the rounding; the update returns Bs up to that rounding
+    got, info = oracle.cp_als_step(order, n, rows.T.copy(), vals.astype(np.float32), Bs)
+    assert info == 0
+    assert np.allclose(got, Bs, rtol=1e-5, atol=1e-5)
+
+
+def test_cp_als_reports_singular_H():
+    n, R = 5, 3
+    T = synth.tensor_small_all_patterns(3, n, 3)
+    cidx, cval = canon(T)
+    B = np.zeros((n, R))          # B^T B = 0: the first pivot is not positive
+    got, info = oracle.cp_als_step(3, n, cidx, cval, B)
+    assert info == 1 and not got.any()
