@@ -19,6 +19,7 @@
  *   - MTTKRP  C[i,r] = sum A[i,k,l,..] B[k,r] B[l,r] ..        (Sec. 5.2.6)
  *   - SSYMV   y[i]   = sum_j A[i,j] x[j]                        (Sec. 5.2.1)
  *   - SYPRD   y      = sum x[i] A[i,j] x[j]                      (Sec. 5.2.3)
+ *   - TTM     C[i,j,l] = sum_k A[k,j,l] B[k,i]                   (Sec. 4.2, 5.2.5)
  *   - CP fit  ||X - sum_r b_r (x) ... (x) b_r||^2, unit weights, over the full
  *     tensor (the symmetric CPD that MTTKRP serves, Sec. 5.2.6).
  * A second, independent MTTKRP form uses per-run integer weights (the
@@ -30,7 +31,9 @@
  * the paper's printed multiplicities 6/3/3/1 and per-row update counts for the
  * 3-way MTTKRP, the lookup-table values [2,0,1,1,0,0,1/3], closed forms
  * N!/prod(m!) for the counts, x^T(Ax) = SYPRD, relabel and input-permutation
- * invariance.  No function here is "parity unpinned".
+ * invariance; for the TTM the assignments of the paper's symmetrised TTM
+ * listing cell by cell, output symmetry, and the MTTKRP obtained by one more
+ * contraction.  No function here is "parity unpinned".
  *
  * Conventions: 0-based indices; coordinate arrays are (order x nnz) row-major,
  * idx[q*nnz + e]; dense factors are row-major n x R.
@@ -246,6 +249,40 @@ int orc_mttkrp_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, cons
                 for (int q = 1; q < order; ++q) t *= B[(int64_t)c[q] * R + r];
                 M[i * R + r] += t;
                 if (Mabs) Mabs[i * R + r] += fabs(t);
+            }
+        } while (next_perm(c, order));
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mode-1 TTM (Sec. 4.2, TTM listing; Sec. 5.2.5)                            */
+/* ------------------------------------------------------------------------ */
+
+/* C[j_2, .., j_N, r] = sum_k A[k, j_2, .., j_N] B[k, r] over the full tensor:
+ * for every distinct permutation pi of every canonical entry,
+ * C[pi_2, .., pi_N, r] += v * B[pi_1, r].  C is dense, row-major
+ * n^(N-1) x R (the rank index fastest), and covers every output position,
+ * including the non-canonical ones.  Cabs (nullable) receives sum |terms|. */
+int orc_ttm_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval, const double* B,
+                 int R, double* C, double* Cabs) {
+    if (order < 2 || order > ORC_MAX_ORDER || R <= 0) return ORC_INVALID;
+    int64_t cells = 1;
+    for (int q = 1; q < order; ++q) cells *= n;
+    memset(C, 0, sizeof(double) * (size_t)cells * (size_t)R);
+    if (Cabs) memset(Cabs, 0, sizeof(double) * (size_t)cells * (size_t)R);
+    int32_t c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_tuple(c, order);
+        double v = (double)cval[e];
+        do {
+            int64_t cell = 0;
+            for (int q = 1; q < order; ++q) cell = cell * n + c[q];
+            for (int r = 0; r < R; ++r) {
+                double t = v * B[(int64_t)c[0] * R + r];
+                C[cell * R + r] += t;
+                if (Cabs) Cabs[cell * R + r] += fabs(t);
             }
         } while (next_perm(c, order));
     }

@@ -38,6 +38,11 @@ MUTANTS = {
     "cpals_transposed_solve": ("orc_cp_als_step", "t -= H[k * R + r] * B_new[i * R + k];",
                                "t -= H[r * R + k] * B_new[i * R + k];",
                                lambda: pins.test_cp_als_step_vs_dense(4, 5, 3)),
+    "ttm_identity_only": ("orc_ttm_enum", "} while (next_perm(c, order));", "} while (0);",
+                          lambda: pins.test_ttm_vs_dense_bruteforce(3, 6, 1)),
+    "ttm_wrong_factor_row": ("orc_ttm_enum", "double t = v * B[(int64_t)c[0] * R + r];",
+                             "double t = v * B[(int64_t)c[1] * R + r];",
+                             lambda: pins.test_paper_ttm_listing_assignments()),
     "counts_wrong_fibers": ("orc_counts", "if (e == 0 || c[0] != prev[0]) *root_fibers += 1;",
                             "*root_fibers += 1;", lambda: pins.test_counts_closed_forms(3)),
 }

@@ -389,3 +389,61 @@ def test_cp_als_reports_singular_H():
     B = np.zeros((n, R))          # B^T B = 0: the first pivot is not positive
     got, info = oracle.cp_als_step(3, n, cidx, cval, B)
     assert info == 1 and not got.any()
+
+
+# ----------------------------------------------------------------------------- TTM
+
+@pytest.mark.parametrize("order,n,seed", [(2, 6, 0), (3, 6, 1), (3, 5, 2), (4, 4, 3)])
+def test_ttm_vs_dense_bruteforce(order, n, seed):
+    """Independent path: the dense full tensor contracted over its first axis with B."""
+    T = synth.tensor_small_all_patterns(order, n, seed, density=0.7)
+    cidx, cval = canon(T)
+    R = 3
+    B = synth.factor_normal(n, R, seed + 10).astype(np.float64)
+    X = dense_full(order, n, cidx, cval)
+    want = np.tensordot(X, B, axes=([0], [0]))
+    got, gabs = oracle.ttm_enum(order, n, cidx, cval, B)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-13)
+    assert np.allclose(gabs, np.tensordot(np.abs(X), np.abs(B), axes=([0], [0])), rtol=1e-12, atol=1e-13)
+
+
+def _ttm_cells(C):
+    """Nonzero (out1, out2, B-row) cells of an order-3 TTM output taken with B = I."""
+    return {tuple(int(x) for x in t) for t in zip(*np.nonzero(C))}
+
+
+def test_paper_ttm_listing_assignments():
+    """With B = I (R = n), each assignment C[i,p,q] += A * B[s,i] lands in its own cell (p, q, s): the
+    oracle's nonzero cells for one stored entry are exactly the listing's assignments, and its
+    canonical-output cells (p <= q) are the three kept by the output-symmetry listing."""
+    gold = json.load(open(os.path.join(GOLD, "paper_ttm_assignments.json")))
+    n = 7
+    B = np.eye(n)
+    cases = {"j<k<l": (1, 3, 5), "j=k<l": (2, 2, 6), "j<k=l": (0, 4, 4), "j=k=l": (3, 3, 3)}
+    for pat, (j, k, l) in cases.items():
+        env = {"j": j, "k": k, "l": l}
+        # the stored permutation of the entry is irrelevant: give it reversed
+        C = oracle.ttm_enum(3, n, np.array([[l], [k], [j]], np.int32), np.array([1.0], np.float32), B,
+                            want_abs=False)
+        want = {tuple(env[s] for s in a) for a in gold["assignments"][pat]}
+        assert _ttm_cells(C) == want, pat
+        assert len(want) == len(gold["assignments"][pat])       # no two assignments share a cell
+        assert np.all(C[np.nonzero(C)] == 1.0)                    # each applied exactly once
+        if pat == "j<k<l":
+            canon_cells = {c for c in _ttm_cells(C) if c[0] <= c[1]}
+            kept = {tuple(env[s] for s in a) for a in gold["canonical_output_assignments_strict"]}
+            assert canon_cells == kept
+            assert len(_ttm_cells(C)) / len(canon_cells) == gold["savings_Sec_5_2_5"]["computations"]
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_ttm_output_symmetry_and_mttkrp_relation(seed):
+    """C[j,l,:] = C[l,j,:] (visible output symmetry), and contracting C with B once more gives the
+    MTTKRP: M[j,r] = sum_l C[j,l,r] B[l,r] (two oracle functions with no shared arithmetic)."""
+    T = synth.tensor_small_all_patterns(3, 9, seed, density=0.5)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(9, 4, seed).astype(np.float64)
+    C = oracle.ttm_enum(3, 9, cidx, cval, B, want_abs=False)
+    assert np.array_equal(C, C.transpose(1, 0, 2))
+    M = oracle.mttkrp_enum(3, 9, cidx, cval, B, want_abs=False)
+    assert np.allclose(np.einsum("jlr,lr->jr", C, B), M, rtol=1e-12, atol=1e-13)
