@@ -54,7 +54,12 @@ def peaks():
 # ---------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+    """Samples nvidia-smi SM clocks and throttle reasons (every 20 ms) while running.
+
+    Started before the warm-up; `window(t0, t1)` marks the timed region (host
+    perf_counter times) so the summary uses the samples read inside it, and
+    falls back to all samples taken under load when the region was shorter than
+    the sampling period (said in the summary)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -63,35 +68,44 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []   # (host time, csv line)
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.perf_counter() + 5.0
+            while not self.lines and time.perf_counter() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def window(self, t0: float, t1: float):
+        self.t0, self.t1 = t0, t1
 
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.05)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    @staticmethod
+    def _parse(lines):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -103,10 +117,19 @@ class ClockSampler:
             for nm, v in zip(names, parts[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+        return sm, mx, reasons
+
+    def summary(self):
+        inside = [ln for t, ln in self.lines if self.t0 is not None and self.t0 <= t <= self.t1 + 0.02]
+        sm, mx, reasons = self._parse(inside)
+        scope = "timed region"
+        if not sm:
+            sm, mx, reasons = self._parse([ln for _, ln in self.lines])
+            scope = "warm-up and timed region (timed region shorter than the 20 ms sampling period)"
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "scope": scope}
 
 
 # ---------------------------------------------------------------------------- helpers
@@ -200,7 +223,9 @@ def run_reference(args):
     T = make_main_tensor()
     import oracle
     B = synth.factor_normal(T.n, MAIN["rank"], MAIN["seed"]).astype(np.float64)
-    sample = min(T.nnz, int(os.environ.get("SYMGPU_REF_SAMPLE", "400000")))
+    # about 8M canonical entries over the whole timed run (a few seconds per million on one core)
+    default_sample = max(20_000, min(400_000, 8_000_000 // max(args.steps, 1)))
+    sample = min(T.nnz, int(os.environ.get("SYMGPU_REF_SAMPLE", str(default_sample))))
     cidx, cval = oracle.canonicalize(T.order, T.n, T.idx[:, :sample], T.val[:sample])
     for _ in range(args.warmup):
         oracle.mttkrp_enum(T.order, T.n, cidx, cval, B, want_abs=False)
@@ -272,19 +297,21 @@ def run_ours(args):
     tune_s = time.perf_counter() - t0
 
     step = lambda: X.mttkrp(B, M=M)
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- timed region (device value)
-    sg.profile_reset()
-    sg.profile_enable(True)
-    D.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(D.local) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+
+        # ---- timed region (device value)
+        sg.profile_reset()
+        sg.profile_enable(True)
+        D.barrier()
+        torch.cuda.synchronize()
         t_wall = time.perf_counter()
         times = timed_steps(torch, step, args.steps, flush, stream)
-        t_wall = time.perf_counter() - t_wall
+        t_end = time.perf_counter()
+        clk.window(t_wall, t_end)
+        t_wall = t_end - t_wall
     D.barrier()
     sg.profile_enable(False)
     prof = sg.profile_read()
@@ -322,6 +349,25 @@ def run_ours(args):
     rt = timed_steps(torch, lambda: X.mttkrp(B, M=M, residual=True, ws=ws_res), 5, flush, stream)
     extras["mttkrp_plus_residual_ms"] = float(np.mean(rt))
     extras["residual"] = float(res.item())
+
+    # ---- one symmetric CP-ALS update (MTTKRP, FP64 Gram, Cholesky inverse, apply), same tensor
+    try:
+        Bn = torch.empty_like(B)
+        ws_als = torch.empty(sg.lib().sym_cp_als_workspace_bytes(X.handle, MAIN["rank"]), dtype=torch.uint8,
+                             device=dev)
+        als = lambda: X.cp_als_step(B, B_out=Bn, ridge=1e-6, ws=ws_als)
+        als()
+        torch.cuda.synchronize()
+        sg.profile_reset()
+        sg.profile_enable(True)
+        at = timed_steps(torch, als, 5, flush, stream)
+        sg.profile_enable(False)
+        ap = sg.profile_read()
+        extras["cp_als_step"] = {"ms": float(np.mean(at)), "rank": MAIN["rank"],
+                                 "per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in ap.items()}}
+        del ws_als, Bn
+    except Exception as e:
+        extras["cp_als_step"] = {"error": repr(e)}
 
     # ---- expanded non-symmetric baseline on the same tensor
     if args.rows == "all" and D.rank == 0:
@@ -448,7 +494,100 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
     t = timed_steps(torch, lambda: sg.spmv(2000, rp, cl, vl, xd, y=y, syprd=True, ws=ws), 50, flush, stream)
     ms = float(np.mean(t))
     rows["ssymv_n2000_nnz20k"] = {"ms": ms, "canonical_nnz_per_s": A.nnz / (ms * 1e-3)}
+    dd = torch.abs(xd)
+    yb = torch.empty_like(dd)
+    for _ in range(5):
+        sg.bellman_step(2000, rp, cl, vl, dd, y=yb)
+    t = timed_steps(torch, lambda: sg.bellman_step(2000, rp, cl, vl, dd, y=yb), 50, flush, stream)
+    rows["ssymv_n2000_nnz20k"]["bellman_ford_step_ms"] = float(np.mean(t))
+    try:
+        rows["ssymv_bellman_n2M_16perrow"] = large_ssymv_row(torch, sg, dev, flush, stream, hbm_peak)
+    except Exception as e:
+        rows["ssymv_bellman_n2M_16perrow"] = {"error": repr(e)}
+    try:
+        rows["ttm3_unif_n2k_nnz5M_r32"] = ttm_row(torch, sg, dev, flush, stream, hbm_peak)
+    except Exception as e:
+        rows["ttm3_unif_n2k_nnz5M_r32"] = {"error": repr(e)}
     return rows
+
+
+def large_ssymv_row(torch, sg, dev, flush, stream, hbm_peak, n=1 << 21, per_row=16, seed=5):
+    """One symmetric matrix, n = 2^21, 16 upper draws per row (device-generated): SSYMV + SYPRD,
+    the full-CSR baseline and one Bellman-Ford min-plus step, all HBM-sized (~0.3 GB per operand)."""
+    batch = sg.make_batch(np.array([n]), per_row, seed)
+    rp = batch.rowptr.to(torch.int32)
+    cl, vl = batch.col, batch.val
+    nnz = int(cl.numel())
+    x = torch.from_numpy(synth.vector_uniform(n, seed)).to(dev)
+    y = torch.empty_like(x)
+    ws = sg.spmv_workspace(n, rp, cl, vl)
+    for _ in range(3):
+        sg.spmv(n, rp, cl, vl, x, y=y, syprd=True, ws=ws)
+    t = timed_steps(torch, lambda: sg.spmv(n, rp, cl, vl, x, y=y, syprd=True, ws=ws), 10, flush, stream)
+    ms = float(np.mean(t))
+    alg = nnz * 8 + (n + 1) * 4 + n * 4 * 3          # col + val, rowptr, x read, y read + write
+    out = {"n": n, "upper_nnz": nnz, "ssymv_syprd_ms": ms, "canonical_nnz_per_s": nnz / (ms * 1e-3),
+           "effective_gbs": alg / (ms * 1e-3) / 1e9, "hbm_frac": alg / (ms * 1e-3) / 1e9 / hbm_peak}
+    F = sg.FullCSR(n, rp, cl, vl)
+    yf = torch.empty_like(x)
+    for _ in range(3):
+        F.spmv(x, y=yf)
+    tf = timed_steps(torch, lambda: F.spmv(x, y=yf), 10, flush, stream)
+    out["full_csr_ms"] = float(np.mean(tf))
+    out["speedup_over_full_csr"] = out["full_csr_ms"] / ms
+    d = torch.abs(x)
+    yb = torch.empty_like(d)
+    for _ in range(3):
+        sg.bellman_step(n, rp, cl, vl, d, y=yb)
+    tb = timed_steps(torch, lambda: sg.bellman_step(n, rp, cl, vl, d, y=yb), 10, flush, stream)
+    out["bellman_ford_step_ms"] = float(np.mean(tb))
+    out["bellman_ford_effective_gbs"] = alg / (out["bellman_ford_step_ms"] * 1e-3) / 1e9
+    return out
+
+
+def ttm_row(torch, sg, dev, flush, stream, hbm_peak, n=2000, nnz=5_000_000, rank=32, seed=3):
+    """Symmetric mode-1 TTM (3-way, uniform): canonical-triangle output (packed), full output
+    (canonical + replication), and the expanded non-symmetric baseline."""
+    T = synth.make_tensor(3, n, nnz, seed, "uniform")
+    X = sg.SymTensor(torch.from_numpy(T.idx).to(dev), torch.from_numpy(T.val).to(dev), n)
+    X.add_leaf_index()
+    info = X.info()
+    B = torch.from_numpy(synth.factor_normal(n, rank, seed)).to(dev)
+    Cp = torch.empty((n * (n + 1) // 2, rank), dtype=torch.float32, device=dev)
+    Cf = torch.empty((n, n, rank), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        X.ttm(B, "packed", C_out=Cp)
+    sg.profile_reset()
+    sg.profile_enable(True)
+    tp = timed_steps(torch, lambda: X.ttm(B, "packed", C_out=Cp), 10, flush, stream)
+    sg.profile_enable(False)
+    prof = sg.profile_read()
+    for _ in range(2):
+        X.ttm(B, "full", C_out=Cf)
+    tf = timed_steps(torch, lambda: X.ttm(B, "full", C_out=Cf), 10, flush, stream)
+    ms_p, ms_f = float(np.mean(tp)), float(np.mean(tf))
+    # stream (+ leaf index) read once, B read once, packed output written once
+    alg = info["nnz"] * 12 + info["nnz_strict"] * 12 + n * rank * 4 + n * (n + 1) // 2 * rank * 4
+    kl, kms = prof.get("ttm", (1, ms_p))
+    out = {"canonical_nnz": info["nnz"], "rank": rank, "packed_ms": ms_p, "full_ms": ms_f,
+           "canonical_nnz_per_s": info["nnz"] / (ms_p * 1e-3),
+           "effective_gbs": alg / (ms_p * 1e-3) / 1e9, "hbm_frac": alg / (ms_p * 1e-3) / 1e9 / hbm_peak,
+           "per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()}}
+    E = X.expanded()
+    Ce = torch.empty((n, n, rank), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        E.ttm(B, C_out=Ce)
+    te = timed_steps(torch, lambda: E.ttm(B, C_out=Ce), 10, flush, stream)
+    out["expanded_ms"] = float(np.mean(te))
+    out["expanded_nnz"] = E.nnz
+    out["speedup_packed_over_expanded"] = out["expanded_ms"] / ms_p
+    out["speedup_full_over_expanded"] = out["expanded_ms"] / ms_f
+    X.ttm(B, "full", C_out=Cf)
+    torch.cuda.synchronize()
+    out["max_abs_diff_full_vs_expanded"] = float((Cf - Ce).abs().max())
+    E.close()
+    X.close()
+    return out
 
 
 def batch_row(torch, sg, dev, flush, stream, hbm_peak, count=4096, per_row=16, seed=3):
@@ -637,10 +776,32 @@ def run_batch_only(args):
     print(json.dumps({"mode": "batch-only (profiling)", "instances": len(sizes), "upper_nnz": int(batch.col.numel())}))
 
 
+def run_ttm_only(args):
+    """Profiling mode for the symmetric TTM row (3-way uniform, n = 2,000, 5M entries, R = 32): the packed
+    and full layouts with the default schedule (leaf-index second pass), `--steps` times each."""
+    import torch
+
+    import paper_2406_09266_gb300 as sg
+    sg.load()
+    dev = torch.device("cuda")
+    n, rank = 2000, 32
+    T = synth.make_tensor(3, n, 5_000_000, 3, "uniform")
+    X = sg.SymTensor(torch.from_numpy(T.idx).to(dev), torch.from_numpy(T.val).to(dev), n)
+    X.add_leaf_index()
+    B = torch.from_numpy(synth.factor_normal(n, rank, 3)).to(dev)
+    Cp = torch.empty((n * (n + 1) // 2, rank), dtype=torch.float32, device=dev)
+    Cf = torch.empty((n, n, rank), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup + args.steps):
+        X.ttm(B, "packed", C_out=Cp)
+        X.ttm(B, "full", C_out=Cf)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "ttm-only (profiling)", "canonical_nnz": X.info()["nnz"], "rank": rank}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rows", default="all", choices=["main", "all"])
@@ -648,6 +809,8 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="profiling mode: setup, warm-up and the timed steps only (no e2e or extra rows), with "
                          "the MTTKRP configuration fixed instead of autotuned")
+    ap.add_argument("--ttm-only", action="store_true",
+                    help="profiling mode: the symmetric TTM kernels on the TTM row's tensor, nothing else")
     ap.add_argument("--batch-only", type=int, default=0, metavar="INSTANCES",
                     help="profiling mode: build a batch of this many instances and run the batched SSYMV a few times")
     args = ap.parse_args()
@@ -657,6 +820,8 @@ def main():
         run_reference(args)
     elif args.batch_only:
         run_batch_only(args)
+    elif args.ttm_only:
+        run_ttm_only(args)
     else:
         run_ours(args)
 

@@ -373,10 +373,46 @@ sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype bdt, int r
  * in FP64; the n x R product runs in FP32 and is stored in B's dtype.
  * info [device, 1 int] (nullable) receives 0, or the 1-based column of a
  * non-positive pivot (then B_out = 0).  B_out must not alias B.  ws >=
- * sym_cp_als_workspace_bytes (it holds M, G, L^{-1} and H^{-1}). */
+ * sym_cp_als_workspace_bytes (it holds M, G, L, L^T, H^{-1} and a status word). */
 size_t sym_cp_als_workspace_bytes(sym_tensor X, int rank);
 sym_status sym_cp_als_step(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, void* B_out,
                            int64_t ldo, double ridge, int* info, void* ws, size_t ws_bytes, sym_stream_t stream);
+
+/* Mode-1 TTM of a fully symmetric 3-way tensor with visible output symmetry
+ * (Sec. 4.2, the symmetrised TTM listing and the output-symmetry listings;
+ * Sec. 5.2.5):
+ *   C[j, l, r] = sum_k A[k, j, l] B[k, r]      (paper: C[i, j, l] = A[k, j, l] * B[k, i])
+ * C is symmetric in (j, l); only the canonical triangle j <= l is computed,
+ * each canonical entry of A is read once and makes one update per distinct
+ * index value (3 for a strict entry: half of its 6 assignments).
+ * Layout of C (device, float32, caller-owned, 16-byte aligned, overwritten),
+ * rank index fastest, `rank` floats per output position:
+ *   SYM_TTM_PACKED: positions (j, l), j <= l, at p = j n - j (j - 1) / 2 + (l - j);
+ *   SYM_TTM_FULL:   n x n positions at j n + l; the lower triangle is filled by a
+ *                   replication pass after the canonical computation.
+ * sym_ttm_output_elems gives the float count (-1 for bad arguments).
+ * B: n x rank (row stride ldb), FP32 or BF16; rank 4..128, multiple of 4.
+ * Order other than 3, or n > 2^21 (whose output could not be stored):
+ * SYM_E_UNSUPPORTED.  Results are accumulated with floating-point atomics:
+ * not bitwise reproducible run to run. */
+typedef enum { SYM_TTM_PACKED = 0, SYM_TTM_FULL = 1 } sym_ttm_layout;
+/* Schedule of the TTM kernels (nullable in sym_ttm: defaults).
+ * entries_per_warp: consecutive canonical entries per warp chunk (multiple of 32);
+ * ctas_per_sm: 0 = one chunk per warp over a full grid; 1..8 = persistent grid
+ *   of that many CTAs per SM, warp w taking chunks w, w + W, ... so the GPU
+ *   walks the sorted stream front to back (output rows stay in L2);
+ * leaf_index: -1 = use the tensor's leaf index when it has one, 0 = never,
+ *   1 = always (SYM_E_INVALID without one).  With it the k = a updates of
+ *   strict entries become per-fiber sums in a second pass. */
+typedef struct {
+    int32_t entries_per_warp;
+    int32_t ctas_per_sm;
+    int32_t leaf_index;
+} sym_ttm_cfg;
+sym_status sym_ttm_default_config(sym_ttm_cfg* out);
+int64_t sym_ttm_output_elems(int64_t n, int rank, sym_ttm_layout layout);
+sym_status sym_ttm(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* C, sym_ttm_layout layout,
+                   const sym_ttm_cfg* cfg, sym_stream_t stream);
 
 /* ===================================================================== */
 /* Baseline: MTTKRP over the fully expanded (non-symmetric) tensor          */
@@ -395,6 +431,12 @@ sym_status sym_expanded_export(sym_expanded E, int32_t* eidx, int64_t ld_out, fl
  * except at chunk seams (entries are sorted by mode 1). */
 sym_status sym_mttkrp_expanded(sym_expanded E, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
                                int64_t ldm, sym_stream_t stream);
+/* Plain mode-1 TTM over the expanded 3-way tensor (no symmetry used): every
+ * output position of the full n x n x rank layout (SYM_TTM_FULL) is computed,
+ * each (c_1, c_2) fiber summed in registers.  Order other than 3:
+ * SYM_E_UNSUPPORTED. */
+sym_status sym_ttm_expanded(sym_expanded E, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* C,
+                            sym_stream_t stream);
 sym_status sym_expanded_destroy(sym_expanded E);
 
 /* ===================================================================== */

@@ -68,7 +68,8 @@ def lib():
                                      C.POINTER(C.c_int64)]
             L.orc_cp_als_step.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, C.c_double,
                                           f64p, C.POINTER(C.c_int)]
-            L.orc_ttm_enum.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, f64p, f64p]
+            L.orc_ttm_enum.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, i32p, C.c_int64,
+                                       f64p, f64p]
             for name in ("orc_ttm_enum", "orc_cp_als_step", "orc_canonicalize", "orc_check_canonical", "orc_counts", "orc_mttkrp_enum",
                          "orc_mttkrp_runs", "orc_check_upper_csr", "orc_ssymv_enum", "orc_syprd_enum",
                          "orc_bellman_enum", "orc_cpfit", "orc_expand"):
@@ -219,18 +220,27 @@ def cp_als_step(order, n, cidx, cval, B, ridge=0.0):
     return out, info.value
 
 
-def ttm_enum(order, n, cidx, cval, B, want_abs=True):
+def ttm_enum(order, n, cidx, cval, B, want_abs=True, rows=None):
     """Definitional mode-1 TTM, FP64: C[j_2..j_N, r] = sum_k A[k, j_2..j_N] B[k, r].
 
-    Returns the full dense output, shape (n,)*(order-1) + (R,) (and its |terms| sums)."""
+    Returns the full dense output, shape (n,)*(order-1) + (R,) (and its |terms| sums); with `rows`
+    only the slices C[j_2 = rows[s], ...], stacked in that order."""
     cidx = _c(cidx, np.int32)
     cval = _c(cval, np.float32)
     B = _c(B, np.float64)
     R = B.shape[1]
-    shape = (n,) * (order - 1) + (R,)
+    slot = None
+    first = n
+    if rows is not None:
+        rows = np.asarray(rows)
+        slot = np.full(n, -1, dtype=np.int32)
+        slot[rows] = np.arange(rows.size, dtype=np.int32)
+        first = rows.size
+    shape = (first,) + (n,) * (order - 2) + (R,)
     Cm = np.zeros(shape, dtype=np.float64)
     Ca = np.zeros(shape, dtype=np.float64) if want_abs else None
-    _check(lib().orc_ttm_enum(order, n, cval.shape[0], _p(cidx), _p(cval), _p(B), R, _p(Cm), _p(Ca)), "ttm_enum")
+    _check(lib().orc_ttm_enum(order, n, cval.shape[0], _p(cidx), _p(cval), _p(B), R, _p(slot), first, _p(Cm),
+                              _p(Ca)), "ttm_enum")
     return (Cm, Ca) if want_abs else Cm
 
 

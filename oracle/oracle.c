@@ -263,12 +263,15 @@ int orc_mttkrp_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, cons
  * for every distinct permutation pi of every canonical entry,
  * C[pi_2, .., pi_N, r] += v * B[pi_1, r].  C is dense, row-major
  * n^(N-1) x R (the rank index fastest), and covers every output position,
- * including the non-canonical ones.  Cabs (nullable) receives sum |terms|. */
+ * including the non-canonical ones.  Cabs (nullable) receives sum |terms|.
+ * row_slot (nullable, length n) restricts the work to the first output index
+ * j_2 with row_slot[j_2] >= 0 and stores that slice at slot row_slot[j_2]
+ * (C is then nslots x n^(N-2) x R). */
 int orc_ttm_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval, const double* B,
-                 int R, double* C, double* Cabs) {
+                 int R, const int32_t* row_slot, int64_t nslots, double* C, double* Cabs) {
     if (order < 2 || order > ORC_MAX_ORDER || R <= 0) return ORC_INVALID;
-    int64_t cells = 1;
-    for (int q = 1; q < order; ++q) cells *= n;
+    int64_t cells = row_slot ? nslots : n;
+    for (int q = 2; q < order; ++q) cells *= n;
     memset(C, 0, sizeof(double) * (size_t)cells * (size_t)R);
     if (Cabs) memset(Cabs, 0, sizeof(double) * (size_t)cells * (size_t)R);
     int32_t c[ORC_MAX_ORDER];
@@ -277,8 +280,9 @@ int orc_ttm_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, const f
         sort_tuple(c, order);
         double v = (double)cval[e];
         do {
-            int64_t cell = 0;
-            for (int q = 1; q < order; ++q) cell = cell * n + c[q];
+            int64_t cell = row_slot ? row_slot[c[1]] : c[1];
+            if (cell < 0) continue;
+            for (int q = 2; q < order; ++q) cell = cell * n + c[q];
             for (int r = 0; r < R; ++r) {
                 double t = v * B[(int64_t)c[0] * R + r];
                 C[cell * R + r] += t;

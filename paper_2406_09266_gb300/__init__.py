@@ -25,6 +25,7 @@ STATUS = {0: "SYM_OK", -1: "SYM_E_INVALID", -2: "SYM_E_NONCANONICAL", -3: "SYM_E
           -10: "SYM_E_UNSUPPORTED", -11: "SYM_E_NOTFOUND", 1: "SYM_PENDING"}
 F32, BF16 = 0, 1
 DUP_ERROR, DUP_KEEP_EQUAL = 0, 1
+TTM_PACKED, TTM_FULL = 0, 1
 
 
 class SymError(RuntimeError):
@@ -34,6 +35,10 @@ class SymError(RuntimeError):
 
 
 # ------------------------------------------------------------------ C structs
+
+class TtmCfg(C.Structure):
+    _fields_ = [("entries_per_warp", C.c_int32), ("ctas_per_sm", C.c_int32), ("leaf_index", C.c_int32)]
+
 
 class CsrUpper(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
@@ -164,6 +169,11 @@ _SIGS = {
     "sym_cp_als_workspace_bytes": ([C.c_void_p, C.c_int], C.c_size_t),
     "sym_cp_als_step": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                          C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "sym_ttm_output_elems": ([C.c_int64, C.c_int, C.c_int], C.c_int64),
+    "sym_ttm_default_config": ([C.c_void_p], C.c_int),
+    "sym_ttm": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+                C.c_int),
+    "sym_ttm_expanded": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "sym_expanded_bytes": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_expanded_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p,
                              C.c_void_p], C.c_int),
@@ -465,6 +475,31 @@ class SymTensor:
               "sym_cp_als_step")
         return B_out, info
 
+    def ttm(self, B: torch.Tensor, layout: str = "packed", C_out: torch.Tensor | None = None, cfg: dict | None = None,
+            stream=None):
+        """Mode-1 TTM C[j, l, :] = sum_k A[k, j, l] B[k, :] (order 3).
+
+        layout "packed": the canonical triangle j <= l, shape (n (n + 1) / 2, R);
+        layout "full": shape (n, n, R), the lower triangle filled by replication.
+        cfg: fields of sym_ttm_cfg to override (entries_per_warp, ctas_per_sm, leaf_index)."""
+        rank = B.shape[1]
+        code = {"packed": TTM_PACKED, "full": TTM_FULL}[layout]
+        elems = lib().sym_ttm_output_elems(self.n, rank, code)
+        if elems < 0:
+            raise SymError(-1, "sym_ttm_output_elems")
+        if C_out is None:
+            shape = (self.n * (self.n + 1) // 2, rank) if code == TTM_PACKED else (self.n, self.n, rank)
+            C_out = torch.empty(shape, dtype=torch.float32, device=B.device)
+        if C_out.numel() < elems or not C_out.is_contiguous():
+            raise SymError(-1, "sym_ttm (output buffer)")
+        tc = TtmCfg()
+        check(lib().sym_ttm_default_config(C.byref(tc)), "sym_ttm_default_config")
+        for k, v in (cfg or {}).items():
+            setattr(tc, k, int(v))
+        check(lib().sym_ttm(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(C_out), code,
+                            C.byref(tc), _stream(stream)), "sym_ttm")
+        return C_out
+
     def expanded(self, stream=None) -> "Expanded":
         return Expanded(self, stream)
 
@@ -557,6 +592,15 @@ class Expanded:
         check(lib().sym_mttkrp_expanded(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(M),
                                         M.stride(0), _stream(stream)), "sym_mttkrp_expanded")
         return M
+
+    def ttm(self, B, C_out=None, stream=None):
+        """Plain TTM over the expanded tensor (order 3): full (n, n, R) output."""
+        rank = B.shape[1]
+        if C_out is None:
+            C_out = torch.empty((self.n, self.n, rank), dtype=torch.float32, device=B.device)
+        check(lib().sym_ttm_expanded(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(C_out),
+                                     _stream(stream)), "sym_ttm_expanded")
+        return C_out
 
     def close(self):
         if getattr(self, "handle", None):

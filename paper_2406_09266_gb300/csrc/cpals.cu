@@ -3,10 +3,12 @@
 //   M     = MTTKRP(X, B)                                  (symmetric kernels)
 //   H     = (B^T B) raised elementwise to N-1, + ridge I   (FP64)
 //   B_new = M H^{-1}
-// H is R x R (R <= 128): one CTA factorises it (Cholesky, FP64), inverts the
-// triangular factor and forms H^{-1} = L^{-T} L^{-1}; the n x R product with
-// M runs in FP32 with H^{-1} staged in shared memory.  A non-positive pivot is
-// reported in *info (1-based column) and leaves B_new = 0.
+// H is R x R (R <= 128): one CTA factorises it (right-looking Cholesky, FP64,
+// in shared memory); R warps spread over R/8 CTAs then solve one column of
+// H^{-1} = L^{-T} L^{-1} each (FP64 is slow per SM on this part, so the
+// O(R^3) inverse is not left to one CTA); the n x R product with M runs in
+// FP32 with H^{-1} staged in shared memory.  A non-positive pivot is reported
+// in *info (1-based column) and leaves B_new = 0.
 #include <algorithm>
 
 #include "common.cuh"
@@ -21,65 +23,114 @@ __device__ __forceinline__ int tri_index(int r, int s, int R) {  // r <= s
     return r * R - r * (r - 1) / 2 + (s - r);
 }
 
-// H = G^(o(N-1)) + ridge I; L = chol(H); Linv = L^{-1}; Hinv = Linv^T Linv.
-__global__ void k_chol_inverse(const double* __restrict__ G, int R, int power, double ridge,
-                               double* __restrict__ Linv, float* __restrict__ Hinv, int* __restrict__ info_out) {
-    extern __shared__ double L[];  // R x R, lower triangle used
+// H = G^(o(N-1)) + ridge I, factorised H = L L^T in place (right-looking
+// Cholesky, FP64, one CTA of 32 x 32 threads, the whole matrix in shared
+// memory).  Writes L and L^T (row-major, FP64) and the reciprocals of L's
+// diagonal for the column solves, and the 1-based column of the first
+// non-positive pivot to *info (0 on success).
+__global__ void __launch_bounds__(1024) k_cholesky(const double* __restrict__ G, int R, int power, double ridge,
+                                                   double* __restrict__ Lg, double* __restrict__ LTg,
+                                                   double* __restrict__ dinv, int* __restrict__ fail_out,
+                                                   int* __restrict__ info_out) {
+    extern __shared__ double A[];  // R x R
     __shared__ int s_fail;
-    __shared__ double s_d;
+    __shared__ double s_rd;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_fail = 0;
     for (int k = threadIdx.x; k < R * R; k += blockDim.x) {
         const int r = k / R, c = k % R;
         const double g = G[r <= c ? tri_index(r, c, R) : tri_index(c, r, R)];
         double h = 1.0;
         for (int q = 0; q < power; ++q) h *= g;
-        L[k] = h + (r == c ? ridge : 0.0);
+        A[k] = h + (r == c ? ridge : 0.0);
     }
     __syncthreads();
     for (int j = 0; j < R; ++j) {
         if (threadIdx.x == 0) {
-            double d = L[j * R + j];
-            for (int k = 0; k < j; ++k) d -= L[j * R + k] * L[j * R + k];
+            const double d = A[j * R + j];
             if (!(d > 0.0)) {
                 s_fail = j + 1;
             } else {
-                s_d = sqrt(d);
-                L[j * R + j] = s_d;
+                const double sd = sqrt(d);
+                A[j * R + j] = sd;
+                s_rd = 1.0 / sd;
             }
         }
         __syncthreads();
         if (s_fail) break;
-        for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) {
-            double t = L[i * R + j];
-            for (int k = 0; k < j; ++k) t -= L[i * R + k] * L[j * R + k];
-            L[i * R + j] = t / s_d;
+        const double rd = s_rd;
+        for (int i = j + 1 + threadIdx.x; i < R; i += blockDim.x) A[i * R + j] *= rd;
+        __syncthreads();
+        // trailing lower triangle: A[i][k] -= A[i][j] A[k][j], j < k <= i
+        for (int i = j + 1 + ty; i < R; i += 32) {
+            const double aij = A[i * R + j];
+            for (int k = j + 1 + tx; k <= i; k += 32) A[i * R + k] -= aij * A[k * R + j];
         }
         __syncthreads();
     }
     const int fail = s_fail;
-    if (threadIdx.x == 0 && info_out) *info_out = fail;
-    if (fail) {
-        for (int k = threadIdx.x; k < R * R; k += blockDim.x) Hinv[k] = 0.f;
+    if (threadIdx.x == 0) {
+        *fail_out = fail;
+        if (info_out) *info_out = fail;
+    }
+    if (fail) return;
+    for (int k = threadIdx.x; k < R * R; k += blockDim.x) {
+        const int r = k / R, c = k % R;
+        const double v = (c <= r) ? A[k] : 0.0;
+        Lg[k] = v;             // L[r][c]
+        LTg[c * R + r] = v;    // L^T[c][r]
+    }
+    for (int i = threadIdx.x; i < R; i += blockDim.x) dinv[i] = 1.0 / A[i * R + i];
+}
+
+constexpr int INV_WARPS = 8;  // columns per CTA
+
+// Column c of H^{-1} = L^{-T} L^{-1} e_c, one warp per column: forward solve
+// L y = e_c (y_i = 0 for i < c), then back solve L^T x = y; each step is a
+// dot product over the warp's lanes with a row of L (then of L^T) staged in
+// shared memory.  H^{-1} is symmetric, so the column is written as row c.
+// After a failed factorisation the output is 0.
+__global__ void __launch_bounds__(INV_WARPS * 32) k_inverse_columns(const double* __restrict__ L,
+                                                                   const double* __restrict__ LT,
+                                                                   const double* __restrict__ dinv, int R,
+                                                                   const int* __restrict__ fail,
+                                                                   float* __restrict__ Hinv) {
+    extern __shared__ double sm[];  // R x R factor, then INV_WARPS x R solution vectors
+    double* F = sm;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * INV_WARPS + w;
+    double* y = sm + (size_t)R * R + (size_t)w * R;
+    const bool live = c < R;
+    if (*fail) {
+        if (live)
+            for (int i = lane; i < R; i += 32) Hinv[(int64_t)c * R + i] = 0.f;
         return;
     }
-    // column c of L^{-1} by forward substitution (one thread per column)
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        for (int i = 0; i < R; ++i) {
-            if (i < c) {
-                Linv[i * R + c] = 0.0;
-                continue;
-            }
-            double t = (i == c) ? 1.0 : 0.0;
-            for (int k = c; k < i; ++k) t -= L[i * R + k] * Linv[k * R + c];
-            Linv[i * R + c] = t / L[i * R + i];
+    for (int k = threadIdx.x; k < R * R; k += blockDim.x) F[k] = L[k];
+    if (live)
+        for (int i = lane; i < R; i += 32) y[i] = 0.0;
+    __syncthreads();
+    if (live) {
+        for (int i = c; i < R; ++i) {
+            double t = 0.0;
+            for (int k = c + lane; k < i; k += 32) t += F[i * R + k] * y[k];
+            t = warp_sum(t);
+            if (lane == 0) y[i] = ((i == c ? 1.0 : 0.0) - t) * dinv[i];
+            __syncwarp();
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < R * R; k += blockDim.x) {
-        const int r = k / R, c = k % R;
-        double t = 0.0;
-        for (int q = max(r, c); q < R; ++q) t += Linv[q * R + r] * Linv[q * R + c];
-        Hinv[k] = (float)t;
+    for (int k = threadIdx.x; k < R * R; k += blockDim.x) F[k] = LT[k];
+    __syncthreads();
+    if (live) {
+        for (int i = R - 1; i >= 0; --i) {
+            double t = 0.0;
+            for (int k = i + 1 + lane; k < R; k += 32) t += F[i * R + k] * y[k];
+            t = warp_sum(t);
+            if (lane == 0) y[i] = (y[i] - t) * dinv[i];
+            __syncwarp();
+        }
+        for (int i = lane; i < R; i += 32) Hinv[(int64_t)c * R + i] = (float)y[i];
     }
 }
 
@@ -117,8 +168,11 @@ __global__ void k_apply_inverse(const float* __restrict__ M, int64_t n, int R, c
 struct AlsWs {
     float* M;
     double* G;
-    double* Linv;
+    double* L;
+    double* LT;
+    double* dinv;
     float* Hinv;
+    int* fail;
 };
 
 template <typename C>
@@ -126,8 +180,11 @@ AlsWs layout_als(C& c, int64_t n, int R) {
     AlsWs w;
     w.M = c.template take<float>((size_t)std::max<int64_t>(n, 1) * R);
     w.G = c.template take<double>((size_t)R * (R + 1) / 2);
-    w.Linv = c.template take<double>((size_t)R * R);
+    w.L = c.template take<double>((size_t)R * R);
+    w.LT = c.template take<double>((size_t)R * R);
+    w.dinv = c.template take<double>((size_t)R);
     w.Hinv = c.template take<float>((size_t)R * R);
+    w.fail = c.template take<int>(1);
     return w;
 }
 
@@ -172,10 +229,18 @@ extern "C" sym_status sym_cp_als_step(sym_tensor X, const void* B, sym_dtype bdt
     st = gram_launch(X->n, B, bf16, rank, ldb, w.G, s);
     if (st != SYM_OK) return st;
     const size_t lsmem = sizeof(double) * (size_t)rank * rank;
-    SYM_CUDA(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+    SYM_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
     {
-        SYM_PROF("cp_als_factorise", s);
-        k_chol_inverse<<<1, 128, lsmem, s>>>(w.G, rank, X->order - 1, ridge, w.Linv, w.Hinv, info);
+        SYM_PROF("cp_als_cholesky", s);
+        k_cholesky<<<1, 1024, lsmem, s>>>(w.G, rank, X->order - 1, ridge, w.L, w.LT, w.dinv, w.fail, info);
+        SYM_CHECK_LAUNCH();
+    }
+    {
+        const size_t ismem = lsmem + sizeof(double) * INV_WARPS * (size_t)rank;  // <= 136 KB at rank 128
+        SYM_CUDA(cudaFuncSetAttribute(k_inverse_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+        SYM_PROF("cp_als_inverse", s);
+        k_inverse_columns<<<(rank + INV_WARPS - 1) / INV_WARPS, INV_WARPS * 32, ismem, s>>>(w.L, w.LT, w.dinv, rank,
+                                                                                          w.fail, w.Hinv);
         SYM_CHECK_LAUNCH();
     }
     if (X->n == 0) return SYM_OK;

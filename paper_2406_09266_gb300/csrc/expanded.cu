@@ -369,6 +369,102 @@ extern "C" sym_status sym_mttkrp_expanded(sym_expanded E, const void* B, sym_dty
     }
 }
 
+namespace symgpu {
+namespace {
+
+// Plain mode-1 TTM over the expanded 3-way tensor: with A stored in full and
+// sorted by (c_1, c_2, c_3), C[c_1, c_2, :] = sum over the (c_1, c_2) fiber of
+// v B[c_3, :] (A[k, j, l] = A[j, l, k] for the full tensor), summed in
+// registers and flushed once per fiber; every output position, n x n, is
+// computed.  No symmetry is used.
+template <int KW, int L, bool BF16>
+__global__ void __launch_bounds__(256) k_ttm3_expanded(const uint64_t* __restrict__ klo,
+                                                       const uint64_t* __restrict__ khi,
+                                                       const float* __restrict__ val, int64_t nnz, int bits,
+                                                       int64_t n, const void* __restrict__ B, int64_t ldb, int R,
+                                                       float* __restrict__ C) {
+    constexpr int64_t CHUNK = 256;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L;
+    const int col = 4 * (lane % L);
+    const bool on = col < R;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t start = warp * CHUNK;
+    const int64_t end = min(start + CHUNK, nnz);
+    if (start >= end) return;
+    int32_t ca = -1, cb = -1;
+    float4 acc = f4_zero();
+    for (int64_t b0 = start; b0 < end; b0 += 32) {
+        const int64_t e = b0 + lane;
+        uint64_t mlo = 0, mhi = 0;
+        float mv = 0.f;
+        if (e < end) {
+            mlo = __ldcs(klo + e);
+            if (KW == 2) mhi = __ldcs(khi + e);
+            mv = __ldcs(val + e);
+        }
+#pragma unroll 1
+        for (int t = 0; t < L; ++t) {
+            const int src = g * L + t;
+            const uint64_t lo = __shfl_sync(0xffffffffu, mlo, src);
+            const uint64_t hi = (KW == 2) ? __shfl_sync(0xffffffffu, mhi, src) : 0ull;
+            const float v = __shfl_sync(0xffffffffu, mv, src);
+            if (b0 + src >= end) continue;
+            int32_t c[3];
+            unpack_key<3, KW>(KeyWords{lo, hi}, bits, c);
+            if (c[0] != ca || c[1] != cb) {
+                if (ca >= 0 && on) red_add_f4(C + ((int64_t)ca * n + cb) * R + col, acc);
+                acc = f4_zero();
+                ca = c[0];
+                cb = c[1];
+            }
+            if (on) acc = f4_fmas(load_row4<BF16>(B, c[2], ldb, col), v, acc);
+        }
+    }
+    if (ca >= 0 && on) red_add_f4(C + ((int64_t)ca * n + cb) * R + col, acc);
+}
+
+template <int KW, int L>
+void launch_ttm_exp(const sym_expanded_s* E, const void* B, bool bf16, int64_t ldb, int R, float* C, cudaStream_t s) {
+    const int64_t warps = (E->nnz + 255) / 256;
+    const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    if (bf16)
+        k_ttm3_expanded<KW, L, true><<<grid, 256, 0, s>>>(E->klo, E->khi, E->val, E->nnz, E->bits, E->n, B, ldb, R, C);
+    else
+        k_ttm3_expanded<KW, L, false><<<grid, 256, 0, s>>>(E->klo, E->khi, E->val, E->nnz, E->bits, E->n, B, ldb, R, C);
+}
+
+template <int KW>
+void launch_ttm_exp_l(const sym_expanded_s* E, const void* B, bool bf16, int64_t ldb, int R, float* C,
+                      cudaStream_t s) {
+    const int q = R / 4;
+    if (q <= 1) launch_ttm_exp<KW, 1>(E, B, bf16, ldb, R, C, s);
+    else if (q <= 2) launch_ttm_exp<KW, 2>(E, B, bf16, ldb, R, C, s);
+    else if (q <= 4) launch_ttm_exp<KW, 4>(E, B, bf16, ldb, R, C, s);
+    else if (q <= 8) launch_ttm_exp<KW, 8>(E, B, bf16, ldb, R, C, s);
+    else if (q <= 16) launch_ttm_exp<KW, 16>(E, B, bf16, ldb, R, C, s);
+    else launch_ttm_exp<KW, 32>(E, B, bf16, ldb, R, C, s);
+}
+
+}  // namespace
+}  // namespace symgpu
+
+extern "C" sym_status sym_ttm_expanded(sym_expanded E, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* C,
+                                       sym_stream_t stream) {
+    if (!E || !B || !C) return SYM_E_INVALID;
+    if (E->order != 3 || E->kw != 1) return SYM_E_UNSUPPORTED;
+    if (bdt != SYM_F32 && bdt != SYM_BF16) return SYM_E_INVALID;
+    if (rank < 4 || rank > 128 || rank % 4 != 0 || ldb < rank || ldb % 4) return SYM_E_INVALID;
+    if (!aligned(B, bdt == SYM_BF16 ? 8 : 16) || !aligned(C, 16)) return SYM_E_INVALID;
+    cudaStream_t s = as_stream(stream);
+    SYM_CUDA(cudaMemsetAsync(C, 0, sizeof(float) * (size_t)E->n * E->n * rank, s));
+    if (E->nnz == 0) return SYM_OK;
+    SYM_PROF("ttm_expanded", s);
+    launch_ttm_exp_l<1>(E, B, bdt == SYM_BF16, ldb, rank, C, s);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
 extern "C" sym_status sym_expanded_destroy(sym_expanded E) {
     delete E;
     return SYM_OK;

@@ -139,7 +139,7 @@ __device__ __forceinline__ void warp_range(int64_t nnz, int64_t chunk, int64_t* 
 //           root level only: row c_N receives (N-1)! * sum over its subtree of
 //           v * prod_{q<N} B[c_q], accumulated in registers.
 template <int N, int KW, int L, bool BF16, int MODE>
-__global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict(
+__global__ void __launch_bounds__(MT_THREADS, (N <= 3 && KW == 1 && L > 1) ? 5 : 1) k_mttkrp_strict(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
     int64_t chunk, int stream_hint) {

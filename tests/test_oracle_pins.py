@@ -447,3 +447,13 @@ def test_ttm_output_symmetry_and_mttkrp_relation(seed):
     assert np.array_equal(C, C.transpose(1, 0, 2))
     M = oracle.mttkrp_enum(3, 9, cidx, cval, B, want_abs=False)
     assert np.allclose(np.einsum("jlr,lr->jr", C, B), M, rtol=1e-12, atol=1e-13)
+
+
+def test_ttm_row_restriction_is_a_slice():
+    T = synth.tensor_small_all_patterns(3, 8, 6, density=0.6)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(8, 4, 6).astype(np.float64)
+    full, fa = oracle.ttm_enum(3, 8, cidx, cval, B)
+    rows = np.array([5, 0, 7])
+    part, pa = oracle.ttm_enum(3, 8, cidx, cval, B, rows=rows)
+    assert np.array_equal(part, full[rows]) and np.array_equal(pa, fa[rows])
