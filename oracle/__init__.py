@@ -68,9 +68,17 @@ def lib():
                                      C.POINTER(C.c_int64)]
             L.orc_cp_als_step.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, C.c_double,
                                           f64p, C.POINTER(C.c_int)]
+            L.orc_pcanonicalize.argtypes = [C.c_int, C.c_int, i32p, i64p, C.c_int64, i32p, f32p, C.c_int, i32p,
+                                            f32p, C.POINTER(C.c_int64)]
+            L.orc_pcounts.argtypes = [C.c_int, C.c_int, i32p, C.c_int64, i32p, f32p, C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_double)]
+            L.orc_pmttkrp_enum.argtypes = [C.c_int, C.c_int, i32p, i64p, C.c_int64, i32p, f32p, f64p, C.c_int,
+                                           C.c_int, f64p, f64p]
+            L.orc_pexpand.argtypes = [C.c_int, C.c_int, i32p, C.c_int64, i32p, f32p, C.c_int64, i32p, f32p,
+                                      C.POINTER(C.c_int64)]
             L.orc_ttm_enum.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, i32p, C.c_int64,
                                        f64p, f64p]
-            for name in ("orc_ttm_enum", "orc_cp_als_step", "orc_canonicalize", "orc_check_canonical", "orc_counts", "orc_mttkrp_enum",
+            for name in ("orc_pcanonicalize", "orc_pcounts", "orc_pmttkrp_enum", "orc_pexpand", "orc_ttm_enum", "orc_cp_als_step", "orc_canonicalize", "orc_check_canonical", "orc_counts", "orc_mttkrp_enum",
                          "orc_mttkrp_runs", "orc_check_upper_csr", "orc_ssymv_enum", "orc_syprd_enum",
                          "orc_bellman_enum", "orc_cpfit", "orc_expand"):
                 getattr(L, name).restype = C.c_int
@@ -242,6 +250,69 @@ def ttm_enum(order, n, cidx, cval, B, want_abs=True, rows=None):
     _check(lib().orc_ttm_enum(order, n, cval.shape[0], _p(cidx), _p(cval), _p(B), R, _p(slot), first, _p(Cm),
                               _p(Ca)), "ttm_enum")
     return (Cm, Ca) if want_abs else Cm
+
+
+# ---------------------------------------------------------------- partial symmetry
+
+def _parts(parts, dims=None):
+    part = np.ascontiguousarray(parts, dtype=np.int32)
+    dim = np.ascontiguousarray(dims if dims is not None else [1] * len(parts), dtype=np.int64)
+    return part, dim, int(part.sum())
+
+
+def pcanonicalize(parts, dims, idx, val, dup_policy=0):
+    """Canonical form of a partially symmetric tensor: (cidx (order x m) int32, cval float32)."""
+    part, dim, order = _parts(parts, dims)
+    idx = _c(idx, np.int32).reshape(order, -1)
+    val = _c(val, np.float32)
+    nnz = val.shape[0]
+    cidx = np.zeros((order, max(nnz, 1)), dtype=np.int32)
+    cval = np.zeros(max(nnz, 1), dtype=np.float32)
+    m = C.c_int64(0)
+    _check(lib().orc_pcanonicalize(order, len(part), _p(part), _p(dim), nnz, _p(idx), _p(val), dup_policy, _p(cidx),
+                                   _p(cval), C.byref(m)), "pcanonicalize")
+    m = m.value
+    flat = cidx.reshape(-1)[: order * m].reshape(order, m) if m else np.zeros((order, 0), np.int32)
+    return np.ascontiguousarray(flat), cval[:m].copy()
+
+
+def pcounts(parts, cidx, cval):
+    part, _, order = _parts(parts)
+    cidx = _c(cidx, np.int32)
+    cval = _c(cval, np.float32)
+    ex, ns = C.c_int64(0), C.c_double(0)
+    _check(lib().orc_pcounts(order, len(part), _p(part), cval.shape[0], _p(cidx), _p(cval), C.byref(ex),
+                             C.byref(ns)), "pcounts")
+    return dict(expanded=ex.value, normsq=ns.value)
+
+
+def pmttkrp_enum(parts, dims, cidx, cval, factors, out_part, want_abs=True):
+    """Definitional MTTKRP for part out_part's factor (factors: one dims[p] x R array per part), FP64."""
+    part, dim, order = _parts(parts, dims)
+    cidx = _c(cidx, np.int32)
+    cval = _c(cval, np.float32)
+    R = np.asarray(factors[0]).shape[1]
+    F = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.float64).reshape(-1) for f in factors]))
+    M = np.zeros((int(dim[out_part]), R), dtype=np.float64)
+    Ma = np.zeros_like(M) if want_abs else None
+    _check(lib().orc_pmttkrp_enum(order, len(part), _p(part), _p(dim), cval.shape[0], _p(cidx), _p(cval), _p(F), R,
+                                  out_part, _p(M), _p(Ma)), "pmttkrp_enum")
+    return (M, Ma) if want_abs else M
+
+
+def pexpand(parts, cidx, cval):
+    part, _, order = _parts(parts)
+    cidx = _c(cidx, np.int32)
+    cval = _c(cval, np.float32)
+    nnz = cval.shape[0]
+    cnt = C.c_int64(0)
+    lib().orc_pexpand(order, len(part), _p(part), nnz, _p(cidx), _p(cval), 0, None, None, C.byref(cnt))
+    k = cnt.value
+    eidx = np.zeros((order, max(k, 1)), dtype=np.int32)
+    ev = np.zeros(max(k, 1), dtype=np.float32)
+    _check(lib().orc_pexpand(order, len(part), _p(part), nnz, _p(cidx), _p(cval), max(k, 1), _p(eidx), _p(ev),
+                             C.byref(cnt)), "pexpand")
+    return eidx[:, :k].copy(), ev[:k].copy()
 
 
 def expand(order, cidx, cval):

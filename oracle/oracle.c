@@ -20,6 +20,9 @@
  *   - SSYMV   y[i]   = sum_j A[i,j] x[j]                        (Sec. 5.2.1)
  *   - SYPRD   y      = sum x[i] A[i,j] x[j]                      (Sec. 5.2.3)
  *   - TTM     C[i,j,l] = sum_k A[k,j,l] B[k,i]                   (Sec. 4.2, 5.2.5)
+ *   - partial symmetry: a tensor symmetric only inside parts of its modes
+ *     (Sec. 2 Def. "Partial Symmetry"), each entry standing for the distinct
+ *     arrangements that permute inside parts; MTTKRP per part's factor.
  *   - CP fit  ||X - sum_r b_r (x) ... (x) b_r||^2, unit weights, over the full
  *     tensor (the symmetric CPD that MTTKRP serves, Sec. 5.2.6).
  * A second, independent MTTKRP form uses per-run integer weights (the
@@ -509,6 +512,197 @@ int orc_expand(int order, int64_t nnz, const int32_t* cidx, const float* cval, i
     }
     g_exp_order = order;
     qsort(r, (size_t)k, sizeof(rec_t), cmp_exp);
+    for (int64_t e = 0; e < k; ++e) {
+        for (int q = 0; q < order; ++q) eidx[(int64_t)q * cap + e] = r[e].c[q];
+        evals[e] = r[e].v;
+    }
+    free(r);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Partial symmetry (Sec. 2, Def. "Partial Symmetry"; Sec. 4.1)              */
+/* ------------------------------------------------------------------------ */
+/* The N modes are split into consecutive parts of sizes part[0..nparts); the
+ * modes of part p range over [0, dim[p]).  The tensor is unchanged by any
+ * permutation that moves positions only inside their part, so the canonical
+ * coordinate has its indices non-decreasing inside every part, and a stored
+ * entry stands for every distinct arrangement obtained by permuting inside
+ * parts. */
+
+static int parts_valid(int order, int nparts, const int32_t* part, const int64_t* dim) {
+    if (order < 1 || order > ORC_MAX_ORDER || nparts < 1 || nparts > order) return 0;
+    int total = 0;
+    for (int p = 0; p < nparts; ++p) {
+        if (part[p] < 1 || dim[p] < 1) return 0;
+        total += part[p];
+    }
+    return total == order;
+}
+
+static void sort_within_parts(int32_t* c, int nparts, const int32_t* part) {
+    int q = 0;
+    for (int p = 0; p < nparts; ++p) {
+        sort_tuple(c + q, part[p]);
+        q += part[p];
+    }
+}
+
+/* Next arrangement that permutes positions only inside their parts, the last
+ * part varying fastest: a part that has been through all its distinct
+ * arrangements goes back to ascending order and the next part to the left
+ * advances.  Starting from the canonical tuple this visits every distinct
+ * arrangement once; returns 0 after the last. */
+static int next_part_perm(int32_t* c, int order, int nparts, const int32_t* part) {
+    int start = order;
+    for (int p = nparts - 1; p >= 0; --p) {
+        start -= part[p];
+        if (next_perm(c + start, part[p])) return 1;
+        sort_tuple(c + start, part[p]);
+    }
+    return 0;
+}
+
+/* Canonicalisation: sort inside every part, check each index against its
+ * part's dimension, sort entries lexicographically, resolve duplicates as
+ * orc_canonicalize does. */
+int orc_pcanonicalize(int order, int nparts, const int32_t* part, const int64_t* dim, int64_t nnz,
+                      const int32_t* idx, const float* val, int dup_policy, int32_t* cidx, float* cval,
+                      int64_t* nnz_out) {
+    if (!parts_valid(order, nparts, part, dim) || nnz < 0) return ORC_INVALID;
+    *nnz_out = 0;
+    if (nnz == 0) return ORC_OK;
+    int64_t mdim[ORC_MAX_ORDER];
+    for (int p = 0, q = 0; p < nparts; ++p)
+        for (int t = 0; t < part[p]; ++t) mdim[q++] = dim[p];
+    rec_t* r = (rec_t*)malloc(sizeof(rec_t) * (size_t)nnz);
+    if (!r) return ORC_NOMEM;
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(idx, order, nnz, e, r[e].c);
+        for (int q = 0; q < order; ++q)
+            if (r[e].c[q] < 0 || r[e].c[q] >= mdim[q]) { free(r); return ORC_RANGE; }
+        sort_within_parts(r[e].c, nparts, part);
+        r[e].v = val[e];
+        r[e].pos = e;
+    }
+    g_order_for_cmp = order;
+    qsort(r, (size_t)nnz, sizeof(rec_t), cmp_rec);
+    int64_t m = 0;
+    for (int64_t e = 0; e < nnz; ++e) {
+        if (m > 0) {
+            int same = 1;
+            for (int q = 0; q < order; ++q)
+                if (r[e].c[q] != cidx[(int64_t)q * nnz + (m - 1)]) { same = 0; break; }
+            if (same) {
+                if (dup_policy != 1) { free(r); return ORC_DUPLICATE; }
+                uint32_t ba, bb;
+                memcpy(&ba, &r[e].v, 4);
+                memcpy(&bb, &cval[m - 1], 4);
+                if (ba != bb) { free(r); return ORC_DUPLICATE; }
+                continue;
+            }
+        }
+        for (int q = 0; q < order; ++q) cidx[(int64_t)q * nnz + m] = r[e].c[q];
+        cval[m] = r[e].v;
+        ++m;
+    }
+    free(r);
+    if (m != nnz)
+        for (int q = 1; q < order; ++q)
+            memmove(cidx + (int64_t)q * m, cidx + (int64_t)q * nnz, sizeof(int32_t) * (size_t)m);
+    *nnz_out = m;
+    return ORC_OK;
+}
+
+/* *expanded = number of full-tensor nonzeros (arrangements, by enumeration);
+ * *normsq = ||X||^2 over the full tensor. */
+int orc_pcounts(int order, int nparts, const int32_t* part, int64_t nnz, const int32_t* cidx, const float* cval,
+                int64_t* expanded, double* normsq) {
+    *expanded = 0;
+    *normsq = 0.0;
+    int32_t c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_within_parts(c, nparts, part);
+        int64_t k = 0;
+        do { ++k; } while (next_part_perm(c, order, nparts, part));
+        *expanded += k;
+        *normsq += (double)k * (double)cval[e] * (double)cval[e];
+    }
+    return ORC_OK;
+}
+
+/* MTTKRP for the factor of part out_part: with f the first mode of that part,
+ * M[x_f, r] += v * prod_{q != f} F_{part of q}[x_q, r] for every arrangement x
+ * of every canonical entry (permutations inside parts only) — the full-tensor
+ * MTTKRP restricted to its nonzeros; any mode of the part gives the same M.
+ * F holds the parts' factors one after the other, part p as a row-major
+ * dim[p] x R block.  M is dim[out_part] x R; Mabs (nullable) gets sum |terms|. */
+int orc_pmttkrp_enum(int order, int nparts, const int32_t* part, const int64_t* dim, int64_t nnz,
+                     const int32_t* cidx, const float* cval, const double* F, int R, int out_part, double* M,
+                     double* Mabs) {
+    if (!parts_valid(order, nparts, part, dim) || R <= 0 || out_part < 0 || out_part >= nparts) return ORC_INVALID;
+    const double* fq[ORC_MAX_ORDER];
+    int f = 0;
+    {
+        const double* base = F;
+        int q = 0;
+        for (int p = 0; p < nparts; ++p) {
+            if (p == out_part) f = q;
+            for (int t = 0; t < part[p]; ++t) fq[q++] = base;
+            base += dim[p] * (int64_t)R;
+        }
+    }
+    memset(M, 0, sizeof(double) * (size_t)dim[out_part] * (size_t)R);
+    if (Mabs) memset(Mabs, 0, sizeof(double) * (size_t)dim[out_part] * (size_t)R);
+    int32_t c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_within_parts(c, nparts, part);
+        const double v = (double)cval[e];
+        do {
+            const int64_t i = c[f];
+            for (int r = 0; r < R; ++r) {
+                double t = v;
+                for (int q = 0; q < order; ++q)
+                    if (q != f) t *= fq[q][(int64_t)c[q] * R + r];
+                M[i * R + r] += t;
+                if (Mabs) Mabs[i * R + r] += fabs(t);
+            }
+        } while (next_part_perm(c, order, nparts, part));
+    }
+    return ORC_OK;
+}
+
+/* Every arrangement of every canonical entry (permutations inside parts),
+ * sorted lexicographically: the tensor with no symmetry left.  eidx is
+ * order x cap; *count receives the number of arrangements. */
+int orc_pexpand(int order, int nparts, const int32_t* part, int64_t nnz, const int32_t* cidx, const float* cval,
+                int64_t cap, int32_t* eidx, float* evals, int64_t* count) {
+    int64_t k = 0;
+    int32_t c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_within_parts(c, nparts, part);
+        do { ++k; } while (next_part_perm(c, order, nparts, part));
+    }
+    *count = k;
+    if (k > cap) return ORC_NOMEM;
+    rec_t* r = (rec_t*)malloc(sizeof(rec_t) * (size_t)(k > 0 ? k : 1));
+    if (!r) return ORC_NOMEM;
+    int64_t w = 0;
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_within_parts(c, nparts, part);
+        do {
+            memcpy(r[w].c, c, sizeof(c));
+            r[w].v = cval[e];
+            r[w].pos = w;
+            ++w;
+        } while (next_part_perm(c, order, nparts, part));
+    }
+    g_order_for_cmp = order;
+    qsort(r, (size_t)k, sizeof(rec_t), cmp_rec);
     for (int64_t e = 0; e < k; ++e) {
         for (int q = 0; q < order; ++q) eidx[(int64_t)q * cap + e] = r[e].c[q];
         evals[e] = r[e].v;

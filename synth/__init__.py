@@ -282,6 +282,125 @@ def tensor_small_all_patterns(order: int, n: int, seed: int, density: float = 0.
 
 
 # ----------------------------------------------------------------------------
+# Partially symmetric tensors (symmetric within consecutive groups of modes)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class PartCOO:
+    """A tensor symmetric within each part of a partition of its modes into
+    consecutive groups (`parts` = group sizes, `dims` = one dimension per part),
+    given by one stored coordinate per distinct tuple of per-part multisets.
+
+    idx has shape (order, nnz), int32, positions permuted arbitrarily inside each
+    part; val has shape (nnz,), float32.
+    """
+    parts: tuple
+    dims: tuple
+    idx: np.ndarray
+    val: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def order(self) -> int:
+        return int(sum(self.parts))
+
+    @property
+    def nnz(self) -> int:
+        return int(self.val.shape[0])
+
+    def mode_dims(self) -> list:
+        return [d for s, d in zip(self.parts, self.dims) for _ in range(s)]
+
+
+def _part_sort(rows: np.ndarray, parts) -> np.ndarray:
+    out = rows.copy()
+    q = 0
+    for s in parts:
+        out[:, q:q + s] = np.sort(out[:, q:q + s], axis=1)
+        q += s
+    return out
+
+
+def _draw_distinct_rows(maker, need: int, parts) -> np.ndarray:
+    """Like _draw_distinct, for tuples sorted within parts (first occurrence in draw order wins)."""
+    if need <= 0:
+        return np.zeros((0, int(sum(parts))), dtype=np.int64)
+    drawn, have, factor = [], 0, 1.2
+    while True:
+        m = int((need - have) * factor) + 256
+        drawn.append(_part_sort(maker(m), parts))
+        rows = np.ascontiguousarray(np.concatenate(drawn).astype(np.int64))
+        keys = rows.view(np.dtype((np.void, 8 * rows.shape[1]))).ravel()
+        _, first = np.unique(keys, return_index=True)
+        if first.shape[0] >= need:
+            first.sort()
+            return rows[first[:need]]
+        got = first.shape[0] - have
+        have = first.shape[0]
+        factor = min(8.0, max(1.2, 1.3 * m / max(got, 1)))
+
+
+def _finish_parts(st: Stream, parts, dims, rows: np.ndarray, val: np.ndarray, meta: dict,
+                  scramble: bool) -> PartCOO:
+    nnz = rows.shape[0]
+    if scramble:
+        q = 0
+        for s in parts:
+            if s > 1:
+                keys = st.uniform(nnz * s).reshape(nnz, s)
+                perm = np.argsort(keys, axis=1, kind="stable")
+                rows[:, q:q + s] = np.take_along_axis(rows[:, q:q + s], perm, axis=1)
+            q += s
+        shuffle = np.argsort(st.u64(nnz), kind="stable")
+        rows, val = rows[shuffle], val[shuffle]
+    idx = np.ascontiguousarray(rows.T.astype(np.int32))
+    return PartCOO(tuple(parts), tuple(dims), idx, np.ascontiguousarray(val.astype(np.float32)), meta)
+
+
+def ptensor_uniform(parts, dims, nnz: int, seed: int, scramble: bool = True) -> PartCOO:
+    """nnz distinct canonical tuples, every index uniform on its part's range."""
+    parts, dims = tuple(int(s) for s in parts), tuple(int(d) for d in dims)
+    order = sum(parts)
+    total = 1
+    for s, d in zip(parts, dims):
+        total *= math.comb(d + s - 1, s)
+    if nnz > total:
+        raise ValueError("more nonzeros than canonical positions")
+    st = Stream(seed, tag=300 + 16 * order + len(parts))
+    mdims = [d for s, d in zip(parts, dims) for _ in range(s)]
+
+    def maker(m):
+        return np.stack([st.randint(m, d) for d in mdims], axis=1)
+
+    rows = _draw_distinct_rows(maker, nnz, parts)
+    val = st.normal(nnz)
+    return _finish_parts(st, parts, dims, rows, val, {"recipe": "partial-uniform", "seed": seed}, scramble)
+
+
+def ptensor_small_all_patterns(parts, dims, seed: int, density: float = 0.5) -> PartCOO:
+    """Every canonical tuple of a tiny partially symmetric tensor, kept with probability
+    `density`, plus at least one tuple of every combination of per-part equality patterns."""
+    import itertools
+    parts, dims = tuple(int(s) for s in parts), tuple(int(d) for d in dims)
+    st = Stream(seed, tag=400 + 16 * sum(parts) + len(parts))
+    per_part = [list(itertools.combinations_with_replacement(range(d), s)) for s, d in zip(parts, dims)]
+    rows = np.array([sum(combo, ()) for combo in itertools.product(*per_part)], dtype=np.int64)
+    keep = st.uniform(rows.shape[0]) < density
+    pat = np.zeros(rows.shape[0], dtype=np.int64)
+    bit, q = 0, 0
+    for s in parts:
+        for t in range(s - 1):
+            pat |= (rows[:, q + t] == rows[:, q + t + 1]).astype(np.int64) << bit
+            bit += 1
+        q += s
+    for p in np.unique(pat):
+        keep[np.nonzero(pat == p)[0][0]] = True
+    rows = rows[keep]
+    val = st.normal(rows.shape[0])
+    return _finish_parts(st, parts, dims, rows, val, {"recipe": "partial-all-patterns", "seed": seed}, True)
+
+
+# ----------------------------------------------------------------------------
 # Counter-based coordinate pools (shared definition with the device generator)
 # ----------------------------------------------------------------------------
 

@@ -43,6 +43,13 @@ MUTANTS = {
     "ttm_wrong_factor_row": ("orc_ttm_enum", "double t = v * B[(int64_t)c[0] * R + r];",
                              "double t = v * B[(int64_t)c[1] * R + r];",
                              lambda: pins.test_paper_ttm_listing_assignments()),
+    "pperm_last_part_only": ("next_part_perm", "for (int p = nparts - 1; p >= 0; --p) {",
+                             "for (int p = nparts - 1; p >= nparts - 1; --p) {",
+                             lambda: pins.test_pmttkrp_vs_dense_bruteforce((2, 2), (4, 3))),
+    "pcanon_sort_whole_tuple": ("orc_pcanonicalize", "sort_within_parts(r[e].c, nparts, part);",
+                                "sort_tuple(r[e].c, order);", lambda: pins.test_pcanonicalize_properties()),
+    "pmttkrp_drops_leading_factors": ("orc_pmttkrp_enum", "if (q != f) t *= fq[q]", "if (q > f) t *= fq[q]",
+                                      lambda: pins.test_pmttkrp_vs_dense_bruteforce((1, 2), (4, 5))),
     "counts_wrong_fibers": ("orc_counts", "if (e == 0 || c[0] != prev[0]) *root_fibers += 1;",
                             "*root_fibers += 1;", lambda: pins.test_counts_closed_forms(3)),
 }

@@ -457,3 +457,111 @@ def test_ttm_row_restriction_is_a_slice():
     rows = np.array([5, 0, 7])
     part, pa = oracle.ttm_enum(3, 8, cidx, cval, B, rows=rows)
     assert np.array_equal(part, full[rows]) and np.array_equal(pa, fa[rows])
+
+
+# ----------------------------------------------------------------------------- partial symmetry
+
+def dense_partial(parts, dims, cidx, cval):
+    """Dense tensor with every stored tuple written at all its inside-part arrangements."""
+    mdims = [d for s, d in zip(parts, dims) for _ in range(s)]
+    X = np.zeros(mdims, dtype=np.float64)
+    starts = np.cumsum([0] + list(parts))[:-1]
+    for e in range(cidx.shape[1]):
+        c = [int(x) for x in cidx[:, e]]
+        segs = [list(itertools.permutations(c[s0:s0 + s])) for s0, s in zip(starts, parts)]
+        for combo in itertools.product(*segs):
+            X[tuple(x for seg in combo for x in seg)] = float(cval[e])
+    return X
+
+
+def dense_pmttkrp(X, parts, factors, out_part):
+    """Contract every mode but the first of out_part with its part's factor (einsum, column r shared)."""
+    letters = "abcde"
+    order = X.ndim
+    owner = [p for p, s in enumerate(parts) for _ in range(s)]
+    f = int(np.cumsum([0] + list(parts))[out_part])
+    ins = [letters[:order]]
+    ops = [X]
+    for q in range(order):
+        if q != f:
+            ins.append(letters[q] + "r")
+            ops.append(np.asarray(factors[owner[q]], dtype=np.float64))
+    return np.einsum(",".join(ins) + "->" + letters[f] + "r", *ops)
+
+
+PARTITIONS = [((2, 1), (5, 4)), ((1, 2), (4, 5)), ((2, 2), (4, 3)), ((3, 1), (4, 3)), ((1, 1, 1), (3, 4, 5)),
+              ((2, 1, 2), (3, 2, 3)), ((1, 3), (3, 4))]
+
+
+@pytest.mark.parametrize("parts,dims", PARTITIONS)
+def test_pmttkrp_vs_dense_bruteforce(parts, dims):
+    T = synth.ptensor_small_all_patterns(parts, dims, 3, density=0.6)
+    cidx, cval = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+    R = 3
+    F = [synth.factor_normal(d, R, 10 + p).astype(np.float64) for p, d in enumerate(dims)]
+    X = dense_partial(parts, dims, cidx, cval)
+    for out in range(len(parts)):
+        M, Ma = oracle.pmttkrp_enum(parts, dims, cidx, cval, F, out)
+        assert np.allclose(M, dense_pmttkrp(X, parts, F, out), rtol=1e-12, atol=1e-13), out
+        assert np.allclose(Ma, dense_pmttkrp(np.abs(X), parts, [np.abs(f) for f in F], out), rtol=1e-12,
+                           atol=1e-13), out
+
+
+@pytest.mark.parametrize("order,n", [(2, 6), (3, 6), (4, 5), (5, 4)])
+def test_pmttkrp_one_part_is_full_symmetry(order, n):
+    """A partition with a single part is full symmetry: equals the symmetric MTTKRP's own enumeration."""
+    T = synth.tensor_small_all_patterns(order, n, 17, density=0.6)
+    cidx, cval = oracle.canonicalize(order, n, T.idx, T.val)
+    B = synth.factor_normal(n, 3, 17).astype(np.float64)
+    got = oracle.pmttkrp_enum((order,), (n,), cidx, cval, [B], 0, want_abs=False)
+    want = oracle.mttkrp_enum(order, n, cidx, cval, B, want_abs=False)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("parts,dims", PARTITIONS)
+def test_pcounts_closed_form_and_expansion(parts, dims):
+    T = synth.ptensor_small_all_patterns(parts, dims, 5, density=0.5)
+    cidx, cval = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+    starts = np.cumsum([0] + list(parts))[:-1]
+    closed = 0
+    for e in range(cidx.shape[1]):
+        k = 1
+        for s0, s in zip(starts, parts):
+            seg = cidx[s0:s0 + s, e].tolist()
+            k *= math.factorial(s) // math.prod(math.factorial(seg.count(v)) for v in set(seg))
+        closed += k
+    cnt = oracle.pcounts(parts, cidx, cval)
+    assert cnt["expanded"] == closed
+    X = dense_partial(parts, dims, cidx, cval)
+    assert np.count_nonzero(X) == closed          # values are nonzero normal draws
+    assert math.isclose(cnt["normsq"], float((X ** 2).sum()), rel_tol=1e-12)
+    eidx, ev = oracle.pexpand(parts, cidx, cval)
+    assert eidx.shape[1] == closed
+    rows = [tuple(r) for r in eidx.T.tolist()]
+    assert rows == sorted(rows) and len(set(rows)) == closed
+    assert all(X[r] == v for r, v in zip(rows, ev.astype(np.float64)))
+
+
+def test_pcanonicalize_properties():
+    parts, dims = (2, 1, 2), (6, 3, 5)
+    T = synth.ptensor_uniform(parts, dims, 400, 8)
+    cidx, cval = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+    # non-decreasing inside parts only; across parts any order
+    assert np.all(cidx[0] <= cidx[1]) and np.all(cidx[3] <= cidx[4])
+    assert np.any(cidx[1] > cidx[2]) or np.any(cidx[2] > cidx[3])
+    rows = [tuple(r) for r in cidx.T.tolist()]
+    assert rows == sorted(rows) and len(set(rows)) == len(rows)
+    # any inside-part permutation of the stored tuples gives the same canonical form
+    perm = T.idx[[1, 0, 2, 4, 3]]
+    c2, v2 = oracle.pcanonicalize(parts, dims, perm, T.val)
+    assert np.array_equal(c2, cidx) and np.array_equal(v2, cval)
+    # a permutation across parts is a different tensor (here: out of range for part 2's dimension)
+    swapped = T.idx[[2, 1, 0, 3, 4]]
+    bad = swapped[2] >= 3
+    if bad.any():
+        with pytest.raises(oracle.OracleError) as ei:
+            oracle.pcanonicalize(parts, dims, swapped, T.val)
+        assert ei.value.code == oracle.RANGE
+    # a 2-mode non-symmetric tensor keeps (3, 1) as (3, 1)
+    c3, _ = oracle.pcanonicalize((1, 1), (5, 5), np.array([[3], [1]]), np.array([1.0], np.float32))
+    assert c3[:, 0].tolist() == [3, 1]
