@@ -611,17 +611,28 @@ def batch_row(torch, sg, dev, flush, stream, hbm_peak, count=4096, per_row=16, s
     plan.capture(x, y, sy)
     for _ in range(3):
         plan.launch()
+    t = timed_steps(torch, plan.launch, 10, flush, stream)
+    ms = float(np.mean(t))
+    banded = cfg.band_rows > 0
+    kname = "ssymv_band" if banded else "ssymv_batch"
+    # the kernel alone: plain (non-graph) runs with per-launch events, L2 flushed before each
     sg.profile_reset()
     sg.profile_enable(True)
-    t = timed_steps(torch, plan.launch, 10, flush, stream)
+    timed_steps(torch, lambda: plan.run(x, y, sy), 5, flush, stream)
     sg.profile_enable(False)
-    prof = sg.profile_read()
-    ms = float(np.mean(t))
-    kern_ms = prof.get("ssymv_batch", (1, 0.0))
-    alg = nnz * 8 + (rows + count) * 8 + rows * 4 * 3 + count * 8   # col+val, rowptr, x + y rmw, syprd
+    kern = sg.profile_read().get(kname, (1, 0.0))
+    # algorithmic bytes of what the timed kernels read and write: tile path: col + val, rowptr, x, y zeroed
+    # then reduced, SYPRD; banded path: the packed (row, col) + value copy, x, y zeroed then written / reduced
+    if banded:
+        alg = nnz * 8 + rows * 4 * 3 + count * 8
+    else:
+        alg = nnz * 8 + (rows + count) * 8 + rows * 4 * 3 + count * 8
+    kern_ms = kern[1] / max(kern[0], 1)
     out = {"instances": count, "rows": rows, "upper_nnz": nnz, "generate_s": gen_s, "autotune_s": tune_s,
-           "tile_cfg": cfg.as_dict(), "graph_ms": ms, "canonical_nnz_per_s": nnz / (ms * 1e-3),
-           "effective_gbs": alg / (ms * 1e-3) / 1e9, "hbm_frac": alg / (ms * 1e-3) / 1e9 / hbm_peak}
+           "tile_cfg": cfg.as_dict(), "path": "banded" if banded else "tiles", "graph_ms": ms,
+           "canonical_nnz_per_s": nnz / (ms * 1e-3), "algorithmic_bytes": alg,
+           "effective_gbs": alg / (ms * 1e-3) / 1e9, "hbm_frac": alg / (ms * 1e-3) / 1e9 / hbm_peak,
+           "kernel": kname, "kernel_ms": kern_ms}
     # plain form: one sym_spmv launch per instance (each with its own upper CSR, local indices)
     ro = batch.host_row_off
     rp_h = batch.rowptr.cpu()
@@ -758,7 +769,7 @@ def serving_row(torch, sg, dev, requests=1500, rate=2000.0, pool_size=32, seed=4
 
 
 def run_batch_only(args):
-    """Profiling mode for the batched SSYMV: tile kernel, fixed shape, plain runs (no graph)."""
+    """Profiling mode for the batched SSYMV: one fixed shape (--batch-cfg), plain runs (no graph)."""
     import torch
 
     import paper_2406_09266_gb300 as sg
@@ -769,11 +780,14 @@ def run_batch_only(args):
     x = torch.from_numpy(synth.vector_uniform(int(batch.host_row_off[-1]), 3)).to(dev)
     y = torch.empty_like(x)
     sy = torch.empty(len(sizes), dtype=torch.float64, device=dev)
-    plan = sg.BatchPlan(batch, sg.TileCfg(256, 8, 256, 8, 0, 0, 0))
+    cfg = [int(v) for v in args.batch_cfg.split(",")] if args.batch_cfg else [256, 8, 256, 8, 0, 0, 0]
+    plan = sg.BatchPlan(batch, sg.TileCfg(*cfg))
     for _ in range(args.warmup + args.steps):
         plan.run(x, y, sy)
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "batch-only (profiling)", "instances": len(sizes), "upper_nnz": int(batch.col.numel())}))
+    plan.check()
+    print(json.dumps({"mode": "batch-only (profiling)", "instances": len(sizes), "upper_nnz": int(batch.col.numel()),
+                      "tile_cfg": cfg}))
 
 
 def run_ttm_only(args):
@@ -813,6 +827,8 @@ def main():
                     help="profiling mode: the symmetric TTM kernels on the TTM row's tensor, nothing else")
     ap.add_argument("--batch-only", type=int, default=0, metavar="INSTANCES",
                     help="profiling mode: build a batch of this many instances and run the batched SSYMV a few times")
+    ap.add_argument("--batch-cfg", default="", metavar="FIELDS",
+                    help="batch-only mode: comma-separated sym_tile_cfg fields (default: the tile kernel, 256 rows)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

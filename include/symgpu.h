@@ -186,6 +186,35 @@ typedef struct {
     int32_t x_smem_kb;        /* > 0: each tile copies the first x_smem_kb*256 floats of its x window
                                  (x[row0 ..]) into shared memory and gathers from there; rows_per_tile must
                                  not exceed that many floats */
+    int32_t band_rows;        /* > 0 (multiple of 4, 256..16384): banded path.  Instance b is cut into
+                                 nb = ceil(n_b / band_rows) bands of rows; the upper triangle falls into
+                                 blocks (I, J), I <= J < nb.  The plan keeps a reordered copy of those
+                                 instances' canonical entries (4-byte packed in-band (row, col) + value,
+                                 block by block, row-major inside a block) and one CTA works through one
+                                 row band I at a time with x and y of bands I and J in shared memory: the
+                                 mirrored updates y[j] += a x_i (Sec. 3.1) become shared-memory adds and
+                                 each band of y is reduced into global memory once per block, with
+                                 16-byte vector reductions.  One producer warp streams the entries with
+                                 bulk asynchronous copies (cp.async.bulk + mbarrier) several chunks ahead
+                                 and stages the x bands; the other warps consume.  threads_per_cta
+                                 (64..1024: one producer warp + consumer warps) and ctas_per_sm (1 or 2)
+                                 shape the banded kernel; the band buffers (32 * band_rows bytes) and at
+                                 least two chunks must fit in one CTA's shared memory (SYM_E_INVALID
+                                 otherwise: band_rows up to ~5,600 on GB300).  Instances with
+                                 nb > band_max stay on the tile path (lanes_per_row, rows_per_tile,
+                                 x_smem_kb apply to those).  local_smem_kb must be 0. */
+    int32_t band_max;         /* banded path only: largest band count per instance (1..64) */
+    int32_t band_chunk;       /* banded path only: entries per consumer lane per streamed chunk (a chunk is
+                                 this times 32 x the consumer warps): 4, 8, 16 (0 = 4), or 1, 2 with
+                                 band_order 1.  Smaller chunks leave room for more of them in flight. */
+    int32_t band_order;       /* banded path only: order of the entries inside a block.  0: row-major (each
+                                 lane takes 4 consecutive entries; runs of one row are summed in registers).
+                                 1: bank groups: the plan regroups each block into groups of 32 entries whose
+                                 rows, and whose columns, fall in distinct shared-memory banks where the
+                                 block allows it (a greedy matching per group on the host, relaxed to 2, 3,
+                                 ... entries per bank only for the groups it cannot fill otherwise); a warp
+                                 takes one group at a time, one entry per lane, so its x gathers and y
+                                 reductions meet no bank conflicts.  Padding: at most 31 entries per block. */
 } sym_tile_cfg;
 
 /* A plan: the tile list and the FP64 partial buffers, carved from `arena`. */
@@ -205,6 +234,11 @@ sym_status sym_spmv_batch_run(sym_batch_plan plan, const float* x, float* y, dou
 sym_status sym_spmv_batch_capture(sym_batch_plan plan, const float* x, float* y, double* syprd,
                                   sym_stream_t stream);
 sym_status sym_spmv_batch_graph_launch(sym_batch_plan plan, sym_stream_t stream);
+/* Device-side status of the plan's banded kernel: SYM_E_TIMEOUT when one of
+ * its bounded waits on a bulk copy gave up (the kernel then left the rest of
+ * its work undone and y / syprd are incomplete), SYM_OK otherwise.  The flag is
+ * sticky for the plan's lifetime.  Synchronous (reads one word). */
+sym_status sym_spmv_batch_check(sym_batch_plan plan);
 sym_status sym_spmv_batch_plan_destroy(sym_batch_plan plan);
 
 /* Autotuner: times candidate sym_tile_cfg shapes on this batch (each as a

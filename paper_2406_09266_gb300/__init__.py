@@ -56,7 +56,8 @@ class CsrBatch(C.Structure):
 class TileCfg(C.Structure):
     _fields_ = [("rows_per_tile", C.c_int32), ("lanes_per_row", C.c_int32), ("threads_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("local_smem_kb", C.c_int32), ("tile_order", C.c_int32),
-                ("x_smem_kb", C.c_int32)]
+                ("x_smem_kb", C.c_int32), ("band_rows", C.c_int32), ("band_max", C.c_int32),
+                ("band_chunk", C.c_int32), ("band_order", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -139,6 +140,7 @@ _SIGS = {
     "sym_spmv_batch_run": ([C.c_void_p] * 5, C.c_int),
     "sym_spmv_batch_capture": ([C.c_void_p] * 5, C.c_int),
     "sym_spmv_batch_graph_launch": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_spmv_batch_check": ([C.c_void_p], C.c_int),
     "sym_spmv_batch_plan_destroy": ([C.c_void_p], C.c_int),
     "sym_autotune_spmv_batch": ([C.c_void_p] * 6 + [C.c_size_t, C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p],
                                 C.c_int),
@@ -655,6 +657,10 @@ class BatchPlan:
     def launch(self, stream=None):
         check(lib().sym_spmv_batch_graph_launch(self.handle, _stream(stream)), "sym_spmv_batch_graph_launch")
 
+    def check(self):
+        """Raises if the banded kernel gave up a bounded wait (synchronous)."""
+        check(lib().sym_spmv_batch_check(self.handle), "sym_spmv_batch_check")
+
     def close(self):
         if getattr(self, "handle", None):
             lib().sym_spmv_batch_plan_destroy(self.handle)
@@ -669,7 +675,9 @@ class BatchPlan:
 
 def autotune_batch(batch: BatchCSR, x, y, syprd=None, cache_path=None, stream=None):
     """Times candidate tile shapes on this batch; returns (TileCfg, ms). Cached by device and shape."""
-    nb = lib().sym_spmv_batch_plan_bytes(C.byref(batch.desc), batch._hro(), C.byref(TileCfg(16, 32, 256, 1, 0, 0, 0)))
+    # the largest candidate plans: one-row tiles, or the banded copy of the entries with the smallest bands
+    nb = max(lib().sym_spmv_batch_plan_bytes(C.byref(batch.desc), batch._hro(), C.byref(c))
+             for c in (TileCfg(16, 32, 256, 1, 0, 0, 0), TileCfg(256, 8, 256, 1, 0, 0, 0, 2048, 64)))
     arena = _scratch(nb, batch.rowptr.device)
     best = TileCfg()
     ms = C.c_float(0)

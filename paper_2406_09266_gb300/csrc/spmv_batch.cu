@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "spmv_band.cuh"
 
 struct Tile {
     int64_t row0;      // first global row
@@ -43,6 +44,8 @@ struct sym_batch_plan_s {
     int64_t* local_order;         // [device] those instances, largest first
     unsigned long long* local_counter;  // [device] next local instance
     int local_cap;                // floats of shared memory per CTA for the local path
+    symgpu::BandPlan band;        // banded path (cfg.band_rows > 0)
+    int64_t nslots;               // SYPRD partial slots: tiles + band units
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int device;
@@ -295,21 +298,28 @@ int local_capacity(const sym_tile_cfg* cfg) {
 
 bool is_local(int64_t n, int cap) { return cap > 0 && n <= cap; }
 
-int64_t count_tiles(const int64_t* host_row_off, int64_t count, int rows_per_tile, int cap) {
+int64_t count_tiles(const int64_t* host_row_off, int64_t count, const sym_tile_cfg* cfg, int cap) {
     int64_t nt = 0;
     for (int64_t b = 0; b < count; ++b) {
         const int64_t n = host_row_off[b + 1] - host_row_off[b];
-        if (!is_local(n, cap)) nt += (n + rows_per_tile - 1) / rows_per_tile;
+        if (!is_local(n, cap) && band_count(n, cfg) == 0) nt += (n + cfg->rows_per_tile - 1) / cfg->rows_per_tile;
     }
     return nt;
 }
 
+// SYPRD partial slots: one per tile plus one per band unit (row band).
+int64_t count_slots(const int64_t* host_row_off, int64_t count, const sym_tile_cfg* cfg, int cap) {
+    int64_t ns = count_tiles(host_row_off, count, cfg, cap);
+    for (int64_t b = 0; b < count; ++b) ns += band_count(host_row_off[b + 1] - host_row_off[b], cfg);
+    return ns;
+}
+
 template <typename C>
-void layout_plan(C& c, int64_t ntiles, int64_t count, Tile** tiles, int64_t** first, double** parts,
+void layout_plan(C& c, int64_t ntiles, int64_t nslots, int64_t count, Tile** tiles, int64_t** first, double** parts,
                  unsigned long long** counter, int64_t** local_order, unsigned long long** local_counter) {
     *tiles = c.template take<Tile>((size_t)std::max<int64_t>(ntiles, 1));
     *first = c.template take<int64_t>((size_t)count + 1);
-    *parts = c.template take<double>((size_t)std::max<int64_t>(ntiles, 1));
+    *parts = c.template take<double>((size_t)std::max<int64_t>(nslots, 1));
     *counter = c.template take<unsigned long long>(1);
     *local_order = c.template take<int64_t>((size_t)std::max<int64_t>(count, 1));
     *local_counter = c.template take<unsigned long long>(1);
@@ -335,6 +345,20 @@ bool cfg_ok(const sym_tile_cfg* c) {
     if (c->tile_order != 0 && c->tile_order != 1) return false;
     if (c->x_smem_kb < 0 || c->x_smem_kb > 220) return false;
     if (c->x_smem_kb > 0 && c->rows_per_tile > c->x_smem_kb * 256) return false;  // the rows' own x must fit
+    if (c->band_rows != 0) {
+        if (c->band_rows < 256 || c->band_rows > 16384 || c->band_rows % 4) return false;
+        if (c->band_max < 1 || c->band_max > BAND_MAX_BANDS) return false;
+        if (c->band_order != 0 && c->band_order != 1) return false;
+        const int bc = c->band_chunk;
+        if (bc != 0 && bc != 1 && bc != 2 && bc != 4 && bc != 8 && bc != 16) return false;
+        if ((bc == 1 || bc == 2) && c->band_order != 1) return false;  // row-major needs whole 16-byte vectors
+        if (c->local_smem_kb != 0 || c->ctas_per_sm > 2 || c->threads_per_cta < 64) return false;
+        int st = 0;
+        band_smem(c, &st);
+        if (st < 2) return false;
+    } else if (c->band_max != 0 || c->band_chunk != 0 || c->band_order != 0) {
+        return false;
+    }
     return true;
 }
 
@@ -376,13 +400,7 @@ sym_status batch_enqueue_local(sym_batch_plan_s* P, const float* x, float* y, do
     return SYM_OK;
 }
 
-sym_status batch_enqueue(sym_batch_plan_s* P, const float* x, float* y, double* syprd, cudaStream_t s) {
-    SYM_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(unsigned long long), s));
-    SYM_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)P->A.total_rows, s));
-    if (syprd && P->A.count > 0) SYM_CUDA(cudaMemsetAsync(syprd, 0, sizeof(double) * P->A.count, s));
-    sym_status lst = batch_enqueue_local(P, x, y, syprd, s);
-    if (lst != SYM_OK) return lst;
-    if (P->ntiles == 0) return SYM_OK;
+sym_status batch_enqueue_tiles(sym_batch_plan_s* P, const float* x, float* y, double* syprd, cudaStream_t s) {
     const int threads = P->cfg.threads_per_cta;
     const unsigned grid = (unsigned)std::min<int64_t>((int64_t)sm_count() * P->cfg.ctas_per_sm, P->ntiles);
     if (P->cfg.x_smem_kb > 0) {
@@ -441,7 +459,24 @@ sym_status batch_enqueue(sym_batch_plan_s* P, const float* x, float* y, double* 
 #undef SYM_BATCH_L
         SYM_CHECK_LAUNCH();
     }
-    if (syprd) {
+    return SYM_OK;
+}
+
+sym_status batch_enqueue(sym_batch_plan_s* P, const float* x, float* y, double* syprd, cudaStream_t s) {
+    SYM_CUDA(cudaMemsetAsync(P->counter, 0, sizeof(unsigned long long), s));
+    SYM_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)P->A.total_rows, s));
+    if (syprd && P->A.count > 0) SYM_CUDA(cudaMemsetAsync(syprd, 0, sizeof(double) * P->A.count, s));
+    sym_status st = batch_enqueue_local(P, x, y, syprd, s);
+    if (st != SYM_OK) return st;
+    if (syprd && P->band.nunits > 0)  // row bands without entries leave their slot untouched
+        SYM_CUDA(cudaMemsetAsync(P->tile_partials, 0, sizeof(double) * (size_t)P->nslots, s));
+    st = band_enqueue(P->band, x, y, P->tile_partials, syprd != nullptr, s);
+    if (st != SYM_OK) return st;
+    if (P->ntiles > 0) {
+        st = batch_enqueue_tiles(P, x, y, syprd, s);
+        if (st != SYM_OK) return st;
+    }
+    if (syprd && P->nslots > 0) {
         const unsigned g2 = (unsigned)((P->A.count + 7) / 8);
         k_batch_syprd<<<g2, 256, 0, s>>>(P->tile_partials, P->tile_first, P->A.count, syprd);
         SYM_CHECK_LAUNCH();
@@ -478,8 +513,10 @@ extern "C" size_t sym_spmv_batch_plan_bytes(const sym_csr_batch* A, const int64_
     unsigned long long* k;
     int64_t* lo;
     unsigned long long* lc;
-    layout_plan(c, count_tiles(host_row_off, A->count, cfg->rows_per_tile, local_capacity(cfg)), A->count, &t, &f,
-                &p, &k, &lo, &lc);
+    const int cap = local_capacity(cfg);
+    layout_plan(c, count_tiles(host_row_off, A->count, cfg, cap), count_slots(host_row_off, A->count, cfg, cap),
+                A->count, &t, &f, &p, &k, &lo, &lc);
+    band_size(c.s, A, host_row_off, cfg);
     return c.s.used;
 }
 
@@ -493,7 +530,8 @@ extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const i
     if (!cfg_ok(cfg) || !arena || !aligned(arena, 256)) return SYM_E_INVALID;
     if (arena_bytes < sym_spmv_batch_plan_bytes(A, host_row_off, cfg)) return SYM_E_NOMEM;
     const int cap = local_capacity(cfg);
-    const int64_t ntiles = count_tiles(host_row_off, A->count, cfg->rows_per_tile, cap);
+    const int64_t ntiles = count_tiles(host_row_off, A->count, cfg, cap);
+    const int64_t nslots = count_slots(host_row_off, A->count, cfg, cap);
     std::vector<Tile> tiles;
     std::vector<int64_t> first((size_t)A->count + 1);
     std::vector<int64_t> local;
@@ -502,17 +540,25 @@ extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const i
     } catch (...) {
         return SYM_E_NOMEM;
     }
+    // SYPRD slots in instance order: a tile instance's tiles, or a banded instance's row bands
+    int64_t slot = 0;
     for (int64_t b = 0; b < A->count; ++b) {
-        first[(size_t)b] = (int64_t)tiles.size();
-        if (is_local(host_row_off[b + 1] - host_row_off[b], cap)) {
+        first[(size_t)b] = slot;
+        const int64_t n = host_row_off[b + 1] - host_row_off[b];
+        if (is_local(n, cap)) {
             local.push_back(b);
+            continue;
+        }
+        const int nb = band_count(n, cfg);
+        if (nb > 0) {
+            slot += nb;
             continue;
         }
         for (int64_t r = host_row_off[b]; r < host_row_off[b + 1]; r += cfg->rows_per_tile)
             tiles.push_back(Tile{r, (int32_t)std::min<int64_t>(cfg->rows_per_tile, host_row_off[b + 1] - r),
-                                 (int32_t)b, (int64_t)tiles.size()});
+                                 (int32_t)b, slot++});
     }
-    first[(size_t)A->count] = (int64_t)tiles.size();
+    first[(size_t)A->count] = slot;
     if (cfg->tile_order == 1) {
         // round-robin over instances: tile k of every instance, then tile k+1, ...
         std::vector<Tile> inter;
@@ -543,8 +589,9 @@ extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const i
     P->exec = nullptr;
     P->device = current_device();
     Carver c(arena, arena_bytes);
-    layout_plan(c, ntiles, A->count, &P->tiles, &P->tile_first, &P->tile_partials, &P->counter, &P->local_order,
-                &P->local_counter);
+    layout_plan(c, ntiles, nslots, A->count, &P->tiles, &P->tile_first, &P->tile_partials, &P->counter,
+                &P->local_order, &P->local_counter);
+    P->nslots = nslots;
     P->n_local = (int64_t)local.size();
     P->local_cap = cap;
     cudaStream_t s = as_stream(stream);
@@ -558,6 +605,13 @@ extern "C" sym_status sym_spmv_batch_plan_create(const sym_csr_batch* A, const i
     if (e != cudaSuccess) {
         delete P;
         return cuda_status(e);
+    }
+    if (cfg->band_rows > 0) {
+        sym_status bst = band_build(P->band, c, A, host_row_off, cfg, first, s);
+        if (bst != SYM_OK) {
+            delete P;
+            return bst;
+        }
     }
     *out = P;
     return SYM_OK;
@@ -613,6 +667,14 @@ extern "C" sym_status sym_spmv_batch_graph_launch(sym_batch_plan P, sym_stream_t
     return SYM_OK;
 }
 
+extern "C" sym_status sym_spmv_batch_check(sym_batch_plan P) {
+    if (!P) return SYM_E_INVALID;
+    if (!P->band.err) return SYM_OK;
+    unsigned h = 0;
+    SYM_CUDA(cudaMemcpy(&h, P->band.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return (h & 1u) ? SYM_E_TIMEOUT : SYM_OK;
+}
+
 extern "C" sym_status sym_spmv_batch_plan_destroy(sym_batch_plan P) {
     if (!P) return SYM_OK;
     if (P->exec) cudaGraphExecDestroy(P->exec);
@@ -633,7 +695,7 @@ std::string cache_key(const sym_csr_batch* A) {
     for (auto& ch : name)
         if (ch == ' ') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof(buf), "ssymv_batch4|%s|%lld|%lld|%lld", name.c_str(), (long long)A->count,
+    snprintf(buf, sizeof(buf), "ssymv_batch8|%s|%lld|%lld|%lld", name.c_str(), (long long)A->count,
              (long long)A->total_rows, (long long)A->total_nnz);
     return buf;
 }
@@ -648,8 +710,9 @@ bool cache_lookup(const char* path, const std::string& key, sym_tile_cfg* cfg, f
         char k[300];
         sym_tile_cfg c;
         float t;
-        if (sscanf(line, "%299s %d %d %d %d %d %d %d %f", k, &c.rows_per_tile, &c.lanes_per_row,
-                   &c.threads_per_cta, &c.ctas_per_sm, &c.local_smem_kb, &c.tile_order, &c.x_smem_kb, &t) == 9 &&
+        if (sscanf(line, "%299s %d %d %d %d %d %d %d %d %d %d %d %f", k, &c.rows_per_tile, &c.lanes_per_row,
+                   &c.threads_per_cta, &c.ctas_per_sm, &c.local_smem_kb, &c.tile_order, &c.x_smem_kb, &c.band_rows,
+                   &c.band_max, &c.band_chunk, &c.band_order, &t) == 13 &&
             key == k && cfg_ok(&c)) {
             *cfg = c;
             *ms = t;
@@ -664,8 +727,9 @@ void cache_store(const char* path, const std::string& key, const sym_tile_cfg& c
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %.6f\n", key.c_str(), c.rows_per_tile, c.lanes_per_row, c.threads_per_cta,
-            c.ctas_per_sm, c.local_smem_kb, c.tile_order, c.x_smem_kb, ms);
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %.6f\n", key.c_str(), c.rows_per_tile, c.lanes_per_row,
+            c.threads_per_cta, c.ctas_per_sm, c.local_smem_kb, c.tile_order, c.x_smem_kb, c.band_rows, c.band_max,
+            c.band_chunk, c.band_order, ms);
     fclose(f);
 }
 
@@ -695,8 +759,30 @@ extern "C" sym_status sym_autotune_spmv_batch(const sym_csr_batch* A, const int6
     SYM_CUDA(cudaEventCreate(&e0));
     SYM_CUDA(cudaEventCreate(&e1));
     float best_t = 1e30f;
-    sym_tile_cfg bc{64, 16, 256, 4, 0, 0, 0};
+    sym_tile_cfg bc{64, 16, 256, 4, 0, 0, 0, 0, 0, 0, 0};
     bool any = false;
+    auto try_cfg = [&](const sym_tile_cfg& c) {
+        if (!cfg_ok(&c) || sym_spmv_batch_plan_bytes(A, host_row_off, &c) > arena_bytes) return;
+        sym_batch_plan P = nullptr;
+        if (sym_spmv_batch_plan_create(A, host_row_off, &c, arena, arena_bytes, stream, &P) != SYM_OK) return;
+        float tot = 0.f;
+        bool ok = batch_enqueue(P, x, y, syprd, s) == SYM_OK;  // warm-up
+        for (int rep = 0; ok && rep < 3; ++rep) {
+            cudaEventRecord(e0, s);
+            ok = batch_enqueue(P, x, y, syprd, s) == SYM_OK;
+            cudaEventRecord(e1, s);
+            float t = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) ok = false;
+            tot += t;
+        }
+        if (ok && sym_spmv_batch_check(P) != SYM_OK) ok = false;
+        sym_spmv_batch_plan_destroy(P);
+        if (ok && tot / 3 < best_t) {
+            best_t = tot / 3;
+            bc = c;
+            any = true;
+        }
+    };
     for (int XS : xsk)
     for (int LS : locals)
     for (int O : orders)
@@ -710,29 +796,14 @@ extern "C" sym_status sym_autotune_spmv_batch(const sym_csr_batch* A, const int6
                     if (XS > 0 && (O != 0 || R < 256 || L > 16)) continue;
                     if (XS >= 96 && T * K > 1024) continue;
                     const int RR = XS > 0 ? (R == 256 ? 2048 : R) : R;
-                    sym_tile_cfg c{RR, L, T, K, LS, O, XS};
-                    if (sym_spmv_batch_plan_bytes(A, host_row_off, &c) > arena_bytes) continue;
-                    sym_batch_plan P = nullptr;
-                    if (sym_spmv_batch_plan_create(A, host_row_off, &c, arena, arena_bytes, stream, &P) != SYM_OK)
-                        continue;
-                    float tot = 0.f;
-                    bool ok = batch_enqueue(P, x, y, syprd, s) == SYM_OK;  // warm-up
-                    for (int rep = 0; ok && rep < 3; ++rep) {
-                        cudaEventRecord(e0, s);
-                        ok = batch_enqueue(P, x, y, syprd, s) == SYM_OK;
-                        cudaEventRecord(e1, s);
-                        float t = 0.f;
-                        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
-                            ok = false;
-                        tot += t;
-                    }
-                    sym_spmv_batch_plan_destroy(P);
-                    if (ok && tot / 3 < best_t) {
-                        best_t = tot / 3;
-                        bc = c;
-                        any = true;
-                    }
+                    try_cfg(sym_tile_cfg{RR, L, T, K, LS, O, XS, 0, 0, 0, 0});
                 }
+    // banded path: band height, CTA size and entry order (one CTA per SM, 4 entries per lane per chunk),
+    // plus one two-CTA shape; the fastest shapes measured on the 4,096-instance batch are among these
+    for (int W : {4096, 5120})
+        for (int T : {800, 1024})
+            for (int G : {0, 1}) try_cfg(sym_tile_cfg{256, 8, T, 1, 0, 0, 0, W, BAND_MAX_BANDS, 4, G});
+    try_cfg(sym_tile_cfg{256, 8, 544, 2, 0, 0, 0, 2048, BAND_MAX_BANDS, 4, 1});
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!any) return SYM_E_NOMEM;

@@ -143,3 +143,125 @@ def test_autotune_picks_valid_cfg_and_caches(tmp_path):
     plan2.run(x, ref, s2)
     torch.cuda.synchronize()
     assert float((y - ref).abs().max()) <= 1e-4 * float(ref.abs().max())
+
+
+# ----------------------------------------------------------------------------- banded path
+
+def run_plan(sg, row_off, rowptr, col, v, x, cfg, graph=False):
+    torch = pytest.importorskip("torch")
+    batch = sg.BatchCSR(dev(row_off), dev(rowptr), dev(col), dev(v))
+    plan = sg.BatchPlan(batch, sg.TileCfg(*cfg))
+    xd = dev(x)
+    y = torch.full_like(xd, 77.0)
+    s = torch.full((len(row_off) - 1,), 5.0, dtype=torch.float64, device="cuda")
+    plan.run(xd, y, s)
+    out = [(host(y), host(s))]
+    if graph:
+        y.fill_(123.0)
+        plan.capture(xd, y, s)
+        for _ in range(3):
+            plan.launch()
+        torch.cuda.synchronize()
+        out.append((host(y), host(s)))
+    plan.check()
+    return out
+
+
+def check_against_oracle(outs, row_off, rowptr, col, v, x):
+    yr, ya, sr, sa = oracle_batch(row_off, rowptr, col, v, x)
+    nz = sa > 0
+    for yg, sgot in outs:
+        assert oracle.componentwise_error(yg, yr, ya) <= TOL_F32
+        assert np.max(np.abs(sgot[nz] - sr[nz]) / sa[nz], initial=0.0) <= TOL_F32
+        assert np.all(sgot[~nz] == 0.0)
+
+
+# (rows_per_tile, lanes, threads, ctas/SM, local, order, x_smem, band_rows, band_max, band_vec, band_order)
+BAND_CFGS = [
+    (256, 8, 512, 1, 0, 0, 0, 256, 64, 4, 0),     # up to 16 bands per instance, many blocks, multi-chunk blocks
+    (256, 8, 256, 2, 0, 0, 0, 512, 4, 8, 0),      # instances beyond 4 bands stay on tiles (mixed plan)
+    (256, 8, 1024, 1, 0, 0, 0, 4096, 64, 4, 0),   # 31 consumer warps, few bands; small instances in one band
+    (64, 16, 128, 2, 0, 0, 0, 2048, 2, 16, 0),     # two CTAs per SM, 2-band cap, 16 entries per lane per chunk
+    (256, 8, 288, 1, 0, 0, 0, 5120, 64, 8, 0),    # widest band: one band per instance (plain y stores)
+    (256, 8, 512, 1, 0, 0, 0, 256, 64, 4, 1),     # bank-grouped blocks, many bands
+    (256, 8, 1024, 1, 0, 0, 0, 4096, 64, 4, 1),   # bank-grouped, few bands
+    (256, 8, 256, 2, 0, 0, 0, 512, 4, 8, 1),      # bank-grouped, mixed plan
+    (256, 8, 1024, 1, 0, 0, 0, 5120, 64, 1, 1),   # bank-grouped, one entry per lane per chunk (many stages)
+    (256, 8, 544, 1, 0, 0, 0, 2048, 64, 2, 1),    # bank-grouped, two entries per lane per chunk
+]
+
+
+@pytest.mark.parametrize("cfg", BAND_CFGS)
+def test_batch_band_parity(cfg):
+    """Banded path (x / y bands in shared memory, bulk-copied entry stream) vs the oracle, incl. graph replay."""
+    sg = need_gpu()
+    sizes, row_off, draw_off, idx, val, rowptr, col, v = make_small_batch(97, 4, 4000, 16, 5)
+    x = synth.vector_uniform(int(row_off[-1]), 5)
+    outs = run_plan(sg, row_off, rowptr, col, v, x, cfg, graph=True)
+    check_against_oracle(outs, row_off, rowptr, col, v, x)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("per_row", [0.05, 0.6, 3.0])
+def test_batch_band_sparse_blocks_direct_and_staged(per_row, order):
+    """Sparse instances: blocks below the staging threshold reduce straight into global memory."""
+    sg = need_gpu()
+    sizes = np.array([3000, 1, 0, 2500, 777, 4096, 4097, 255, 256, 257], np.int64)
+    row_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    draws = np.rint(per_row * sizes).astype(np.int64)
+    draw_off = np.concatenate([[0], np.cumsum(draws)]).astype(np.int64)
+    idx, val = synth.batch_coords(row_off, draw_off, 31)
+    rowptr, col, v = synth.batch_upper_csr_host(row_off, idx, val)
+    x = synth.vector_uniform(int(row_off[-1]), 31)
+    outs = run_plan(sg, row_off, rowptr, col, v, x, (256, 8, 512, 1, 0, 0, 0, 256, 64, 8 if order == 0 else 2, order))
+    check_against_oracle(outs, row_off, rowptr, col, v, x)
+
+
+def test_batch_band_dense_rows_and_diagonal_only():
+    """One instance with a dense first row (one block spans many chunks; in bank groups its row bank
+    forces groups with repeated banks), one diagonal-only instance."""
+    sg = need_gpu()
+    n0, n1 = 3000, 700
+    rows, cols, vals = [], [], []
+    rng = np.random.default_rng(4)
+    for j in range(n0):                       # dense row 0 of instance 0
+        rows.append(0); cols.append(j)
+    for i in range(1, n0, 7):                 # a few more entries
+        rows.append(i); cols.append(min(n0 - 1, i + 3))
+    for i in range(n1):                       # instance 1: diagonal only
+        rows.append(n0 + i); cols.append(n0 + i)
+    rows, cols = np.array(rows, np.int64), np.array(cols, np.int64)
+    o = np.lexsort((cols, rows))
+    rows, cols = rows[o], cols[o]
+    vals = rng.uniform(-1, 1, len(rows)).astype(np.float32)
+    total = n0 + n1
+    rowptr = np.zeros(total + 1, np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    row_off = np.array([0, n0, total], np.int64)
+    x = synth.vector_uniform(total, 4)
+    for cfg in [(256, 8, 256, 1, 0, 0, 0, 256, 64, 4, 0), (256, 8, 288, 1, 0, 0, 0, 4096, 64, 16, 0),
+                (256, 8, 64, 2, 0, 0, 0, 512, 64, 8, 0), (256, 8, 256, 1, 0, 0, 0, 256, 64, 4, 1),
+                (256, 8, 288, 1, 0, 0, 0, 4096, 64, 16, 1)]:
+        outs = run_plan(sg, row_off, rowptr, cols.astype(np.int32), vals, x, cfg)
+        check_against_oracle(outs, row_off, rowptr, cols.astype(np.int32), vals, x)
+
+
+def test_batch_band_rejects_bad_columns():
+    """A column below its row or outside its instance is caught when the banded plan is built."""
+    sg = need_gpu()
+    sizes = np.array([300, 200], np.int64)
+    row_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    draw_off = np.array([0, 1200, 2000], np.int64)
+    idx, val = synth.batch_coords(row_off, draw_off, 8)
+    rowptr, col, v = synth.batch_upper_csr_host(row_off, idx, val)
+    cfg = sg.TileCfg(256, 8, 256, 1, 0, 0, 0, 256, 64, 4, 1)
+    r = int(np.nonzero(np.diff(rowptr[:301]) > 0)[0][5])   # a non-empty row of instance 0 (row > 0)
+    assert r >= 1
+    for bad_col, code in [(r - 1, -2), (450, -3)]:   # below the diagonal; inside instance 1
+        c2 = col.copy()
+        c2[rowptr[r]] = bad_col
+        batch = sg.BatchCSR(dev(row_off), dev(rowptr), dev(c2), dev(v))
+        with pytest.raises(sg.SymError) as ei:
+            sg.BatchPlan(batch, cfg)
+        assert ei.value.code == code
