@@ -474,6 +474,62 @@ sym_status sym_ttm_expanded(sym_expanded E, const void* B, sym_dtype bdt, int ra
 sym_status sym_expanded_destroy(sym_expanded E);
 
 /* ===================================================================== */
+/* Partially symmetric tensors (Sec. 2.1, Def. "Partial Symmetry")         */
+/* ===================================================================== */
+
+/* The `order` modes (1..5) are split into `nparts` consecutive parts of sizes
+ * part[0..nparts) (summing to order); the indices of part p range over
+ * [0, dim[p]).  The tensor is unchanged by any permutation that moves positions
+ * only inside their part, so its canonical triangle keeps the indices
+ * non-decreasing inside every part (Sec. 2.1, Def. "Canonical") and one stored
+ * entry stands for every distinct arrangement obtained by permuting inside
+ * parts (prod over parts of s_p! / prod m!).  One part of size `order` is full
+ * symmetry; parts of size 1 are modes without symmetry. */
+typedef struct sym_ptensor_s* sym_ptensor;
+
+typedef struct {
+    int32_t order;
+    int32_t nparts;
+    int32_t key_bits;            /* sum over modes of ceil(log2 dim) (<= 128) */
+    int64_t nnz;                 /* canonical entries kept */
+    int64_t expanded_nnz;        /* full-tensor nonzeros: sum of the arrangements (exact) */
+    int64_t duplicates_dropped;  /* SYM_DUP_KEEP_EQUAL copies removed */
+    double normsq;               /* ||X||^2 over the full tensor (FP64) */
+} sym_ptensor_info_t;
+
+/* Arena (kept by the handle) and workspace (create only) bytes.  part, dim [host]. */
+sym_status sym_ptensor_create_bytes(int order, int nparts, const int32_t* part, const int64_t* dim, int64_t nnz,
+                                    size_t* arena_bytes, size_t* ws_bytes);
+/* Canonicalises the coordinate list idx [device, order arrays of nnz int32 at
+ * stride ld_idx] / val [device, nnz floats] on the device: sort inside every
+ * part, check each index against its part's dimension (SYM_E_RANGE), sort
+ * entries lexicographically, resolve repeated tuples by `dup`
+ * (SYM_E_DUPLICATE).  Any inside-part permutation of a stored tuple gives the
+ * same tensor.  Synchronises `stream`. */
+sym_status sym_ptensor_create(int order, int nparts, const int32_t* part, const int64_t* dim, int64_t nnz,
+                              const int32_t* idx, int64_t ld_idx, const float* val, sym_dup_policy dup, void* arena,
+                              size_t arena_bytes, void* ws, size_t ws_bytes, sym_stream_t stream, sym_ptensor* out);
+sym_status sym_ptensor_info(sym_ptensor X, sym_ptensor_info_t* out);
+/* Canonical entries in lexicographic order: cidx [device, order arrays at
+ * stride ld_out >= nnz], cval [device, nnz]. */
+sym_status sym_ptensor_export(sym_ptensor X, int32_t* cidx, int64_t ld_out, float* cval, sym_stream_t stream);
+/* MTTKRP for the factor of part out_part: with f the first mode of that part,
+ * M[i, r] = sum over the full tensor's nonzeros x with x_f = i of
+ * X[x] * prod_{q != f} F_{part of q}[x_q, r] (Sec. 5.2.6 with one factor per
+ * part; any mode of the part gives the same M).  factors [host array of
+ * nparts device pointers]: part p's factor, dim[p] x rank, row stride ldf[p]
+ * [host] (multiple of 4), FP32 or BF16 (16- / 8-byte aligned rows).  M
+ * [device, dim[out_part] x rank, row stride ldm, 16-byte aligned] is
+ * overwritten.  rank: 4..128, multiple of 4.  Per canonical entry and per
+ * distinct index value u of the output part, one 16-byte-per-lane reduction:
+ * M[u] += v W_u prod(F_P rows of the part's other positions)
+ * prod_{Q != P} E(c_Q) prod(F_Q rows), W_u and E the integer arrangement
+ * counts.  FP32 accumulation with floating-point atomics. */
+sym_status sym_pmttkrp(sym_ptensor X, const void* const* factors, const int64_t* ldf, sym_dtype dtype, int rank,
+                       int out_part, float* M, int64_t ldm, sym_stream_t stream);
+sym_status sym_ptensor_destroy(sym_ptensor X);
+
+/* ===================================================================== */
 /* Serving: continuous batching of MTTKRP requests                          */
 /* ===================================================================== */
 

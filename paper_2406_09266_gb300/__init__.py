@@ -75,6 +75,14 @@ class TensorInfo(C.Structure):
         return d
 
 
+class PTensorInfo(C.Structure):
+    _fields_ = [("order", C.c_int32), ("nparts", C.c_int32), ("key_bits", C.c_int32), ("nnz", C.c_int64),
+                ("expanded_nnz", C.c_int64), ("duplicates_dropped", C.c_int64), ("normsq", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Request(C.Structure):
     _fields_ = [("X", C.c_void_p), ("B", C.c_void_p), ("bdt", C.c_int), ("rank", C.c_int32), ("ldb", C.c_int64),
                 ("M", C.c_void_p), ("ldm", C.c_int64), ("want_residual", C.c_int32), ("user_tag", C.c_uint64)]
@@ -184,6 +192,15 @@ _SIGS = {
     "sym_mttkrp_expanded": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64,
                              C.c_void_p], C.c_int),
     "sym_expanded_destroy": ([C.c_void_p], C.c_int),
+    "sym_ptensor_create_bytes": ([C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
+                                 C.c_int),
+    "sym_ptensor_create": ([C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                            C.c_int, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_ptensor_info": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_ptensor_export": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_pmttkrp": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64,
+                     C.c_void_p], C.c_int),
+    "sym_ptensor_destroy": ([C.c_void_p], C.c_int),
     "sym_server_arena_bytes": ([C.c_void_p], C.c_size_t),
     "sym_server_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p], C.c_int),
     "sym_batch_submit": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -607,6 +624,78 @@ class Expanded:
     def close(self):
         if getattr(self, "handle", None):
             lib().sym_expanded_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ partially symmetric tensors
+
+class PTensor:
+    """A partially symmetric sparse tensor (sym_ptensor_*): modes split into consecutive parts of sizes
+    `parts`, part p's indices in [0, dims[p]); symmetric under permutations inside each part."""
+
+    def __init__(self, idx: torch.Tensor, val: torch.Tensor, parts, dims, dup: int = DUP_ERROR, stream=None):
+        if idx.dim() != 2 or idx.dtype != torch.int32 or not idx.is_cuda:
+            raise TypeError("idx must be a (order, nnz) int32 CUDA tensor")
+        if val.dtype != torch.float32 or not val.is_cuda:
+            raise TypeError("val must be a float32 CUDA tensor")
+        order, nnz = idx.shape
+        idx = idx.contiguous()
+        self._part = (C.c_int32 * len(parts))(*[int(p) for p in parts])
+        self._dim = (C.c_int64 * len(dims))(*[int(d) for d in dims])
+        ab, wb = C.c_size_t(0), C.c_size_t(0)
+        check(lib().sym_ptensor_create_bytes(order, len(parts), self._part, self._dim, nnz, C.byref(ab), C.byref(wb)),
+              "sym_ptensor_create_bytes")
+        self.arena = _scratch(ab.value, idx.device)
+        ws = _scratch(wb.value, idx.device)
+        h = C.c_void_p()
+        check(lib().sym_ptensor_create(order, len(parts), self._part, self._dim, nnz, _ptr(idx), max(nnz, 1),
+                                       _ptr(val.contiguous()), dup, _ptr(self.arena), self.arena.numel(), _ptr(ws),
+                                       ws.numel(), _stream(stream), C.byref(h)), "sym_ptensor_create")
+        self.handle = h
+        self.order, self.parts, self.dims = order, tuple(int(p) for p in parts), tuple(int(d) for d in dims)
+        self.device = idx.device
+
+    def info(self) -> dict:
+        inf = PTensorInfo()
+        check(lib().sym_ptensor_info(self.handle, C.byref(inf)), "sym_ptensor_info")
+        return inf.as_dict()
+
+    @property
+    def nnz(self) -> int:
+        return self.info()["nnz"]
+
+    def export(self, stream=None):
+        """(cidx (order x nnz) int32, cval) on the device, lexicographic order."""
+        nnz = self.nnz
+        cidx = torch.empty((self.order, max(nnz, 1)), dtype=torch.int32, device=self.device)
+        cval = torch.empty(max(nnz, 1), dtype=torch.float32, device=self.device)
+        check(lib().sym_ptensor_export(self.handle, _ptr(cidx), max(nnz, 1), _ptr(cval), _stream(stream)),
+              "sym_ptensor_export")
+        return cidx[:, :nnz], cval[:nnz]
+
+    def mttkrp(self, factors, out_part: int, M=None, stream=None):
+        """MTTKRP for part out_part's factor; factors: one (dims[p], R) CUDA tensor per part, all FP32 or all BF16."""
+        rank = factors[0].shape[1]
+        dt = _dtype_code(factors[0])
+        if any(_dtype_code(f) != dt or f.shape[1] != rank for f in factors):
+            raise TypeError("factors must share dtype and rank")
+        ptrs = (C.c_void_p * len(factors))(*[f.data_ptr() for f in factors])
+        lds = (C.c_int64 * len(factors))(*[f.stride(0) for f in factors])
+        if M is None:
+            M = torch.empty((self.dims[out_part], rank), dtype=torch.float32, device=factors[0].device)
+        check(lib().sym_pmttkrp(self.handle, ptrs, lds, dt, rank, out_part, _ptr(M), M.stride(0), _stream(stream)),
+              "sym_pmttkrp")
+        return M
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sym_ptensor_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
