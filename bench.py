@@ -508,7 +508,44 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
         rows["ttm3_unif_n2k_nnz5M_r32"] = ttm_row(torch, sg, dev, flush, stream, hbm_peak)
     except Exception as e:
         rows["ttm3_unif_n2k_nnz5M_r32"] = {"error": repr(e)}
+    try:
+        rows["pmttkrp_parts22_n20k_nnz5M_r32"] = ptensor_row(torch, sg, dev, flush, stream, hbm_peak)
+    except Exception as e:
+        rows["pmttkrp_parts22_n20k_nnz5M_r32"] = {"error": repr(e)}
     return rows
+
+
+def ptensor_row(torch, sg, dev, flush, stream, hbm_peak, parts=(2, 2), dims=(20_000, 20_000), nnz=5_000_000,
+                rank=32, seed=4):
+    """Partially symmetric 4-way tensor (symmetric inside modes {1,2} and inside {3,4}), uniform indices:
+    the MTTKRP for each part's factor, against the same kernel on the tensor with its symmetry expanded."""
+    T = synth.ptensor_uniform(parts, dims, nnz, seed)
+    X = sg.PTensor(torch.from_numpy(T.idx).to(dev), torch.from_numpy(T.val).to(dev), parts, dims)
+    info = X.info()
+    F = [torch.from_numpy(synth.factor_normal(d, rank, seed + p)).to(dev) for p, d in enumerate(dims)]
+    out = {"parts": list(parts), "dims": list(dims), "canonical_nnz": info["nnz"], "rank": rank,
+           "expanded_nnz": info["expanded_nnz"], "read_reduction": info["expanded_nnz"] / max(info["nnz"], 1)}
+    Ms = [torch.empty((d, rank), dtype=torch.float32, device=dev) for d in dims]
+    per_mode = [F[p] for p, s_ in enumerate(parts) for _ in range(s_)]
+    first = np.cumsum([0] + list(parts))[:-1]
+    E = X.expand()
+    for o in range(len(parts)):
+        for _ in range(3):
+            X.mttkrp(F, o, M=Ms[o])
+        ms = float(np.mean(timed_steps(torch, lambda: X.mttkrp(F, o, M=Ms[o]), 10, flush, stream)))
+        ref = X.mttkrp(F, o)
+        Me = E.mttkrp(per_mode, int(first[o]))
+        ems = float(np.mean(timed_steps(torch, lambda: E.mttkrp(per_mode, int(first[o]), M=Me), 5, flush, stream)))
+        torch.cuda.synchronize()
+        # bytes: canonical entries (4 int32 + value), the factor rows read once, M zeroed and reduced
+        alg = info["nnz"] * (4 * len(T.idx) + 4) + sum(d * rank * 4 for d in dims) + 2 * dims[o] * rank * 4
+        out[f"part{o}"] = {"ms": ms, "canonical_nnz_per_s": info["nnz"] / (ms * 1e-3),
+                           "effective_gbs": alg / (ms * 1e-3) / 1e9, "hbm_frac": alg / (ms * 1e-3) / 1e9 / hbm_peak,
+                           "expanded_ms": ems, "speedup_sym_over_expanded": ems / ms,
+                           "max_abs_diff_vs_expanded": float((Me - ref).abs().max())}
+    E.close()
+    X.close()
+    return out
 
 
 def large_ssymv_row(torch, sg, dev, flush, stream, hbm_peak, n=1 << 21, per_row=16, seed=5):
@@ -812,6 +849,19 @@ def run_ttm_only(args):
     print(json.dumps({"mode": "ttm-only (profiling)", "canonical_nnz": X.info()["nnz"], "rank": rank}))
 
 
+def run_ptensor_only(args):
+    """The partially symmetric MTTKRP row alone (also the profiling entry for its kernel)."""
+    import torch
+
+    import paper_2406_09266_gb300 as sg
+    sg.load()
+    dev = torch.device("cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    hbm_peak, _ = peaks()
+    out = ptensor_row(torch, sg, dev, flush, torch.cuda.current_stream(), hbm_peak)
+    print(json.dumps({"mode": "ptensor-only", "pmttkrp_parts22_n20k_nnz5M_r32": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -825,6 +875,8 @@ def main():
                          "the MTTKRP configuration fixed instead of autotuned")
     ap.add_argument("--ttm-only", action="store_true",
                     help="profiling mode: the symmetric TTM kernels on the TTM row's tensor, nothing else")
+    ap.add_argument("--ptensor-only", action="store_true",
+                    help="profiling mode: the partially symmetric MTTKRP row alone")
     ap.add_argument("--batch-only", type=int, default=0, metavar="INSTANCES",
                     help="profiling mode: build a batch of this many instances and run the batched SSYMV a few times")
     ap.add_argument("--batch-cfg", default="", metavar="FIELDS",
@@ -838,6 +890,8 @@ def main():
         run_batch_only(args)
     elif args.ttm_only:
         run_ttm_only(args)
+    elif args.ptensor_only:
+        run_ptensor_only(args)
     else:
         run_ours(args)
 

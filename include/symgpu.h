@@ -527,6 +527,16 @@ sym_status sym_ptensor_export(sym_ptensor X, int32_t* cidx, int64_t ld_out, floa
  * counts.  FP32 accumulation with floating-point atomics. */
 sym_status sym_pmttkrp(sym_ptensor X, const void* const* factors, const int64_t* ldf, sym_dtype dtype, int rank,
                        int out_part, float* M, int64_t ldm, sym_stream_t stream);
+/* Baseline: the same tensor with its symmetry expanded away — every inside-
+ * part arrangement of every canonical entry stored (info.expanded_nnz
+ * entries), as a tensor with `order` parts of size 1 (no symmetry left);
+ * sym_pmttkrp on it with the first mode of a part as out_part gives that
+ * part's MTTKRP without exploiting symmetry.  The expansion runs on the
+ * device (arrangement counts, scan, next-permutation inside parts) and is
+ * then canonicalised like any input.  Synchronises `stream`. */
+sym_status sym_ptensor_expand_bytes(sym_ptensor X, size_t* arena_bytes, size_t* ws_bytes);
+sym_status sym_ptensor_expand(sym_ptensor X, void* arena, size_t arena_bytes, void* ws, size_t ws_bytes,
+                              sym_stream_t stream, sym_ptensor* out);
 sym_status sym_ptensor_destroy(sym_ptensor X);
 
 /* ===================================================================== */

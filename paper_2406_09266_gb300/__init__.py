@@ -200,6 +200,9 @@ _SIGS = {
     "sym_ptensor_export": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "sym_pmttkrp": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64,
                      C.c_void_p], C.c_int),
+    "sym_ptensor_expand_bytes": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_ptensor_expand": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p],
+                           C.c_int),
     "sym_ptensor_destroy": ([C.c_void_p], C.c_int),
     "sym_server_arena_bytes": ([C.c_void_p], C.c_size_t),
     "sym_server_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p], C.c_int),
@@ -678,6 +681,23 @@ class PTensor:
         check(lib().sym_ptensor_export(self.handle, _ptr(cidx), max(nnz, 1), _ptr(cval), _stream(stream)),
               "sym_ptensor_export")
         return cidx[:, :nnz], cval[:nnz]
+
+    def expand(self, stream=None) -> "PTensor":
+        """The same tensor with every inside-part arrangement stored (one part per mode: no symmetry left)."""
+        ab, wb = C.c_size_t(0), C.c_size_t(0)
+        check(lib().sym_ptensor_expand_bytes(self.handle, C.byref(ab), C.byref(wb)), "sym_ptensor_expand_bytes")
+        arena = _scratch(ab.value, self.device)
+        ws = _scratch(wb.value, self.device)
+        h = C.c_void_p()
+        check(lib().sym_ptensor_expand(self.handle, _ptr(arena), arena.numel(), _ptr(ws), ws.numel(),
+                                       _stream(stream), C.byref(h)), "sym_ptensor_expand")
+        del ws
+        E = PTensor.__new__(PTensor)
+        E.handle, E.arena, E.device = h, arena, self.device
+        E.order = self.order
+        E.parts = (1,) * self.order
+        E.dims = tuple(d for s_, d in zip(self.parts, self.dims) for _ in range(s_))
+        return E
 
     def mttkrp(self, factors, out_part: int, M=None, stream=None):
         """MTTKRP for part out_part's factor; factors: one (dims[p], R) CUDA tensor per part, all FP32 or all BF16."""

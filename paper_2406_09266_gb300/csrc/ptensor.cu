@@ -21,6 +21,7 @@
 // W_u = (s_P - 1)! m_u / prod_t m_t! arrangements that put u first.  So per
 // canonical entry and per distinct u:
 //   M[u, :] += v * W_u * prod_{c_P minus u} F_P * prod_{Q != P} E(c_Q) prod F_Q.
+#include <algorithm>
 #include <new>
 #include <string.h>
 
@@ -276,6 +277,64 @@ __global__ void __launch_bounds__(256) k_pmttkrp(ModeArgs A, const int32_t* __re
             const int W = fact_small(A.s - 1) * m / denP;
             red_add_f4(M + (int64_t)c[q] * ldm + col, f4_scale(t, base * (float)W));
         }
+    }
+}
+
+// Arrangement count of each canonical entry (for the expansion offsets).
+template <int N>
+__global__ void k_pcount(PartDesc D, const int32_t* __restrict__ idx, int64_t ld, int64_t nnz,
+                         int64_t* __restrict__ cnt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    int32_t c[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) c[q] = idx[(int64_t)q * ld + e];
+    cnt[e] = (int64_t)arrangements<N>(c, D);
+}
+
+// Writes every inside-part arrangement of entry e at off[e] ...: each part
+// steps through the distinct permutations of its multiset (next permutation
+// in lexicographic order), the last part fastest.
+template <int N>
+__global__ void k_pexpand(PartDesc D, const int32_t* __restrict__ idx, int64_t ld, const float* __restrict__ val,
+                          int64_t nnz, const int64_t* __restrict__ off, int32_t* __restrict__ out, int64_t ld_out,
+                          float* __restrict__ out_val) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    int32_t c[N];
+    for (int q = 0; q < N; ++q) c[q] = idx[(int64_t)q * ld + e];
+    const float v = val[e];
+    int64_t w = off[e];
+    for (;;) {
+        for (int q = 0; q < N; ++q) out[(int64_t)q * ld_out + w] = c[q];
+        out_val[w] = v;
+        ++w;
+        bool advanced = false;
+        for (int p = D.nparts - 1; p >= 0 && !advanced; --p) {
+            const int f = D.first[p], s = D.size[p];
+            int i = s - 2;
+            while (i >= 0 && c[f + i] >= c[f + i + 1]) --i;
+            if (i >= 0) {
+                int j = s - 1;
+                while (c[f + j] <= c[f + i]) --j;
+                int32_t t = c[f + i];
+                c[f + i] = c[f + j];
+                c[f + j] = t;
+                for (int a = i + 1, b = s - 1; a < b; ++a, --b) {
+                    t = c[f + a];
+                    c[f + a] = c[f + b];
+                    c[f + b] = t;
+                }
+                advanced = true;
+            } else {
+                for (int a = 0, b = s - 1; a < b; ++a, --b) {  // back to ascending, carry to the part before
+                    const int32_t t = c[f + a];
+                    c[f + a] = c[f + b];
+                    c[f + b] = t;
+                }
+            }
+        }
+        if (!advanced) break;
     }
 }
 
@@ -549,4 +608,80 @@ extern "C" sym_status sym_pmttkrp(sym_ptensor X, const void* const* factors, con
 extern "C" sym_status sym_ptensor_destroy(sym_ptensor X) {
     delete X;
     return SYM_OK;
+}
+
+// ---------------------------------------------------------------- expansion (baseline)
+
+extern "C" sym_status sym_ptensor_expand_bytes(sym_ptensor X, size_t* arena_bytes, size_t* ws_bytes) {
+    if (!X) return SYM_E_INVALID;
+    const PartDesc& D = X->D;
+    const int64_t E = X->info.expanded_nnz;
+    int32_t part[5];
+    int64_t dim[5];
+    for (int q = 0; q < D.order; ++q) {
+        part[q] = 1;
+        dim[q] = D.dim[D.part_of[q]];
+    }
+    size_t ca = 0, cw = 0;
+    sym_status st = sym_ptensor_create_bytes(D.order, D.order, part, dim, E, &ca, &cw);
+    if (st != SYM_OK) return st;
+    Sizer w;
+    w.take<int64_t>((size_t)std::max<int64_t>(X->info.nnz, 1) + 1);           // counts -> offsets
+    w.take<char>(scan_ws_bytes(std::max<int64_t>(X->info.nnz, 1) + 1));
+    w.take<int32_t>((size_t)std::max<int64_t>(E, 1) * (size_t)D.order);        // expanded coordinate list
+    w.take<float>((size_t)std::max<int64_t>(E, 1));
+    w.take<char>(cw);
+    if (arena_bytes) *arena_bytes = ca;
+    if (ws_bytes) *ws_bytes = w.used;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_ptensor_expand(sym_ptensor X, void* arena, size_t arena_bytes, void* ws, size_t ws_bytes,
+                                         sym_stream_t stream, sym_ptensor* out) {
+    if (!X || !out) return SYM_E_INVALID;
+    *out = nullptr;
+    size_t na = 0, nw = 0;
+    sym_status st = sym_ptensor_expand_bytes(X, &na, &nw);
+    if (st != SYM_OK) return st;
+    if (!arena || !ws || !aligned(arena, 256) || !aligned(ws, 256)) return SYM_E_INVALID;
+    if (arena_bytes < na || ws_bytes < nw) return SYM_E_NOMEM;
+    const PartDesc& D = X->D;
+    const int64_t nnz = X->info.nnz, E = X->info.expanded_nnz;
+    cudaStream_t s = as_stream(stream);
+    Carver W(ws, ws_bytes);
+    int64_t* offs = W.take<int64_t>((size_t)std::max<int64_t>(nnz, 1) + 1);
+    char* sws = W.take<char>(scan_ws_bytes(std::max<int64_t>(nnz, 1) + 1));
+    int32_t* eidx = W.take<int32_t>((size_t)std::max<int64_t>(E, 1) * (size_t)D.order);
+    float* evals = W.take<float>((size_t)std::max<int64_t>(E, 1));
+    const size_t rest = ws_bytes - W.used;
+    char* cws = W.take<char>(1);
+    if (!cws) return SYM_E_NOMEM;
+    if (nnz > 0) {
+        const unsigned g = (unsigned)((nnz + 255) / 256);
+#define SYM_PX_CASE(NN)                                                                                  \
+    k_pcount<NN><<<g, 256, 0, s>>>(D, X->idx, X->cap, nnz, offs);                                       \
+    SYM_CHECK_LAUNCH();                                                                                  \
+    st = exclusive_scan_i64(offs, offs, nnz, sws, s);                                                    \
+    if (st != SYM_OK) return st;                                                                         \
+    k_pexpand<NN><<<g, 256, 0, s>>>(D, X->idx, X->cap, X->val, nnz, offs, eidx, std::max<int64_t>(E, 1), \
+                                    evals);                                                              \
+    SYM_CHECK_LAUNCH();
+        switch (D.order) {
+            case 1: { SYM_PX_CASE(1) } break;
+            case 2: { SYM_PX_CASE(2) } break;
+            case 3: { SYM_PX_CASE(3) } break;
+            case 4: { SYM_PX_CASE(4) } break;
+            default: { SYM_PX_CASE(5) } break;
+        }
+#undef SYM_PX_CASE
+    }
+    int32_t part[5];
+    int64_t dim[5];
+    for (int q = 0; q < D.order; ++q) {
+        part[q] = 1;
+        dim[q] = D.dim[D.part_of[q]];
+    }
+    // cws .. end of ws is the create workspace (256-byte aligned: the carve above)
+    return sym_ptensor_create(D.order, D.order, part, dim, E, eidx, std::max<int64_t>(E, 1), evals, SYM_DUP_ERROR,
+                              arena, arena_bytes, cws, rest, stream, out);
 }

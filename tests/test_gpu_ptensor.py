@@ -137,3 +137,30 @@ def test_ptensor_errors_and_empty():
     Fd, _, _ = factors(dims, 8, 1)
     M = E.mttkrp(Fd, 0)
     assert float(M.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("parts,dims", [((2, 1), (5, 4)), ((2, 2), (4, 3)), ((1, 3), (3, 4)), ((2, 1, 2), (3, 2, 3)),
+                                        ((5,), (4,))])
+def test_expand_baseline_matches_oracle(parts, dims):
+    """The device expansion stores exactly the oracle's arrangements; the MTTKRP on it (no symmetry left)
+    equals the symmetric one for every part."""
+    sg = need_gpu()
+    T = synth.ptensor_small_all_patterns(parts, dims, 6, density=0.7)
+    X = sg.PTensor(dev(T.idx), dev(T.val), parts, dims)
+    cidx, cval = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+    E = X.expand()
+    ei, ev = E.export()
+    oi, ov = oracle.pexpand(parts, cidx, cval)
+    assert np.array_equal(host(ei), oi) and np.array_equal(host(ev).view(np.uint32), ov.view(np.uint32))
+    assert E.info()["expanded_nnz"] == X.info()["expanded_nnz"] == oi.shape[1]
+    rank = 8
+    Fd, F64, _ = factors(dims, rank, 50)
+    per_mode = [Fd[p] for p, s in enumerate(parts) for _ in range(s)]
+    first = np.cumsum([0] + list(parts))[:-1]
+    for out in range(len(parts)):
+        Ms = X.mttkrp(Fd, out)
+        Me = E.mttkrp(per_mode, int(first[out]))
+        torch.cuda.synchronize()
+        ref, ref_abs = oracle.pmttkrp_enum(parts, dims, cidx, cval, F64, out)
+        assert oracle.componentwise_error(host(Ms), ref, ref_abs) <= TOL_F32
+        assert oracle.componentwise_error(host(Me), ref, ref_abs) <= TOL_F32
