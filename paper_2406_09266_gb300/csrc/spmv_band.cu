@@ -46,6 +46,21 @@ namespace {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// 32-bit shared-window accesses (explicit state space: no generic-address checks).
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void reds_add_f32(uint32_t a, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;\n" ::"r"(a), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -107,33 +122,47 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 
 // ---------------------------------------------------------------- device helpers
 
-// g[0..w) += s[0..w) (or = when `plain`), then s[0..w) = 0.  16-byte vector
-// reductions on the aligned body.  Thread t touches the same elements of s in
-// both passes, so no barrier is needed before the zeroing.
+// g[0..w) += s[0..w) (or = when `plain`), then s[0..w) = 0.  s is placed in
+// shared memory with the same 16-byte phase as g (the y buffers carry a lead
+// of 0..3 floats), so the aligned body moves as 16-byte vectors on both
+// sides: one shared load, one global vector reduction (skipped when all four
+// are zero) and one shared store per 4 elements.  Thread t touches the same
+// elements in every pass, so no barrier is needed before the zeroing.
 __device__ __forceinline__ void band_flush(float* g, float* s, int w, bool plain, int t, int nt) {
-    if (plain) {
-        for (int k = t; k < w; k += nt) {
-            g[k] = s[k];
-            s[k] = 0.f;
-        }
-        return;
-    }
     const int head = min(w, (int)(((16u - ((uint32_t)reinterpret_cast<uintptr_t>(g) & 15u)) & 15u) >> 2));
     for (int k = t; k < head; k += nt) {
-        if (s[k] != 0.f) atomicAdd(g + k, s[k]);
+        if (plain) {
+            g[k] = s[k];
+        } else if (s[k] != 0.f) {
+            atomicAdd(g + k, s[k]);
+        }
         s[k] = 0.f;
     }
     const int nv = (w - head) >> 2;
+    float4* sv = reinterpret_cast<float4*>(s + head);
+    float4* gv = reinterpret_cast<float4*>(g + head);
     for (int v = t; v < nv; v += nt) {
-        const int k = head + 4 * v;
-        const float4 q = make_float4(s[k], s[k + 1], s[k + 2], s[k + 3]);
-        if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f) red_add_f4(g + k, q);
-        s[k] = s[k + 1] = s[k + 2] = s[k + 3] = 0.f;
+        const float4 q = sv[v];
+        if (plain) {
+            gv[v] = q;
+        } else if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f) {
+            red_add_f4(reinterpret_cast<float*>(gv + v), q);
+        }
+        sv[v] = f4_zero();
     }
     for (int k = head + 4 * nv + t; k < w; k += nt) {
-        if (s[k] != 0.f) atomicAdd(g + k, s[k]);
+        if (plain) {
+            g[k] = s[k];
+        } else if (s[k] != 0.f) {
+            atomicAdd(g + k, s[k]);
+        }
         s[k] = 0.f;
     }
+}
+
+// Offset (0..3 floats) that gives a shared buffer the 16-byte phase of g.
+__device__ __forceinline__ int phase_of(const float* g) {
+    return (int)(((uint32_t)reinterpret_cast<uintptr_t>(g) >> 2) & 3u);
 }
 
 // A thread's 4 consecutive entries of a block (one 16-byte vector of each
@@ -180,21 +209,36 @@ __device__ __forceinline__ void band_vec4(uint4 pk, float4 av, const float* xI, 
     }
 }
 
-// One entry of a bank group (one per lane; the group's rows, and its columns,
-// are spread over the 32 banks where the block allows it).  The row part and
-// the mirrored part are each one reduction; padding contributes nothing.
-template <int MODE, bool SYPRD>
-__device__ __forceinline__ void band_one(uint32_t k, float a, const float* xI, float* yI, const float* xJ, float* yJ,
-                                         float& sp) {
-    if (k == BAND_PAD) return;  // only in a block's last group
-    const int r = (int)(k >> 16), c = (int)(k & 0xffffu);
-    const float xr = xI[r];
-    const float xc = MODE == 0 ? xI[c] : (MODE == 1 ? xJ[c] : __ldg(xJ + c));
-    const float t = a * xc;
-    atomicAdd(&yI[r], t);
-    const bool off_diag = MODE != 0 || c != r;
-    if (off_diag) atomicAdd(MODE == 0 ? &yI[c] : &yJ[c], a * xr);
-    if (SYPRD) sp = fmaf(off_diag ? 2.f * t : t, xr, sp);
+// One lane's entries of a chunk of bank groups: groups cw, cw + NC, ... (one
+// entry per lane each; the group's rows, and its columns, are spread over the
+// 32 banks where the block allows it).  MODE as for band_vec4; shared-memory
+// operands are 32-bit shared-window addresses (xI, yI: band I; xJ, yJ: band J
+// in modes 0 and 1), band J in global memory in mode 2 (gxJ, gyJ).  The row
+// part and the mirrored part are one reduction each; padding contributes nothing.
+template <int MODE, bool SYPRD, int EPL>
+__device__ __forceinline__ void band_groups(uint32_t gi, uint32_t gv, int m, int first, int stride, uint32_t xI,
+                                            uint32_t yI, uint32_t xJ, uint32_t yJ, const float* gxJ, float* gyJ,
+                                            float& sp) {
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+        const int e = first + q * stride;
+        if (e >= m) break;
+        const uint32_t k = lds_u32(gi + 4u * (uint32_t)e);
+        if (k == BAND_PAD) break;  // padding only trails a block's last group
+        const float a = lds_f32(gv + 4u * (uint32_t)e);
+        const uint32_t r4 = (k >> 16) << 2, c4 = (k & 0xffffu) << 2;
+        const float xr = lds_f32(xI + r4);
+        const float xc = MODE == 2 ? __ldg(gxJ + (c4 >> 2)) : lds_f32((MODE == 0 ? xI : xJ) + c4);
+        const float t = a * xc;
+        reds_add_f32(yI + r4, t);
+        const bool off_diag = MODE != 0 || c4 != r4;
+        if (MODE == 2) {
+            atomicAdd(gyJ + (c4 >> 2), a * xr);
+        } else if (off_diag) {
+            reds_add_f32((MODE == 0 ? yI : yJ) + c4, a * xr);
+        }
+        if (SYPRD) sp = fmaf(off_diag ? 2.f * t : t, xr, sp);
+    }
 }
 
 // (hi, lo) += v exactly (two-sum, no branch): hi + lo carries every bit of the
@@ -274,9 +318,9 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
     const int WB = W + 4;                       // staged x band with its alignment lead
     float* xIb = reinterpret_cast<float*>(band_smem);  // [2][WB]
     float* xJb = xIb + 2 * WB;                          // [2][WB]
-    float* yIb = xJb + 2 * WB;                          // [2][W]
-    float* yJb = yIb + 2 * W;                           // [2][W]
-    uint32_t* ring_i = reinterpret_cast<uint32_t*>(yJb + 2 * W);
+    float* yIb = xJb + 2 * WB;                          // [2][WB] (y band with its 16-byte phase lead)
+    float* yJb = yIb + 2 * WB;                          // [2][WB]
+    uint32_t* ring_i = reinterpret_cast<uint32_t*>(yJb + 2 * WB);
     float* ring_v = reinterpret_cast<float*>(ring_i + (size_t)S * CH);
     BandTask* tbuf = reinterpret_cast<BandTask*>(ring_v + (size_t)S * CH);  // [2][TASKS_PER_BUF]
     ChunkMeta* meta = reinterpret_cast<ChunkMeta*>(tbuf + 2 * TASKS_PER_BUF);
@@ -288,7 +332,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
     uint64_t* xJ_empty = xJ_full + 2;
     uint64_t* t_full = xJ_empty + 2;
     const int t_begin = cta_ptr[blockIdx.x], t_end = cta_ptr[blockIdx.x + 1];
-    for (int k = tid; k < 4 * W; k += blockDim.x) yIb[k] = 0.f;  // y_I and y_J buffers start at zero
+    for (int k = tid; k < 4 * WB; k += blockDim.x) yIb[k] = 0.f;  // y_I and y_J buffers start at zero
     if (tid == 0) {
         for (int k = 0; k < S; ++k) {
             mbar_init(&full[k], 1);
@@ -427,29 +471,24 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
             ++scnt;
         }
         const float* xI = xIb + bI * WB + cm.leadI;
-        float* yI = yIb + bI * W;
+        float* yI = yIb + bI * WB + phase_of(y + cm.base + (int64_t)cm.I * W);
         const uint4* vi = reinterpret_cast<const uint4*>(ring_i + (size_t)slot * CH);
         const float4* vv = reinterpret_cast<const float4*>(ring_v + (size_t)slot * CH);
+        float* yJ1 = yJb + bJ * WB + phase_of(y + cm.base + (int64_t)cm.J * W);  // staged y_J (mode 1)
         float sp = 0.f;
         if (cm.flags & TASK_GROUPED) {
             // groups of 32 entries: warp cw takes groups cw, cw + NC, ...; one entry per lane
-            const uint32_t* gi = ring_i + (size_t)slot * CH;
-            const float* gv = ring_v + (size_t)slot * CH;
-#pragma unroll
-            for (int q = 0; q < EPL; ++q) {
-                const int e = (q * NC + cw) * BAND_GROUP + lane;
-                if (e < cm.m) {
-                    const uint32_t kk = gi[e];
-                    const float a = gv[e];
-                    if (mode == 0) {
-                        band_one<0, SYPRD>(kk, a, xI, yI, xI, yI, sp);
-                    } else if (mode == 1) {
-                        band_one<1, SYPRD>(kk, a, xI, yI, xJb + bJ * WB + cm.leadJ, yJb + bJ * W, sp);
-                    } else {
-                        const int64_t off = cm.base + (int64_t)cm.J * W;
-                        band_one<2, SYPRD>(kk, a, xI, yI, x + off, y + off, sp);
-                    }
-                }
+            const uint32_t gi = smem_u32(ring_i + (size_t)slot * CH), gv = smem_u32(ring_v + (size_t)slot * CH);
+            const int first = cw * BAND_GROUP + lane, stride = NC * BAND_GROUP;
+            const uint32_t sxI = smem_u32(xI), syI = smem_u32(yI);
+            if (mode == 0) {
+                band_groups<0, SYPRD, EPL>(gi, gv, cm.m, first, stride, sxI, syI, sxI, syI, nullptr, nullptr, sp);
+            } else if (mode == 1) {
+                band_groups<1, SYPRD, EPL>(gi, gv, cm.m, first, stride, sxI, syI,
+                                           smem_u32(xJb + bJ * WB + cm.leadJ), smem_u32(yJ1), nullptr, nullptr, sp);
+            } else {
+                const int64_t off = cm.base + (int64_t)cm.J * W;
+                band_groups<2, SYPRD, EPL>(gi, gv, cm.m, first, stride, sxI, syI, 0u, 0u, x + off, y + off, sp);
             }
         } else
 #pragma unroll
@@ -461,7 +500,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
                 if (mode == 0) {
                     band_vec4<0, SYPRD>(pk, av, xI, yI, xI, yI, sp);
                 } else if (mode == 1) {
-                    band_vec4<1, SYPRD>(pk, av, xI, yI, xJb + bJ * WB + cm.leadJ, yJb + bJ * W, sp);
+                    band_vec4<1, SYPRD>(pk, av, xI, yI, xJb + bJ * WB + cm.leadJ, yJ1, sp);
                 } else {
                     const int64_t off = cm.base + (int64_t)cm.J * W;
                     band_vec4<2, SYPRD>(pk, av, xI, yI, x + off, y + off, sp);
@@ -477,7 +516,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
                 if (cm.flags & TASK_LAST) mbar_arrive(&xI_empty[bI]);
             }
             consumer_sync(nct);  // every update of this block is in y_I / y_J
-            if (mode == 1) band_flush(y + cm.base + (int64_t)cm.J * W, yJb + bJ * W, cm.wJ, false, ct, nct);
+            if (mode == 1) band_flush(y + cm.base + (int64_t)cm.J * W, yJ1, cm.wJ, false, ct, nct);
             if (cm.flags & TASK_LAST) {
                 band_flush(y + cm.base + (int64_t)cm.I * W, yI, cm.wI, (cm.flags & TASK_SINGLE) != 0, ct, nct);
                 if (SYPRD) {
@@ -816,7 +855,7 @@ size_t band_smem(const sym_tile_cfg* cfg, int* stages) {
     // x_I, x_J double buffers (W + 4 floats each), y_I, y_J double buffers,
     // two task buffers, the x / task barriers; then per ring slot the chunk,
     // its ChunkMeta and its two barriers
-    const int64_t fixed = 4LL * (8LL * cfg->band_rows + 16) + 2LL * TASKS_PER_BUF * (int64_t)sizeof(BandTask) + 10 * 8;
+    const int64_t fixed = 4LL * (8LL * cfg->band_rows + 32) + 2LL * TASKS_PER_BUF * (int64_t)sizeof(BandTask) + 10 * 8;
     const int64_t chunk = 32LL * epl * (cfg->threads_per_cta / 32 - 1);  // entries
     const int64_t per_stage = chunk * 8 + (int64_t)sizeof(ChunkMeta) + 16;
     const int64_t st = std::min<int64_t>(16, (budget - fixed) / per_stage);
