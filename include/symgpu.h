@@ -196,8 +196,9 @@ typedef struct {
                                  each band of y is reduced into global memory once per block, with
                                  16-byte vector reductions.  One producer warp streams the entries with
                                  bulk asynchronous copies (cp.async.bulk + mbarrier) several chunks ahead
-                                 and stages the x bands; the other warps consume.  threads_per_cta
-                                 (64..1024: one producer warp + consumer warps) and ctas_per_sm (1 or 2)
+                                 and stages the x bands, one warp reduces the finished y bands into
+                                 global memory, the other warps consume.  threads_per_cta (96..1024: one
+                                 producer warp + one flusher warp + consumer warps) and ctas_per_sm (1 or 2)
                                  shape the banded kernel; the band buffers (32 * band_rows bytes) and at
                                  least two chunks must fit in one CTA's shared memory (SYM_E_INVALID
                                  otherwise: band_rows up to ~5,600 on GB300).  Instances with

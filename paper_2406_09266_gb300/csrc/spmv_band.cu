@@ -115,11 +115,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Barrier among the consumer warps only (the producer warp never joins it).
-__device__ __forceinline__ void consumer_sync(int nthreads) {
-    asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
-}
-
 // ---------------------------------------------------------------- device helpers
 
 // g[0..w) += s[0..w) (or = when `plain`), then s[0..w) = 0.  s is placed in
@@ -295,12 +290,14 @@ __device__ __forceinline__ void fetch_tasks(BandTask* buf, const BandTask* tasks
 
 // Warp-specialised persistent kernel.  Warp 0 (one lane) is the producer: it
 // walks the CTA's task list, stages x of band I / J into double buffers and
-// streams the entries into a ring of `S` chunk slots.  Warps 1.. consume:
+// streams the entries into a ring of `S` chunk slots.  Warps 2.. consume:
 // each takes EPL entries per lane of every chunk (bank groups, or 16-byte
-// vectors of 4 row-major entries),
-// and they meet at a named barrier only at the end of a block (to reduce y_J)
-// and of a unit (y_I, SYPRD partial).  Every wait is bounded (~2 s); on a
-// timeout the kernel records bit 0 of *err and stops.
+// vectors of 4 row-major entries) and never waits for the other consumers:
+// it releases a chunk, an x band or a y band with one mbarrier arrival.
+// Warp 1 flushes: once every consumer has released a y band it reduces the
+// band into global memory, zeroes it and hands it back (y_I with the row
+// band's SYPRD partial).  Every wait is bounded (~2 s); on a timeout the
+// kernel records bit 0 of *err and stops.
 template <bool SYPRD, int EPL>
 __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restrict__ tasks,
                                                         const int32_t* __restrict__ cta_ptr,
@@ -310,9 +307,9 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
                                                         double* __restrict__ partials, int W, int S,
                                                         unsigned* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char band_smem[];
-    __shared__ double s_red[32];
+    __shared__ double s_red[2][32];  // per y_I buffer: one SYPRD partial per consumer warp
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NC = (int)(blockDim.x >> 5) - 1;  // consumer warps
+    const int NC = (int)(blockDim.x >> 5) - 2;  // consumer warps (warp 0 produces, warp 1 flushes)
     const int NV = NC * 32;                     // 16-byte vectors per chunk per step (row-major blocks)
     const int CH = NV * EPL;                    // entries per chunk
     const int WB = W + 4;                       // staged x band with its alignment lead
@@ -331,6 +328,10 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
     uint64_t* xJ_full = xI_empty + 2;
     uint64_t* xJ_empty = xJ_full + 2;
     uint64_t* t_full = xJ_empty + 2;
+    uint64_t* yJ_done = t_full + 2;  // [2] consumers finished a block with this y_J buffer
+    uint64_t* yJ_free = yJ_done + 2; // [2] the flusher reduced and zeroed it
+    uint64_t* yI_done = yJ_free + 2; // [2] the same for y_I at the end of a row band
+    uint64_t* yI_free = yI_done + 2;
     const int t_begin = cta_ptr[blockIdx.x], t_end = cta_ptr[blockIdx.x + 1];
     for (int k = tid; k < 4 * WB; k += blockDim.x) yIb[k] = 0.f;  // y_I and y_J buffers start at zero
     if (tid == 0) {
@@ -344,6 +345,10 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
             mbar_init(&xI_empty[k], NC);
             mbar_init(&xJ_empty[k], NC);
             mbar_init(&t_full[k], 1);
+            mbar_init(&yJ_done[k], NC);
+            mbar_init(&yJ_free[k], 1);
+            mbar_init(&yI_done[k], NC);
+            mbar_init(&yI_free[k], 1);
         }
         mbar_init_fence();
     }
@@ -432,9 +437,50 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         return;
     }
 
+    if (warp == 1) {
+        // ------------------------------------------------------------ flusher
+        // Walks the same task list: when every consumer warp is done with a
+        // y band it reduces the band into global memory (16-byte vectors),
+        // zeroes it and hands it back; at a row band's end it also sums the
+        // consumer warps' SYPRD partials into the unit's FP64 slot.
+        int ucnt = 0, scnt = 0;
+        for (int t = t_begin; t < t_end; ++t) {
+            const BandTask T = tasks[t];
+            if ((T.flags >> TASK_MODE_SHIFT) == 1) {
+                const int b = scnt & 1;
+                if (!mbar_wait_bounded(&yJ_done[b], (uint32_t)((scnt >> 1) & 1))) {
+                    if (lane == 0) atomicOr(err, 1u);
+                    return;
+                }
+                float* g = y + T.base + (int64_t)T.J * W;
+                band_flush(g, yJb + b * WB + phase_of(g), T.wJ, false, lane, 32);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&yJ_free[b]);
+                ++scnt;
+            }
+            if (T.flags & TASK_LAST) {
+                const int b = ucnt & 1;
+                if (!mbar_wait_bounded(&yI_done[b], (uint32_t)((ucnt >> 1) & 1))) {
+                    if (lane == 0) atomicOr(err, 1u);
+                    return;
+                }
+                float* g = y + T.base + (int64_t)T.I * W;
+                band_flush(g, yIb + b * WB + phase_of(g), T.wI, (T.flags & TASK_SINGLE) != 0, lane, 32);
+                if (SYPRD && lane == 0) {
+                    double tot = 0.0;
+                    for (int q = 0; q < NC; ++q) tot += s_red[b][q];  // fixed order
+                    partials[T.slot] = tot;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&yI_free[b]);
+                ++ucnt;
+            }
+        }
+        return;
+    }
+
     // ---------------------------------------------------------------- consumers
-    const int ct = tid - 32, nct = NC * 32;  // consumer thread index / count
-    const int cw = warp - 1;
+    const int cw = warp - 2;
     int ucnt = 0, scnt = 0;
     int bI = 0, bJ = 0;
     float s_hi = 0.f, s_lo = 0.f;
@@ -456,7 +502,8 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         const int mode = cm.flags >> TASK_MODE_SHIFT;
         if (cm.flags & TASK_FIRST) {
             bI = ucnt & 1;
-            if (!mbar_wait_bounded(&xI_full[bI], (uint32_t)((ucnt >> 1) & 1))) {
+            if (!mbar_wait_bounded(&xI_full[bI], (uint32_t)((ucnt >> 1) & 1)) ||
+                (ucnt >= 2 && !mbar_wait_bounded(&yI_free[bI], (uint32_t)(((ucnt >> 1) - 1) & 1)))) {
                 if (lane == 0) atomicOr(err, 1u);
                 break;
             }
@@ -464,7 +511,8 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         }
         if ((cm.flags & CM_FIRST_SEG) && mode == 1) {
             bJ = scnt & 1;
-            if (!mbar_wait_bounded(&xJ_full[bJ], (uint32_t)((scnt >> 1) & 1))) {
+            if (!mbar_wait_bounded(&xJ_full[bJ], (uint32_t)((scnt >> 1) & 1)) ||
+                (scnt >= 2 && !mbar_wait_bounded(&yJ_free[bJ], (uint32_t)(((scnt >> 1) - 1) & 1)))) {
                 if (lane == 0) atomicOr(err, 1u);
                 break;
             }
@@ -511,24 +559,21 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
         if (cm.flags & CM_LAST_SEG) {
-            if (lane == 0) {
-                if (mode == 1) mbar_arrive(&xJ_empty[bJ]);
-                if (cm.flags & TASK_LAST) mbar_arrive(&xI_empty[bI]);
+            // this warp is done with the block: release x_J / y_J (and x_I / y_I at a row band's end)
+            double w = 0.0;
+            if (SYPRD && (cm.flags & TASK_LAST)) {
+                w = warp_sum((double)s_hi + (double)s_lo);
+                s_hi = s_lo = 0.f;
             }
-            consumer_sync(nct);  // every update of this block is in y_I / y_J
-            if (mode == 1) band_flush(y + cm.base + (int64_t)cm.J * W, yJ1, cm.wJ, false, ct, nct);
-            if (cm.flags & TASK_LAST) {
-                band_flush(y + cm.base + (int64_t)cm.I * W, yI, cm.wI, (cm.flags & TASK_SINGLE) != 0, ct, nct);
-                if (SYPRD) {
-                    const double w = warp_sum((double)s_hi + (double)s_lo);
-                    if (lane == 0) s_red[cw] = w;
-                    consumer_sync(nct);
-                    if (ct == 0) {
-                        double tot = 0.0;
-                        for (int q = 0; q < NC; ++q) tot += s_red[q];
-                        partials[cm.slot] = tot;
-                    }
-                    s_hi = s_lo = 0.f;
+            if (lane == 0) {
+                if (mode == 1) {
+                    mbar_arrive(&xJ_empty[bJ]);
+                    mbar_arrive(&yJ_done[bJ]);
+                }
+                if (cm.flags & TASK_LAST) {
+                    if (SYPRD) s_red[bI][cw] = w;
+                    mbar_arrive(&xI_empty[bI]);
+                    mbar_arrive(&yI_done[bI]);
                 }
             }
         }
@@ -839,7 +884,7 @@ int band_count(int64_t n, const sym_tile_cfg* cfg) {
 
 size_t band_smem(const sym_tile_cfg* cfg, int* stages) {
     *stages = 0;
-    if (!cfg || cfg->band_rows <= 0 || cfg->ctas_per_sm < 1 || cfg->threads_per_cta < 64) return 0;
+    if (!cfg || cfg->band_rows <= 0 || cfg->ctas_per_sm < 1 || cfg->threads_per_cta < 96) return 0;
     const int epl = band_epl(cfg);
     if (epl != 1 && epl != 2 && epl != 4 && epl != 8 && epl != 16) return 0;
     int optin = 0, per_sm = 0;
@@ -851,12 +896,12 @@ size_t band_smem(const sym_tile_cfg* cfg, int* stages) {
         per_sm = 233472;
     }
     const int64_t budget =
-        std::min<int64_t>(optin, per_sm / cfg->ctas_per_sm - 1024) - (int64_t)sizeof(double) * 32 - 64;
+        std::min<int64_t>(optin, per_sm / cfg->ctas_per_sm - 1024) - (int64_t)sizeof(double) * 64 - 64;
     // x_I, x_J double buffers (W + 4 floats each), y_I, y_J double buffers,
     // two task buffers, the x / task barriers; then per ring slot the chunk,
     // its ChunkMeta and its two barriers
-    const int64_t fixed = 4LL * (8LL * cfg->band_rows + 32) + 2LL * TASKS_PER_BUF * (int64_t)sizeof(BandTask) + 10 * 8;
-    const int64_t chunk = 32LL * epl * (cfg->threads_per_cta / 32 - 1);  // entries
+    const int64_t fixed = 4LL * (8LL * cfg->band_rows + 32) + 2LL * TASKS_PER_BUF * (int64_t)sizeof(BandTask) + 18 * 8;
+    const int64_t chunk = 32LL * epl * (cfg->threads_per_cta / 32 - 2);  // entries
     const int64_t per_stage = chunk * 8 + (int64_t)sizeof(ChunkMeta) + 16;
     const int64_t st = std::min<int64_t>(16, (budget - fixed) / per_stage);
     if (st < 2) return 0;

@@ -352,7 +352,7 @@ bool cfg_ok(const sym_tile_cfg* c) {
         const int bc = c->band_chunk;
         if (bc != 0 && bc != 1 && bc != 2 && bc != 4 && bc != 8 && bc != 16) return false;
         if ((bc == 1 || bc == 2) && c->band_order != 1) return false;  // row-major needs whole 16-byte vectors
-        if (c->local_smem_kb != 0 || c->ctas_per_sm > 2 || c->threads_per_cta < 64) return false;
+        if (c->local_smem_kb != 0 || c->ctas_per_sm > 2 || c->threads_per_cta < 96) return false;
         int st = 0;
         band_smem(c, &st);
         if (st < 2) return false;

@@ -29,7 +29,7 @@ def plan_bytes(sg, sizes, nnz, cfg):
 def test_gpu_test_band_shapes_are_valid(sg):
     from tests.test_gpu_batch import BAND_CFGS
     extra = [(256, 8, 256, 1, 0, 0, 0, 256, 64, 4, 0), (256, 8, 288, 1, 0, 0, 0, 4096, 64, 16, 0),
-             (256, 8, 64, 2, 0, 0, 0, 512, 64, 8, 0), (256, 8, 512, 1, 0, 0, 0, 256, 64, 8, 0),
+             (256, 8, 96, 2, 0, 0, 0, 512, 64, 8, 0), (256, 8, 512, 1, 0, 0, 0, 256, 64, 8, 0),
              (256, 8, 256, 1, 0, 0, 0, 256, 64, 4, 1), (256, 8, 288, 1, 0, 0, 0, 4096, 64, 16, 1)]
     for cfg in BAND_CFGS + extra:
         assert plan_bytes(sg, [4000, 4000], 100_000, cfg) > 0, cfg

@@ -241,7 +241,7 @@ def test_batch_band_dense_rows_and_diagonal_only():
     row_off = np.array([0, n0, total], np.int64)
     x = synth.vector_uniform(total, 4)
     for cfg in [(256, 8, 256, 1, 0, 0, 0, 256, 64, 4, 0), (256, 8, 288, 1, 0, 0, 0, 4096, 64, 16, 0),
-                (256, 8, 64, 2, 0, 0, 0, 512, 64, 8, 0), (256, 8, 256, 1, 0, 0, 0, 256, 64, 4, 1),
+                (256, 8, 96, 2, 0, 0, 0, 512, 64, 8, 0), (256, 8, 256, 1, 0, 0, 0, 256, 64, 4, 1),
                 (256, 8, 288, 1, 0, 0, 0, 4096, 64, 16, 1)]:
         outs = run_plan(sg, row_off, rowptr, cols.astype(np.int32), vals, x, cfg)
         check_against_oracle(outs, row_off, rowptr, cols.astype(np.int32), vals, x)
