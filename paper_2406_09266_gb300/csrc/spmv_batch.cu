@@ -804,6 +804,7 @@ extern "C" sym_status sym_autotune_spmv_batch(const sym_csr_batch* A, const int6
         for (int T : {800, 1024})
             for (int G : {0, 1}) try_cfg(sym_tile_cfg{256, 8, T, 1, 0, 0, 0, W, BAND_MAX_BANDS, 4, G});
     try_cfg(sym_tile_cfg{256, 8, 544, 2, 0, 0, 0, 2048, BAND_MAX_BANDS, 4, 1});
+    try_cfg(sym_tile_cfg{256, 8, 512, 2, 0, 0, 0, 2048, BAND_MAX_BANDS, 4, 1});
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!any) return SYM_E_NOMEM;
