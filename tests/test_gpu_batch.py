@@ -265,3 +265,33 @@ def test_batch_band_rejects_bad_columns():
         with pytest.raises(sg.SymError) as ei:
             sg.BatchPlan(batch, cfg)
         assert ei.value.code == code
+
+
+@pytest.mark.parametrize("cfg", [(256, 8, 512, 1, 0, 0, 0, 256, 64, 4, 1), (256, 8, 1024, 1, 0, 0, 0, 4096, 64, 4, 0)])
+def test_batch_band_tiny_empty_and_entryless(cfg):
+    """Banded path on tiny, empty and entry-less instances, and on a batch with no entries at all."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    for sizes, draws in [(np.array([1, 5, 1, 300, 2, 64, 0, 7], np.int64), np.array([0, 3, 1, 5000, 0, 700, 0, 0])),
+                         (np.array([10, 20], np.int64), np.array([0, 0]))]:
+        row_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        draw_off = np.concatenate([[0], np.cumsum(draws)]).astype(np.int64)
+        idx, val = synth.batch_coords(row_off, draw_off, 13)
+        rowptr, col, v = synth.batch_upper_csr_host(row_off, idx, val)
+        x = synth.vector_uniform(int(row_off[-1]), 13)
+        if col.size == 0:   # keep the device arrays non-empty; total_nnz = 0
+            batch = sg.BatchCSR(dev(row_off), dev(rowptr), dev(np.zeros(1, np.int32))[:0],
+                                dev(np.zeros(1, np.float32))[:0])
+        else:
+            batch = sg.BatchCSR(dev(row_off), dev(rowptr), dev(col), dev(v))
+        plan = sg.BatchPlan(batch, sg.TileCfg(*cfg))
+        y = torch.full((int(row_off[-1]),), 9.0, device="cuda")
+        s = torch.full((len(sizes),), 9.0, dtype=torch.float64, device="cuda")
+        plan.run(dev(x), y, s)
+        plan.check()
+        yr, ya, sr, sa = oracle_batch(row_off, rowptr, col, v, x)
+        assert oracle.componentwise_error(host(y), yr, ya) <= TOL_F32
+        nz = sa > 0
+        assert np.all(host(s)[~nz] == 0.0)
+        if nz.any():
+            assert np.max(np.abs(host(s)[nz] - sr[nz]) / sa[nz]) <= TOL_F32
