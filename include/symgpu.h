@@ -238,7 +238,8 @@ sym_status sym_spmv_batch_graph_launch(sym_batch_plan plan, sym_stream_t stream)
 /* Device-side status of the plan's banded kernel: SYM_E_TIMEOUT when one of
  * its bounded waits on a bulk copy gave up (the kernel then left the rest of
  * its work undone and y / syprd are incomplete), SYM_OK otherwise.  The flag is
- * sticky for the plan's lifetime.  Synchronous (reads one word). */
+ * sticky for the plan's lifetime.  Synchronises the device (the plan may have
+ * run on any stream), then reads one word. */
 sym_status sym_spmv_batch_check(sym_batch_plan plan);
 sym_status sym_spmv_batch_plan_destroy(sym_batch_plan plan);
 

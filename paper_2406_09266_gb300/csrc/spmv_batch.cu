@@ -671,6 +671,7 @@ extern "C" sym_status sym_spmv_batch_check(sym_batch_plan P) {
     if (!P) return SYM_E_INVALID;
     if (!P->band.err) return SYM_OK;
     unsigned h = 0;
+    SYM_CUDA(cudaDeviceSynchronize());  // the plan may have run on any stream
     SYM_CUDA(cudaMemcpy(&h, P->band.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
     return (h & 1u) ? SYM_E_TIMEOUT : SYM_OK;
 }
