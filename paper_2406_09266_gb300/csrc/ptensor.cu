@@ -338,6 +338,81 @@ __global__ void k_pexpand(PartDesc D, const int32_t* __restrict__ idx, int64_t l
     }
 }
 
+// The same update when the output part starts at mode 0: the canonical entries
+// are sorted by c_0, so each warp takes a contiguous chunk of entries and each
+// lane group a strided, still sorted, subsequence of it; the update of row
+// c_0 is summed in registers along each run of equal c_0 and reduced once per
+// run (F_P[c_0] loaded once per run too).  The other distinct values of the
+// output part still take one reduction per entry.
+template <int N, bool BF16>
+__global__ void __launch_bounds__(256) k_pmttkrp_root(ModeArgs A, const int32_t* __restrict__ idx, int64_t ld,
+                                                      const float* __restrict__ val, int64_t nnz, int R, int GP,
+                                                      float* __restrict__ M, int64_t ldm, int64_t chunk) {
+    const int lane = threadIdx.x & 31;
+    const int col = 4 * (lane & (GP - 1));
+    const int per_warp = 32 / GP;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t start = warp * chunk, end = min(start + chunk, nnz);
+    if (start >= end || col >= R) return;
+    int32_t cur = -1;
+    float4 acc = f4_zero(), row0 = f4_zero();
+    for (int64_t e = start + lane / GP; e < end; e += per_warp) {
+        int32_t c[N];
+        float4 row[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) c[q] = idx[(int64_t)q * ld + e];
+        if (c[0] != cur) {
+            if (cur >= 0) red_add_f4(M + (int64_t)cur * ldm + col, acc);
+            cur = c[0];
+            acc = f4_zero();
+            row0 = load_row4<BF16>(A.F[0], c[0], A.ld[0], col);
+        }
+        row[0] = row0;
+#pragma unroll
+        for (int q = 1; q < N; ++q) row[q] = load_row4<BF16>(A.F[q], c[q], A.ld[q], col);
+        bool same[N];
+        int runpos[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            same[q] = q > 0 && A.pos[q] > 0 && c[q] == c[q > 0 ? q - 1 : 0];
+            runpos[q] = same[q] ? runpos[q > 0 ? q - 1 : 0] + 1 : 1;
+        }
+        float4 prod = make_float4(1.f, 1.f, 1.f, 1.f);
+        int num = 1, den = 1, denP = 1;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if (A.inP[q]) {
+                denP *= runpos[q];
+            } else {
+                prod = f4_mul(prod, row[q]);
+                num *= A.pos[q] + 1;
+                den *= runpos[q];
+            }
+        }
+        const float base = val[e] * (float)(num / den);
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if (!A.inP[q] || same[q]) continue;
+            int m = 0;
+            float4 t = prod;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                if (!A.inP[k]) continue;
+                if (c[k] == c[q]) ++m;
+                if (k != q) t = f4_mul(t, row[k]);
+            }
+            const int W = fact_small(A.s - 1) * m / denP;
+            t = f4_scale(t, base * (float)W);
+            if (q == 0) {
+                acc = make_float4(acc.x + t.x, acc.y + t.y, acc.z + t.z, acc.w + t.w);  // row c_0: summed along the run
+            } else {
+                red_add_f4(M + (int64_t)c[q] * ldm + col, t);
+            }
+        }
+    }
+    if (cur >= 0) red_add_f4(M + (int64_t)cur * ldm + col, acc);
+}
+
 __global__ void k_zero_rows(float* __restrict__ M, int64_t rows, int R, int64_t ldm) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = rows * (int64_t)R;
@@ -588,8 +663,16 @@ extern "C" sym_status sym_pmttkrp(sym_ptensor X, const void* const* factors, con
     const int64_t warps = (nnz + (32 / GP) - 1) / (32 / GP);
     const unsigned grid = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)sm_count() * 16);
     SYM_PROF("pmttkrp", s);
+    const bool root = out_part == 0;  // output part starts at mode 0: entries sorted by its first index
+    const int64_t chunk = 256;
+    const unsigned rgrid = (unsigned)(((nnz + chunk - 1) / chunk + 7) / 8);
 #define SYM_PM_CASE(NN)                                                                                         \
-    if (dtype == SYM_BF16)                                                                                      \
+    if (root && dtype == SYM_BF16)                                                                              \
+        k_pmttkrp_root<NN, true><<<rgrid, 256, 0, s>>>(A, X->idx, X->cap, X->val, nnz, rank, GP, M, ldm, chunk); \
+    else if (root)                                                                                              \
+        k_pmttkrp_root<NN, false><<<rgrid, 256, 0, s>>>(A, X->idx, X->cap, X->val, nnz, rank, GP, M, ldm,       \
+                                                        chunk);                                                 \
+    else if (dtype == SYM_BF16)                                                                                 \
         k_pmttkrp<NN, true><<<grid, 256, 0, s>>>(A, X->idx, X->cap, X->val, nnz, rank, GP, M, ldm);       \
     else                                                                                                        \
         k_pmttkrp<NN, false><<<grid, 256, 0, s>>>(A, X->idx, X->cap, X->val, nnz, rank, GP, M, ldm);

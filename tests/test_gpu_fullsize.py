@@ -105,3 +105,24 @@ def test_fullsize_batch_sampled_instances():
         sr, sa = oracle.syprd(r1 - r0, rp, cl, vl, x[r0:r1].astype(np.float64))
         assert oracle.componentwise_error(yh[r0:r1], yr, ya) <= TOL_F32, b
         assert abs(sh[b] - sr) / sa <= TOL_F32, b
+
+
+def test_fullsize_ptensor_parts22():
+    """The partially symmetric bench workload: parts (2, 2), n = 20,000 per part, 5M canonical entries, R = 32.
+    Canonical form and counts exact; every row of both parts' MTTKRP within the FP32 tolerance."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    parts, dims, rank = (2, 2), (20_000, 20_000), 32
+    T = synth.ptensor_uniform(parts, dims, 5_000_000, 4)
+    X = sg.PTensor(dev(T.idx), dev(T.val), parts, dims)
+    cidx, cval = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+    gi, gv = X.export()
+    assert np.array_equal(host(gi), cidx) and np.array_equal(host(gv), cval)
+    cnt = oracle.pcounts(parts, cidx, cval)
+    assert X.info()["expanded_nnz"] == cnt["expanded"]
+    F = [synth.factor_normal(d, rank, 4 + p) for p, d in enumerate(dims)]
+    Fd = [dev(f) for f in F]
+    for out in range(2):
+        M = host(X.mttkrp(Fd, out))
+        ref, ref_abs = oracle.pmttkrp_enum(parts, dims, cidx, cval, [f.astype(np.float64) for f in F], out)
+        assert oracle.componentwise_error(M, ref, ref_abs) <= TOL_F32, out
