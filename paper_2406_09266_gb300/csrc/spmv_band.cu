@@ -365,6 +365,8 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
             fetch_tasks(tbuf + b * TASKS_PER_BUF, tasks, t_begin + b * TASKS_PER_BUF,
                         min(TASKS_PER_BUF, ntask - b * TASKS_PER_BUF), &t_full[b]);
         int64_t k = 0;  // chunks issued
+        int pslot = 0;        // ring slot of chunk k (k % S)
+        uint32_t pphase = 0;  // (k / S) & 1
         int ucnt = 0, scnt = 0;
         int leadI = 0;
         bool ok = true;
@@ -392,8 +394,8 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
                 ++scnt;
             }
             for (int o = 0; o < T.cnt; o += CH, ++k) {
-                const int slot = (int)(k % S);
-                if (k >= S && !(ok = mbar_wait_bounded(&empty[slot], (uint32_t)(((k / S) - 1) & 1)))) break;
+                const int slot = pslot;
+                if (k >= S && !(ok = mbar_wait_bounded(&empty[slot], pphase ^ 1u))) break;  // previous use drained
                 const int m = min(CH, T.cnt - o);
                 ChunkMeta& cm = meta[slot];
                 cm.base = T.base;
@@ -412,11 +414,15 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
                 mbar_expect_tx(&full[slot], 2u * bytes);
                 bulk_g2s(ring_i + (size_t)slot * CH, eidx + T.start + o, bytes, &full[slot]);
                 bulk_g2s(ring_v + (size_t)slot * CH, evals + T.start + o, bytes, &full[slot]);
+                if (++pslot == S) {
+                    pslot = 0;
+                    pphase ^= 1u;
+                }
             }
         }
         if (ok) {
-            const int slot = (int)(k % S);
-            if (k < S || (ok = mbar_wait_bounded(&empty[slot], (uint32_t)(((k / S) - 1) & 1)))) {
+            const int slot = pslot;
+            if (k < S || (ok = mbar_wait_bounded(&empty[slot], pphase ^ 1u))) {
                 meta[slot].flags = CM_END;
                 mbar_arrive(&full[slot]);
                 ++k;
@@ -484,9 +490,10 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
     int ucnt = 0, scnt = 0;
     int bI = 0, bJ = 0;
     float s_hi = 0.f, s_lo = 0.f;
-    for (int64_t k = 0;; ++k) {
-        const int slot = (int)(k % S);
-        if (!mbar_wait_bounded(&full[slot], (uint32_t)((k / S) & 1))) {
+    int slot = 0;         // ring slot of the next chunk
+    uint32_t phase = 0;   // its phase parity
+    for (;;) {
+        if (!mbar_wait_bounded(&full[slot], phase)) {
             if (lane == 0) atomicOr(err, 1u);
             break;
         }
@@ -576,6 +583,10 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
                     mbar_arrive(&yI_done[bI]);
                 }
             }
+        }
+        if (++slot == S) {
+            slot = 0;
+            phase ^= 1u;
         }
     }
 }
