@@ -56,6 +56,12 @@ struct PCounters {
     double normsq;
 };
 
+// a / b for small integers when b divides a (arrangement counts): the
+// correctly rounded reciprocal times a is within a few ulps of the integer
+// quotient, so rounding to the nearest integer gives it exactly, without the
+// integer-division routine a run-time divisor needs.
+__device__ __forceinline__ float exact_quot(int a, int b) { return rintf((float)a * __frcp_rn((float)b)); }
+
 __host__ __device__ __forceinline__ int fact_small(int k) {
     const int f[6] = {1, 1, 2, 6, 24, 120};
     return f[k];
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(256) k_pmttkrp(ModeArgs A, const int32_t* __re
                 den *= runpos[q];
             }
         }
-        const float base = val[e] * (float)(num / den);
+        const float base = val[e] * exact_quot(num, den);
         // one update per distinct value u of part P, at the first mode of its run
 #pragma unroll
         for (int q = 0; q < N; ++q) {
@@ -274,8 +280,8 @@ __global__ void __launch_bounds__(256) k_pmttkrp(ModeArgs A, const int32_t* __re
                 if (c[k] == c[q]) ++m;
                 if (k != q) t = f4_mul(t, row[k]);
             }
-            const int W = fact_small(A.s - 1) * m / denP;
-            red_add_f4(M + (int64_t)c[q] * ldm + col, f4_scale(t, base * (float)W));
+            const float W = exact_quot(fact_small(A.s - 1) * m, denP);
+            red_add_f4(M + (int64_t)c[q] * ldm + col, f4_scale(t, base * W));
         }
     }
 }
@@ -389,7 +395,7 @@ __global__ void __launch_bounds__(256) k_pmttkrp_root(ModeArgs A, const int32_t*
                 den *= runpos[q];
             }
         }
-        const float base = val[e] * (float)(num / den);
+        const float base = val[e] * exact_quot(num, den);
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             if (!A.inP[q] || same[q]) continue;
@@ -401,8 +407,8 @@ __global__ void __launch_bounds__(256) k_pmttkrp_root(ModeArgs A, const int32_t*
                 if (c[k] == c[q]) ++m;
                 if (k != q) t = f4_mul(t, row[k]);
             }
-            const int W = fact_small(A.s - 1) * m / denP;
-            t = f4_scale(t, base * (float)W);
+            const float W = exact_quot(fact_small(A.s - 1) * m, denP);
+            t = f4_scale(t, base * W);
             if (q == 0) {
                 acc = make_float4(acc.x + t.x, acc.y + t.y, acc.z + t.z, acc.w + t.w);  // row c_0: summed along the run
             } else {
