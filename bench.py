@@ -482,24 +482,7 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
             r["expanded_error"] = str(e)
         rows[name] = r
         X.close()
-    # SSYMV + SYPRD, n = 2000, 20k upper nonzeros (launch-latency bound)
-    A = synth.upper_csr_uniform(2000, 20000, 0)
-    x = synth.vector_uniform(2000, 0)
-    t_ = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    rp, cl, vl, xd = t_(A.rowptr), t_(A.col), t_(A.val), t_(x)
-    y = torch.empty(2000, dtype=torch.float32, device=dev)
-    ws = sg.spmv_workspace(2000, rp, cl, vl)
-    for _ in range(5):
-        sg.spmv(2000, rp, cl, vl, xd, y=y, syprd=True, ws=ws)
-    t = timed_steps(torch, lambda: sg.spmv(2000, rp, cl, vl, xd, y=y, syprd=True, ws=ws), 50, flush, stream)
-    ms = float(np.mean(t))
-    rows["ssymv_n2000_nnz20k"] = {"ms": ms, "canonical_nnz_per_s": A.nnz / (ms * 1e-3)}
-    dd = torch.abs(xd)
-    yb = torch.empty_like(dd)
-    for _ in range(5):
-        sg.bellman_step(2000, rp, cl, vl, dd, y=yb)
-    t = timed_steps(torch, lambda: sg.bellman_step(2000, rp, cl, vl, dd, y=yb), 50, flush, stream)
-    rows["ssymv_n2000_nnz20k"]["bellman_ford_step_ms"] = float(np.mean(t))
+    rows["ssymv_n2000_nnz20k"] = small_ssymv_row(torch, sg, dev, flush, stream)
     try:
         rows["ssymv_bellman_n2M_16perrow"] = large_ssymv_row(torch, sg, dev, flush, stream, hbm_peak)
     except Exception as e:
@@ -513,6 +496,47 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
     except Exception as e:
         rows["pmttkrp_parts22_n20k_nnz5M_r32"] = {"error": repr(e)}
     return rows
+
+
+def small_ssymv_row(torch, sg, dev, flush, stream, n=2000, nnz=20000, seed=0, K=50):
+    """SSYMV + SYPRD on the 2,000 x 2,000, 1 % dense matrix: launch-latency bound.
+    `ms`: each call between its own events (L2 flushed before each); `graph_ms`:
+    the same call captured once in a CUDA graph and replayed (no host work
+    inside the timed window)."""
+    A = synth.upper_csr_uniform(n, nnz, seed)
+    x = synth.vector_uniform(n, seed)
+    t_ = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rp, cl, vl, xd = t_(A.rowptr), t_(A.col), t_(A.val), t_(x)
+    y = torch.empty(n, dtype=torch.float32, device=dev)
+    ws = sg.spmv_workspace(n, rp, cl, vl)
+    for _ in range(5):
+        sg.spmv(n, rp, cl, vl, xd, y=y, syprd=True, ws=ws)
+    t = timed_steps(torch, lambda: sg.spmv(n, rp, cl, vl, xd, y=y, syprd=True, ws=ws), K, flush, stream)
+    ms = float(np.mean(t))
+    row = {"ms": ms, "p50_ms": float(np.median(t)), "canonical_nnz_per_s": A.nnz / (ms * 1e-3),
+           "path": "cluster_1launch" if sg.spmv_single_launch(n, A.nnz) else "multi_block"}
+    s_out = torch.empty(1, dtype=torch.float64, device=dev)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        sg.spmv_noalloc(n, rp, cl, vl, xd, y, s_out, stream=side)
+    side.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        sg.spmv_noalloc(n, rp, cl, vl, xd, y, s_out, stream=side)
+    for _ in range(5):
+        g.replay()
+    torch.cuda.synchronize()
+    t = timed_steps(torch, g.replay, K, flush, stream)
+    row["graph_ms"] = float(np.mean(t))
+    row["graph_p50_ms"] = float(np.median(t))
+    dd = torch.abs(xd)
+    yb = torch.empty_like(dd)
+    for _ in range(5):
+        sg.bellman_step(n, rp, cl, vl, dd, y=yb)
+    t = timed_steps(torch, lambda: sg.bellman_step(n, rp, cl, vl, dd, y=yb), K, flush, stream)
+    row["bellman_ford_step_ms"] = float(np.mean(t))
+    return row
 
 
 def ptensor_row(torch, sg, dev, flush, stream, hbm_peak, parts=(2, 2), dims=(20_000, 20_000), nnz=5_000_000,
@@ -862,6 +886,18 @@ def run_ptensor_only(args):
     print(json.dumps({"mode": "ptensor-only", "pmttkrp_parts22_n20k_nnz5M_r32": out}))
 
 
+def run_small_only(args):
+    import torch
+
+    import paper_2406_09266_gb300 as sg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sg.load()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = small_ssymv_row(torch, sg, dev, flush, torch.cuda.current_stream(), K=args.steps)
+    print(json.dumps({"mode": "small-only", "ssymv_n2000_nnz20k": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -877,6 +913,8 @@ def main():
                     help="profiling mode: the symmetric TTM kernels on the TTM row's tensor, nothing else")
     ap.add_argument("--ptensor-only", action="store_true",
                     help="profiling mode: the partially symmetric MTTKRP row alone")
+    ap.add_argument("--small-only", action="store_true",
+                    help="profiling mode: the 2,000 x 2,000 SSYMV + SYPRD row alone")
     ap.add_argument("--batch-only", type=int, default=0, metavar="INSTANCES",
                     help="profiling mode: build a batch of this many instances and run the batched SSYMV a few times")
     ap.add_argument("--batch-cfg", default="", metavar="FIELDS",
@@ -892,6 +930,8 @@ def main():
         run_ttm_only(args)
     elif args.ptensor_only:
         run_ptensor_only(args)
+    elif args.small_only:
+        run_small_only(args)
     else:
         run_ours(args)
 

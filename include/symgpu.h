@@ -112,9 +112,22 @@ size_t sym_spmv_workspace_bytes(const sym_csr_upper* A);
  * off-diagonal terms weighted 2 (invisible output symmetry, Sec. 3.2.2), per-
  * block partials formed in FP32 and the cross-block sum in FP64.  x, y: n
  * floats [device], 16-byte aligned not required.  ws may be NULL when syprd is
- * NULL.  The CSR is trusted (use sym_csr_upper_check to validate). */
+ * NULL.  The CSR is trusted (use sym_csr_upper_check to validate).
+ * Matrices with n <= 8192 whose x, a partial y, rowptr, 1/8 of the entries
+ * and the exchange inbox fit in 160 KiB of shared memory per CTA run as one
+ * launch of one 8-CTA thread-block cluster (a partial y per CTA in shared
+ * memory, exchanged by bulk copies between the CTAs and summed in a fixed
+ * order; FP32 SYPRD partials per warp, FP64 across warps and CTAs; column
+ * indices outside [0, n) are skipped; if the exchange does not complete within
+ * about 2 s, y and SYPRD are set to NaN); larger ones as a memset, the SSYMV
+ * kernel and the FP64 finaliser. */
 sym_status sym_spmv(const sym_csr_upper* A, const float* x, float* y, double* syprd, void* ws,
                     size_t ws_bytes, sym_stream_t stream);
+
+/* 1 when sym_spmv / sym_spmv_noalloc run A as the one-launch cluster form, 0
+ * otherwise (also for an invalid descriptor).  Host-only: reads the descriptor
+ * fields n and nnz, touches no device memory. */
+int sym_spmv_single_launch(const sym_csr_upper* A);
 
 /* Allocation-free variant of sym_spmv (the paper has no counterpart: it is a
  * service to callers that cannot allocate).  For callers that cannot hand the

@@ -136,6 +136,7 @@ _SIGS = {
     "sym_spmv_workspace_bytes": ([C.c_void_p], C.c_size_t),
     "sym_spmv": ([C.c_void_p] * 5 + [C.c_size_t, C.c_void_p], C.c_int),
     "sym_spmv_noalloc": ([C.c_void_p] * 5, C.c_int),
+    "sym_spmv_single_launch": ([C.c_void_p], C.c_int),
     "sym_csr_upper_check": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_bellman_step": ([C.c_void_p] * 4, C.c_int),
     "sym_csr_expand_bytes": ([C.c_void_p, C.c_void_p], C.c_size_t),
@@ -305,6 +306,12 @@ def spmv(n, rowptr, col, val, x, y=None, syprd=False, ws=None, stream=None):
     check(lib().sym_spmv(C.byref(A), _ptr(x), _ptr(y), _ptr(s_out), _ptr(ws), ws.numel() if ws is not None else 0,
                          _stream(stream)), "sym_spmv")
     return (y, s_out) if syprd else y
+
+
+def spmv_single_launch(n, nnz) -> bool:
+    """True when sym_spmv runs an n x n upper CSR with nnz entries as the one-launch cluster form (host-only)."""
+    A = CsrUpper(int(n), int(nnz), 1, 1, 1)
+    return bool(lib().sym_spmv_single_launch(C.byref(A)))
 
 
 def spmv_noalloc(n, rowptr, col, val, x, y, syprd_out=None, stream=None):

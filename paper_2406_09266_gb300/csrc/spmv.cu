@@ -290,11 +290,12 @@ void layout_full(C& c, int64_t n, int64_t full_nnz, int32_t** rp, int32_t** col,
 
 sym_status ssymv_launch(const sym_csr_upper* A, const float* x, float* y, double* syprd, double* partials,
                         cudaStream_t s) {
-    SYM_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)A->n, s));
     if (A->n == 0) {
         if (syprd) SYM_CUDA(cudaMemsetAsync(syprd, 0, sizeof(double), s));
         return SYM_OK;
     }
+    if (ssymv_single_launch(A)) return ssymv_cluster_launch(A, x, y, syprd, s);
+    SYM_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)A->n, s));
     switch (spmv_lanes(A->n, A->nnz)) {
         case 2: return launch_ssymv_l<2>(A, x, y, syprd, partials, s);
         case 4: return launch_ssymv_l<4>(A, x, y, syprd, partials, s);

@@ -55,6 +55,34 @@ def test_host_side_calls_without_gpu(libpath):
     assert L.sym_mttkrp(None, None, 0, 64, 64, None, 64, None, None, 0, None) == -1
 
 
+def test_spmv_path_choice(libpath):
+    """The one-launch cluster form is chosen on the host from n and nnz alone:
+    n <= 8192 and x, a partial y, rowptr, 1/8 of the entries and the exchange
+    inbox within 160 KiB."""
+    import paper_2406_09266_gb300 as sg
+    sg.load(libpath)
+
+    def smem(n, nnz):
+        r4 = lambda v: (v + 3) // 4 * 4
+        S = r4((n + 7) // 8)
+        return 4 * (r4(n) + 8 * S + r4(n + 1) + 2 * r4((nnz + 7) // 8) + 7 * S + 32 + 32 + 4)
+
+    assert sg.spmv_single_launch(2000, 20000)
+    assert sg.spmv_single_launch(1, 0) and sg.spmv_single_launch(1, 1)
+    assert not sg.spmv_single_launch(0, 0)
+    assert not sg.spmv_single_launch(8193, 10)
+    assert not sg.spmv_single_launch(5000, 160000)
+    for n in (1, 64, 257, 2000, 4096, 8192):
+        lo, hi = 0, 1 << 22
+        while lo < hi:  # largest nnz the library accepts
+            mid = (lo + hi + 1) // 2
+            if sg.spmv_single_launch(n, mid):
+                lo = mid
+            else:
+                hi = mid - 1
+        assert 0 < lo and smem(n, lo) <= 160 * 1024 < smem(n, lo + 1), (n, lo)
+
+
 def test_missing_library_fails_loudly(tmp_path):
     import paper_2406_09266_gb300 as sg
     with pytest.raises(RuntimeError):
