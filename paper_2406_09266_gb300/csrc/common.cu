@@ -23,6 +23,24 @@ int current_device() {
     return d;
 }
 
+sym_status raise_smem_limit(const void* func, size_t bytes) {
+    if (bytes <= 48 * 1024) return SYM_OK;  // within the default limit of every kernel
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void*, int>, size_t>> raised;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& r : raised)
+        if (r.first.first == func && r.first.second == dev) {
+            if (r.second >= bytes) return SYM_OK;
+            SYM_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+            r.second = bytes;
+            return SYM_OK;
+        }
+    SYM_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    raised.push_back({{func, dev}, bytes});
+    return SYM_OK;
+}
+
 int sm_count() {
     static int cached[64] = {0};
     int d = current_device();

@@ -21,6 +21,12 @@ sym_status cuda_status(cudaError_t e);
 
 #define SYM_CHECK_LAUNCH() SYM_CUDA(cudaGetLastError())
 
+#define SYM_TRY(call)                          \
+    do {                                       \
+        sym_status _st = (call);               \
+        if (_st != SYM_OK) return _st;         \
+    } while (0)
+
 inline cudaStream_t as_stream(sym_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -50,6 +56,14 @@ struct Sizer {
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 int sm_count();
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` and never lowers it, so that launches of one kernel with
+// different sizes from several host threads cannot undercut one another.
+sym_status raise_smem_limit(const void* func, size_t bytes);
+template <typename K>
+inline sym_status raise_smem_limit(K* kernel, size_t bytes) {
+    return raise_smem_limit(reinterpret_cast<const void*>(kernel), bytes);
+}
 int current_device();
 
 // Records an event pair around a kernel launch when profiling is enabled.

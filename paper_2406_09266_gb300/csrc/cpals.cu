@@ -229,7 +229,7 @@ extern "C" sym_status sym_cp_als_step(sym_tensor X, const void* B, sym_dtype bdt
     st = gram_launch(X->n, B, bf16, rank, ldb, w.G, s);
     if (st != SYM_OK) return st;
     const size_t lsmem = sizeof(double) * (size_t)rank * rank;
-    SYM_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+    SYM_TRY(raise_smem_limit(k_cholesky, lsmem));
     {
         SYM_PROF("cp_als_cholesky", s);
         k_cholesky<<<1, 1024, lsmem, s>>>(w.G, rank, X->order - 1, ridge, w.L, w.LT, w.dinv, w.fail, info);
@@ -237,7 +237,7 @@ extern "C" sym_status sym_cp_als_step(sym_tensor X, const void* B, sym_dtype bdt
     }
     {
         const size_t ismem = lsmem + sizeof(double) * INV_WARPS * (size_t)rank;  // <= 136 KB at rank 128
-        SYM_CUDA(cudaFuncSetAttribute(k_inverse_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+        SYM_TRY(raise_smem_limit(k_inverse_columns, ismem));
         SYM_PROF("cp_als_inverse", s);
         k_inverse_columns<<<(rank + INV_WARPS - 1) / INV_WARPS, INV_WARPS * 32, ismem, s>>>(w.L, w.LT, w.dinv, rank,
                                                                                           w.fail, w.Hinv);
@@ -249,10 +249,10 @@ extern "C" sym_status sym_cp_als_step(sym_tensor X, const void* B, sym_dtype bdt
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * 4, (work + 255) / 256));
     SYM_PROF("cp_als_apply", s);
     if (bf16) {
-        SYM_CUDA(cudaFuncSetAttribute(k_apply_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem));
+        SYM_TRY(raise_smem_limit(k_apply_inverse<true>, asmem));
         k_apply_inverse<true><<<grid, 256, asmem, s>>>(w.M, X->n, rank, w.Hinv, B_out, ldo);
     } else {
-        SYM_CUDA(cudaFuncSetAttribute(k_apply_inverse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem));
+        SYM_TRY(raise_smem_limit(k_apply_inverse<false>, asmem));
         k_apply_inverse<false><<<grid, 256, asmem, s>>>(w.M, X->n, rank, w.Hinv, B_out, ldo);
     }
     SYM_CHECK_LAUNCH();

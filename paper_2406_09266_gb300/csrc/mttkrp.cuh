@@ -747,8 +747,7 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
         } else if (cfg.strict_kernel == SYM_MTTKRP_PIPELINED) {
             const SinkPlan sp = plan_sink(X->n, R, cfg.strict_smem_kb, cfg.b_share_pct);
             if (sp.bytes > 48 * 1024)
-                SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_strict_pipe<N, KW, L, BF16>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.bytes));
+                SYM_TRY(raise_smem_limit(k_mttkrp_strict_pipe<N, KW, L, BF16>, sp.bytes));
             unsigned grid;
             if (cfg.entries_per_warp > 0) {
                 const int64_t warps = (ns + cfg.entries_per_warp - 1) / cfg.entries_per_warp;
@@ -768,8 +767,7 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             while (st_threads > 64 && per_warp * (st_threads / 32) > 96 * 1024) st_threads /= 2;
             const size_t smem = per_warp * (st_threads / 32);
             if (smem > 48 * 1024)
-                SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_strict_staged<N, KW, L, BF16>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                SYM_TRY(raise_smem_limit(k_mttkrp_strict_staged<N, KW, L, BF16>, smem));
             const int64_t warps = (ns + chunk - 1) / chunk;
             const unsigned grid = (unsigned)((warps * 32 + st_threads - 1) / st_threads);
             SYM_PROF("mttkrp_strict", s);
@@ -790,8 +788,7 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
         const uint64_t* dhi = X->khi ? X->khi + ns : nullptr;
         const SinkPlan sp = plan_sink(X->n, R, cfg.diag_smem_kb, cfg.b_share_pct);
         if (sp.bytes > 48 * 1024)
-            SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_entries<N, KW, L, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sp.bytes));
+            SYM_TRY(raise_smem_limit(k_mttkrp_entries<N, KW, L, BF16>, sp.bytes));
         const int dthreads = sp.bytes > 0 ? 512 : 256;
         const int64_t gpc = (dthreads / 32) * (32 / L);
         const int64_t cap = sp.bytes > 0 ? (int64_t)sms * (sp.bytes > 100 * 1024 ? 1 : 2) : (int64_t)sms * 16;

@@ -865,8 +865,7 @@ struct SizerCarver {
 
 template <bool SYPRD, int EPL>
 sym_status launch_band_v(const BandPlan& P, const float* x, float* y, double* partials, cudaStream_t s) {
-    SYM_CUDA(cudaFuncSetAttribute(k_ssymv_band<SYPRD, EPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)P.smem));
+    SYM_TRY(raise_smem_limit(k_ssymv_band<SYPRD, EPL>, P.smem));
     k_ssymv_band<SYPRD, EPL><<<P.grid, P.threads, P.smem, s>>>(P.tasks, P.cta_ptr, P.eidx, P.evals, x, P.x_rows, y,
                                                                 partials, P.W, P.stages, P.err);
     SYM_CHECK_LAUNCH();

@@ -372,14 +372,12 @@ sym_status batch_enqueue_local(sym_batch_plan_s* P, const float* x, float* y, do
 #define SYM_LOCAL_L(LL)                                                                                          \
     case LL:                                                                                                     \
         if (syprd) {                                                                                             \
-            SYM_CUDA(cudaFuncSetAttribute(k_ssymv_batch_local<LL, true>,                                         \
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
+            SYM_TRY(raise_smem_limit(k_ssymv_batch_local<LL, true>, smem));                                      \
             k_ssymv_batch_local<LL, true><<<grid, threads, smem, s>>>(P->local_order, P->n_local, P->A.row_off, \
                                                                       P->A.rowptr, P->A.col, P->A.val, x, y,   \
                                                                       syprd, P->local_counter, P->local_cap);  \
         } else {                                                                                                 \
-            SYM_CUDA(cudaFuncSetAttribute(k_ssymv_batch_local<LL, false>,                                        \
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
+            SYM_TRY(raise_smem_limit(k_ssymv_batch_local<LL, false>, smem));                                     \
             k_ssymv_batch_local<LL, false><<<grid, threads, smem, s>>>(P->local_order, P->n_local,              \
                                                                        P->A.row_off, P->A.rowptr, P->A.col,    \
                                                                        P->A.val, x, y, syprd,                  \
@@ -410,14 +408,12 @@ sym_status batch_enqueue_tiles(sym_batch_plan_s* P, const float* x, float* y, do
 #define SYM_XS_L(LL)                                                                                              \
     case LL:                                                                                                      \
         if (syprd) {                                                                                              \
-            SYM_CUDA(cudaFuncSetAttribute(k_ssymv_batch_xs<LL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                          (int)smem));                                                            \
+            SYM_TRY(raise_smem_limit(k_ssymv_batch_xs<LL, true>, smem));                                          \
             k_ssymv_batch_xs<LL, true><<<grid, threads, smem, s>>>(P->tiles, P->ntiles, P->A.row_off, P->A.rowptr, \
                                                                    P->A.col, P->A.val, x, y, P->tile_partials,    \
                                                                    P->counter, S);                                 \
         } else {                                                                                                  \
-            SYM_CUDA(cudaFuncSetAttribute(k_ssymv_batch_xs<LL, false>,                                            \
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));              \
+            SYM_TRY(raise_smem_limit(k_ssymv_batch_xs<LL, false>, smem));                                         \
             k_ssymv_batch_xs<LL, false><<<grid, threads, smem, s>>>(P->tiles, P->ntiles, P->A.row_off,            \
                                                                     P->A.rowptr, P->A.col, P->A.val, x, y,        \
                                                                     P->tile_partials, P->counter, S);             \

@@ -298,13 +298,11 @@ sym_status launch_cluster(const sym_csr_upper* A, const ClusterShape& sh, const 
                           cudaStream_t s) {
     SYM_PROF("ssymv_cluster", s);
     if (syprd) {
-        SYM_CUDA(cudaFuncSetAttribute(k_ssymv_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sh.smem));
+        SYM_TRY(raise_smem_limit(k_ssymv_cluster<true>, sh.smem));
         k_ssymv_cluster<true><<<CL_CTAS, CL_THREADS, sh.smem, s>>>(
             (int)A->n, (int)A->nnz, sh.per, sh.slice, sh.xw, sh.rw, A->rowptr, A->col, A->val, x, y, syprd);
     } else {
-        SYM_CUDA(cudaFuncSetAttribute(k_ssymv_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sh.smem));
+        SYM_TRY(raise_smem_limit(k_ssymv_cluster<false>, sh.smem));
         k_ssymv_cluster<false><<<CL_CTAS, CL_THREADS, sh.smem, s>>>(
             (int)A->n, (int)A->nnz, sh.per, sh.slice, sh.xw, sh.rw, A->rowptr, A->col, A->val, x, y, syprd);
     }

@@ -128,3 +128,36 @@ def test_cluster_form_syprd_is_deterministic_and_graph_capturable():
     assert float(s_out.item()) == first
     e_y, e_s = errors(sg, A, x, y, s_out)
     assert e_y <= TOL_F32 and e_s <= TOL_F32, (e_y, e_s)
+
+
+def test_cluster_form_from_several_host_threads():
+    """Calls with different shared-memory sizes from several host threads, each on its own stream:
+    the kernel's shared-memory limit is only ever raised, so no launch is undercut by another."""
+    import threading
+    sg = need_gpu()
+    cases = [(300, 3000, 21), (2000, 20000, 22), (6000, 60000, 23), (8000, 30000, 24)]
+    data = []
+    for n, nnz, seed in cases:
+        assert sg.spmv_single_launch(n, nnz)
+        A = synth.upper_csr_uniform(n, nnz, seed)
+        x = synth.vector_uniform(n, seed)
+        yr, ya = oracle.ssymv(n, A.rowptr, A.col, A.val, x.astype(np.float64))
+        data.append((n, dev(A.rowptr), dev(A.col), dev(A.val), dev(x), yr, ya))
+    errs = [[] for _ in cases]
+
+    def work(k):
+        n, rp, cl, vl, xd, yr, ya = data[k]
+        st = torch.cuda.Stream()
+        y = torch.empty(n, dtype=torch.float32, device="cuda")
+        for _ in range(20):
+            sg.spmv(n, rp, cl, vl, xd, y=y, stream=st)
+            st.synchronize()
+            errs[k].append(oracle.componentwise_error(host(y), yr, ya))
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(len(cases))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for k in range(len(cases)):
+        assert len(errs[k]) == 20 and max(errs[k]) <= TOL_F32, (cases[k], errs[k][:3])
