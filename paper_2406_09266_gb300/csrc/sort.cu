@@ -182,6 +182,89 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     }
 }
 
+// Stable scatter of 64-bit keys through shared memory: the same ranks as
+// k_radix_scatter place the tile in digit order in shared memory first, then
+// consecutive threads write consecutive output positions of each digit's run
+// (coalesced stores instead of one scattered 8-byte store per item).
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint64_t* __restrict__ klo,
+                                                                     const uint32_t* __restrict__ pay,
+                                                                     uint64_t* __restrict__ olo,
+                                                                     uint32_t* __restrict__ opay, int64_t n, int shift,
+                                                                     const uint32_t* __restrict__ offsets,
+                                                                     int64_t ntiles) {
+    static_assert(RS_THREADS == RADIX, "one thread per digit in the tile scan");
+    __shared__ uint32_t cnt[RS_WARPS][RADIX];
+    __shared__ uint32_t gbase[RADIX];  // output position of the digit's run in this tile, minus its start in the tile
+    __shared__ uint32_t wsum[RS_WARPS];
+    __shared__ uint64_t s_lo[RS_TILE];
+    __shared__ uint32_t s_pl[RS_TILE];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < RS_WARPS * RADIX; t += RS_THREADS) (&cnt[0][0])[t] = 0;
+    __syncthreads();
+    const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t wbase = tbase + (int64_t)w * (32 * RS_ROUNDS);
+    uint64_t lo[RS_ROUNDS];
+    uint32_t pl[RS_ROUNDS];
+    unsigned dg[RS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t i = wbase + r * 32 + lane;
+        if (i < n) {
+            lo[r] = klo[i];
+            pl[r] = pay[i];
+            dg[r] = (unsigned)((lo[r] >> shift) & (RADIX - 1));
+            atomicAdd(&cnt[w][dg[r]], 1u);
+        } else {
+            dg[r] = 0xffffu;  // sentinel group, never placed
+        }
+    }
+    __syncthreads();
+    // Thread d: the digit's count in the tile, its start in the tile (exclusive
+    // scan over digits), and the per-warp starts within its run.
+    {
+        const int d = threadIdx.x;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) tot += cnt[ww][d];
+        const uint32_t incl = warp_incl_scan(tot);
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        uint32_t start = incl - tot;
+        for (int k = 0; k < w; ++k) start += wsum[k];
+        gbase[d] = offsets[(int64_t)d * ntiles + blockIdx.x] - start;
+        uint32_t run = start;
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) {
+            const uint32_t c = cnt[ww][d];
+            cnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned ltmask = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+        const unsigned rank = __popc(peers & ltmask);
+        if (dg[r] != 0xffffu) {
+            const uint32_t p = cnt[w][dg[r]] + rank;
+            s_lo[p] = lo[r];
+            s_pl[p] = pl[r];
+        }
+        __syncwarp();
+        if (dg[r] != 0xffffu && rank == 0) cnt[w][dg[r]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int m = n - tbase < RS_TILE ? (int)(n - tbase) : RS_TILE;
+    for (int j = threadIdx.x; j < m; j += RS_THREADS) {
+        const uint64_t k = s_lo[j];
+        const uint32_t pos = gbase[(unsigned)((k >> shift) & (RADIX - 1))] + (uint32_t)j;
+        olo[pos] = k;
+        opay[pos] = s_pl[j];
+    }
+}
+
 }  // namespace
 
 size_t scan_ws_bytes(int64_t n) {
@@ -236,8 +319,8 @@ sym_status radix_sort_pairs(int kw, uint64_t* klo, uint64_t* khi, uint32_t* pay,
             k_radix_scatter<2><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(a_lo, a_hi, a_p, b_lo, b_hi, b_p, n, shift,
                                                                       offs, ntiles);
         } else {
-            k_radix_scatter<1><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(a_lo, a_hi, a_p, b_lo, b_hi, b_p, n, shift,
-                                                                      offs, ntiles);
+            k_radix_scatter_staged<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(a_lo, a_p, b_lo, b_p, n, shift, offs,
+                                                                         ntiles);
         }
         SYM_CHECK_LAUNCH();
         uint64_t* t = a_lo; a_lo = b_lo; b_lo = t;
