@@ -101,70 +101,78 @@ __global__ void __launch_bounds__(CT) k_mark(const uint64_t* __restrict__ klo, c
                                              const uint32_t* __restrict__ pay, const float* __restrict__ val,
                                              int64_t nnz, int bits, int policy, uint32_t* __restrict__ flag_s,
                                              uint32_t* __restrict__ flag_d, DevCounters* cnt) {
+    // Grid-stride over the sorted entries; every warp keeps its counts in
+    // registers and the CTA sends them to the global counters once, so the
+    // same-address global atomics scale with the grid, not with nnz.
+    constexpr int NP = 1 << (N - 1);
     __shared__ unsigned long long s_pat[16];
-    __shared__ unsigned long long s_misc[6];  // expanded, root, l2, strict, kept, dups
-    __shared__ unsigned long long s_mis;
+    __shared__ unsigned long long s_misc[7];  // expanded, root, l2, strict, kept, dups, mismatches
     __shared__ double s_norm[CT / 32];
     if (threadIdx.x < 16) s_pat[threadIdx.x] = 0;
-    if (threadIdx.x < 6) s_misc[threadIdx.x] = 0;
-    if (threadIdx.x == 0) s_mis = 0;
+    if (threadIdx.x < 7) s_misc[threadIdx.x] = 0;
     __syncthreads();
-    int64_t p = (int64_t)blockIdx.x * CT + threadIdx.x;
-    double nrm = 0.0;
-    bool dup = false, mismatch = false, keep = false, new_root = false, new_l2 = false;
-    int pat = -1;
-    unsigned ex = 0;
-    if (p < nnz) {
-        KeyWords k{klo[p], KW == 2 ? khi[p] : 0ull};
-        int32_t c[N], pc[N];
-        unpack_key<N, KW>(k, bits, c);
-        if (p > 0) {
-            KeyWords kp{klo[p - 1], KW == 2 ? khi[p - 1] : 0ull};
-            dup = (kp.lo == k.lo) && (kp.hi == k.hi);
-            unpack_key<N, KW>(kp, bits, pc);
-            if (dup && policy == SYM_DUP_KEEP_EQUAL)
-                mismatch = __float_as_uint(val[pay[p]]) != __float_as_uint(val[pay[p - 1]]);
-        }
-        keep = !dup;
-        pat = 0;
-#pragma unroll
-        for (int q = 0; q + 1 < N; ++q) pat |= (c[q] == c[q + 1]) ? (1 << q) : 0;
-        flag_s[p] = (keep && pat == 0) ? 1u : 0u;
-        flag_d[p] = (keep && pat != 0) ? 1u : 0u;
-        if (keep) {
-            ex = (unsigned)distinct_perms<N>(c);
-            new_root = (p == 0 || pc[0] != c[0]);
-            new_l2 = (p == 0 || pc[0] != c[0] || pc[1] != c[1]);
-            double v = (double)val[pay[p]];
-            nrm = (double)ex * v * v;
-        }
-    }
-    // warp-aggregated counts, one shared-memory update per warp and counter
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const unsigned ex_sum = __reduce_add_sync(full, ex);
-    const int n_root = __popc(__ballot_sync(full, new_root));
-    const int n_l2 = __popc(__ballot_sync(full, new_l2));
-    const int n_strict = __popc(__ballot_sync(full, keep && pat == 0));
-    const int n_keep = __popc(__ballot_sync(full, keep));
-    const int n_dup = __popc(__ballot_sync(full, dup));
-    const int n_mis = __popc(__ballot_sync(full, mismatch));
+    unsigned long long w_ex = 0, w_root = 0, w_l2 = 0, w_strict = 0, w_keep = 0, w_dup = 0, w_mis = 0;
+    unsigned long long w_pat[NP];
 #pragma unroll
-    for (int q = 0; q < (1 << (N - 1)); ++q) {
-        const int cq = __popc(__ballot_sync(full, keep && pat == q));
-        if (lane == 0 && cq) atomicAdd(&s_pat[q], (unsigned long long)cq);
+    for (int q = 0; q < NP; ++q) w_pat[q] = 0;
+    double nrm = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * CT;
+    for (int64_t base = (int64_t)blockIdx.x * CT + (threadIdx.x & ~31); base < nnz; base += stride) {
+        const int64_t p = base + lane;  // the loop bound is per warp: the ballots below see every lane
+        bool dup = false, mismatch = false, keep = false, new_root = false, new_l2 = false;
+        int pat = -1;
+        unsigned ex = 0;
+        if (p < nnz) {
+            KeyWords k{klo[p], KW == 2 ? khi[p] : 0ull};
+            int32_t c[N], pc[N];
+            unpack_key<N, KW>(k, bits, c);
+            if (p > 0) {
+                KeyWords kp{klo[p - 1], KW == 2 ? khi[p - 1] : 0ull};
+                dup = (kp.lo == k.lo) && (kp.hi == k.hi);
+                unpack_key<N, KW>(kp, bits, pc);
+                if (dup && policy == SYM_DUP_KEEP_EQUAL)
+                    mismatch = __float_as_uint(val[pay[p]]) != __float_as_uint(val[pay[p - 1]]);
+            }
+            keep = !dup;
+            pat = 0;
+#pragma unroll
+            for (int q = 0; q + 1 < N; ++q) pat |= (c[q] == c[q + 1]) ? (1 << q) : 0;
+            flag_s[p] = (keep && pat == 0) ? 1u : 0u;
+            flag_d[p] = (keep && pat != 0) ? 1u : 0u;
+            if (keep) {
+                ex = (unsigned)distinct_perms<N>(c);
+                new_root = (p == 0 || pc[0] != c[0]);
+                new_l2 = (p == 0 || pc[0] != c[0] || pc[1] != c[1]);
+                const double v = (double)val[pay[p]];
+                nrm += (double)ex * v * v;
+            }
+        }
+        w_ex += __reduce_add_sync(full, ex);
+        w_root += __popc(__ballot_sync(full, new_root));
+        w_l2 += __popc(__ballot_sync(full, new_l2));
+        w_strict += __popc(__ballot_sync(full, keep && pat == 0));
+        w_keep += __popc(__ballot_sync(full, keep));
+        w_dup += __popc(__ballot_sync(full, dup));
+        w_mis += __popc(__ballot_sync(full, mismatch));
+#pragma unroll
+        for (int q = 0; q < NP; ++q) w_pat[q] += __popc(__ballot_sync(full, keep && pat == q));
     }
     if (lane == 0) {
-        if (ex_sum) atomicAdd(&s_misc[0], (unsigned long long)ex_sum);
-        if (n_root) atomicAdd(&s_misc[1], (unsigned long long)n_root);
-        if (n_l2) atomicAdd(&s_misc[2], (unsigned long long)n_l2);
-        if (n_strict) atomicAdd(&s_misc[3], (unsigned long long)n_strict);
-        if (n_keep) atomicAdd(&s_misc[4], (unsigned long long)n_keep);
-        if (n_dup) atomicAdd(&s_misc[5], (unsigned long long)n_dup);
-        if (n_mis) atomicAdd(&s_mis, (unsigned long long)n_mis);
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            if (w_pat[q]) atomicAdd(&s_pat[q], w_pat[q]);
+        if (w_ex) atomicAdd(&s_misc[0], w_ex);
+        if (w_root) atomicAdd(&s_misc[1], w_root);
+        if (w_l2) atomicAdd(&s_misc[2], w_l2);
+        if (w_strict) atomicAdd(&s_misc[3], w_strict);
+        if (w_keep) atomicAdd(&s_misc[4], w_keep);
+        if (w_dup) atomicAdd(&s_misc[5], w_dup);
+        if (w_mis) atomicAdd(&s_misc[6], w_mis);
     }
     nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) s_norm[threadIdx.x >> 5] = nrm;
+    if (lane == 0) s_norm[threadIdx.x >> 5] = nrm;
     __syncthreads();
     if (threadIdx.x < 16 && s_pat[threadIdx.x]) atomicAdd(&cnt->by_pattern[threadIdx.x], s_pat[threadIdx.x]);
     if (threadIdx.x == 16) {
@@ -174,7 +182,7 @@ __global__ void __launch_bounds__(CT) k_mark(const uint64_t* __restrict__ klo, c
         atomicAdd(&cnt->nnz_strict, s_misc[3]);
         atomicAdd(&cnt->nnz_kept, s_misc[4]);
         atomicAdd(&cnt->dup_seen, s_misc[5]);
-        atomicAdd(&cnt->dup_mismatch, s_mis);
+        atomicAdd(&cnt->dup_mismatch, s_misc[6]);
     }
     if (threadIdx.x == 32) {
         double t = 0.0;
@@ -400,10 +408,11 @@ sym_status launch_create_kernels(int kw, const int32_t* idx, int64_t ld, const f
     uint32_t* sp;
     sym_status st = radix_sort_pairs(kw, lo0, hi0, p0, lo1, hi1, p1, nnz, N * bits, radix, s, &slo, &shi, &sp);
     if (st != SYM_OK) return st;
+    const unsigned gm = (unsigned)std::min<int64_t>((int64_t)g, (int64_t)sm_count() * 8);
     if (kw == 1)
-        k_mark<N, 1><<<g, CT, 0, s>>>(slo, shi, sp, val, nnz, bits, policy, fs, fd, cnt);
+        k_mark<N, 1><<<gm, CT, 0, s>>>(slo, shi, sp, val, nnz, bits, policy, fs, fd, cnt);
     else
-        k_mark<N, 2><<<g, CT, 0, s>>>(slo, shi, sp, val, nnz, bits, policy, fs, fd, cnt);
+        k_mark<N, 2><<<gm, CT, 0, s>>>(slo, shi, sp, val, nnz, bits, policy, fs, fd, cnt);
     SYM_CHECK_LAUNCH();
     st = exclusive_scan_u32(fs, ps, nnz, scan, s);
     if (st != SYM_OK) return st;
