@@ -35,8 +35,10 @@ namespace {
 constexpr int CL_CTAS = 8;
 constexpr int CL_THREADS = 512;
 constexpr int CL_WARPS = CL_THREADS / 32;
+// Size limits of the one-launch form (set, not tuned: the crossover with the
+// multi-block form has not been measured).
 constexpr int CL_MAX_N = 8192;
-constexpr size_t CL_SMEM_CAP = 160 * 1024;  // beyond this the multi-block form is faster
+constexpr size_t CL_SMEM_CAP = 160 * 1024;
 
 struct ClusterShape {
     int slice = 0;  // rows of y each CTA owns (multiple of 4)
