@@ -87,6 +87,37 @@ sym_status sym_profile_enable(int on);
 int sym_profile_read(sym_profile_entry* out, int max_entries);
 sym_status sym_profile_reset(void);
 
+/* Measured ceilings of the operations the kernels are made of (no paper
+ * counterpart: the denominators of the roofline fractions the benchmarks
+ * report).  Each kind times one kernel of the primitive operation alone:
+ *   SYM_CEIL_FMA         FP32 fused multiply-add issue; *rate in FLOP/s.
+ *   SYM_CEIL_ROW_GATHER  random rows of `rank` floats read from a table of
+ *                        `rows` rows (L2-resident when it fits); rows/s.
+ *   SYM_CEIL_ROW_RED     random rows reduced with 16-byte vector `red`; rows/s.
+ *   SYM_CEIL_GATHER_RED  one random gather and one random reduction; entries/s.
+ *   SYM_CEIL_SMEM_F32    a row added with float atomics into a shared-memory
+ *                        table of `rows` rows (rows * rank * 4 <= 200 KiB); rows/s.
+ *   SYM_CEIL_SMEM_U32    the same with 32-bit integer atomics; rows/s.
+ *   SYM_CEIL_HBM_COPY    streaming copy of `rows` 16-byte elements; bytes/s
+ *                        (read + write).
+ * `ops` row operations (FMA: about ops / 2^11 FLOP per thread) per launch,
+ * `reps` timed launches after one warm-up.  buf [device, 256-byte aligned,
+ * >= sym_ceiling_bytes] is scratch, overwritten.  Synchronous; *ms = mean time
+ * of one launch.  Row kinds need rank in 4..128 with rank / 4 a power of two. */
+typedef enum {
+    SYM_CEIL_FMA = 0,
+    SYM_CEIL_ROW_GATHER = 1,
+    SYM_CEIL_ROW_RED = 2,
+    SYM_CEIL_GATHER_RED = 3,
+    SYM_CEIL_SMEM_F32 = 4,
+    SYM_CEIL_SMEM_U32 = 5,
+    SYM_CEIL_HBM_COPY = 6
+} sym_ceiling_kind;
+/* Bytes of scratch for sym_ceiling_run (0 = invalid arguments). */
+size_t sym_ceiling_bytes(int kind, int64_t rows, int rank);
+sym_status sym_ceiling_run(int kind, void* buf, size_t buf_bytes, int64_t rows, int rank, int64_t ops, int reps,
+                           sym_stream_t stream, double* rate, float* ms);
+
 /* ===================================================================== */
 /* SSYMV / SYPRD over an upper-triangle CSR (Sec. 3.1 figure "spmv_code",  */
 /* Sec. 5.2.1 SSYMV y[i] = A[i,j] x[j], Sec. 5.2.3 SYPRD y = x[i]A[i,j]x[j]) */
@@ -124,10 +155,33 @@ size_t sym_spmv_workspace_bytes(const sym_csr_upper* A);
 sym_status sym_spmv(const sym_csr_upper* A, const float* x, float* y, double* syprd, void* ws,
                     size_t ws_bytes, sym_stream_t stream);
 
+/* Row partition of SSYMV / SYPRD (the natural shard of the product over
+ * several devices: row ranges, then one sum of y and of SYPRD; Sec. 3.1 with
+ * the rows split).  Adds the contribution of the stored entries of rows
+ * [row_begin, row_end) -- y[i] += a x[j] and, for j > i, y[j] += a x[i] -- into
+ * y (accumulate = 1) or into zeros (accumulate = 0; all n entries of y are
+ * cleared first).  syprd [device, nullable] receives those rows' share of
+ * x^T A x, sum_i x[i] (2 sum_{j>i} a_ij x[j] + a_ii x[i]), FP32 per block and
+ * FP64 across blocks.  Summing y and syprd over any partition of [0, n) into row
+ * ranges gives sym_spmv's results (up to rounding).  Always the multi-block
+ * form.  ws [device] >= sym_spmv_workspace_bytes(A) when syprd is given. */
+sym_status sym_spmv_rows(const sym_csr_upper* A, const float* x, float* y, double* syprd, int64_t row_begin,
+                         int64_t row_end, int accumulate, void* ws, size_t ws_bytes, sym_stream_t stream);
+
 /* 1 when sym_spmv / sym_spmv_noalloc run A as the one-launch cluster form, 0
  * otherwise (also for an invalid descriptor).  Host-only: reads the descriptor
  * fields n and nnz, touches no device memory. */
 int sym_spmv_single_launch(const sym_csr_upper* A);
+
+/* Test hook of the one-launch form's bounded inbox wait (no paper
+ * counterpart): runs A as the cluster form with the wait limited to
+ * wait_limit_ns (<= 0: the normal 2 s); for skip_to in 0..7 no CTA pushes its
+ * partial y (or its SYPRD partial) into CTA skip_to's inbox, so that CTA's
+ * wait runs out with no copy in flight towards it and it writes NaN to its
+ * rows of y (CTA 0 also to syprd); the other rows are exact.  skip_to = -1: a
+ * normal run.  SYM_E_UNSUPPORTED when A does not take the one-launch form. */
+sym_status sym_spmv_cluster_bounded(const sym_csr_upper* A, const float* x, float* y, double* syprd,
+                                    int64_t wait_limit_ns, int skip_to, sym_stream_t stream);
 
 /* Allocation-free variant of sym_spmv (the paper has no counterpart: it is a
  * service to callers that cannot allocate).  For callers that cannot hand the
@@ -136,11 +190,14 @@ int sym_spmv_single_launch(const sym_csr_upper* A);
  * must not call cudaMalloc because it can synchronise the device.  It computes
  * exactly what sym_spmv computes; the per-block FP64 SYPRD partials live in a
  * 256 KiB array compiled into the library, which every GPU that loads the
- * library keeps until the process exits.  Limit: n <= 262,144 rows, otherwise
- * SYM_E_UNSUPPORTED (use sym_spmv with a workspace).  The first call on a
- * device looks up the array's device address (make it before any stream
- * capture).  Calls share the array, so calls whose work overlaps on the GPU
- * race and must be serialised by the caller.  Allocates nothing. */
+ * library keeps until the process exits.  Limit, for calls with syprd only:
+ * at most 32,768 partial slots (sym_spmv_workspace_bytes(A) <= 256 KiB; always
+ * true for n <= 262,144 rows), otherwise SYM_E_UNSUPPORTED (use sym_spmv with a
+ * workspace); calls without syprd have no size limit.  The first call with
+ * syprd on a device looks up the array's device address (make it before any
+ * stream capture); the address is kept, so do not call this again on a device
+ * after cudaDeviceReset.  Calls share the array, so calls whose work overlaps
+ * on the GPU race and must be serialised by the caller.  Allocates nothing. */
 sym_status sym_spmv_noalloc(const sym_csr_upper* A, const float* x, float* y, double* syprd, sym_stream_t stream);
 
 /* Validates an upper CSR on the device; *bad [device, 1 int64] receives the
@@ -254,6 +311,18 @@ sym_status sym_spmv_batch_graph_launch(sym_batch_plan plan, sym_stream_t stream)
  * sticky for the plan's lifetime.  Synchronises the device (the plan may have
  * run on any stream), then reads one word. */
 sym_status sym_spmv_batch_check(sym_batch_plan plan);
+/* Clears the plan's device status word (enqueued on `stream`). */
+sym_status sym_spmv_batch_clear_status(sym_batch_plan plan, sym_stream_t stream);
+/* Test hook of the bounded waits (no paper counterpart): sym_spmv_batch_run
+ * with every bounded wait of the banded kernel limited to wait_limit_ns (<= 0:
+ * the normal 2 s) and, for skip_chunk >= 0, chunk `skip_chunk` of the first
+ * CTA's entry stream withheld (never announced, never copied), so that the
+ * consumers' wait on it runs out without any copy left in flight.  The kernel
+ * then sets bit 0 of the status word (sym_spmv_batch_check reports
+ * SYM_E_TIMEOUT), leaves the rest of its work undone and returns; y and syprd
+ * are incomplete.  The plan itself is not changed. */
+sym_status sym_spmv_batch_run_bounded(sym_batch_plan plan, const float* x, float* y, double* syprd,
+                                      int64_t wait_limit_ns, int64_t skip_chunk, sym_stream_t stream);
 sym_status sym_spmv_batch_plan_destroy(sym_batch_plan plan);
 
 /* Autotuner: times candidate sym_tile_cfg shapes on this batch (each as a
@@ -375,6 +444,18 @@ size_t sym_mttkrp_workspace_bytes(sym_tensor X, int rank, sym_dtype bdt, int wan
 sym_status sym_mttkrp(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
                       int64_t ldm, double* residual, void* ws, size_t ws_bytes, sym_stream_t stream);
 
+/* Entry partition of the MTTKRP (the natural shard over several devices:
+ * contiguous ranges of canonical entries with the factor replicated, then one
+ * sum of the partial outputs).  Adds the contribution of canonical entries
+ * [first, first + count) -- in the order sym_tensor_export writes them: the
+ * strict stream, then the diagonal stream -- into M (accumulate = 1) or into
+ * zeros (accumulate = 0).  Summing M over any partition of [0, nnz) gives
+ * sym_mttkrp's M (up to rounding).  Uses the tensor's kernel configuration but
+ * always walks the canonical stream (a leaf index covers the whole tensor and is
+ * not used for a part).  Arguments as for sym_mttkrp. */
+sym_status sym_mttkrp_range(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
+                            int64_t ldm, int64_t first, int64_t count, int accumulate, sym_stream_t stream);
+
 /* Kernel configuration of one tensor's MTTKRP calls (all variants compute the
  * same result; they differ in speed).  The autotuner below picks one. */
 typedef enum {
@@ -382,21 +463,30 @@ typedef enum {
     SYM_MTTKRP_PIPELINED = 1,    /* the same with the next leaf gather issued early; chunked or persistent;
                                     optional shared-memory hot rows */
     SYM_MTTKRP_UNFACTORISED = 2, /* one entry per lane group, every position updated separately */
-    SYM_MTTKRP_STAGED = 3        /* the plain kernel with the next batch's leaf factor rows copied into a
+    SYM_MTTKRP_STAGED = 3,       /* the plain kernel with the next batch's leaf factor rows copied into a
                                     shared-memory double buffer (cp.async) while the current batch runs */
+    SYM_MTTKRP_HOT = 4           /* persistent CTAs, chunks taken from a per-CTA counter, rows [0, H) of M
+                                    accumulated and rows [0, HB) of B read in shared memory, several leaf
+                                    gathers in flight; with leaf_index = 1 and a leaf index, two passes with no
+                                    per-entry reduction: the canonical stream for every position but the leaf,
+                                    then the leaf index for its root (the largest index of each tuple) */
 } sym_mttkrp_kernel;
 typedef struct {
     int32_t strict_kernel;     /* sym_mttkrp_kernel for the strict stream */
     int32_t entries_per_warp;  /* work chunk per warp, a multiple of 32; 0 = persistent contiguous slices
                                   (pipelined kernel only) */
-    int32_t threads_per_cta;   /* pipelined / unfactorised / staged kernels: 64..512 */
+    int32_t threads_per_cta;   /* pipelined / unfactorised / staged kernels: 64..512; hot kernel: 64..1024 */
     int32_t ctas_per_sm;       /* persistent grids: CTAs per SM */
-    int32_t strict_smem_kb;    /* pipelined kernel: shared memory per CTA for hot (low-index) rows, 0 = none */
+    int32_t strict_smem_kb;    /* pipelined / hot kernels: shared memory per CTA for hot (low-index) rows,
+                                  0 = none */
     int32_t diag_smem_kb;      /* diagonal stream: the same, 0 = none */
     int32_t b_share_pct;       /* share of that shared memory holding rows of B (the rest holds rows of M) */
     int32_t leaf_index;        /* plain kernel: 1 = take the leaf position from the tensor's leaf index (see
-                                  sym_tensor_add_leaf_index) instead of one reduction per entry */
-    int32_t vec_per_lane;      /* plain kernel: float4 column groups per lane, 1 or 2 (2 needs rank >= 8) */
+                                  sym_tensor_add_leaf_index) instead of one reduction per entry; hot kernel:
+                                  1 = walk the leaf index instead of the canonical stream (ignored without one) */
+    int32_t vec_per_lane;      /* plain kernel: float4 column groups per lane, 1 or 2 (2 needs rank >= 8);
+                                  hot kernel: leaf gathers issued together per lane group, 1 or 4 (4 needs
+                                  rank >= 16) */
     int32_t stream_hint;       /* plain kernel: 1 = read the canonical stream with evict-first loads so it does not
                                   displace factor rows from L1 / L2 */
     int32_t l1_pref;           /* plain kernel: 1 = ask for the largest L1 (no shared-memory carveout) */
@@ -552,6 +642,23 @@ sym_status sym_pmttkrp(sym_ptensor X, const void* const* factors, const int64_t*
 sym_status sym_ptensor_expand_bytes(sym_ptensor X, size_t* arena_bytes, size_t* ws_bytes);
 sym_status sym_ptensor_expand(sym_ptensor X, void* arena, size_t arena_bytes, void* ws, size_t ws_bytes,
                               sym_stream_t stream, sym_ptensor* out);
+/* Mode-1 TTM of a partially symmetric order-3 tensor (Sec. 2.1, Def.
+ * "Partial Symmetry", with the TTM of Sec. 4.2 and Sec. 5.2.5):
+ *   C[j, l, r] = sum_k A[k, j, l] B[k, r]
+ * over the full tensor, i.e. every canonical entry applied once for each of
+ * its distinct inside-part arrangements.  B [device]: dim(part of mode 1) x
+ * rank, row stride ldb, FP32 or BF16 (widened on load); rank 4..128, multiple
+ * of 4.  C [device, float32, 16-byte aligned, overwritten], rank index fastest:
+ *   SYM_TTM_FULL:   d2 x d3 positions at j d3 + l (d_q = range of mode q);
+ *   SYM_TTM_PACKED: only when modes 2 and 3 are in one part (C symmetric in
+ *                   (j, l)): positions j <= l at j d - j (j - 1) / 2 + (l - j).
+ * sym_pttm_output_elems gives the float count (-1: order other than 3, bad
+ * rank, or PACKED without the output symmetry).  Other orders:
+ * SYM_E_UNSUPPORTED.  Floating-point atomics: not bitwise reproducible. */
+int64_t sym_pttm_output_elems(sym_ptensor X, int rank, int layout);
+sym_status sym_pttm(sym_ptensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* C, int layout,
+                    sym_stream_t stream);
+
 sym_status sym_ptensor_destroy(sym_ptensor X);
 
 /* ===================================================================== */
@@ -609,7 +716,14 @@ typedef struct {
     int64_t peak_inflight, peak_bytes;
 } sym_server_stats;
 sym_status sym_server_stats_get(sym_server S, sym_server_stats* out);
-/* Drains in-flight work (bounded by cfg.wait_limit_ns) and stops the thread. */
+/* Drains queued and in-flight work (bounded by cfg.wait_limit_ns), stops the
+ * scheduler thread and frees the server.  If the limit runs out it returns
+ * SYM_E_TIMEOUT: queued requests are dropped, requests already on the device
+ * keep running, and the handle must not be used again.  The server's own
+ * streams, events and pinned buffers are then released by its scheduler thread
+ * once the last in-flight request completes; the caller must keep the arena,
+ * the tensors and every buffer of the in-flight requests alive until the device
+ * has finished them (for instance until cudaDeviceSynchronize returns). */
 sym_status sym_server_destroy(sym_server S);
 
 #if defined(__GNUC__)

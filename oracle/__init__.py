@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (portable flags; no FMA contraction)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -57,6 +57,8 @@ def lib():
                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
             L.orc_mttkrp_enum.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, f64p,
                                           f64p, u8p]
+            L.orc_mttkrp_enum_threads.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, f64p,
+                                                  C.c_int]
             L.orc_mttkrp_runs.argtypes = [C.c_int, C.c_int64, C.c_int64, i32p, f32p, f64p, C.c_int, f64p]
             L.orc_check_upper_csr.argtypes = [C.c_int64, i32p, i32p]
             L.orc_ssymv_enum.argtypes = [C.c_int64, i32p, i32p, f32p, f64p, f64p, f64p]
@@ -72,6 +74,7 @@ def lib():
                                             f32p, C.POINTER(C.c_int64)]
             L.orc_pcounts.argtypes = [C.c_int, C.c_int, i32p, C.c_int64, i32p, f32p, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_double)]
+            L.orc_pttm_enum.argtypes = [C.c_int, i32p, i64p, C.c_int64, i32p, f32p, f64p, C.c_int, f64p, f64p]
             L.orc_pmttkrp_enum.argtypes = [C.c_int, C.c_int, i32p, i64p, C.c_int64, i32p, f32p, f64p, C.c_int,
                                            C.c_int, f64p, f64p]
             L.orc_pexpand.argtypes = [C.c_int, C.c_int, i32p, C.c_int64, i32p, f32p, C.c_int64, i32p, f32p,
@@ -158,6 +161,19 @@ def mttkrp_enum(order, n, cidx, cval, B, want_abs=True, rows=None):
                                _p(mask))
     _check(rc, "mttkrp_enum")
     return (M, Ma) if want_abs else M
+
+
+def mttkrp_enum_threads(order, n, cidx, cval, B, threads):
+    """The definitional MTTKRP on `threads` host threads (contiguous entry ranges, private FP64 outputs
+    summed in thread order): the multi-core timing baseline."""
+    cidx = _c(cidx, np.int32)
+    cval = _c(cval, np.float32)
+    B = _c(B, np.float64)
+    M = np.zeros((n, B.shape[1]), dtype=np.float64)
+    rc = lib().orc_mttkrp_enum_threads(order, n, cval.shape[0], _p(cidx), _p(cval), _p(B), B.shape[1], _p(M),
+                                       int(threads))
+    _check(rc, "mttkrp_enum_threads")
+    return M
 
 
 def mttkrp_runs(order, n, cidx, cval, B):
@@ -298,6 +314,24 @@ def pmttkrp_enum(parts, dims, cidx, cval, factors, out_part, want_abs=True):
     _check(lib().orc_pmttkrp_enum(order, len(part), _p(part), _p(dim), cval.shape[0], _p(cidx), _p(cval), _p(F), R,
                                   out_part, _p(M), _p(Ma)), "pmttkrp_enum")
     return (M, Ma) if want_abs else M
+
+
+def pttm_enum(parts, dims, cidx, cval, B, want_abs=True):
+    """Definitional mode-1 TTM of a partially symmetric order-3 tensor, FP64: C (d2, d3, R) dense, with
+    C[pi_2, pi_3, :] += v B[pi_1, :] for every inside-part arrangement pi of every canonical entry."""
+    part, dim, order = _parts(parts, dims)
+    if order != 3:
+        raise ValueError("order-3 tensors only")
+    cidx = _c(cidx, np.int32)
+    cval = _c(cval, np.float32)
+    B = _c(B, np.float64)
+    R = B.shape[1]
+    dq = [int(dim[p]) for p in range(len(part)) for _ in range(int(part[p]))]
+    Cm = np.zeros((dq[1], dq[2], R), dtype=np.float64)
+    Ca = np.zeros_like(Cm) if want_abs else None
+    _check(lib().orc_pttm_enum(len(part), _p(part), _p(dim), cval.shape[0], _p(cidx), _p(cval), _p(B), R, _p(Cm),
+                               _p(Ca)), "pttm_enum")
+    return (Cm, Ca) if want_abs else Cm
 
 
 def pexpand(parts, cidx, cval):

@@ -41,6 +41,7 @@
  * Conventions: 0-based indices; coordinate arrays are (order x nnz) row-major,
  * idx[q*nnz + e]; dense factors are row-major n x R.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -234,13 +235,10 @@ int orc_counts(int order, int64_t nnz, const int32_t* cidx, const float* cval, i
  * of every canonical entry; this is the full-tensor MTTKRP restricted to its
  * nonzeros.  Mabs (nullable) receives sum |terms| per output element.
  * row_mask (nullable, length n) limits the work to selected output rows. */
-int orc_mttkrp_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval,
-                    const double* B, int R, double* M, double* Mabs, const uint8_t* row_mask) {
-    if (order < 2 || order > ORC_MAX_ORDER || R <= 0) return ORC_INVALID;
-    memset(M, 0, sizeof(double) * (size_t)n * (size_t)R);
-    if (Mabs) memset(Mabs, 0, sizeof(double) * (size_t)n * (size_t)R);
+static void mttkrp_enum_range(int order, int64_t nnz, const int32_t* cidx, const float* cval, const double* B,
+                              int R, double* M, double* Mabs, const uint8_t* row_mask, int64_t e0, int64_t e1) {
     int32_t c[ORC_MAX_ORDER];
-    for (int64_t e = 0; e < nnz; ++e) {
+    for (int64_t e = e0; e < e1; ++e) {
         load_tuple(cidx, order, nnz, e, c);
         sort_tuple(c, order);
         double v = (double)cval[e];
@@ -255,7 +253,83 @@ int orc_mttkrp_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, cons
             }
         } while (next_perm(c, order));
     }
+}
+
+int orc_mttkrp_enum(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval,
+                    const double* B, int R, double* M, double* Mabs, const uint8_t* row_mask) {
+    if (order < 2 || order > ORC_MAX_ORDER || R <= 0) return ORC_INVALID;
+    memset(M, 0, sizeof(double) * (size_t)n * (size_t)R);
+    if (Mabs) memset(Mabs, 0, sizeof(double) * (size_t)n * (size_t)R);
+    mttkrp_enum_range(order, nnz, cidx, cval, B, R, M, Mabs, row_mask, 0, nnz);
     return ORC_OK;
+}
+
+/* The same definitional MTTKRP on `threads` POSIX threads (the timing baseline
+ * on all host cores): thread t takes the contiguous entries
+ * [nnz t / T, nnz (t + 1) / T) into a private FP64 output, and the private
+ * outputs are added into M in thread order, so the result does not depend on
+ * scheduling. */
+struct enum_job {
+    int order;
+    int64_t n, nnz, e0, e1;
+    const int32_t* cidx;
+    const float* cval;
+    const double* B;
+    int R;
+    double* M;
+};
+
+static void* enum_job_run(void* arg) {
+    struct enum_job* j = (struct enum_job*)arg;
+    mttkrp_enum_range(j->order, j->nnz, j->cidx, j->cval, j->B, j->R, j->M, NULL, NULL, j->e0, j->e1);
+    return NULL;
+}
+
+int orc_mttkrp_enum_threads(int order, int64_t n, int64_t nnz, const int32_t* cidx, const float* cval,
+                            const double* B, int R, double* M, int threads) {
+    if (order < 2 || order > ORC_MAX_ORDER || R <= 0 || threads < 1 || threads > 1024) return ORC_INVALID;
+    const size_t cells = (size_t)n * (size_t)R;
+    memset(M, 0, sizeof(double) * cells);
+    struct enum_job* jobs = (struct enum_job*)calloc((size_t)threads, sizeof(struct enum_job));
+    pthread_t* tid = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+    int* started = (int*)calloc((size_t)threads, sizeof(int));
+    if (!jobs || !tid || !started) {
+        free(jobs);
+        free(tid);
+        free(started);
+        return ORC_NOMEM;
+    }
+    int rc = ORC_OK;
+    for (int t = 0; t < threads; ++t) {
+        struct enum_job* j = &jobs[t];
+        j->order = order;
+        j->n = n;
+        j->nnz = nnz;
+        j->e0 = nnz * t / threads;
+        j->e1 = nnz * (t + 1) / threads;
+        j->cidx = cidx;
+        j->cval = cval;
+        j->B = B;
+        j->R = R;
+        j->M = (double*)calloc(cells > 0 ? cells : 1, sizeof(double));
+        if (!j->M) {
+            rc = ORC_NOMEM;
+            break;
+        }
+    }
+    for (int t = 0; t < threads && rc == ORC_OK; ++t)
+        if (pthread_create(&tid[t], NULL, enum_job_run, &jobs[t]) == 0) started[t] = 1;
+        else enum_job_run(&jobs[t]);  /* no thread: run it here */
+    for (int t = 0; t < threads; ++t)
+        if (started[t]) pthread_join(tid[t], NULL);
+    if (rc == ORC_OK)
+        for (int t = 0; t < threads; ++t)
+            for (size_t k = 0; k < cells; ++k) M[k] += jobs[t].M[k];
+    for (int t = 0; t < threads; ++t) free(jobs[t].M);
+    free(jobs);
+    free(tid);
+    free(started);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -673,6 +747,45 @@ int orc_pmttkrp_enum(int order, int nparts, const int32_t* part, const int64_t* 
     }
     return ORC_OK;
 }
+
+/* Mode-1 TTM of a partially symmetric order-3 tensor (Sec. 2.1, Def.
+ * "Partial Symmetry"; the TTM of Sec. 4.2 and Sec. 5.2.5 with the contracted
+ * factor of the first mode's part):
+ *   C[j_2, j_3, r] = sum_k A[k, j_2, j_3] B[k, r]
+ * over the full tensor, i.e. for every distinct inside-part arrangement pi of
+ * every canonical entry, C[pi_2, pi_3, r] += v * B[pi_1, r].  B is
+ * dim(part of mode 1) x R; C is dense row-major d_2 x d_3 x R (d_q the range of
+ * mode q), the rank index fastest.  Cabs (nullable) receives sum |terms|. */
+int orc_pttm_enum(int nparts, const int32_t* part, const int64_t* dim, int64_t nnz, const int32_t* cidx,
+                  const float* cval, const double* B, int R, double* C, double* Cabs) {
+    const int order = 3;
+    if (!parts_valid(order, nparts, part, dim) || R <= 0) return ORC_INVALID;
+    int64_t dq[3];
+    {
+        int q = 0;
+        for (int p = 0; p < nparts; ++p)
+            for (int t = 0; t < part[p]; ++t) dq[q++] = dim[p];
+    }
+    const size_t cells = (size_t)dq[1] * (size_t)dq[2] * (size_t)R;
+    memset(C, 0, sizeof(double) * cells);
+    if (Cabs) memset(Cabs, 0, sizeof(double) * cells);
+    int32_t c[ORC_MAX_ORDER];
+    for (int64_t e = 0; e < nnz; ++e) {
+        load_tuple(cidx, order, nnz, e, c);
+        sort_within_parts(c, nparts, part);
+        const double v = (double)cval[e];
+        do {
+            const int64_t o = ((int64_t)c[1] * dq[2] + c[2]) * R;
+            for (int r = 0; r < R; ++r) {
+                const double t = v * B[(int64_t)c[0] * R + r];
+                C[o + r] += t;
+                if (Cabs) Cabs[o + r] += fabs(t);
+            }
+        } while (next_part_perm(c, order, nparts, part));
+    }
+    return ORC_OK;
+}
+
 
 /* Every arrangement of every canonical entry (permutations inside parts),
  * sorted lexicographically: the tensor with no symmetry left.  eidx is

@@ -114,7 +114,7 @@ class MttkrpCfg(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-MTTKRP_PLAIN, MTTKRP_PIPELINED, MTTKRP_UNFACTORISED = 0, 1, 2
+MTTKRP_PLAIN, MTTKRP_PIPELINED, MTTKRP_UNFACTORISED, MTTKRP_STAGED, MTTKRP_HOT = 0, 1, 2, 3, 4
 
 
 class ProfileEntry(C.Structure):
@@ -133,9 +133,14 @@ _SIGS = {
     "sym_profile_enable": ([C.c_int], C.c_int),
     "sym_profile_read": ([C.c_void_p, C.c_int], C.c_int),
     "sym_profile_reset": ([], C.c_int),
+    "sym_ceiling_bytes": ([C.c_int, C.c_int64, C.c_int], C.c_size_t),
+    "sym_ceiling_run": ([C.c_int, C.c_void_p, C.c_size_t, C.c_int64, C.c_int, C.c_int64, C.c_int, C.c_void_p,
+                         C.c_void_p, C.c_void_p], C.c_int),
     "sym_spmv_workspace_bytes": ([C.c_void_p], C.c_size_t),
     "sym_spmv": ([C.c_void_p] * 5 + [C.c_size_t, C.c_void_p], C.c_int),
     "sym_spmv_noalloc": ([C.c_void_p] * 5, C.c_int),
+    "sym_spmv_rows": ([C.c_void_p] * 4 + [C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p],
+                      C.c_int),
     "sym_spmv_single_launch": ([C.c_void_p], C.c_int),
     "sym_csr_upper_check": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_bellman_step": ([C.c_void_p] * 4, C.c_int),
@@ -150,6 +155,9 @@ _SIGS = {
     "sym_spmv_batch_capture": ([C.c_void_p] * 5, C.c_int),
     "sym_spmv_batch_graph_launch": ([C.c_void_p, C.c_void_p], C.c_int),
     "sym_spmv_batch_check": ([C.c_void_p], C.c_int),
+    "sym_spmv_batch_clear_status": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_spmv_batch_run_bounded": ([C.c_void_p] * 4 + [C.c_int64, C.c_int64, C.c_void_p], C.c_int),
+    "sym_spmv_cluster_bounded": ([C.c_void_p] * 4 + [C.c_int64, C.c_int, C.c_void_p], C.c_int),
     "sym_spmv_batch_plan_destroy": ([C.c_void_p], C.c_int),
     "sym_autotune_spmv_batch": ([C.c_void_p] * 6 + [C.c_size_t, C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p],
                                 C.c_int),
@@ -171,6 +179,8 @@ _SIGS = {
     "sym_mttkrp_workspace_bytes": ([C.c_void_p, C.c_int, C.c_int, C.c_int], C.c_size_t),
     "sym_mttkrp": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                     C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "sym_mttkrp_range": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
+                          C.c_int64, C.c_int, C.c_void_p], C.c_int),
     "sym_mttkrp_set_chunk": ([C.c_void_p, C.c_int], C.c_int),
     "sym_mttkrp_default_config": ([C.c_void_p], C.c_int),
     "sym_mttkrp_set_config": ([C.c_void_p, C.c_void_p], C.c_int),
@@ -205,6 +215,8 @@ _SIGS = {
     "sym_ptensor_expand": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p],
                            C.c_int),
     "sym_ptensor_destroy": ([C.c_void_p], C.c_int),
+    "sym_pttm_output_elems": ([C.c_void_p, C.c_int, C.c_int], C.c_int64),
+    "sym_pttm": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "sym_server_arena_bytes": ([C.c_void_p], C.c_size_t),
     "sym_server_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p], C.c_int),
     "sym_batch_submit": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -286,6 +298,23 @@ def profile_read() -> dict:
 
 # ------------------------------------------------------------------ SSYMV / SYPRD
 
+CEILINGS = {"fma": 0, "row_gather": 1, "row_red": 2, "gather_red": 3, "smem_f32": 4, "smem_u32": 5, "hbm_copy": 6}
+
+
+def ceiling(kind: str, rows: int = 0, rank: int = 64, ops: int = 1 << 26, reps: int = 10, device=None,
+            stream=None):
+    """Times one primitive operation alone (sym_ceiling_run); returns (rate, ms per launch)."""
+    k = CEILINGS[kind]
+    nbytes = lib().sym_ceiling_bytes(k, rows, rank)
+    if nbytes == 0:
+        raise SymError(-1, "sym_ceiling_bytes")
+    buf = _scratch(nbytes, device or torch.device("cuda", torch.cuda.current_device()))
+    rate, ms = C.c_double(0), C.c_float(0)
+    check(lib().sym_ceiling_run(k, _ptr(buf), nbytes, rows, rank, ops, reps, _stream(stream), C.byref(rate),
+                                C.byref(ms)), "sym_ceiling_run")
+    return rate.value, ms.value
+
+
 def csr_upper(n, rowptr, col, val) -> CsrUpper:
     return CsrUpper(int(n), int(col.numel()), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
 
@@ -306,6 +335,31 @@ def spmv(n, rowptr, col, val, x, y=None, syprd=False, ws=None, stream=None):
     check(lib().sym_spmv(C.byref(A), _ptr(x), _ptr(y), _ptr(s_out), _ptr(ws), ws.numel() if ws is not None else 0,
                          _stream(stream)), "sym_spmv")
     return (y, s_out) if syprd else y
+
+
+def spmv_rows(n, rowptr, col, val, x, row_begin, row_end, y=None, syprd=False, accumulate=False, ws=None,
+              stream=None):
+    """One row-range part of y = A x (and of x^T A x): sym_spmv_rows."""
+    A = csr_upper(n, rowptr, col, val)
+    if y is None:
+        y = torch.empty(n, dtype=torch.float32, device=x.device)
+    s_out = torch.empty(1, dtype=torch.float64, device=x.device) if syprd else None
+    if syprd and ws is None:
+        ws = _scratch(lib().sym_spmv_workspace_bytes(C.byref(A)), x.device)
+    check(lib().sym_spmv_rows(C.byref(A), _ptr(x), _ptr(y), _ptr(s_out), int(row_begin), int(row_end),
+                              int(accumulate), _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream)),
+          "sym_spmv_rows")
+    return (y, s_out) if syprd else y
+
+
+def spmv_cluster_bounded(n, rowptr, col, val, x, wait_limit_ns=0, skip_to=-1, stream=None):
+    """Test hook of the one-launch form's inbox wait (sym_spmv_cluster_bounded); returns (y, syprd)."""
+    A = csr_upper(n, rowptr, col, val)
+    y = torch.empty(n, dtype=torch.float32, device=x.device)
+    s_out = torch.empty(1, dtype=torch.float64, device=x.device)
+    check(lib().sym_spmv_cluster_bounded(C.byref(A), _ptr(x), _ptr(y), _ptr(s_out), int(wait_limit_ns), int(skip_to),
+                                         _stream(stream)), "sym_spmv_cluster_bounded")
+    return y, s_out
 
 
 def spmv_single_launch(n, nnz) -> bool:
@@ -474,6 +528,16 @@ class SymTensor:
         check(lib().sym_mttkrp(self.handle, _ptr(B), bdt, rank, B.stride(0), _ptr(M), M.stride(0), _ptr(res),
                                _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream)), "sym_mttkrp")
         return (M, res) if residual else M
+
+    def mttkrp_range(self, B: torch.Tensor, first: int, count: int, M: torch.Tensor | None = None,
+                     accumulate: bool = False, stream=None):
+        """Contribution of canonical entries [first, first + count) to the MTTKRP (sym_mttkrp_range)."""
+        rank = B.shape[1]
+        if M is None:
+            M = torch.empty((self.n, rank), dtype=torch.float32, device=B.device)
+        check(lib().sym_mttkrp_range(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(M), M.stride(0),
+                                     int(first), int(count), int(accumulate), _stream(stream)), "sym_mttkrp_range")
+        return M
 
     def upper_csr(self, stream=None):
         """Order-2 tensors: (rowptr int64, col int32, val) of the canonical entries as an upper CSR."""
@@ -720,6 +784,19 @@ class PTensor:
               "sym_pmttkrp")
         return M
 
+    def ttm(self, B, layout: str = "full", C_out=None, stream=None):
+        """Mode-1 TTM (order 3): C[j, l, :] = sum_k A[k, j, l] B[k, :]; 'packed' when modes 2, 3 share a part."""
+        rank = B.shape[1]
+        code = TTM_PACKED if layout == "packed" else TTM_FULL
+        elems = lib().sym_pttm_output_elems(self.handle, rank, code)
+        if elems < 0:
+            raise SymError(-1, "sym_pttm_output_elems")
+        if C_out is None:
+            C_out = torch.empty(elems, dtype=torch.float32, device=B.device)
+        check(lib().sym_pttm(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(C_out), code,
+                             _stream(stream)), "sym_pttm")
+        return C_out
+
     def close(self):
         if getattr(self, "handle", None):
             lib().sym_ptensor_destroy(self.handle)
@@ -776,6 +853,14 @@ class BatchPlan:
     def check(self):
         """Raises if the banded kernel gave up a bounded wait (synchronous)."""
         check(lib().sym_spmv_batch_check(self.handle), "sym_spmv_batch_check")
+
+    def clear_status(self, stream=None):
+        check(lib().sym_spmv_batch_clear_status(self.handle, _stream(stream)), "sym_spmv_batch_clear_status")
+
+    def run_bounded(self, x, y, syprd=None, wait_limit_ns=0, skip_chunk=-1, stream=None):
+        """Test hook: run with a short wait limit and optionally one chunk withheld (sym_spmv_batch_run_bounded)."""
+        check(lib().sym_spmv_batch_run_bounded(self.handle, _ptr(x), _ptr(y), _ptr(syprd), int(wait_limit_ns),
+                                               int(skip_chunk), _stream(stream)), "sym_spmv_batch_run_bounded")
 
     def close(self):
         if getattr(self, "handle", None):

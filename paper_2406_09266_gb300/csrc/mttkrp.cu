@@ -268,19 +268,40 @@ sym_status mttkrp_core(const sym_tensor_s* X, const void* B, bool bf16, int R, i
     return mttkrp_core_cfg(X, B, bf16, R, ldb, M, ldm, X->cfg, s);
 }
 
+// The tensor restricted to canonical entries [first, first + count): the
+// strict stream precedes the diagonal stream in the same arrays, so the part is
+// one contiguous slice whose first max(0, min(nnz_strict, first + count) - first)
+// entries are strict.  The leaf index describes the whole strict stream and is
+// dropped.
+sym_tensor_s tensor_part(const sym_tensor_s* X, int64_t first, int64_t count) {
+    sym_tensor_s P = *X;
+    P.klo = X->klo + first;
+    P.khi = X->khi ? X->khi + first : nullptr;
+    P.val = X->val + first;
+    P.nnz = count;
+    P.nnz_strict = std::max<int64_t>(0, std::min<int64_t>(X->nnz_strict, first + count) - first);
+    P.rklo = nullptr;
+    P.rkhi = nullptr;
+    P.rval = nullptr;
+    return P;
+}
+
 sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
     if (!c) return SYM_E_INVALID;
-    if (c->strict_kernel < 0 || c->strict_kernel > 3) return SYM_E_INVALID;
+    if (c->strict_kernel < 0 || c->strict_kernel > 4) return SYM_E_INVALID;
     if (c->entries_per_warp < 0 || c->entries_per_warp % 32 != 0 || c->entries_per_warp > (1 << 24))
         return SYM_E_INVALID;
     if (c->entries_per_warp == 0 && c->strict_kernel != SYM_MTTKRP_PIPELINED) return SYM_E_INVALID;
-    if (c->threads_per_cta < 64 || c->threads_per_cta > 512 || c->threads_per_cta % 32) return SYM_E_INVALID;
+    const int max_threads = c->strict_kernel == SYM_MTTKRP_HOT ? 1024 : 512;
+    if (c->threads_per_cta < 64 || c->threads_per_cta > max_threads || c->threads_per_cta % 32) return SYM_E_INVALID;
     if (c->ctas_per_sm < 1 || c->ctas_per_sm > 8) return SYM_E_INVALID;
     if (c->strict_smem_kb < 0 || c->strict_smem_kb > 220 || c->diag_smem_kb < 0 || c->diag_smem_kb > 220)
         return SYM_E_INVALID;
     if (c->b_share_pct < 0 || c->b_share_pct > 100) return SYM_E_INVALID;
     if (c->leaf_index != 0 && c->leaf_index != 1) return SYM_E_INVALID;
-    if (c->vec_per_lane != 1 && c->vec_per_lane != 2) return SYM_E_INVALID;
+    if (c->strict_kernel == SYM_MTTKRP_HOT ? (c->vec_per_lane != 1 && c->vec_per_lane != 4)
+                                           : (c->vec_per_lane != 1 && c->vec_per_lane != 2))
+        return SYM_E_INVALID;
     if ((c->stream_hint != 0 && c->stream_hint != 1) || (c->l1_pref != 0 && c->l1_pref != 1)) return SYM_E_INVALID;
     return SYM_OK;
 }
@@ -360,6 +381,32 @@ extern "C" sym_status sym_mttkrp(sym_tensor X, const void* B, sym_dtype bdt, int
     if (st != SYM_OK) return st;
     if (residual) return residual_launch(X, B, bf16, rank, ldb, M, ldm, residual, ws, ws_bytes, s);
     return SYM_OK;
+}
+
+extern "C" sym_status sym_mttkrp_range(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
+                                       int64_t ldm, int64_t first, int64_t count, int accumulate,
+                                       sym_stream_t stream) {
+    sym_status st = validate_mttkrp_args(X, B, bdt, rank, ldb, M, ldm);
+    if (st != SYM_OK) return st;
+    if (first < 0 || count < 0 || first > X->nnz || count > X->nnz - first) return SYM_E_INVALID;
+    if (accumulate != 0 && accumulate != 1) return SYM_E_INVALID;
+    cudaStream_t s = as_stream(stream);
+    if (!accumulate) {
+        if (ldm == rank)
+            SYM_CUDA(cudaMemsetAsync(M, 0, sizeof(float) * (size_t)X->n * rank, s));
+        else
+            SYM_CUDA(cudaMemset2DAsync(M, sizeof(float) * ldm, 0, sizeof(float) * rank, X->n, s));
+    }
+    if (count == 0) return SYM_OK;
+    const sym_tensor_s P = tensor_part(X, first, count);
+    const bool bf16 = bdt == SYM_BF16;
+    switch (X->order) {
+        case 2: return launch_mttkrp_order<2>(&P, B, bf16, rank, ldb, M, ldm, X->cfg, s);
+        case 3: return launch_mttkrp_order<3>(&P, B, bf16, rank, ldb, M, ldm, X->cfg, s);
+        case 4: return launch_mttkrp_order<4>(&P, B, bf16, rank, ldb, M, ldm, X->cfg, s);
+        case 5: return launch_mttkrp_order<5>(&P, B, bf16, rank, ldb, M, ldm, X->cfg, s);
+        default: return SYM_E_UNSUPPORTED;
+    }
 }
 
 extern "C" sym_status sym_mttkrp_default_config(sym_mttkrp_cfg* out) {

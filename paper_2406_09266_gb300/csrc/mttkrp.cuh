@@ -63,7 +63,9 @@ struct RowSink {
     __device__ __forceinline__ void add(int64_t row, int col, float4 v) const {
         if (row < H) {
             float* p = smem + row * R + col;
-            const int rot = (col >> 2) & 3;
+            // lanes l, l+8, l+16, l+24 share a bank group of four; their rotations differ
+            const int lane = threadIdx.x & 31;
+            const int rot = lane + (lane >> 3);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int j = (k + rot) & 3;
@@ -619,6 +621,155 @@ __global__ void __launch_bounds__(512) k_mttkrp_strict_pipe(
     }
 }
 
+// Persistent strict-stream kernel (SYM_MTTKRP_HOT): rows [0, HB) of B read
+// from a shared-memory copy, rows [0, H) of M accumulated in one, the leaf
+// factor rows of D consecutive entries requested together, and a choice of the
+// positions it updates:
+//   MODE 0: every position (leaf reductions per entry, fiber flushes above);
+//   MODE 1: all but the leaf (the leaf's rows are left to a MODE 2 pass);
+//   MODE 2: the root only, over the leaf index (tuples reversed and sorted, so
+//           the root is the LARGEST index of each tuple): row c_N receives
+//           (N-1)! times the sum over its subtree of v prod_{q<N} B[c_q],
+//           accumulated in registers along the root fiber.
+// MODE 1 over the canonical stream plus MODE 2 over the leaf index cover every
+// position exactly once with no per-entry reduction: the smallest indices
+// (the hottest rows under skewed distributions, where reductions would
+// contend) are roots or middle levels of the canonical order, and the largest
+// index of each tuple is the root of the second pass.  The per-entry work of
+// both passes is then one factor-row gather and one FMA row; the gathers of
+// the second pass are the small (hot) indices, which the shared-memory copy
+// of B serves.
+//
+// Work: CTA c owns the contiguous slice [nnz c / G, nnz (c + 1) / G) of the
+// stream; its warps take chunks of `chunk` entries from a shared counter.
+// Fiber state is flushed at the end of every chunk.  The shared copy of M is
+// zeroed at start and reduced into M once per CTA at the end.
+constexpr int hot_max_threads(int D) { return D >= 4 ? 768 : 1024; }
+
+template <int N, int KW, int L, bool BF16, int MODE, int D>
+__global__ void __launch_bounds__(hot_max_threads(D), 1) k_mttkrp_strict_hot(
+    const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
+    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
+    int64_t chunk, int H, int HB, int stream_hint) {
+    static_assert(D >= 1 && D <= L && L % D == 0, "prefetch depth divides the lanes per entry");
+    extern __shared__ float4 sink_mem[];
+    __shared__ unsigned long long s_next;
+    constexpr int LV = N - 1;
+    float* sm_m = reinterpret_cast<float*>(sink_mem);
+    float* sm_b = sm_m + (size_t)H * R;
+    const RowSink sink{sm_m, H, R, M, ldm};
+    const RowSource<BF16> src_b{sm_b, HB, R, B, ldb};
+    const int64_t c0 = nnz * blockIdx.x / gridDim.x, c1 = nnz * (blockIdx.x + 1) / gridDim.x;
+    sink_zero(sm_m, H * R);
+    source_fill<BF16>(sm_b, HB, R, B, ldb);
+    if (threadIdx.x == 0) s_next = (unsigned long long)c0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L;
+    const int col = 4 * (lane % L);
+    const bool on = col < R;
+
+    for (;;) {
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(&s_next, (unsigned long long)chunk);
+        const int64_t start = (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        if (start >= c1) break;
+        const int64_t end = min(start + chunk, c1);
+
+        int32_t cur[LV];
+        float4 Brow[LV], P[LV], T[LV];
+#pragma unroll
+        for (int q = 0; q < LV; ++q) {
+            cur[q] = -1;
+            Brow[q] = f4_zero();
+            P[q] = f4_zero();
+            T[q] = f4_zero();
+        }
+        bool have = false;
+        for (int64_t b0 = start; b0 < end; b0 += 32) {
+            const int64_t e = b0 + lane;
+            uint64_t mlo = 0, mhi = 0;
+            float mv = 0.f;
+            if (e < end) {
+                if (stream_hint) {
+                    mlo = __ldcs(klo + e);
+                    if (KW == 2) mhi = __ldcs(khi + e);
+                    mv = __ldcs(val + e);
+                } else {
+                    mlo = klo[e];
+                    if (KW == 2) mhi = khi[e];
+                    mv = val[e];
+                }
+            }
+            // entries of this group in this batch: b0 + g L + t, valid while t < nval
+            const int64_t left = end - (b0 + g * L);
+            const int nval = left <= 0 ? 0 : (left >= L ? L : (int)left);
+#pragma unroll 1
+            for (int t0 = 0; t0 < L; t0 += D) {
+                int32_t c[D][N];
+                float v[D];
+                float4 bl[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) {  // D leaf gathers in flight at once
+                    const int src = g * L + t0 + d;
+                    const uint64_t lo = __shfl_sync(0xffffffffu, mlo, src);
+                    const uint64_t hi = (KW == 2) ? __shfl_sync(0xffffffffu, mhi, src) : 0ull;
+                    v[d] = __shfl_sync(0xffffffffu, mv, src);
+                    decode_entry<N, KW>(lo, hi, bits, c[d]);
+                    bl[d] = (t0 + d < nval && on) ? src_b.get(c[d][N - 1], col) : f4_zero();
+                }
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    if (t0 + d >= nval || !on) continue;
+                    int dl = LV;
+#pragma unroll
+                    for (int q = LV - 1; q >= 0; --q)
+                        if (!have || c[d][q] != cur[q]) dl = q;
+                    if (dl < LV) {
+                        if (have) {
+#pragma unroll
+                            for (int q = LV - 1; q >= 0; --q) {
+                                if (q >= dl) {
+                                    if (MODE != 2 || q == 0) {
+                                        const float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+                                        sink.add(cur[q], col, f4_scale(out, w));
+                                    }
+                                    if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+                                    T[q] = f4_zero();
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < LV; ++q) {
+                            if (q >= dl) {
+                                cur[q] = c[d][q];
+                                // the root row's own factor is not needed when only the root is flushed
+                                Brow[q] = (MODE != 2 || q > 0) ? src_b.get(c[d][q], col) : f4_zero();
+                                if (MODE != 2) P[q] = (q > 0) ? f4_mul(P[q - 1], Brow[q]) : Brow[q];
+                            }
+                        }
+                        have = true;
+                    }
+                    T[LV - 1] = f4_fmas(bl[d], v[d], T[LV - 1]);
+                    if (MODE == 0) sink.add(c[d][N - 1], col, f4_scale(P[LV - 1], w * v[d]));
+                }
+            }
+        }
+        if (have && on) {
+#pragma unroll
+            for (int q = LV - 1; q >= 0; --q) {
+                if (MODE != 2 || q == 0) {
+                    const float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+                    sink.add(cur[q], col, f4_scale(out, w));
+                }
+                if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+            }
+        }
+    }
+    __syncthreads();
+    sink_flush(sm_m, H, R, M, ldm);
+}
+
 // One entry per lane group, any equality pattern (the diagonal stream; with
 // all-distinct entries it is the unfactorised per-entry form).  Grid-stride
 // over entries; optional shared-memory hot rows as above.
@@ -704,6 +855,48 @@ inline SinkPlan plan_sink(int64_t n, int R, int kb, int b_share_pct) {
     return SinkPlan{H, HB, (size_t)(H + HB) * row};
 }
 
+template <int N, int KW, int L, bool BF16, int MODE, int D>
+sym_status launch_hot_md(unsigned grid, int threads, const SinkPlan& sp, const uint64_t* klo, const uint64_t* khi,
+                         const float* val, int64_t cnt, int bits, const void* B, int64_t ldb, int R, float* M,
+                         int64_t ldm, float w, int64_t chunk, int stream_hint, const char* name, cudaStream_t s) {
+    SYM_TRY(raise_smem_limit(k_mttkrp_strict_hot<N, KW, L, BF16, MODE, D>, sp.bytes));
+    threads = std::min(threads, hot_max_threads(D));
+    SYM_PROF(name, s);
+    k_mttkrp_strict_hot<N, KW, L, BF16, MODE, D><<<grid, threads, sp.bytes, s>>>(
+        klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w, chunk, sp.H, sp.HB, stream_hint);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+// Prefetch depth: 4 leaf gathers in flight per lane group when the rank
+// spans at least 4 lanes (depth >= 4), else 1.
+template <int N, int KW, int L, bool BF16, int MODE>
+sym_status launch_hot_m(int depth, unsigned grid, int threads, const SinkPlan& sp, const uint64_t* klo,
+                        const uint64_t* khi, const float* val, int64_t cnt, int bits, const void* B, int64_t ldb,
+                        int R, float* M, int64_t ldm, float w, int64_t chunk, int stream_hint, const char* name,
+                        cudaStream_t s) {
+    if (depth >= 4 && L >= 4)
+        return launch_hot_md<N, KW, L, BF16, MODE, (L >= 4 ? 4 : 1)>(grid, threads, sp, klo, khi, val, cnt, bits, B,
+                                                                     ldb, R, M, ldm, w, chunk, stream_hint, name, s);
+    return launch_hot_md<N, KW, L, BF16, MODE, 1>(grid, threads, sp, klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
+                                                  chunk, stream_hint, name, s);
+}
+
+template <int N, int KW, int L, bool BF16>
+sym_status launch_hot(int mode, int depth, unsigned grid, int threads, const SinkPlan& sp, const uint64_t* klo,
+                      const uint64_t* khi, const float* val, int64_t cnt, int bits, const void* B, int64_t ldb, int R,
+                      float* M, int64_t ldm, float w, int64_t chunk, int stream_hint, const char* name,
+                      cudaStream_t s) {
+    switch (mode) {
+        case 0: return launch_hot_m<N, KW, L, BF16, 0>(depth, grid, threads, sp, klo, khi, val, cnt, bits, B, ldb, R,
+                                                       M, ldm, w, chunk, stream_hint, name, s);
+        case 1: return launch_hot_m<N, KW, L, BF16, 1>(depth, grid, threads, sp, klo, khi, val, cnt, bits, B, ldb, R,
+                                                       M, ldm, w, chunk, stream_hint, name, s);
+        default: return launch_hot_m<N, KW, L, BF16, 2>(depth, grid, threads, sp, klo, khi, val, cnt, bits, B, ldb,
+                                                        R, M, ldm, w, chunk, stream_hint, name, s);
+    }
+}
+
 template <int N, int KW, int L, bool BF16>
 sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int64_t ldb, float* M, int64_t ldm,
                                const sym_mttkrp_cfg& cfg, cudaStream_t s) {
@@ -760,6 +953,25 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             k_mttkrp_strict_pipe<N, KW, L, BF16><<<grid, threads, sp.bytes, s>>>(
                 X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
                 std::max<int64_t>(0, cfg.entries_per_warp), sp.H, sp.HB);
+        } else if (cfg.strict_kernel == SYM_MTTKRP_HOT) {
+            // leaf_index = 1 with a leaf index: two passes (canonical stream without the leaf, then the
+            // leaf index for the root only); otherwise one pass over the canonical stream
+            const bool two = cfg.leaf_index != 0 && X->rklo != nullptr;
+            const SinkPlan sp = plan_sink(X->n, R, cfg.strict_smem_kb, cfg.b_share_pct);
+            const SinkPlan sp2 = plan_sink(X->n, R, cfg.strict_smem_kb, 100);  // root pass: rows of B only
+            const int hthreads = std::max(64, std::min(1024, (int)cfg.threads_per_cta)) / 32 * 32;
+            const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
+            const unsigned grid = (unsigned)std::max<int64_t>(
+                1, std::min<int64_t>((int64_t)sms * std::max(1, (int)cfg.ctas_per_sm), (ns + chunk - 1) / chunk));
+            const int depth = cfg.vec_per_lane;  // leaf gathers in flight per lane group (1 or 4)
+            sym_status hs = launch_hot<N, KW, L, BF16>(two ? 1 : 0, depth, grid, hthreads, sp, X->klo, X->khi, X->val,
+                                                       ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
+                                                       cfg.stream_hint, "mttkrp_strict", s);
+            if (hs == SYM_OK && two)
+                hs = launch_hot<N, KW, L, BF16>(2, depth, grid, hthreads, sp2, X->rklo, X->rkhi, X->rval, ns, X->bits,
+                                                B, ldb, R, M, ldm, (float)fact[N - 1], chunk, cfg.stream_hint,
+                                                "mttkrp_strict_leaf", s);
+            if (hs != SYM_OK) return hs;
         } else if (cfg.strict_kernel == SYM_MTTKRP_STAGED) {
             const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
             const size_t per_warp = (size_t)2 * 32 * L * stage_lane_bytes<BF16>();

@@ -419,6 +419,57 @@ __global__ void __launch_bounds__(256) k_pmttkrp_root(ModeArgs A, const int32_t*
     if (cur >= 0) red_add_f4(M + (int64_t)cur * ldm + col, acc);
 }
 
+// Mode-1 TTM of a partially symmetric order-3 tensor (the TTM of Sec. 4.2 with
+// the symmetry of Def. "Partial Symmetry"): C[j, l, :] = sum_k A[k, j, l] B[k, :]
+// over the full tensor.  One lane group per canonical entry (sorted inside
+// parts); each distinct inside-part arrangement (a1, a2, a3) of it adds
+// v B[a1, :] to output position (a2, a3).  Packed layout (modes 2 and 3 in one
+// part, so C is symmetric in (j, l)): only arrangements with a2 <= a3 are
+// applied, at the canonical position a2 d - a2 (a2 - 1) / 2 + (a3 - a2); the
+// mirrored arrangement holds the same value and is not stored.
+template <bool BF16, bool PACKED>
+__global__ void __launch_bounds__(256) k_pttm3(PartDesc D, const int32_t* __restrict__ idx, int64_t ld,
+                                               const float* __restrict__ val, int64_t nnz, const void* __restrict__ B,
+                                               int64_t ldb, int R, int GP, float* __restrict__ C, int64_t d3) {
+    // the six permutations of three positions
+    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const int lane = threadIdx.x & 31;
+    const int col = 4 * (lane & (GP - 1));
+    const int per_warp = 32 / GP;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e0 = warp * per_warp; e0 < nnz; e0 += nwarps * per_warp) {
+        const int64_t e = e0 + lane / GP;
+        if (e >= nnz || col >= R) continue;
+        int32_t c[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) c[q] = idx[(int64_t)q * ld + e];
+        const float v = val[e];
+        int32_t seen[6][3];
+        int ns = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            // only permutations inside parts
+            bool inside = true;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) inside = inside && D.part_of[perm[k][q]] == D.part_of[q];
+            if (!inside) continue;
+            const int32_t a1 = c[perm[k][0]], a2 = c[perm[k][1]], a3 = c[perm[k][2]];
+            bool dup = false;  // the same arrangement from an earlier permutation (repeated indices)
+            for (int t = 0; t < ns; ++t) dup = dup || (seen[t][0] == a1 && seen[t][1] == a2 && seen[t][2] == a3);
+            if (dup) continue;
+            seen[ns][0] = a1;
+            seen[ns][1] = a2;
+            seen[ns][2] = a3;
+            ++ns;
+            if (PACKED && a2 > a3) continue;
+            const int64_t pos = PACKED ? (int64_t)a2 * d3 - (int64_t)a2 * (a2 - 1) / 2 + (a3 - a2)
+                                       : (int64_t)a2 * d3 + a3;
+            red_add_f4(C + pos * R + col, f4_scale(load_row4<BF16>(B, a1, ldb, col), v));
+        }
+    }
+}
+
 __global__ void k_zero_rows(float* __restrict__ M, int64_t rows, int R, int64_t ldm) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = rows * (int64_t)R;
@@ -690,6 +741,50 @@ extern "C" sym_status sym_pmttkrp(sym_ptensor X, const void* const* factors, con
         default: SYM_PM_CASE(5) break;
     }
 #undef SYM_PM_CASE
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+extern "C" int64_t sym_pttm_output_elems(sym_ptensor X, int rank, int layout) {
+    if (!X || X->D.order != 3 || rank < 4 || rank > 128 || rank % 4) return -1;
+    const PartDesc& D = X->D;
+    const int64_t d2 = D.dim[D.part_of[1]], d3 = D.dim[D.part_of[2]];
+    if (layout == SYM_TTM_FULL) return d2 * d3 * rank;
+    if (layout == SYM_TTM_PACKED && D.part_of[1] == D.part_of[2]) return d2 * (d2 + 1) / 2 * rank;
+    return -1;
+}
+
+extern "C" sym_status sym_pttm(sym_ptensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* C,
+                               int layout, sym_stream_t stream) {
+    if (!X || !B || !C) return SYM_E_INVALID;
+    if (X->D.order != 3) return SYM_E_UNSUPPORTED;
+    const int64_t elems = sym_pttm_output_elems(X, rank, layout);
+    if (elems < 0) return SYM_E_INVALID;
+    if (bdt != SYM_F32 && bdt != SYM_BF16) return SYM_E_INVALID;
+    if (ldb < rank || ldb % 4 || !aligned(B, bdt == SYM_BF16 ? 8 : 16) || !aligned(C, 16)) return SYM_E_INVALID;
+    const PartDesc& D = X->D;
+    cudaStream_t s = as_stream(stream);
+    SYM_CUDA(cudaMemsetAsync(C, 0, sizeof(float) * (size_t)elems, s));
+    const int64_t nnz = X->info.nnz;
+    if (nnz == 0) return SYM_OK;
+    int GP = 1;
+    while (GP < rank / 4) GP <<= 1;
+    const int64_t warps = (nnz + (32 / GP) - 1) / (32 / GP);
+    const unsigned grid = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)sm_count() * 16);
+    const int64_t d3 = D.dim[D.part_of[2]];
+    const bool packed = layout == SYM_TTM_PACKED;
+    SYM_PROF("pttm", s);
+    if (bdt == SYM_BF16) {
+        if (packed)
+            k_pttm3<true, true><<<grid, 256, 0, s>>>(D, X->idx, X->cap, X->val, nnz, B, ldb, rank, GP, C, d3);
+        else
+            k_pttm3<true, false><<<grid, 256, 0, s>>>(D, X->idx, X->cap, X->val, nnz, B, ldb, rank, GP, C, d3);
+    } else {
+        if (packed)
+            k_pttm3<false, true><<<grid, 256, 0, s>>>(D, X->idx, X->cap, X->val, nnz, B, ldb, rank, GP, C, d3);
+        else
+            k_pttm3<false, false><<<grid, 256, 0, s>>>(D, X->idx, X->cap, X->val, nnz, B, ldb, rank, GP, C, d3);
+    }
     SYM_CHECK_LAUNCH();
     return SYM_OK;
 }

@@ -75,6 +75,7 @@ struct sym_server_s {
     size_t inflight_bytes = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
+    bool orphaned = false;  // destroy timed out: the scheduler releases everything when it exits
     std::thread th;
     sym_server_stats stats{};
     int64_t inflight = 0;
@@ -82,7 +83,20 @@ struct sym_server_s {
     void run();
     void finish(Slot& s, sym_status st);
     void launch(Slot& s);
+    void release();
 };
+
+// Streams, events and pinned buffers of the slots (host-side resources only).
+void sym_server_s::release() {
+    for (auto& s : slots) {
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.res_host) cudaFreeHost(s.res_host);
+        s.stream = nullptr;
+        s.done = nullptr;
+        s.res_host = nullptr;
+    }
+}
 
 void sym_server_s::finish(Slot& s, sym_status st) {
     sym_result res{};
@@ -185,6 +199,15 @@ void sym_server_s::run() {
             stats.launches += 1;
         }
         if (to_launch.empty() && !progressed) std::this_thread::sleep_for(std::chrono::microseconds(10));
+    }
+    bool self_release;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        self_release = orphaned;
+    }
+    if (self_release) {  // nobody joins this thread any more: the last in-flight request has completed
+        release();
+        delete this;
     }
 }
 
@@ -331,27 +354,24 @@ extern "C" sym_status sym_server_destroy(sym_server S) {
         S->cv_sched.notify_all();
         while (!(S->queue.empty() && S->inflight == 0)) {
             if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+                if (S->queue.empty() && S->inflight == 0) break;  // finished just as the limit ran out
                 st = SYM_E_TIMEOUT;
-                // drop queued requests; in-flight ones finish on their own
+                // drop queued requests; in-flight ones finish on their own, and the scheduler thread
+                // (which exits once they have) then releases the server itself
                 for (auto& p : S->queue) S->live.erase(p.ticket);
                 S->queue.clear();
+                S->orphaned = true;
                 break;
             }
         }
     }
     S->cv_sched.notify_all();
-    if (st == SYM_OK) {
-        S->th.join();
-    } else {
-        // the scheduler exits once in-flight work completes; do not block on it
-        S->th.detach();
+    if (st != SYM_OK) {
+        S->th.detach();  // S is released by the scheduler thread; do not touch it after this
         return st;
     }
-    for (auto& s : S->slots) {
-        cudaStreamDestroy(s.stream);
-        cudaEventDestroy(s.done);
-        cudaFreeHost(s.res_host);
-    }
+    S->th.join();
+    S->release();
     delete S;
     return st;
 }

@@ -29,16 +29,17 @@ __device__ __forceinline__ float group_sum(float v, int L) {
     return v;
 }
 
-// One group of L lanes per row; rows are dealt to groups in order.
+// One group of L lanes per row; rows [row0, row_end) are dealt to groups in order.
 template <int L, bool SYPRD>
-__global__ void __launch_bounds__(SV_THREADS) k_ssymv(int64_t n, const int32_t* __restrict__ rowptr,
+__global__ void __launch_bounds__(SV_THREADS) k_ssymv(int64_t row0, int64_t row_end, const int32_t* __restrict__ rowptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ val,
                                                       const float* __restrict__ x, float* __restrict__ y,
                                                       double* __restrict__ partials) {
     constexpr int GPC = SV_THREADS / L;
     const int lane = threadIdx.x & 31;
     const int s = lane % L;
-    const int64_t i = (int64_t)blockIdx.x * GPC + threadIdx.x / L;
+    const int64_t i = row0 + (int64_t)blockIdx.x * GPC + threadIdx.x / L;
+    const int64_t n = row_end;
     float rowsum = 0.f, syp = 0.f;
     if (i < n) {
         const float xi = x[i];
@@ -89,14 +90,15 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int64_t coun
 
 template <int L>
 sym_status launch_ssymv_l(const sym_csr_upper* A, const float* x, float* y, double* syprd, double* partials,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t row0 = 0, int64_t row_end = -1) {
     constexpr int GPC = SV_THREADS / L;
-    const unsigned grid = (unsigned)((A->n + GPC - 1) / GPC);
+    if (row_end < 0) row_end = A->n;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, (row_end - row0 + GPC - 1) / GPC);
     SYM_PROF("ssymv", s);
     if (syprd)
-        k_ssymv<L, true><<<grid, SV_THREADS, 0, s>>>(A->n, A->rowptr, A->col, A->val, x, y, partials);
+        k_ssymv<L, true><<<grid, SV_THREADS, 0, s>>>(row0, row_end, A->rowptr, A->col, A->val, x, y, partials);
     else
-        k_ssymv<L, false><<<grid, SV_THREADS, 0, s>>>(A->n, A->rowptr, A->col, A->val, x, y, partials);
+        k_ssymv<L, false><<<grid, SV_THREADS, 0, s>>>(row0, row_end, A->rowptr, A->col, A->val, x, y, partials);
     SYM_CHECK_LAUNCH();
     if (syprd) {
         k_sum_partials<<<1, 1024, 0, s>>>(partials, grid, syprd);
@@ -307,6 +309,22 @@ sym_status ssymv_launch(const sym_csr_upper* A, const float* x, float* y, double
 
 size_t ssymv_partials_bytes(const sym_csr_upper* A) { return align_up(sizeof(double) * ssymv_ctas(A), 256); }
 
+// Rows [r0, r1) only, multi-block form, y not cleared.
+sym_status ssymv_rows_launch(const sym_csr_upper* A, const float* x, float* y, double* syprd, double* partials,
+                             int64_t r0, int64_t r1, cudaStream_t s) {
+    if (r1 <= r0) {
+        if (syprd) SYM_CUDA(cudaMemsetAsync(syprd, 0, sizeof(double), s));
+        return SYM_OK;
+    }
+    switch (spmv_lanes(A->n, A->nnz)) {
+        case 2: return launch_ssymv_l<2>(A, x, y, syprd, partials, s, r0, r1);
+        case 4: return launch_ssymv_l<4>(A, x, y, syprd, partials, s, r0, r1);
+        case 8: return launch_ssymv_l<8>(A, x, y, syprd, partials, s, r0, r1);
+        case 16: return launch_ssymv_l<16>(A, x, y, syprd, partials, s, r0, r1);
+        default: return launch_ssymv_l<32>(A, x, y, syprd, partials, s, r0, r1);
+    }
+}
+
 sym_status validate_csr(const sym_csr_upper* A) {
     if (!A || A->n < 0 || A->nnz < 0 || A->n > 0x7fffffffLL || A->nnz > 0x7fffffffLL) return SYM_E_INVALID;
     if (A->n > 0 && !A->rowptr) return SYM_E_INVALID;
@@ -333,6 +351,23 @@ extern "C" sym_status sym_spmv(const sym_csr_upper* A, const float* x, float* y,
         if (ws_bytes < ssymv_partials_bytes(A)) return SYM_E_NOMEM;
     }
     return ssymv_launch(A, x, y, syprd, static_cast<double*>(ws), as_stream(stream));
+}
+
+extern "C" sym_status sym_spmv_rows(const sym_csr_upper* A, const float* x, float* y, double* syprd,
+                                    int64_t row_begin, int64_t row_end, int accumulate, void* ws, size_t ws_bytes,
+                                    sym_stream_t stream) {
+    sym_status st = validate_csr(A);
+    if (st != SYM_OK) return st;
+    if (row_begin < 0 || row_end < row_begin || row_end > A->n) return SYM_E_INVALID;
+    if (accumulate != 0 && accumulate != 1) return SYM_E_INVALID;
+    if (A->n > 0 && (!x || !y)) return SYM_E_INVALID;
+    if (syprd) {
+        if (!ws || !aligned(ws, 256)) return SYM_E_INVALID;
+        if (ws_bytes < ssymv_partials_bytes(A)) return SYM_E_NOMEM;
+    }
+    cudaStream_t s = as_stream(stream);
+    if (!accumulate && A->n > 0) SYM_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)A->n, s));
+    return ssymv_rows_launch(A, x, y, syprd, static_cast<double*>(ws), row_begin, row_end, s);
 }
 
 extern "C" sym_status sym_csr_upper_check(const sym_csr_upper* A, int64_t* bad, sym_stream_t stream) {

@@ -92,14 +92,15 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Waits for the phase of `parity` to complete; gives up after ~2 s.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Waits for the phase of `parity` to complete; gives up after `limit_ns`
+// (2 s in normal runs).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         for (int k = 0; k < 64; ++k)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -296,8 +297,10 @@ __device__ __forceinline__ void fetch_tasks(BandTask* buf, const BandTask* tasks
 // it releases a chunk, an x band or a y band with one mbarrier arrival.
 // Warp 1 flushes: once every consumer has released a y band it reduces the
 // band into global memory, zeroes it and hands it back (y_I with the row
-// band's SYPRD partial).  Every wait is bounded (~2 s); on a timeout the
-// kernel records bit 0 of *err and stops.
+// band's SYPRD partial).  Every wait is bounded (wait_ns, 2 s in normal
+// runs); on a timeout the kernel records bit 0 of *err and stops, and the
+// producer still waits (bounded) for every copy it issued before it exits.
+// skip_chunk >= 0 is a test hook: CTA 0 withholds that chunk of its stream.
 template <bool SYPRD, int EPL>
 __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restrict__ tasks,
                                                         const int32_t* __restrict__ cta_ptr,
@@ -305,7 +308,8 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
                                                         const float* __restrict__ evals, const float* __restrict__ x,
                                                         int64_t x_rows, float* __restrict__ y,
                                                         double* __restrict__ partials, int W, int S,
-                                                        unsigned* __restrict__ err) {
+                                                        unsigned* __restrict__ err, uint64_t wait_ns,
+                                                        int64_t skip_chunk) {
     extern __shared__ __align__(128) unsigned char band_smem[];
     __shared__ double s_red[2][32];  // per y_I buffer: one SYPRD partial per consumer warp
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         bool ok = true;
         for (int t = 0; t < ntask && ok; ++t) {
             const int b = t / TASKS_PER_BUF, ti = t % TASKS_PER_BUF;
-            if (ti == 0 && !(ok = mbar_wait_bounded(&t_full[b & 1], (uint32_t)((b >> 1) & 1)))) break;
+            if (ti == 0 && !(ok = mbar_wait_bounded(&t_full[b & 1], (uint32_t)((b >> 1) & 1), wait_ns))) break;
             const BandTask T = tbuf[(b & 1) * TASKS_PER_BUF + ti];
             if ((ti == TASKS_PER_BUF - 1 || t == ntask - 1) && b + 2 < nbatch)  // buffer read out: refill it
                 fetch_tasks(tbuf + (b & 1) * TASKS_PER_BUF, tasks, t_begin + (b + 2) * TASKS_PER_BUF,
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
             const int mode = T.flags >> TASK_MODE_SHIFT;
             if (T.flags & TASK_FIRST) {
                 const int bI = ucnt & 1;
-                if (ucnt >= 2 && !(ok = mbar_wait_bounded(&xI_empty[bI], (uint32_t)(((ucnt >> 1) - 1) & 1))))
+                if (ucnt >= 2 && !(ok = mbar_wait_bounded(&xI_empty[bI], (uint32_t)(((ucnt >> 1) - 1) & 1), wait_ns)))
                     break;
                 leadI = stage_x(xIb + bI * WB, x + T.base + (int64_t)T.I * W, T.wI, x_end, x16, &xI_full[bI]);
                 ++ucnt;
@@ -388,15 +392,24 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
             int leadJ = 0;
             if (mode == 1) {
                 const int bJ = scnt & 1;
-                if (scnt >= 2 && !(ok = mbar_wait_bounded(&xJ_empty[bJ], (uint32_t)(((scnt >> 1) - 1) & 1))))
+                if (scnt >= 2 && !(ok = mbar_wait_bounded(&xJ_empty[bJ], (uint32_t)(((scnt >> 1) - 1) & 1), wait_ns)))
                     break;
                 leadJ = stage_x(xJb + bJ * WB, x + T.base + (int64_t)T.J * W, T.wJ, x_end, x16, &xJ_full[bJ]);
                 ++scnt;
             }
             for (int o = 0; o < T.cnt; o += CH, ++k) {
                 const int slot = pslot;
-                if (k >= S && !(ok = mbar_wait_bounded(&empty[slot], pphase ^ 1u))) break;  // previous use drained
+                if (k >= S && !(ok = mbar_wait_bounded(&empty[slot], pphase ^ 1u, wait_ns))) break;  // previous use drained
                 const int m = min(CH, T.cnt - o);
+                if (blockIdx.x == 0 && k == skip_chunk) {
+                    // test hook: this chunk is never delivered (no arrival, no copy), so the
+                    // consumers' bounded wait on it runs out; nothing is left in flight
+                    if (++pslot == S) {
+                        pslot = 0;
+                        pphase ^= 1u;
+                    }
+                    continue;
+                }
                 ChunkMeta& cm = meta[slot];
                 cm.base = T.base;
                 cm.slot = T.slot;
@@ -422,7 +435,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         }
         if (ok) {
             const int slot = pslot;
-            if (k < S || (ok = mbar_wait_bounded(&empty[slot], pphase ^ 1u))) {
+            if (k < S || (ok = mbar_wait_bounded(&empty[slot], pphase ^ 1u, wait_ns))) {
                 meta[slot].flags = CM_END;
                 mbar_arrive(&full[slot]);
                 ++k;
@@ -431,14 +444,14 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         if (!ok) atomicOr(err, 1u);
         // Every copy issued into this CTA's shared memory lands before the
         // producer thread (and so the CTA) exits.
-        for (int64_t j = k > S ? k - S : 0; j < k; ++j) mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1));
+        for (int64_t j = k > S ? k - S : 0; j < k; ++j) mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1), wait_ns);
         for (int b = 0; b < 2; ++b) {
             const int ui = ucnt - 1 - ((ucnt - 1 - b) & 1);  // last use of x_I buffer b
-            if (ui >= 0) mbar_wait_bounded(&xI_full[b], (uint32_t)((ui >> 1) & 1));
+            if (ui >= 0) mbar_wait_bounded(&xI_full[b], (uint32_t)((ui >> 1) & 1), wait_ns);
             const int si = scnt - 1 - ((scnt - 1 - b) & 1);
-            if (si >= 0) mbar_wait_bounded(&xJ_full[b], (uint32_t)((si >> 1) & 1));
+            if (si >= 0) mbar_wait_bounded(&xJ_full[b], (uint32_t)((si >> 1) & 1), wait_ns);
             const int bi = nbatch - 1 - ((nbatch - 1 - b) & 1);  // last batch in task buffer b
-            if (bi >= 0) mbar_wait_bounded(&t_full[b], (uint32_t)((bi >> 1) & 1));
+            if (bi >= 0) mbar_wait_bounded(&t_full[b], (uint32_t)((bi >> 1) & 1), wait_ns);
         }
         return;
     }
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
             const BandTask T = tasks[t];
             if ((T.flags >> TASK_MODE_SHIFT) == 1) {
                 const int b = scnt & 1;
-                if (!mbar_wait_bounded(&yJ_done[b], (uint32_t)((scnt >> 1) & 1))) {
+                if (!mbar_wait_bounded(&yJ_done[b], (uint32_t)((scnt >> 1) & 1), wait_ns)) {
                     if (lane == 0) atomicOr(err, 1u);
                     return;
                 }
@@ -466,7 +479,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
             }
             if (T.flags & TASK_LAST) {
                 const int b = ucnt & 1;
-                if (!mbar_wait_bounded(&yI_done[b], (uint32_t)((ucnt >> 1) & 1))) {
+                if (!mbar_wait_bounded(&yI_done[b], (uint32_t)((ucnt >> 1) & 1), wait_ns)) {
                     if (lane == 0) atomicOr(err, 1u);
                     return;
                 }
@@ -493,7 +506,7 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
     int slot = 0;         // ring slot of the next chunk
     uint32_t phase = 0;   // its phase parity
     for (;;) {
-        if (!mbar_wait_bounded(&full[slot], phase)) {
+        if (!mbar_wait_bounded(&full[slot], phase, wait_ns)) {
             if (lane == 0) atomicOr(err, 1u);
             break;
         }
@@ -509,8 +522,8 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         const int mode = cm.flags >> TASK_MODE_SHIFT;
         if (cm.flags & TASK_FIRST) {
             bI = ucnt & 1;
-            if (!mbar_wait_bounded(&xI_full[bI], (uint32_t)((ucnt >> 1) & 1)) ||
-                (ucnt >= 2 && !mbar_wait_bounded(&yI_free[bI], (uint32_t)(((ucnt >> 1) - 1) & 1)))) {
+            if (!mbar_wait_bounded(&xI_full[bI], (uint32_t)((ucnt >> 1) & 1), wait_ns) ||
+                (ucnt >= 2 && !mbar_wait_bounded(&yI_free[bI], (uint32_t)(((ucnt >> 1) - 1) & 1), wait_ns))) {
                 if (lane == 0) atomicOr(err, 1u);
                 break;
             }
@@ -518,8 +531,8 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
         }
         if ((cm.flags & CM_FIRST_SEG) && mode == 1) {
             bJ = scnt & 1;
-            if (!mbar_wait_bounded(&xJ_full[bJ], (uint32_t)((scnt >> 1) & 1)) ||
-                (scnt >= 2 && !mbar_wait_bounded(&yJ_free[bJ], (uint32_t)(((scnt >> 1) - 1) & 1)))) {
+            if (!mbar_wait_bounded(&xJ_full[bJ], (uint32_t)((scnt >> 1) & 1), wait_ns) ||
+                (scnt >= 2 && !mbar_wait_bounded(&yJ_free[bJ], (uint32_t)(((scnt >> 1) - 1) & 1), wait_ns))) {
                 if (lane == 0) atomicOr(err, 1u);
                 break;
             }
@@ -867,7 +880,8 @@ template <bool SYPRD, int EPL>
 sym_status launch_band_v(const BandPlan& P, const float* x, float* y, double* partials, cudaStream_t s) {
     SYM_TRY(raise_smem_limit(k_ssymv_band<SYPRD, EPL>, P.smem));
     k_ssymv_band<SYPRD, EPL><<<P.grid, P.threads, P.smem, s>>>(P.tasks, P.cta_ptr, P.eidx, P.evals, x, P.x_rows, y,
-                                                                partials, P.W, P.stages, P.err);
+                                                                partials, P.W, P.stages, P.err, P.wait_ns,
+                                                                P.skip_chunk);
     SYM_CHECK_LAUNCH();
     return SYM_OK;
 }

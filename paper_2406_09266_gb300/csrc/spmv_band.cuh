@@ -64,6 +64,8 @@ struct BandPlan {
     uint32_t* eidx = nullptr;      // [device] packed (row - I W) << 16 | (col - J W)
     float* evals = nullptr;        // [device]
     unsigned* err = nullptr;       // [device] bit 0: a bounded wait ran out; bits 1, 2: bad column (plan time)
+    uint64_t wait_ns = 2000000000ull;  // limit of every bounded wait in the kernel
+    int64_t skip_chunk = -1;       // test hook: chunk of CTA 0 that is never delivered (-1: none)
 };
 
 // Instances on the banded path and their band counts (0 = tile path).

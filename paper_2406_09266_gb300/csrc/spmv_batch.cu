@@ -663,6 +663,24 @@ extern "C" sym_status sym_spmv_batch_graph_launch(sym_batch_plan P, sym_stream_t
     return SYM_OK;
 }
 
+extern "C" sym_status sym_spmv_batch_run_bounded(sym_batch_plan P, const float* x, float* y, double* syprd,
+                                                 int64_t wait_limit_ns, int64_t skip_chunk, sym_stream_t stream) {
+    if (!P || (P->A.total_rows > 0 && (!x || !y))) return SYM_E_INVALID;
+    const BandPlan saved = P->band;
+    P->band.wait_ns = wait_limit_ns > 0 ? (uint64_t)wait_limit_ns : 2000000000ull;
+    P->band.skip_chunk = skip_chunk < 0 ? -1 : skip_chunk;
+    const sym_status st = batch_enqueue(P, x, y, syprd, as_stream(stream));
+    P->band = saved;
+    return st;
+}
+
+extern "C" sym_status sym_spmv_batch_clear_status(sym_batch_plan P, sym_stream_t stream) {
+    if (!P) return SYM_E_INVALID;
+    if (!P->band.err) return SYM_OK;
+    SYM_CUDA(cudaMemsetAsync(P->band.err, 0, sizeof(unsigned), as_stream(stream)));
+    return SYM_OK;
+}
+
 extern "C" sym_status sym_spmv_batch_check(sym_batch_plan P) {
     if (!P) return SYM_E_INVALID;
     if (!P->band.err) return SYM_OK;

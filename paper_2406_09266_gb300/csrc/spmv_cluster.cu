@@ -123,8 +123,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for phase 0 of `bar` to complete; gives up after about 2 s.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar) {
+// Waits for phase 0 of `bar` to complete; gives up after `limit_ns` (2 s in
+// normal runs).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint64_t limit_ns) {
     if (mbar_try_wait(bar, 0)) return true;
     uint64_t t0;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
@@ -133,7 +134,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar) {
             if (mbar_try_wait(bar, 0)) return true;
         uint64_t t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > 2000000000ull) return false;
+        if (t - t0 > limit_ns) return false;
     }
 }
 
@@ -162,11 +163,14 @@ __device__ __forceinline__ int last_le(const int32_t* rp, int lo, int n, int v) 
 // start in different banks), finds the row of its first entry by binary search
 // and keeps the row sum in a register until the row changes (a row split
 // between threads or CTAs adds one partial sum per piece).
+// wait_ns bounds the inbox wait.  skip_to >= 0 is a test hook: no CTA pushes
+// anything into CTA skip_to's inbox, so its wait runs out with no copy in
+// flight towards it; it then writes NaN to its rows (and to SYPRD if it is CTA 0).
 template <bool SYPRD>
 __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS, 1)
     k_ssymv_cluster(int n, int nnz, int per, int slice, int xw, int rw, const int32_t* __restrict__ rowptr,
                     const int32_t* __restrict__ col, const float* __restrict__ val, const float* __restrict__ x,
-                    float* __restrict__ y, double* __restrict__ syprd) {
+                    float* __restrict__ y, double* __restrict__ syprd, uint64_t wait_ns, int skip_to) {
     extern __shared__ __align__(16) unsigned char cl_smem[];
     float* xs = reinterpret_cast<float*>(cl_smem);
     float* yp = xs + xw;  // this CTA's partial y, CL_CTAS slices
@@ -255,16 +259,16 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS, 1)
     if (tid == 0) {
         const uint32_t bar = smem_u32(mbar);
         for (uint32_t c = 0; c < CL_CTAS; ++c) {
-            if (c == rank) continue;
+            if (c == rank || (int)c == skip_to) continue;
             const uint32_t slot = rank < c ? rank : rank - 1;  // this CTA's slot in the inbox of CTA c
             bulk_s2c(map_rank(smem_u32(inbox + slot * slice), c), smem_u32(yp + c * slice), slice_bytes,
                      map_rank(bar, c));
         }
-        if (SYPRD && rank != 0)
+        if (SYPRD && rank != 0 && skip_to != 0)
             bulk_s2c(map_rank(smem_u32(sinbox + 2 * rank), 0), smem_u32(sinbox + 2 * rank), 16u, map_rank(bar, 0));
         asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
     }
-    const bool ok = mbar_wait_bounded(smem_u32(mbar));
+    const bool ok = mbar_wait_bounded(smem_u32(mbar), wait_ns);
 
     // Rows [r slice, (r+1) slice): the CL_CTAS partials summed in CTA order.
     const int r0 = (int)rank * slice;
@@ -297,16 +301,18 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS, 1)
 }
 
 sym_status launch_cluster(const sym_csr_upper* A, const ClusterShape& sh, const float* x, float* y, double* syprd,
-                          cudaStream_t s) {
+                          cudaStream_t s, uint64_t wait_ns = 2000000000ull, int skip_to = -1) {
     SYM_PROF("ssymv_cluster", s);
     if (syprd) {
         SYM_TRY(raise_smem_limit(k_ssymv_cluster<true>, sh.smem));
-        k_ssymv_cluster<true><<<CL_CTAS, CL_THREADS, sh.smem, s>>>(
-            (int)A->n, (int)A->nnz, sh.per, sh.slice, sh.xw, sh.rw, A->rowptr, A->col, A->val, x, y, syprd);
+        k_ssymv_cluster<true><<<CL_CTAS, CL_THREADS, sh.smem, s>>>((int)A->n, (int)A->nnz, sh.per, sh.slice, sh.xw,
+                                                                   sh.rw, A->rowptr, A->col, A->val, x, y, syprd,
+                                                                   wait_ns, skip_to);
     } else {
         SYM_TRY(raise_smem_limit(k_ssymv_cluster<false>, sh.smem));
-        k_ssymv_cluster<false><<<CL_CTAS, CL_THREADS, sh.smem, s>>>(
-            (int)A->n, (int)A->nnz, sh.per, sh.slice, sh.xw, sh.rw, A->rowptr, A->col, A->val, x, y, syprd);
+        k_ssymv_cluster<false><<<CL_CTAS, CL_THREADS, sh.smem, s>>>((int)A->n, (int)A->nnz, sh.per, sh.slice, sh.xw,
+                                                                    sh.rw, A->rowptr, A->col, A->val, x, y, syprd,
+                                                                    wait_ns, skip_to);
     }
     SYM_CHECK_LAUNCH();
     return SYM_OK;
@@ -330,4 +336,17 @@ sym_status ssymv_cluster_launch(const sym_csr_upper* A, const float* x, float* y
 extern "C" int sym_spmv_single_launch(const sym_csr_upper* A) {
     if (symgpu::validate_csr(A) != SYM_OK) return 0;
     return symgpu::ssymv_single_launch(A) ? 1 : 0;
+}
+
+extern "C" sym_status sym_spmv_cluster_bounded(const sym_csr_upper* A, const float* x, float* y, double* syprd,
+                                               int64_t wait_limit_ns, int skip_to, sym_stream_t stream) {
+    using namespace symgpu;
+    sym_status st = validate_csr(A);
+    if (st != SYM_OK) return st;
+    if (A->n > 0 && (!x || !y)) return SYM_E_INVALID;
+    if (skip_to < -1 || skip_to >= CL_CTAS) return SYM_E_INVALID;
+    ClusterShape sh;
+    if (A->n == 0 || !cluster_shape(A, &sh)) return SYM_E_UNSUPPORTED;
+    const uint64_t limit = wait_limit_ns > 0 ? (uint64_t)wait_limit_ns : 2000000000ull;
+    return launch_cluster(A, sh, x, y, syprd, as_stream(stream), limit, skip_to);
 }

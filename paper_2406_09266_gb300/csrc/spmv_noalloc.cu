@@ -13,10 +13,14 @@
 // holds it (256 KiB) until the process exits.  Its host-side name is only a
 // stand-in, so the device address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on
-// that device; make that first call before any stream capture.  All calls
+// that device that asks for SYPRD; make that first call before any stream
+// capture.  The looked-up address is kept for the life of the process: after
+// cudaDeviceReset the module may load at another address, so a process that
+// resets a device must not call this entry point on it again.  All calls
 // share the array: calls whose work overlaps on the GPU (other streams, other
 // threads) race on it and must be serialised by the caller.  Nothing in it has
-// to start at zero: each call writes every slot it later reads.
+// to start at zero: each call writes every slot it later reads.  Only SYPRD
+// uses the array, so the size limit applies only to calls that ask for it.
 #include <mutex>
 
 #include "common.cuh"
@@ -24,8 +28,7 @@
 
 namespace {
 
-constexpr int64_t kNoAllocSlots = 32768;        // FP64 partials: 256 KiB per device
-constexpr int64_t kNoAllocMaxRows = 8 * kNoAllocSlots;  // at most one slot per 8 rows is used
+constexpr int64_t kNoAllocSlots = 32768;  // FP64 partials: 256 KiB per device (one slot per 8+ rows)
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double g_noalloc_partials[kNoAllocSlots];
@@ -57,12 +60,12 @@ extern "C" sym_status sym_spmv_noalloc(const sym_csr_upper* A, const float* x, f
     sym_status st = validate_csr(A);
     if (st != SYM_OK) return st;
     if (A->n > 0 && (!x || !y)) return SYM_E_INVALID;
-    if (A->n > kNoAllocMaxRows) return SYM_E_UNSUPPORTED;  // more partial slots than the fixed array holds
     double* partials = nullptr;
     if (syprd) {
+        // more partial slots than the fixed array holds: refused before anything is looked up or enqueued
+        if (ssymv_partials_bytes(A) > sizeof(double) * (size_t)kNoAllocSlots) return SYM_E_UNSUPPORTED;
         st = noalloc_partials(&partials);
         if (st != SYM_OK) return st;
-        if (ssymv_partials_bytes(A) > sizeof(double) * (size_t)kNoAllocSlots) return SYM_E_UNSUPPORTED;
     }
     return ssymv_launch(A, x, y, syprd, partials, as_stream(stream));
 }

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_helpers import TOL_F32, dev, host, need_gpu
+from tests.gpu_helpers import TOL_F32, dev, host, need_gpu, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -295,3 +295,31 @@ def test_batch_band_tiny_empty_and_entryless(cfg):
         assert np.all(host(s)[~nz] == 0.0)
         if nz.any():
             assert np.max(np.abs(host(s)[nz] - sr[nz]) / sa[nz]) <= TOL_F32
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_batch_band_wait_runs_out_without_fault(order):
+    """The banded kernel's bounded waits made to run out: the first CTA's first chunk is withheld (never
+    announced, never copied) and every wait is limited to 1 ms.  The kernel returns, the plan's status word
+    reports SYM_E_TIMEOUT, and after clearing it the next normal run is clean and matches the oracle."""
+    sg = need_gpu()
+    sizes, row_off, draw_off, idx, val, rowptr, col, v = make_small_batch(64, 4, 4000, 16, 9)
+    x = synth.vector_uniform(int(row_off[-1]), 9)
+    batch = sg.BatchCSR(dev(row_off), dev(rowptr), dev(col), dev(v))
+    plan = sg.BatchPlan(batch, sg.TileCfg(256, 8, 512, 1, 0, 0, 0, 256, 64, 4, order))
+    xd = dev(x)
+    y = torch.zeros_like(xd)
+    s = torch.zeros(len(row_off) - 1, dtype=torch.float64, device="cuda")
+    plan.run_bounded(xd, y, s, wait_limit_ns=1_000_000, skip_chunk=0)
+    torch.cuda.synchronize()
+    with pytest.raises(sg.SymError) as e:
+        plan.check()
+    assert e.value.code == -7   # SYM_E_TIMEOUT
+    plan.clear_status()
+    plan.run(xd, y, s)
+    plan.check()
+    check_against_oracle([(host(y), host(s))], row_off, rowptr, col, v, x)
+    # the hook with nothing withheld is a normal run
+    plan.run_bounded(xd, y, s, wait_limit_ns=1_000_000)
+    plan.check()
+    check_against_oracle([(host(y), host(s))], row_off, rowptr, col, v, x)

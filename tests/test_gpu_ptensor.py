@@ -164,3 +164,52 @@ def test_expand_baseline_matches_oracle(parts, dims):
         ref, ref_abs = oracle.pmttkrp_enum(parts, dims, cidx, cval, F64, out)
         assert oracle.componentwise_error(host(Ms), ref, ref_abs) <= TOL_F32
         assert oracle.componentwise_error(host(Me), ref, ref_abs) <= TOL_F32
+
+
+PARTITIONS3 = [((1, 2), (40, 50)), ((2, 1), (50, 40)), ((1, 1, 1), (30, 40, 50)), ((3,), (45,))]
+
+
+@pytest.mark.parametrize("parts,dims", PARTITIONS3)
+@pytest.mark.parametrize("rank", [4, 12, 32, 128])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_pttm_matches_oracle(parts, dims, rank, bf16):
+    """Mode-1 TTM of a partially symmetric order-3 tensor, full layout (and packed where modes 2, 3 share a
+    part), every equality pattern inside every part, ragged entry counts."""
+    sg = need_gpu()
+    T = synth.ptensor_small_all_patterns(parts, dims, 11, density=0.15)
+    X = sg.PTensor(dev(T.idx), dev(T.val), parts, dims)
+    cidx, cval = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+    Fd, F64, Fb = factors(dims[:1], rank, 9, bf16)
+    used = Fb[0] if bf16 else F64[0]
+    want, wabs = oracle.pttm_enum(parts, dims, cidx, cval, used)
+    got = host(X.ttm(Fd[0], "full")).reshape(want.shape)
+    assert oracle.componentwise_error(got, want, wabs) <= TOL_F32
+    if bf16:
+        w32, a32 = oracle.pttm_enum(parts, dims, cidx, cval, F64[0])
+        assert oracle.componentwise_error(got, w32, a32) <= TOL_BF16
+    if parts in ((1, 2), (3,)):
+        d = dims[-1]
+        pk = host(X.ttm(Fd[0], "packed"))
+        j, l = np.triu_indices(d)
+        ref = want[j, l].reshape(-1)
+        assert oracle.componentwise_error(pk, ref, wabs[j, l].reshape(-1)) <= TOL_F32
+    else:
+        with pytest.raises(sg.SymError):
+            X.ttm(Fd[0], "packed")
+    X.close()
+
+
+def test_pttm_one_part_matches_symmetric_ttm():
+    """One part of three modes is full symmetry: the same output as sym_ttm on the symmetric tensor."""
+    sg = need_gpu()
+    T = synth.tensor_uniform(3, 60, 4000, 12)
+    Xp = sg.PTensor(dev(T.idx), dev(T.val), (3,), (60,))
+    Xs = sg.SymTensor(dev(T.idx), dev(T.val), 60)
+    B = dev(synth.factor_normal(60, 16, 12))
+    a = host(Xp.ttm(B, "packed"))
+    b = host(Xs.ttm(B, "packed"))
+    cidx, cval = oracle.canonicalize(3, 60, T.idx, T.val)
+    want, wabs = oracle.ttm_enum(3, 60, cidx, cval, synth.factor_normal(60, 16, 12).astype(np.float64))
+    j, l = np.triu_indices(60)
+    assert oracle.componentwise_error(a, want[j, l].reshape(-1), wabs[j, l].reshape(-1)) <= TOL_F32
+    assert oracle.componentwise_error(b.reshape(-1), want[j, l].reshape(-1), wabs[j, l].reshape(-1)) <= TOL_F32

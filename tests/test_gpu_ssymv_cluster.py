@@ -161,3 +161,36 @@ def test_cluster_form_from_several_host_threads():
         t.join()
     for k in range(len(cases)):
         assert len(errs[k]) == 20 and max(errs[k]) <= TOL_F32, (cases[k], errs[k][:3])
+
+
+@pytest.mark.parametrize("skip_to", [3, 0])
+def test_cluster_inbox_wait_runs_out_without_fault(skip_to):
+    """The bounded inbox wait made to run out: no CTA pushes into CTA skip_to's inbox (nothing is left in
+    flight towards it), the wait limit is 1 ms; that CTA's rows come back NaN (and SYPRD when it is CTA 0),
+    every other row is exact, and the next normal call is clean."""
+    sg = need_gpu()
+    n, nnz = 2000, 20000
+    A = synth.upper_csr_uniform(n, nnz, 41)
+    x = synth.vector_uniform(n, 42)
+    rp, cl, vl, xd = dev(A.rowptr), dev(A.col), dev(A.val), dev(x)
+    y, s = sg.spmv_cluster_bounded(n, rp, cl, vl, xd, wait_limit_ns=1_000_000, skip_to=skip_to)
+    torch.cuda.synchronize()
+    yh = host(y)
+    bad = np.isnan(yh)
+    assert bad.any()
+    rows = np.nonzero(bad)[0]
+    assert rows.max() - rows.min() + 1 == len(rows)   # one contiguous slice: the skipped CTA's rows
+    yr, ya = oracle.ssymv(n, A.rowptr, A.col, A.val, x.astype(np.float64))
+    ok = ~bad
+    assert oracle.componentwise_error(yh[ok], yr[ok], ya[ok]) <= TOL_F32
+    sr, sa = oracle.syprd(n, A.rowptr, A.col, A.val, x.astype(np.float64))
+    if skip_to == 0:
+        assert rows.min() == 0 and np.isnan(float(s.item()))
+    else:
+        assert rows.min() > 0 and abs(float(s.item()) - sr) <= TOL_F32 * sa
+    # a normal run afterwards, through the hook with no skip and through sym_spmv
+    y2, s2 = sg.spmv_cluster_bounded(n, rp, cl, vl, xd)
+    y3, s3 = sg.spmv(n, rp, cl, vl, xd, syprd=True)
+    for yy, ss in ((y2, s2), (y3, s3)):
+        assert oracle.componentwise_error(host(yy), yr, ya) <= TOL_F32
+        assert abs(float(ss.item()) - sr) <= TOL_F32 * sa

@@ -16,9 +16,9 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
 # (function whose body is edited, old text, new text, pin that must fail)
 MUTANTS = {
-    "enum_identity_only": ("orc_mttkrp_enum", "} while (next_perm(c, order));", "} while (0);",
+    "enum_identity_only": ("mttkrp_enum_range", "} while (next_perm(c, order));", "} while (0);",
                            lambda: pins.test_mttkrp_vs_dense_bruteforce(3, 6, 0)),
-    "enum_dropped_factor": ("orc_mttkrp_enum", "for (int q = 1; q < order; ++q)", "for (int q = 2; q < order; ++q)",
+    "enum_dropped_factor": ("mttkrp_enum_range", "for (int q = 1; q < order; ++q)", "for (int q = 2; q < order; ++q)",
                             lambda: pins.test_mttkrp_vs_dense_bruteforce(4, 5, 0)),
     "runs_wrong_weight": ("orc_mttkrp_runs", "int64_t den = fact(m[t] - 1);", "int64_t den = fact(m[t]);",
                           lambda: pins.test_paper_normalized_update_counts("runs")),
@@ -50,6 +50,10 @@ MUTANTS = {
                                 "sort_tuple(r[e].c, order);", lambda: pins.test_pcanonicalize_properties()),
     "pmttkrp_drops_leading_factors": ("orc_pmttkrp_enum", "if (q != f) t *= fq[q]", "if (q > f) t *= fq[q]",
                                       lambda: pins.test_pmttkrp_vs_dense_bruteforce((1, 2), (4, 5))),
+    "pttm_identity_only": ("orc_pttm_enum", "} while (next_part_perm(c, order, nparts, part));", "} while (0);",
+                           lambda: pins.test_pttm_vs_dense_bruteforce((1, 2), (4, 5))),
+    "pttm_wrong_factor_row": ("orc_pttm_enum", "v * B[(int64_t)c[0] * R + r]", "v * B[(int64_t)c[1] * R + r]",
+                              lambda: pins.test_pttm_contracted_again_is_pmttkrp((3,), (5,))),
     "counts_wrong_fibers": ("orc_counts", "if (e == 0 || c[0] != prev[0]) *root_fibers += 1;",
                             "*root_fibers += 1;", lambda: pins.test_counts_closed_forms(3)),
 }
@@ -63,8 +67,8 @@ def build_mutant(tmp_path, func, old, new):
     c = tmp_path / "mut.c"
     c.write_text(mut)
     so = tmp_path / "libmut.so"
-    subprocess.check_call(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
-                           str(c), "-lm"])
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-o",
+                           str(so), str(c), "-lm"])
     return str(so)
 
 

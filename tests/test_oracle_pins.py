@@ -185,6 +185,18 @@ def test_mttkrp_vs_dense_bruteforce(order, n, seed):
     assert np.allclose(Ma, dense_mttkrp_abs(X, B), rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("order,n", [(3, 6), (4, 5), (5, 4)])
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_mttkrp_threads_vs_dense_bruteforce(order, n, threads):
+    """The multi-threaded timing form equals the dense brute force (and so the definitional form)."""
+    T = synth.tensor_small_all_patterns(order, n, 5)
+    cidx, cval = canon(T)
+    B = synth.factor_normal(n, 5, 5).astype(np.float64)
+    want = dense_mttkrp(dense_full(order, n, cidx, cval), B)
+    Mt = oracle.mttkrp_enum_threads(order, n, cidx, cval, B, threads)
+    assert np.allclose(Mt, want, rtol=1e-12, atol=1e-12)
+
+
 def test_mttkrp_row_mask_matches_full():
     T = synth.tensor_small_all_patterns(4, 6, 3)
     cidx, cval = canon(T)
@@ -505,6 +517,49 @@ def test_pmttkrp_vs_dense_bruteforce(parts, dims):
         assert np.allclose(M, dense_pmttkrp(X, parts, F, out), rtol=1e-12, atol=1e-13), out
         assert np.allclose(Ma, dense_pmttkrp(np.abs(X), parts, [np.abs(f) for f in F], out), rtol=1e-12,
                            atol=1e-13), out
+
+
+PARTITIONS3 = [((1, 2), (4, 5)), ((2, 1), (5, 4)), ((1, 1, 1), (3, 4, 5)), ((3,), (5,))]
+
+
+@pytest.mark.parametrize("parts,dims", PARTITIONS3)
+def test_pttm_vs_dense_bruteforce(parts, dims):
+    """Mode-1 TTM of a partially symmetric order-3 tensor against the dense contraction of the tensor
+    expanded over every inside-part arrangement."""
+    T = synth.ptensor_small_all_patterns(parts, dims, 7, density=0.6)
+    cidx, cval = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+    B = synth.factor_normal(dims[0], 3, 21).astype(np.float64)
+    X = dense_partial(parts, dims, cidx, cval)
+    Cm, Ca = oracle.pttm_enum(parts, dims, cidx, cval, B)
+    assert np.allclose(Cm, np.einsum("kjl,kr->jlr", X, B), rtol=1e-12, atol=1e-13)
+    assert np.allclose(Ca, np.einsum("kjl,kr->jlr", np.abs(X), np.abs(B)), rtol=1e-12, atol=1e-13)
+    if parts in ((1, 2), (3,)):   # modes 2 and 3 in one part: the output is symmetric
+        assert np.array_equal(Cm, Cm.transpose(1, 0, 2))
+
+
+@pytest.mark.parametrize("parts,dims", PARTITIONS3)
+def test_pttm_contracted_again_is_pmttkrp(parts, dims):
+    """Contracting the TTM output with the factors of modes 2 and 3 gives B^T weighted MTTKRP rows of part 0:
+    sum_{j,l} C[j,l,r] F2[j,r] F3[l,r] = sum_k B[k,r] M0[k,r]."""
+    T = synth.ptensor_small_all_patterns(parts, dims, 8, density=0.7)
+    cidx, cval = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+    R = 4
+    F = [synth.factor_normal(d, R, 30 + p).astype(np.float64) for p, d in enumerate(dims)]
+    owner = [p for p, sz in enumerate(parts) for _ in range(sz)]
+    Cm = oracle.pttm_enum(parts, dims, cidx, cval, F[owner[0]], want_abs=False)
+    M0 = oracle.pmttkrp_enum(parts, dims, cidx, cval, F, 0, want_abs=False)
+    lhs = np.einsum("jlr,jr,lr->r", Cm, F[owner[1]], F[owner[2]])
+    rhs = np.einsum("kr,kr->r", F[owner[0]], M0)
+    assert np.allclose(lhs, rhs, rtol=1e-11, atol=1e-12)
+
+
+def test_pttm_one_part_is_full_symmetry_ttm():
+    T = synth.tensor_small_all_patterns(3, 7, 19, density=0.6)
+    cidx, cval = oracle.canonicalize(3, 7, T.idx, T.val)
+    B = synth.factor_normal(7, 3, 19).astype(np.float64)
+    got = oracle.pttm_enum((3,), (7,), cidx, cval, B, want_abs=False)
+    want = oracle.ttm_enum(3, 7, cidx, cval, B, want_abs=False)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-13)
 
 
 @pytest.mark.parametrize("order,n", [(2, 6), (3, 6), (4, 5), (5, 4)])
