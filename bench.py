@@ -216,6 +216,29 @@ def oracle_sample_rate(T, rank, target_s=12.0):
                                           f"rank {rank}, {dt:.1f} s"}
 
 
+def oracle_threads_rate(T, rank, target_s=8.0):
+    """The FP64 oracle's threaded definitional MTTKRP on every core this process may run on
+    (len(os.sched_getaffinity(0))), on a bounded sample of the workload."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    B = synth.factor_normal(T.n, rank, MAIN["seed"]).astype(np.float64)
+    probe = min(T.nnz, 400_000)
+    cidx, cval = oracle.canonicalize(T.order, T.n, T.idx[:, :probe], T.val[:probe])
+    t0 = time.perf_counter()
+    oracle.mttkrp_enum_threads(T.order, T.n, cidx, cval, B, cores)
+    rate = probe / max(time.perf_counter() - t0, 1e-9)
+    size = int(min(T.nnz, max(probe, rate * target_s)))
+    cidx, cval = oracle.canonicalize(T.order, T.n, T.idx[:, :size], T.val[:size])
+    t0 = time.perf_counter()
+    oracle.mttkrp_enum_threads(T.order, T.n, cidx, cval, B, cores)
+    dt = time.perf_counter() - t0
+    return cidx.shape[1] / dt, {"kind": "oracle", "cores": cores,
+                                "sample": f"first {size} of {T.nnz} entries of the shuffled coordinate list "
+                                          f"({cidx.shape[1]} canonical), FP64 definitional MTTKRP on {cores} host "
+                                          f"threads (contiguous entry ranges, private outputs summed in order), "
+                                          f"rank {rank}, {dt:.1f} s"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -237,7 +260,9 @@ def run_reference(args):
     out = {"impl": "reference", "metric": "canonical_nnz_per_s", "value": v, "unit": "canonical nnz/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD_NAME, "sample_canonical_nnz": int(cidx.shape[1])},
+           "config": {"workload": WORKLOAD_NAME, "sample_canonical_nnz": int(cidx.shape[1]), "same_config": False,
+                      "note": "the oracle arm times a bounded sample of the workload's entries each step (a full "
+                              "20M-entry step takes about 10 s on one core); the metric is per canonical entry"},
            "cpu_baseline": {"value": v, "unit": "canonical nnz/s", "cores": 1, "kind": "oracle",
                             "sample": f"first {sample} entries of the shuffled coordinate list, FP64 definitional "
                                       f"MTTKRP per step"},
@@ -248,15 +273,62 @@ def run_reference(args):
 # ---------------------------------------------------------------------------- GPU arm
 
 def timed_steps(torch, step, K, flush_buf, stream):
-    """Runs K steps, each between its own CUDA events; L2 flushed before each step."""
+    """Runs K steps, each between its own CUDA events; L2 flushed before each step (flush_buf None: warm L2)."""
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     for k in range(K):
-        flush_buf.fill_(k & 0xff)
+        if flush_buf is not None:
+            flush_buf.fill_(k & 0xff)
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in evs]
+
+
+def measure_ceilings(sg):
+    """Measured ceilings of the primitive operations (sym_ceiling_run), each timed alone on this GPU:
+    FP32 FMA issue, random L2 row gathers / vector row reductions / both at the three MTTKRP row shapes,
+    and a streaming copy of our own.  The denominators of the per-kernel roofline fractions."""
+    c = {"fp32_fma_flop_per_s": sg.ceiling("fma", ops=1 << 28, reps=5)[0]}
+    for n, R in ((100_000, 64), (20_000, 32), (2_000, 16)):
+        for k in ("row_gather", "row_red", "gather_red"):
+            c[f"{k}_rows_per_s_n{n}_r{R}"] = sg.ceiling(k, rows=n, rank=R, ops=1 << 25, reps=5)[0]
+    c["hbm_copy_bytes_per_s"] = sg.ceiling("hbm_copy", rows=1 << 27, ops=0, reps=10)[0]
+    return c
+
+
+def l2_roof(gathers, reds, R, ceil, n_tag, kernel_ms):
+    """Roofline of an L2-bound MTTKRP pass: it moves `gathers` random factor rows and `reds` random vector row
+    reductions of R floats through L2.  The ceiling time for that mix is taken from the measured primitives:
+    min(gathers, reds) pairs at the gather+reduction rate, the rest at the gather-only or reduction-only rate."""
+    g_rate = ceil[f"row_gather_rows_per_s_{n_tag}"]
+    r_rate = ceil[f"row_red_rows_per_s_{n_tag}"]
+    gr_rate = ceil[f"gather_red_rows_per_s_{n_tag}"]
+    pairs = min(gathers, reds)
+    t_ceil = pairs / gr_rate + (gathers - pairs) / g_rate + (reds - pairs) / r_rate
+    row_bytes = (gathers + reds) * R * 4
+    t = kernel_ms * 1e-3
+    return {"bound": "l2", "achieved": row_bytes / t / 1e9, "peak": row_bytes / t_ceil / 1e9, "unit": "GB/s",
+            "frac": t_ceil / t, "row_gathers": int(gathers), "row_reductions": int(reds),
+            "peak_source": "measured (sym_ceiling_run: random row gathers / vector row reductions in L2, this run)"}
+
+
+def sampled_row_errors(order, n, idx, val, B32, M, Mb=None, Bb=None, rows=64, seed=0):
+    """Componentwise error of the GPU result on a sample of output rows, against the FP64 oracle (the
+    definitional enumeration restricted to those rows).  BF16: against the oracle on the FP32 factor (gate
+    1e-2) and on the BF16-rounded factor (expected <= 1e-5)."""
+    import oracle
+    sel = np.unique(np.concatenate([np.arange(min(8, n)),
+                                    synth.Stream(seed, tag=91).randint(rows, n)]))
+    cidx, cval = oracle.canonicalize(order, n, idx, val)
+    ref, ra = oracle.mttkrp_enum(order, n, cidx, cval, B32.astype(np.float64), rows=sel)
+    out = {"rows_sampled": int(len(sel)),
+           "f32_componentwise": oracle.componentwise_error(M[sel], ref[sel], ra[sel])}
+    if Mb is not None:
+        out["bf16_vs_f32_factor_componentwise"] = oracle.componentwise_error(Mb[sel], ref[sel], ra[sel])
+        rb, rba = oracle.mttkrp_enum(order, n, cidx, cval, Bb.astype(np.float64), rows=sel)
+        out["bf16_vs_bf16_factor_componentwise"] = oracle.componentwise_error(Mb[sel], rb[sel], rba[sel])
+    return out
 
 
 def run_ours(args):
@@ -325,11 +397,23 @@ def run_ours(args):
     kw_bytes = 8 * (2 if info["key_bits"] * 3 > 64 else 1)
     alg_bytes = info["nnz_strict"] * (kw_bytes + 4) + T.n * MAIN["rank"] * 4 * 3   # stream + B read + M rmw
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_mttkrp_strict<3,1,16,f32>", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-            "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_kind,
-            "traffic": recorded_traffic("mttkrp_strict", WORKLOAD_NAME),
-            "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": per_launch_ms,
-            "share_of_step": strict_ms / max(sum(v[1] for v in prof.values()), 1e-12)}
+    # The kernel's binding roof is L2, not HBM: per strict entry it gathers the leaf's factor row and reduces
+    # into the leaf's output row (R floats each), and per (c1, c2) fiber and per c1 fiber one more of each.
+    # Those algorithmic row operations, at the measured random-row ceilings of this GPU, give the ceiling time.
+    ceil = measure_ceilings(sg) if D.rank == 0 and not args.kernel_only else None
+    if ceil is not None:
+        rows_ops = info["nnz_strict"] + info["l2_fibers"] + info["root_fibers"]
+        roof = l2_roof(rows_ops, rows_ops, MAIN["rank"], ceil, "n100000_r64", per_launch_ms)
+    else:
+        roof = {"bound": "l2", "achieved": None, "peak": None, "unit": "GB/s", "frac": None}
+    roof.update({"kernel": "k_mttkrp_strict<3,1,16,f32>", "traffic": recorded_traffic("mttkrp_strict", WORKLOAD_NAME),
+                 "launch_ms": per_launch_ms,
+                 "share_of_step": strict_ms / max(sum(v[1] for v in prof.values()), 1e-12),
+                 "hbm": {"algorithmic_bytes_per_launch": alg_bytes, "achieved_gbs": achieved, "peak_gbs": hbm_peak,
+                         "frac": achieved / hbm_peak, "peak_source": peak_kind},
+                 "fp32_issue": {"flop_per_launch": info["nnz_strict"] * 3 * 3 * MAIN["rank"],
+                                "frac": (info["nnz_strict"] * 9 * MAIN["rank"] / (per_launch_ms * 1e-3)
+                                         / ceil["fp32_fma_flop_per_s"]) if ceil else None}})
 
     if args.kernel_only:
         if D.rank == 0:
@@ -338,10 +422,23 @@ def run_ours(args):
         D.close()
         return
 
+    # the same step with L2 left warm between steps (inputs stay L2-resident: B, M and part of the stream)
+    warm = timed_steps(torch, step, max(5, min(args.steps, 20)), None, stream)
     extras = {"per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
+              "warm_l2_ms_per_step": float(np.mean(warm)),
               "mttkrp_config": tuned_cfg, "autotune_s": tune_s,
               "canonicalise_ms": create_ms, "tensor": {k: info[k] for k in (
                   "nnz", "nnz_strict", "nnz_diag", "expanded_nnz", "root_fibers", "l2_fibers")}}
+
+    # ---- error of the timed result on sampled rows, against the FP64 oracle
+    if D.rank == 0:
+        try:
+            Mh = M.cpu().numpy()
+            extras["error"] = sampled_row_errors(3, T.n, T.idx, T.val, Bh, Mh)
+            extras["error"]["gate"] = "f32 <= 1e-5 componentwise (FP64 oracle, sampled output rows)"
+        except Exception as e:
+            extras["error"] = {"error": repr(e)}
+        extras["ceilings"] = ceil
 
     # ---- CP-fit residual cost (FP64), same tensor
     Mr, res = X.mttkrp(B, residual=True, ws=ws_res)
@@ -445,6 +542,13 @@ def run_ours(args):
         meta["value"] = rate
         meta["unit"] = "canonical nnz/s"
         out["cpu_baseline"] = meta
+        try:
+            rate_t, meta_t = oracle_threads_rate(T, MAIN["rank"])
+            meta_t["value"] = rate_t
+            meta_t["unit"] = "canonical nnz/s"
+            out["cpu_baseline_all_cores"] = meta_t
+        except Exception as e:
+            out["cpu_baseline_all_cores"] = {"error": repr(e)}
     if D.rank == 0:
         print(json.dumps(out))
     D.close()
@@ -460,14 +564,31 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
         info = X.info()
         B32 = synth.factor_normal(n, rank, 2)
         r = {"canonical_nnz": info["nnz"], "nnz_diag": info["nnz_diag"]}
+        res = {}
+        X.add_leaf_index()
+        tune_cache = os.path.join(__import__("tempfile").gettempdir(), "symgpu_tune.txt")
         for tag, Bt in (("f32", torch.from_numpy(B32).to(dev)),
                         ("bf16", torch.from_numpy(synth.bf16_rne(B32).view(np.int16)).to(dev).view(torch.bfloat16))):
             M = torch.empty((n, rank), dtype=torch.float32, device=dev)
+            cfg, _ = X.autotune(Bt, M=M, cache_path=tune_cache)
             for _ in range(3):
                 X.mttkrp(Bt, M=M)
+            sg.profile_reset()
+            sg.profile_enable(True)
             t = timed_steps(torch, lambda: X.mttkrp(Bt, M=M), 10, flush, stream)
+            sg.profile_enable(False)
+            prof = sg.profile_read()
             ms = float(np.mean(t))
-            r[tag] = {"ms": ms, "canonical_nnz_per_s": info["nnz"] / (ms * 1e-3)}
+            r[tag] = {"ms": ms, "canonical_nnz_per_s": info["nnz"] / (ms * 1e-3), "mttkrp_config": cfg,
+                      "per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()}}
+            X.mttkrp(Bt, M=M)
+            res[tag] = M.cpu().numpy()
+        try:
+            r["error"] = sampled_row_errors(order, n, T.idx, T.val, B32, res["f32"], res["bf16"],
+                                            synth.bf16_to_f32(synth.bf16_rne(B32)))
+            r["error"]["gate"] = "f32 <= 1e-5, bf16 vs f32 factor <= 1e-2 (componentwise, FP64 oracle)"
+        except Exception as e:
+            r["error"] = {"error": repr(e)}
         try:
             E = X.expanded()
             Me = torch.empty((n, rank), dtype=torch.float32, device=dev)

@@ -100,6 +100,10 @@ sym_status sym_profile_reset(void);
  *   SYM_CEIL_SMEM_U32    the same with 32-bit integer atomics; rows/s.
  *   SYM_CEIL_HBM_COPY    streaming copy of `rows` 16-byte elements; bytes/s
  *                        (read + write).
+ *   SYM_CEIL_BULK_GATHER random rows read with one bulk copy (cp.async.bulk)
+ *                        per row into shared memory; rows/s.
+ *   SYM_CEIL_BULK_RED    random rows reduced from shared memory with one bulk
+ *                        reduction (cp.reduce.async.bulk .add.f32) per row; rows/s.
  * `ops` row operations (FMA: about ops / 2^11 FLOP per thread) per launch,
  * `reps` timed launches after one warm-up.  buf [device, 256-byte aligned,
  * >= sym_ceiling_bytes] is scratch, overwritten.  Synchronous; *ms = mean time
@@ -111,7 +115,9 @@ typedef enum {
     SYM_CEIL_GATHER_RED = 3,
     SYM_CEIL_SMEM_F32 = 4,
     SYM_CEIL_SMEM_U32 = 5,
-    SYM_CEIL_HBM_COPY = 6
+    SYM_CEIL_HBM_COPY = 6,
+    SYM_CEIL_BULK_GATHER = 7,
+    SYM_CEIL_BULK_RED = 8
 } sym_ceiling_kind;
 /* Bytes of scratch for sym_ceiling_run (0 = invalid arguments). */
 size_t sym_ceiling_bytes(int kind, int64_t rows, int rank);
@@ -469,7 +475,11 @@ typedef enum {
                                     accumulated and rows [0, HB) of B read in shared memory, several leaf
                                     gathers in flight; with leaf_index = 1 and a leaf index, two passes with no
                                     per-entry reduction: the canonical stream for every position but the leaf,
-                                    then the leaf index for its root (the largest index of each tuple) */
+                                    then the leaf index for its root (the largest index of each tuple) */,
+    SYM_MTTKRP_LANE = 5          /* chunked warps whose lanes decode one entry each and find its first changed
+                                    fiber level, the group then stepping through the entries with one broadcast
+                                    per entry; with leaf_index = 1 and a leaf index, the same two passes as the
+                                    hot kernel */
 } sym_mttkrp_kernel;
 typedef struct {
     int32_t strict_kernel;     /* sym_mttkrp_kernel for the strict stream */
@@ -485,8 +495,8 @@ typedef struct {
                                   sym_tensor_add_leaf_index) instead of one reduction per entry; hot kernel:
                                   1 = walk the leaf index instead of the canonical stream (ignored without one) */
     int32_t vec_per_lane;      /* plain kernel: float4 column groups per lane, 1 or 2 (2 needs rank >= 8);
-                                  hot kernel: leaf gathers issued together per lane group, 1 or 4 (4 needs
-                                  rank >= 16) */
+                                  hot and lane kernels: leaf gathers issued together per lane group, 1 or 4
+                                  (4 needs rank >= 16) */
     int32_t stream_hint;       /* plain kernel: 1 = read the canonical stream with evict-first loads so it does not
                                   displace factor rows from L1 / L2 */
     int32_t l1_pref;           /* plain kernel: 1 = ask for the largest L1 (no shared-memory carveout) */

@@ -114,7 +114,7 @@ class MttkrpCfg(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-MTTKRP_PLAIN, MTTKRP_PIPELINED, MTTKRP_UNFACTORISED, MTTKRP_STAGED, MTTKRP_HOT = 0, 1, 2, 3, 4
+MTTKRP_PLAIN, MTTKRP_PIPELINED, MTTKRP_UNFACTORISED, MTTKRP_STAGED, MTTKRP_HOT, MTTKRP_LANE = 0, 1, 2, 3, 4, 5
 
 
 class ProfileEntry(C.Structure):
@@ -298,7 +298,8 @@ def profile_read() -> dict:
 
 # ------------------------------------------------------------------ SSYMV / SYPRD
 
-CEILINGS = {"fma": 0, "row_gather": 1, "row_red": 2, "gather_red": 3, "smem_f32": 4, "smem_u32": 5, "hbm_copy": 6}
+CEILINGS = {"fma": 0, "row_gather": 1, "row_red": 2, "gather_red": 3, "smem_f32": 4, "smem_u32": 5, "hbm_copy": 6,
+            "bulk_gather": 7, "bulk_red": 8}
 
 
 def ceiling(kind: str, rows: int = 0, rank: int = 64, ops: int = 1 << 26, reps: int = 10, device=None,

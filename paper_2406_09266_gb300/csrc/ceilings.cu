@@ -114,6 +114,96 @@ __global__ void __launch_bounds__(CEIL_THREADS) k_ceil_smem(int H, int R, int64_
     if (threadIdx.x == 0 && tab[0] == -1.0f) out[blockIdx.x & 1023] = tab[1];
 }
 
+// ---------------------------------------------------------------- bulk-copy (TMA engine) row operations
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Lane 0 of each warp moves CEIL_BULK rows per iteration with single-instruction
+// bulk copies: BULK_GATHER copies random rows of B (R floats each) into the
+// warp's shared buffer (completion counted on an mbarrier; the wait is bounded
+// and records a timeout instead of hanging); BULK_RED reduces the warp's shared
+// buffer into random rows of M (cp.reduce.async.bulk .add.f32), waiting for the
+// reads of the previous group before the next one.  Rows/s = CEIL_BULK x
+// iterations x warps / time.
+constexpr int CEIL_BULK = 8;
+
+template <bool RED>
+__global__ void __launch_bounds__(CEIL_THREADS) k_ceil_bulk(const float* __restrict__ Bt, float* __restrict__ Mt,
+                                                          int64_t n, int R, int64_t iters, float* out) {
+    extern __shared__ __align__(128) unsigned char bulk_smem[];
+    __shared__ __align__(8) uint64_t bar[CEIL_THREADS / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t row_bytes = (uint32_t)R * 4u;
+    float* buf = reinterpret_cast<float*>(bulk_smem) + (size_t)warp * CEIL_BULK * R;
+    for (int k = lane; k < CEIL_BULK * R; k += 32) buf[k] = 1.0f;
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar[warp])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the buffer is visible to the bulk copies
+    __syncwarp();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float acc = 0.f;
+    uint32_t phase = 0;
+    for (int64_t it = 0; it < iters; ++it) {
+        if (lane == 0) {
+            if (!RED)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(&bar[warp])),
+                             "r"(row_bytes * CEIL_BULK)
+                             : "memory");
+#pragma unroll
+            for (int k = 0; k < CEIL_BULK; ++k) {
+                const uint32_t h = fmix32((uint32_t)((it * nw + gw) * CEIL_BULK + k) * 2u + 1u);
+                const int64_t r = pick_row(h, n);
+                if (RED)
+                    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;\n" ::"l"(
+                                     Mt + r * R),
+                                 "r"(smem_addr(buf + k * R)), "r"(row_bytes)
+                                 : "memory");
+                else
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                            smem_addr(buf + k * R)),
+                        "l"(Bt + r * R), "r"(row_bytes), "r"(smem_addr(&bar[warp]))
+                        : "memory");
+            }
+            if (RED) {
+                asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+            }
+        }
+        if (!RED) {
+            // bounded wait for this iteration's rows (records a timeout, never hangs); on a timeout
+            // it waits once more, bounded, for the copies still in flight, then stops
+            uint32_t ok = 0;
+            for (int spin = 0; spin < (1 << 22) && !ok; ++spin)
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
+                    "p;\n}\n"
+                    : "=r"(ok)
+                    : "r"(smem_addr(&bar[warp])), "r"(phase)
+                    : "memory");
+            if (!ok) {
+                if (lane == 0) atomicOr(reinterpret_cast<unsigned*>(out) + 1023, 2u);
+                for (int spin = 0; spin < (1 << 22) && !ok; ++spin)
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, "
+                        "1, 0, p;\n}\n"
+                        : "=r"(ok)
+                        : "r"(smem_addr(&bar[warp])), "r"(phase)
+                        : "memory");
+                break;
+            }
+            phase ^= 1u;
+            acc += buf[lane % R];
+            __syncwarp();  // every lane has read before the next copies overwrite the buffer
+        }
+    }
+    if (RED && lane == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+    if (acc == -1.0f) out[0] = acc;
+}
+
 __global__ void k_ceil_copy(const float4* __restrict__ a, float4* __restrict__ b, int64_t n4) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += (int64_t)gridDim.x * blockDim.x)
         b[k] = __ldcs(a + k);
@@ -144,6 +234,14 @@ sym_status launch_rows(int kind, float* buf, int64_t n, int R, int64_t iters, un
             SYM_TRY(raise_smem_limit(k_ceil_smem<L, true>, smem));
             k_ceil_smem<L, true><<<grid, CEIL_THREADS, smem, s>>>(H, R, iters, out);
             break;
+        case SYM_CEIL_BULK_GATHER:
+            SYM_TRY(raise_smem_limit(k_ceil_bulk<false>, smem));
+            k_ceil_bulk<false><<<grid, CEIL_THREADS, smem, s>>>(Bt, Mt, n, R, iters, out);
+            break;
+        case SYM_CEIL_BULK_RED:
+            SYM_TRY(raise_smem_limit(k_ceil_bulk<true>, smem));
+            k_ceil_bulk<true><<<grid, CEIL_THREADS, smem, s>>>(Bt, Mt, n, R, iters, out);
+            break;
         default:
             return SYM_E_INVALID;
     }
@@ -151,7 +249,8 @@ sym_status launch_rows(int kind, float* buf, int64_t n, int R, int64_t iters, un
     return SYM_OK;
 }
 
-bool row_kind(int kind) { return kind >= SYM_CEIL_ROW_GATHER && kind <= SYM_CEIL_SMEM_U32; }
+bool bulk_kind(int kind) { return kind == SYM_CEIL_BULK_GATHER || kind == SYM_CEIL_BULK_RED; }
+bool row_kind(int kind) { return (kind >= SYM_CEIL_ROW_GATHER && kind <= SYM_CEIL_SMEM_U32) || bulk_kind(kind); }
 bool smem_kind(int kind) { return kind == SYM_CEIL_SMEM_F32 || kind == SYM_CEIL_SMEM_U32; }
 
 }  // namespace
@@ -184,12 +283,16 @@ extern "C" sym_status sym_ceiling_run(int kind, void* buf, size_t buf_bytes, int
         smem = (size_t)rows * rank * sizeof(float);
         if (rows < 1 || smem > 200 * 1024) return SYM_E_INVALID;
     }
+    if (bulk_kind(kind)) smem = (size_t)(CEIL_THREADS / 32) * CEIL_BULK * rank * sizeof(float);
     // Launch shape: 8 CTAs of 256 threads per SM (row kinds: as resident as
     // shared memory allows), each group doing iters row operations.
     int ctas_per_sm = 8;
     if (smem_kind(kind)) ctas_per_sm = std::max<int>(1, std::min<int>(8, (int)((220 * 1024) / std::max<size_t>(smem, 1))));
     const unsigned grid = (unsigned)(sms * ctas_per_sm);
-    const int64_t groups = (int64_t)grid * (CEIL_THREADS / 32) * (row_kind(kind) ? (32 / lanes) : 1);
+    if (bulk_kind(kind)) ctas_per_sm = std::max<int>(1, std::min<int>(8, (int)((200 * 1024) / smem)));
+    const unsigned grid_b = (unsigned)(sms * ctas_per_sm);
+    const int64_t groups = bulk_kind(kind) ? (int64_t)grid_b * (CEIL_THREADS / 32) * CEIL_BULK
+                                           : (int64_t)grid * (CEIL_THREADS / 32) * (row_kind(kind) ? (32 / lanes) : 1);
     const int64_t iters = std::max<int64_t>(1, ops / std::max<int64_t>(groups, 1));
     float* fb = static_cast<float*>(buf);
 
@@ -206,6 +309,7 @@ extern "C" sym_status sym_ceiling_run(int kind, void* buf, size_t buf_bytes, int
             SYM_CHECK_LAUNCH();
             return SYM_OK;
         }
+        if (bulk_kind(kind)) return launch_rows<1>(kind, fb, rows, rank, iters, grid_b, smem, (int)rows, s);
         switch (lanes) {
             case 1: return launch_rows<1>(kind, fb, rows, rank, iters, grid, smem, (int)rows, s);
             case 2: return launch_rows<2>(kind, fb, rows, rank, iters, grid, smem, (int)rows, s);
@@ -216,8 +320,10 @@ extern "C" sym_status sym_ceiling_run(int kind, void* buf, size_t buf_bytes, int
             default: return SYM_E_INVALID;
         }
     };
-    if (row_kind(kind) && !smem_kind(kind))
-        SYM_CUDA(cudaMemsetAsync(buf, 0, (size_t)2 * rows * rank * sizeof(float), s));
+    if (row_kind(kind) && !smem_kind(kind)) {
+        if (bulk_kind(kind) && !aligned(buf, 16)) return SYM_E_INVALID;
+        SYM_CUDA(cudaMemsetAsync(buf, 0, (size_t)2 * rows * rank * sizeof(float) + 4096, s));
+    }
     SYM_TRY(launch());  // warm-up (and L2 fill for the row kinds)
     cudaEvent_t e0, e1;
     SYM_CUDA(cudaEventCreate(&e0));

@@ -26,9 +26,9 @@ namespace symgpu {
 namespace {
 
 constexpr int GRAM_ROWS = 32;
-constexpr int GRAM_PPT = 20;       // (r, s) pairs per thread
-constexpr int GRAM_THREADS = 512;  // 512 x 20 >= 8256 pairs of R = 128
-static_assert(GRAM_THREADS * GRAM_PPT >= 128 * 129 / 2, "one CTA must cover every pair of the largest rank");
+constexpr int GRAM_THREADS = 544;          // >= 528 blocks of 4 x 4 pairs in the upper block triangle of R = 128
+constexpr int GRAM_ROWS_PER_CTA = 128;     // rows of B per CTA (4 tiles)
+static_assert(GRAM_THREADS >= 32 * 33 / 2, "one CTA must cover every block of the largest rank");
 
 template <bool BF16>
 __device__ __forceinline__ float load_b(const void* B, int64_t i, int64_t ldb, int r) {
@@ -54,56 +54,73 @@ __device__ __forceinline__ void tri_pair(int p, int R, int* r_out, int* s_out) {
 }
 
 // G[r,s] += sum_i B[i,r] B[i,s] over this CTA's rows, for r <= s only (G is
-// symmetric); G is stored as the packed upper triangle.
+// symmetric); G is stored as the packed upper triangle.  Thread t owns one
+// 4 x 4 block (r in [4 bi, 4 bi + 4), s in [4 bj, 4 bj + 4)) of the upper block
+// triangle bi <= bj, so each staged row costs it two 16-byte shared loads for
+// 16 products.  Per 32-row tile every product is split exactly into two floats
+// and accumulated as a double-float pair; the tile sums are added in FP64.
 template <bool BF16>
 __global__ void __launch_bounds__(GRAM_THREADS) k_gram(const void* __restrict__ B, int64_t n, int64_t ldb, int R,
                                                        double* __restrict__ G, int64_t rows_per_cta) {
     extern __shared__ float tile[];  // GRAM_ROWS x R
-    const int pairs = R * (R + 1) / 2;
-    double acc[GRAM_PPT];
-    int pr_rs[GRAM_PPT];  // r << 16 | s
+    const int RB = R / 4;
+    const int nblk = RB * (RB + 1) / 2;
+    int bi = 0, bj = 0;
+    const bool active = (int)threadIdx.x < nblk;
+    if (active) tri_pair((int)threadIdx.x, RB, &bi, &bj);
+    double acc[16];
 #pragma unroll
-    for (int k = 0; k < GRAM_PPT; ++k) {
-        acc[k] = 0.0;
-        const int pr = threadIdx.x + k * blockDim.x;
-        int r = 0, s = 0;
-        if (pr < pairs) tri_pair(pr, R, &r, &s);
-        pr_rs[k] = (r << 16) | s;
-    }
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
     const int64_t r1 = min(n, r0 + rows_per_cta);
     for (int64_t t0 = r0; t0 < r1; t0 += GRAM_ROWS) {
         const int rows = (int)((r1 - t0) < GRAM_ROWS ? (r1 - t0) : GRAM_ROWS);
         __syncthreads();
         for (int k = threadIdx.x; k < GRAM_ROWS * R; k += blockDim.x) {
-            int i = k / R, r = k % R;
+            const int i = k / R, r = k % R;
             tile[k] = (i < rows) ? load_b<BF16>(B, t0 + i, ldb, r) : 0.f;
         }
         __syncthreads();
+        if (!active) continue;
+        float hi[16], lo[16];
 #pragma unroll
-        for (int k = 0; k < GRAM_PPT; ++k) {
-            const int pr = threadIdx.x + k * blockDim.x;
-            if (pr >= pairs) break;
-            const int r = pr_rs[k] >> 16, s = pr_rs[k] & 0xffff;
-            float hi = 0.f, lo = 0.f;
-            for (int i = 0; i < rows; ++i) {
-                const float a = tile[i * R + r], b = tile[i * R + s];
-                const float p = a * b;
-                const float e = fmaf(a, b, -p);  // a*b == p + e exactly
-                const float t = hi + p;           // two-sum of hi and p
-                const float bp = t - hi;
-                const float err = (hi - (t - bp)) + (p - bp);
-                hi = t;
-                lo += err + e;
-            }
-            acc[k] += (double)hi + (double)lo;
+        for (int k = 0; k < 16; ++k) hi[k] = lo[k] = 0.f;
+        for (int i = 0; i < rows; ++i) {
+            const float4 a4 = *reinterpret_cast<const float4*>(tile + i * R + 4 * bi);
+            const float4 b4 = *reinterpret_cast<const float4*>(tile + i * R + 4 * bj);
+            const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int k = 4 * u + v;
+                    const float p = a[u] * b[v];
+                    const float e = fmaf(a[u], b[v], -p);  // a*b == p + e exactly
+                    const float t = hi[k] + p;             // two-sum of hi and p
+                    const float bp = t - hi[k];
+                    const float err = (hi[k] - (t - bp)) + (p - bp);
+                    hi[k] = t;
+                    lo[k] += err + e;
+                }
         }
-    }
 #pragma unroll
-    for (int k = 0; k < GRAM_PPT; ++k) {
-        const int pr = threadIdx.x + k * blockDim.x;
-        if (pr < pairs) atomicAdd(&G[pr], acc[k]);
+        for (int k = 0; k < 16; ++k) acc[k] += (double)hi[k] + (double)lo[k];
     }
+    if (!active) return;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = 4 * bi + u, sidx = 4 * bj + v;
+            if (r > sidx) continue;  // lower half of a diagonal block
+            atomicAdd(&G[r * R - r * (r - 1) / 2 + (sidx - r)], acc[4 * u + v]);
+        }
+}
+
+// CTA size of k_gram: one thread per 4 x 4 block of the upper block triangle.
+int gram_threads(int R) {
+    const int RB = R / 4;
+    return std::max(32, (RB * (RB + 1) / 2 + 31) / 32 * 32);
 }
 
 // xm += sum_{i,r} B[i,r] M[i,r] in FP64 (exact products).
@@ -181,12 +198,9 @@ sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int 
     if (!w.G || !w.xm) return SYM_E_NOMEM;
     SYM_CUDA(cudaMemsetAsync(ws, 0, c.used, s));
     const int sms = sm_count();
-    const int tri = R * (R + 1) / 2;
-    const int threads = std::max(128, std::min(GRAM_THREADS, ((tri + GRAM_PPT - 1) / GRAM_PPT + 31) / 32 * 32));
-    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(2 * sms, (X->n + GRAM_ROWS - 1) / GRAM_ROWS));
-    int64_t rows_per_cta = (X->n + ctas - 1) / ctas;
-    rows_per_cta = (rows_per_cta + GRAM_ROWS - 1) / GRAM_ROWS * GRAM_ROWS;
-    const unsigned grid = (unsigned)((X->n + rows_per_cta - 1) / rows_per_cta);
+    const int threads = gram_threads(R);
+    const int64_t rows_per_cta = GRAM_ROWS_PER_CTA;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, (X->n + rows_per_cta - 1) / rows_per_cta);
     const size_t smem = sizeof(float) * GRAM_ROWS * R;
     {
         SYM_PROF("cpfit_gram", s);
@@ -214,13 +228,9 @@ sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int 
 sym_status gram_launch(int64_t n, const void* B, bool bf16, int R, int64_t ldb, double* G, cudaStream_t s) {
     SYM_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)R * (R + 1) / 2, s));
     if (n == 0) return SYM_OK;
-    const int sms = sm_count();
-    const int tri = R * (R + 1) / 2;
-    const int threads = std::max(128, std::min(GRAM_THREADS, ((tri + GRAM_PPT - 1) / GRAM_PPT + 31) / 32 * 32));
-    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(2 * sms, (n + GRAM_ROWS - 1) / GRAM_ROWS));
-    int64_t rows_per_cta = (n + ctas - 1) / ctas;
-    rows_per_cta = (rows_per_cta + GRAM_ROWS - 1) / GRAM_ROWS * GRAM_ROWS;
-    const unsigned grid = (unsigned)((n + rows_per_cta - 1) / rows_per_cta);
+    const int threads = gram_threads(R);
+    const int64_t rows_per_cta = GRAM_ROWS_PER_CTA;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, (n + rows_per_cta - 1) / rows_per_cta);
     const size_t smem = sizeof(float) * GRAM_ROWS * R;
     SYM_PROF("gram", s);
     if (bf16)
@@ -288,7 +298,7 @@ sym_tensor_s tensor_part(const sym_tensor_s* X, int64_t first, int64_t count) {
 
 sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
     if (!c) return SYM_E_INVALID;
-    if (c->strict_kernel < 0 || c->strict_kernel > 4) return SYM_E_INVALID;
+    if (c->strict_kernel < 0 || c->strict_kernel > 5) return SYM_E_INVALID;
     if (c->entries_per_warp < 0 || c->entries_per_warp % 32 != 0 || c->entries_per_warp > (1 << 24))
         return SYM_E_INVALID;
     if (c->entries_per_warp == 0 && c->strict_kernel != SYM_MTTKRP_PIPELINED) return SYM_E_INVALID;
@@ -299,8 +309,8 @@ sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
         return SYM_E_INVALID;
     if (c->b_share_pct < 0 || c->b_share_pct > 100) return SYM_E_INVALID;
     if (c->leaf_index != 0 && c->leaf_index != 1) return SYM_E_INVALID;
-    if (c->strict_kernel == SYM_MTTKRP_HOT ? (c->vec_per_lane != 1 && c->vec_per_lane != 4)
-                                           : (c->vec_per_lane != 1 && c->vec_per_lane != 2))
+    const bool depth_field = c->strict_kernel == SYM_MTTKRP_HOT || c->strict_kernel == SYM_MTTKRP_LANE;
+    if (depth_field ? (c->vec_per_lane != 1 && c->vec_per_lane != 4) : (c->vec_per_lane != 1 && c->vec_per_lane != 2))
         return SYM_E_INVALID;
     if ((c->stream_hint != 0 && c->stream_hint != 1) || (c->l1_pref != 0 && c->l1_pref != 1)) return SYM_E_INVALID;
     return SYM_OK;

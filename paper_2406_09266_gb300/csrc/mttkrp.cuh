@@ -640,10 +640,12 @@ __global__ void __launch_bounds__(512) k_mttkrp_strict_pipe(
 // the second pass are the small (hot) indices, which the shared-memory copy
 // of B serves.
 //
-// Work: CTA c owns the contiguous slice [nnz c / G, nnz (c + 1) / G) of the
-// stream; its warps take chunks of `chunk` entries from a shared counter.
-// Fiber state is flushed at the end of every chunk.  The shared copy of M is
-// zeroed at start and reduced into M once per CTA at the end.
+// Work: the stream is cut into chunks of `chunk` entries and warp w of the
+// W warps of the grid takes chunks w, w + W, w + 2W, ...: every warp samples
+// every region of the stream, so regions whose entries cost more (short
+// fibers, contended rows) do not pile up on a few CTAs.  Fiber state is
+// flushed at the end of every chunk.  The shared copy of M is zeroed at start
+// and reduced into M once per CTA at the end.
 constexpr int hot_max_threads(int D) { return D >= 4 ? 768 : 1024; }
 
 template <int N, int KW, int L, bool BF16, int MODE, int D>
@@ -653,28 +655,23 @@ __global__ void __launch_bounds__(hot_max_threads(D), 1) k_mttkrp_strict_hot(
     int64_t chunk, int H, int HB, int stream_hint) {
     static_assert(D >= 1 && D <= L && L % D == 0, "prefetch depth divides the lanes per entry");
     extern __shared__ float4 sink_mem[];
-    __shared__ unsigned long long s_next;
     constexpr int LV = N - 1;
     float* sm_m = reinterpret_cast<float*>(sink_mem);
     float* sm_b = sm_m + (size_t)H * R;
     const RowSink sink{sm_m, H, R, M, ldm};
     const RowSource<BF16> src_b{sm_b, HB, R, B, ldb};
-    const int64_t c0 = nnz * blockIdx.x / gridDim.x, c1 = nnz * (blockIdx.x + 1) / gridDim.x;
     sink_zero(sm_m, H * R);
     source_fill<BF16>(sm_b, HB, R, B, ldb);
-    if (threadIdx.x == 0) s_next = (unsigned long long)c0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int g = lane / L;
     const int col = 4 * (lane % L);
     const bool on = col < R;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
 
-    for (;;) {
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(&s_next, (unsigned long long)chunk);
-        const int64_t start = (int64_t)__shfl_sync(0xffffffffu, got, 0);
-        if (start >= c1) break;
-        const int64_t end = min(start + chunk, c1);
+    for (int64_t start = gwarp * chunk; start < nnz; start += nwarps * chunk) {
+        const int64_t end = min(start + chunk, nnz);
 
         int32_t cur[LV];
         float4 Brow[LV], P[LV], T[LV];
@@ -768,6 +765,146 @@ __global__ void __launch_bounds__(hot_max_threads(D), 1) k_mttkrp_strict_hot(
     }
     __syncthreads();
     sink_flush(sm_m, H, R, M, ldm);
+}
+
+// Strict-stream kernel with lane-parallel decoding (SYM_MTTKRP_LANE).
+//
+// The other strict kernels have all L lanes of a group shuffle, decode and
+// compare every entry's key; that scalar work, repeated by every lane, is most
+// of their instructions.  Here the group's lanes decode L consecutive entries
+// in parallel, one each, and each finds the first fiber level at which its
+// entry differs from the entry before it (the previous lane's, or for the
+// group's first lane the last entry of the group's previous batch).  The group
+// then steps through its L entries with one broadcast of a packed word (leaf
+// row << 3 | first changed level) and one of the value per entry; coordinates
+// of the upper levels are broadcast only when a fiber changes.
+//
+// Work: warp w takes entries [w chunk, (w + 1) chunk); its G = 32 / L groups
+// split that range into G contiguous parts.  MODE as for the hot kernel:
+// 0 every position, 1 all but the leaf, 2 the root only (over the leaf index).
+// D leaf rows are requested before the D entries are processed.
+template <int N, int KW, int L, bool BF16, int MODE, int D>
+__global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
+    const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
+    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
+    int64_t chunk, int stream_hint) {
+    static_assert(N >= 2 && N <= 5, "order");
+    static_assert(D >= 1 && D <= L && L % D == 0, "prefetch depth divides the lanes per entry");
+    constexpr int LV = N - 1;
+    constexpr int G = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L, sl = lane % L;
+    const int col = 4 * sl;
+    const bool on = col < R;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t ws = warp * chunk;
+    if (ws >= nnz) return;
+    const int64_t we = min(ws + chunk, nnz);
+    const int64_t sub = (we - ws + G - 1) / G;
+    const int64_t gs = min(ws + g * sub, we), ge = min(gs + sub, we);
+    const int nb = (int)((sub + L - 1) / L);  // batches: the same count for every group of the warp
+
+    int32_t cur[LV], lastc[LV];
+    float4 Brow[LV], P[LV], T[LV];
+#pragma unroll
+    for (int q = 0; q < LV; ++q) {
+        cur[q] = -1;
+        lastc[q] = -1;
+        Brow[q] = f4_zero();
+        P[q] = f4_zero();
+        T[q] = f4_zero();
+    }
+    bool have = false;
+    for (int b = 0; b < nb; ++b) {
+        // ---- lane-parallel decode: this lane's entry and its first changed level
+        const int64_t e = gs + (int64_t)b * L + sl;
+        const bool valid = e < ge;
+        uint64_t lo = 0, hi = 0;
+        float v = 0.f;
+        if (valid) {
+            if (stream_hint) {
+                lo = __ldcs(klo + e);
+                if (KW == 2) hi = __ldcs(khi + e);
+                v = __ldcs(val + e);
+            } else {
+                lo = klo[e];
+                if (KW == 2) hi = khi[e];
+                v = val[e];
+            }
+        }
+        int32_t c[N];
+        decode_entry<N, KW>(lo, hi, bits, c);
+        int d = LV;
+#pragma unroll
+        for (int q = LV - 1; q >= 0; --q) {
+            const int32_t up = __shfl_up_sync(0xffffffffu, c[q], 1, L);
+            const int32_t prev = sl == 0 ? lastc[q] : up;
+            if (c[q] != prev) d = q;
+        }
+        if (b == 0 && sl == 0) d = 0;  // the group's first entry opens every level
+        const uint32_t packed = ((uint32_t)c[N - 1] << 3) | (uint32_t)d;
+#pragma unroll
+        for (int q = 0; q < LV; ++q) lastc[q] = __shfl_sync(0xffffffffu, c[q], g * L + L - 1);
+
+        // ---- the group steps through its L entries, D at a time
+#pragma unroll 1
+        for (int t0 = 0; t0 < L; t0 += D) {
+            uint32_t pk[D];
+            float vt[D];
+            float4 bl[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                pk[k] = __shfl_sync(0xffffffffu, packed, g * L + t0 + k);
+                vt[k] = __shfl_sync(0xffffffffu, v, g * L + t0 + k);
+                const bool ok = on && (gs + (int64_t)b * L + t0 + k < ge);
+                bl[k] = ok ? load_row4<BF16>(B, (int64_t)(pk[k] >> 3), ldb, col) : f4_zero();
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if (gs + (int64_t)b * L + t0 + k >= ge) break;  // group-uniform
+                const int dt = (int)(pk[k] & 7u);
+                if (dt < LV) {
+                    if (have && on) {
+#pragma unroll
+                        for (int q = LV - 1; q >= 0; --q) {
+                            if (q >= dt) {
+                                if (MODE != 2 || q == 0) {
+                                    const float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+                                    red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+                                }
+                                if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+                                T[q] = f4_zero();
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < LV; ++q) {
+                        if (q >= dt) {
+                            cur[q] = __shfl_sync(gmask, c[q], t0 + k, L);
+                            Brow[q] = (on && (MODE != 2 || q > 0)) ? load_row4<BF16>(B, cur[q], ldb, col)
+                                                                   : f4_zero();
+                            if (MODE != 2) P[q] = (q > 0) ? f4_mul(P[q - 1], Brow[q]) : Brow[q];
+                        }
+                    }
+                    have = true;
+                }
+                T[LV - 1] = f4_fmas(bl[k], vt[k], T[LV - 1]);
+                if (MODE == 0 && on)
+                    red_add_f4(M + (int64_t)(pk[k] >> 3) * ldm + col, f4_scale(P[LV - 1], w * vt[k]));
+            }
+        }
+    }
+    if (have && on) {
+#pragma unroll
+        for (int q = LV - 1; q >= 0; --q) {
+            if (MODE != 2 || q == 0) {
+                const float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+                red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+            }
+            if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+        }
+    }
 }
 
 // One entry per lane group, any equality pattern (the diagonal stream; with
@@ -897,6 +1034,23 @@ sym_status launch_hot(int mode, int depth, unsigned grid, int threads, const Sin
     }
 }
 
+template <int N, int KW, int L, bool BF16, int MODE>
+sym_status launch_lane_m(int depth, int64_t cnt, const uint64_t* klo, const uint64_t* khi, const float* val, int bits,
+                         const void* B, int64_t ldb, int R, float* M, int64_t ldm, float w, int64_t chunk,
+                         int stream_hint, const char* name, cudaStream_t s) {
+    const int64_t warps = (cnt + chunk - 1) / chunk;
+    const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    SYM_PROF(name, s);
+    if (depth >= 4 && L >= 4)
+        k_mttkrp_lane<N, KW, L, BF16, MODE, (L >= 4 ? 4 : 1)><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M,
+                                                                                 ldm, w, chunk, stream_hint);
+    else
+        k_mttkrp_lane<N, KW, L, BF16, MODE, 1><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
+                                                                   chunk, stream_hint);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
 template <int N, int KW, int L, bool BF16>
 sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int64_t ldb, float* M, int64_t ldm,
                                const sym_mttkrp_cfg& cfg, cudaStream_t s) {
@@ -972,6 +1126,22 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
                                                 B, ldb, R, M, ldm, (float)fact[N - 1], chunk, cfg.stream_hint,
                                                 "mttkrp_strict_leaf", s);
             if (hs != SYM_OK) return hs;
+        } else if (cfg.strict_kernel == SYM_MTTKRP_LANE && X->n <= (1 << 29)) {  // leaf row << 3 fits 32 bits
+            // leaf_index = 1 with a leaf index: the canonical stream for every position but the leaf, then
+            // the leaf index for its root; otherwise one pass over the canonical stream
+            const bool two = cfg.leaf_index != 0 && X->rklo != nullptr;
+            const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
+            sym_status ls = two ? launch_lane_m<N, KW, L, BF16, 1>(cfg.vec_per_lane, ns, X->klo, X->khi, X->val,
+                                                                   X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
+                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s)
+                                : launch_lane_m<N, KW, L, BF16, 0>(cfg.vec_per_lane, ns, X->klo, X->khi, X->val,
+                                                                   X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
+                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s);
+            if (ls == SYM_OK && two)
+                ls = launch_lane_m<N, KW, L, BF16, 2>(cfg.vec_per_lane, ns, X->rklo, X->rkhi, X->rval, X->bits, B, ldb,
+                                                      R, M, ldm, (float)fact[N - 1], chunk, cfg.stream_hint,
+                                                      "mttkrp_strict_leaf", s);
+            if (ls != SYM_OK) return ls;
         } else if (cfg.strict_kernel == SYM_MTTKRP_STAGED) {
             const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
             const size_t per_warp = (size_t)2 * 32 * L * stage_lane_bytes<BF16>();

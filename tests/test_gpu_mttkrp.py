@@ -295,3 +295,46 @@ def test_mttkrp_hot_kernel_rejects_bad_config():
         cfg.update(bad)
         with pytest.raises(sg.SymError):
             X.set_config(**cfg)
+
+
+LANE_CONFIGS = [
+    # (chunk, depth, leaf_index)
+    (256, 1, 1), (512, 4, 1), (32, 1, 0), (96, 4, 0), (1024, 1, 0), (64, 4, 1),
+]
+
+
+@pytest.mark.parametrize("k", range(len(LANE_CONFIGS)))
+@pytest.mark.parametrize("case", ["zipf3_r64", "zipf3_r12_bf16", "unif2_r4", "unif4_r32", "unif5_r16",
+                                  "unif3_two_word_keys", "zipf3_r128"])
+def test_mttkrp_lane_kernel(k, case):
+    """Lane-parallel decoding (each lane decodes one entry and finds its first changed fiber level), one pass
+    or two passes (canonical stream without the leaf, leaf index for the root), 1 or 4 leaf gathers in flight,
+    chunks that split fibers between warps and between the groups of a warp."""
+    sg = need_gpu()
+    chunk, depth, leaf = LANE_CONFIGS[k]
+    bf16 = case.endswith("bf16")
+    if case.startswith("zipf3"):
+        R = {"zipf3_r64": 64, "zipf3_r12_bf16": 12, "zipf3_r128": 128}[case]
+        T = synth.tensor3_zipf(3000, 80000, 24)
+    elif case == "unif2_r4":
+        T, R = synth.tensor_uniform(2, 700, 9001, 25), 4
+    elif case == "unif4_r32":
+        T, R = synth.tensor_uniform(4, 80, 30001, 26), 32
+    elif case == "unif5_r16":
+        T, R = synth.tensor_uniform(5, 20, 8003, 27), 16
+    else:
+        T, R = synth.tensor_uniform(3, 5_000_000, 20003, 28), 16   # 3 x 23 bits: two-word keys
+    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
+    if leaf and T.order >= 3:
+        X.add_leaf_index()
+    X.set_config(strict_kernel=sg.MTTKRP_LANE, entries_per_warp=chunk, threads_per_cta=256, leaf_index=leaf,
+                 vec_per_lane=depth, stream_hint=1)
+    Bt, B32, Bused = factor(T.n, R, 6, bf16)
+    M = host(X.mttkrp(Bt))
+    cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
+    ref, ra = oracle.mttkrp_enum(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+    e = oracle.componentwise_error(M, ref, ra)
+    assert e <= TOL_F32, e
+    if bf16:
+        ref32, ra32 = oracle.mttkrp_enum(T.order, T.n, cidx, cval, B32.astype(np.float64))
+        assert oracle.componentwise_error(M, ref32, ra32) <= TOL_BF16
