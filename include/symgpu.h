@@ -403,6 +403,24 @@ sym_status sym_tensor_leaf_index_bytes(sym_tensor X, size_t* arena_bytes, size_t
 sym_status sym_tensor_add_leaf_index(sym_tensor X, void* arena, size_t arena_bytes, void* ws, size_t ws_bytes,
                                      sym_stream_t stream);
 
+/* Relocatable image of a tensor (no paper counterpart: the residency
+ * mechanism of the serving runtime).  sym_tensor_save writes the tensor's
+ * canonical arrays (and its leaf index, if it has one) with a header into
+ * `host` [host, >= sym_tensor_image_bytes(X) bytes; pinned memory makes the
+ * copies asynchronous], enqueued on `stream`: the image is complete once the
+ * stream has reached that point.  sym_tensor_load rebuilds a tensor from an
+ * image into `arena` [device, 256-byte aligned, >= sym_tensor_load_bytes(host)]
+ * with copies enqueued on `stream`; the handle is returned at once and is
+ * usable by work enqueued after the copies on the same stream (or on streams
+ * that wait for it).  The image must stay unchanged until those copies have
+ * completed.  A loaded tensor computes exactly what the saved one did. */
+size_t sym_tensor_image_bytes(sym_tensor X);
+sym_status sym_tensor_save(sym_tensor X, void* host, size_t host_bytes, sym_stream_t stream);
+size_t sym_tensor_load_bytes(const void* host);
+/* The tensor_info of the tensor an image holds (read from the host header). */
+sym_status sym_tensor_image_info(const void* host, sym_tensor_info_t* out);
+sym_status sym_tensor_load(const void* host, void* arena, size_t arena_bytes, sym_stream_t stream, sym_tensor* out);
+
 /* Order-2 tensors: the canonical entries as an upper-triangle CSR (row i holds
  * columns j >= i, ascending).  rowptr: n+1 int64, col: nnz int32, val: nnz
  * floats, all [device]; ws >= sym_tensor_upper_csr_ws_bytes(X). */
@@ -471,32 +489,30 @@ typedef enum {
     SYM_MTTKRP_UNFACTORISED = 2, /* one entry per lane group, every position updated separately */
     SYM_MTTKRP_STAGED = 3,       /* the plain kernel with the next batch's leaf factor rows copied into a
                                     shared-memory double buffer (cp.async) while the current batch runs */
-    SYM_MTTKRP_HOT = 4           /* persistent CTAs, chunks taken from a per-CTA counter, rows [0, H) of M
-                                    accumulated and rows [0, HB) of B read in shared memory, several leaf
-                                    gathers in flight; with leaf_index = 1 and a leaf index, two passes with no
-                                    per-entry reduction: the canonical stream for every position but the leaf,
-                                    then the leaf index for its root (the largest index of each tuple) */,
-    SYM_MTTKRP_LANE = 5          /* chunked warps whose lanes decode one entry each and find its first changed
+    SYM_MTTKRP_LANE = 4          /* chunked warps whose lanes decode one entry each and find its first changed
                                     fiber level, the group then stepping through the entries with one broadcast
-                                    per entry; with leaf_index = 1 and a leaf index, the same two passes as the
-                                    hot kernel */
+                                    per entry; with leaf_index = 1 and a leaf index, two passes with no
+                                    per-entry reduction: the canonical stream for every position but the leaf,
+                                    then the leaf index for its root (the largest index of each tuple),
+                                    unfactorised below the root when strict_smem_kb = 0 */
 } sym_mttkrp_kernel;
 typedef struct {
     int32_t strict_kernel;     /* sym_mttkrp_kernel for the strict stream */
     int32_t entries_per_warp;  /* work chunk per warp, a multiple of 32; 0 = persistent contiguous slices
                                   (pipelined kernel only) */
-    int32_t threads_per_cta;   /* pipelined / unfactorised / staged kernels: 64..512; hot kernel: 64..1024 */
-    int32_t ctas_per_sm;       /* persistent grids: CTAs per SM */
-    int32_t strict_smem_kb;    /* pipelined / hot kernels: shared memory per CTA for hot (low-index) rows,
-                                  0 = none */
+    int32_t threads_per_cta;   /* pipelined / unfactorised / staged kernels: 64..512 */
+    int32_t ctas_per_sm;       /* persistent grids: CTAs per SM; lane kernel: entries per warp of the
+                                  unfactorised root pass / 64 */
+    int32_t strict_smem_kb;    /* pipelined kernel: shared memory per CTA for hot (low-index) rows, 0 = none;
+                                  lane kernel: 0 = unfactorised root pass, 1 = factorised root pass */
     int32_t diag_smem_kb;      /* diagonal stream: the same, 0 = none */
     int32_t b_share_pct;       /* share of that shared memory holding rows of B (the rest holds rows of M) */
     int32_t leaf_index;        /* plain kernel: 1 = take the leaf position from the tensor's leaf index (see
-                                  sym_tensor_add_leaf_index) instead of one reduction per entry; hot kernel:
-                                  1 = walk the leaf index instead of the canonical stream (ignored without one) */
+                                  sym_tensor_add_leaf_index) instead of one reduction per entry (also for the
+                                  lane kernel; ignored without a leaf index) */
     int32_t vec_per_lane;      /* plain kernel: float4 column groups per lane, 1 or 2 (2 needs rank >= 8);
-                                  hot and lane kernels: leaf gathers issued together per lane group, 1 or 4
-                                  (4 needs rank >= 16) */
+                                  lane kernel: leaf gathers issued together per lane group, 1 or 4 (4 needs
+                                  rank >= 16) */
     int32_t stream_hint;       /* plain kernel: 1 = read the canonical stream with evict-first loads so it does not
                                   displace factor rows from L1 / L2 */
     int32_t l1_pref;           /* plain kernel: 1 = ask for the largest L1 (no shared-memory carveout) */
@@ -702,12 +718,15 @@ typedef struct {
     int32_t max_slots;         /* requests in flight at once (device streams) */
     int32_t max_rank;          /* largest rank accepted */
     size_t hbm_budget_bytes;   /* bound on the bytes touched by requests in flight */
-    int32_t coalesce_small;    /* launch small admitted requests as one grouped launch */
-    int64_t small_nnz;         /* "small" threshold for coalescing */
+    int32_t coalesce_small;    /* 1: the small requests admitted in one scheduler pass share one slot and run back
+                                  to back on its stream with one completion event (up to 16 per group) */
+    int64_t small_nnz;         /* "small": at most this many canonical entries (also picks high-priority slots) */
     int64_t wait_limit_ns;     /* bound used by sym_server_destroy's drain */
+    size_t pool_bytes;         /* device pool for registered tensors (part of the arena and of the budget) */
 } sym_server_cfg;
 
-/* Device scratch the server needs (per-slot residual workspaces). */
+/* Device scratch the server needs (per-slot residual workspaces, then the
+ * registered-tensor pool of cfg.pool_bytes). */
 size_t sym_server_arena_bytes(const sym_server_cfg* cfg);
 /* Starts the scheduler thread.  arena [device] holds per-slot scratch. */
 sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, size_t arena_bytes, int device,
@@ -716,14 +735,29 @@ sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, size_t aren
  * validated on the host first: a bad one fails here with SYM_E_BADREQ or
  * SYM_E_BUDGET and gets no ticket. */
 sym_status sym_batch_submit(sym_server S, const sym_request* req, uint64_t* ticket);
+/* Registered tensors (residency managed by the server, no paper counterpart):
+ * `image` [host] is a tensor image from sym_tensor_save that the caller keeps
+ * unchanged for the server's lifetime.  The tensor is loaded into the pool when
+ * a request needs it and dropped (least recently used first, never while a
+ * request in flight uses it) when another one needs the room.  SYM_E_BUDGET if
+ * it could never fit in the pool. */
+sym_status sym_server_register(sym_server S, const void* image, uint64_t* id);
+/* As sym_batch_submit for a registered tensor (req->X is ignored); the request
+ * is validated on the host, and SYM_E_NOTFOUND names an unknown id. */
+sym_status sym_batch_submit_registered(sym_server S, uint64_t id, const sym_request* req, uint64_t* ticket);
 /* SYM_PENDING until the request finishes; then its result (once). */
 sym_status sym_batch_poll(sym_server S, uint64_t ticket, sym_result* out);
 /* Blocks up to timeout_ns for the result (SYM_E_TIMEOUT if it runs out). */
 sym_status sym_batch_wait(sym_server S, uint64_t ticket, int64_t timeout_ns, sym_result* out);
 typedef struct {
     int64_t submitted, admitted, completed, rejected;
-    int64_t launches, grouped_launches;
-    int64_t peak_inflight, peak_bytes;
+    int64_t launches;          /* slot launches (a grouped launch counts once) */
+    int64_t grouped_launches;  /* launches that ran two or more small requests */
+    int64_t peak_inflight;     /* requests in flight at once */
+    int64_t peak_bytes;        /* in-flight factor / output / tensor bytes plus resident pool bytes */
+    int64_t loads;             /* registered tensors brought into the pool */
+    int64_t evictions;         /* registered tensors dropped from the pool to make room */
+    int64_t peak_resident_bytes, resident_bytes;
 } sym_server_stats;
 sym_status sym_server_stats_get(sym_server S, sym_server_stats* out);
 /* Drains queued and in-flight work (bounded by cfg.wait_limit_ns), stops the

@@ -95,13 +95,15 @@ class Result(C.Structure):
 
 class ServerCfg(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_rank", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
-                ("coalesce_small", C.c_int32), ("small_nnz", C.c_int64), ("wait_limit_ns", C.c_int64)]
+                ("coalesce_small", C.c_int32), ("small_nnz", C.c_int64), ("wait_limit_ns", C.c_int64),
+                ("pool_bytes", C.c_size_t)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
                 ("rejected", C.c_int64), ("launches", C.c_int64), ("grouped_launches", C.c_int64),
-                ("peak_inflight", C.c_int64), ("peak_bytes", C.c_int64)]
+                ("peak_inflight", C.c_int64), ("peak_bytes", C.c_int64), ("loads", C.c_int64),
+                ("evictions", C.c_int64), ("peak_resident_bytes", C.c_int64), ("resident_bytes", C.c_int64)]
 
 
 class MttkrpCfg(C.Structure):
@@ -114,7 +116,7 @@ class MttkrpCfg(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-MTTKRP_PLAIN, MTTKRP_PIPELINED, MTTKRP_UNFACTORISED, MTTKRP_STAGED, MTTKRP_HOT, MTTKRP_LANE = 0, 1, 2, 3, 4, 5
+MTTKRP_PLAIN, MTTKRP_PIPELINED, MTTKRP_UNFACTORISED, MTTKRP_STAGED, MTTKRP_LANE = 0, 1, 2, 3, 4
 
 
 class ProfileEntry(C.Structure):
@@ -168,6 +170,10 @@ _SIGS = {
     "sym_tensor_export": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "sym_tensor_destroy": ([C.c_void_p], C.c_int),
     "sym_tensor_upper_csr_ws_bytes": ([C.c_void_p], C.c_size_t),
+    "sym_tensor_image_bytes": ([C.c_void_p], C.c_size_t),
+    "sym_tensor_save": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "sym_tensor_load_bytes": ([C.c_void_p], C.c_size_t),
+    "sym_tensor_load": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p], C.c_int),
     "sym_tensor_leaf_index_bytes": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_tensor_add_leaf_index": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p],
                                   C.c_int),
@@ -221,6 +227,9 @@ _SIGS = {
     "sym_server_create": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p], C.c_int),
     "sym_batch_submit": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_batch_poll": ([C.c_void_p, C.c_uint64, C.c_void_p], C.c_int),
+    "sym_server_register": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_batch_submit_registered": ([C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_tensor_image_info": ([C.c_void_p, C.c_void_p], C.c_int),
     "sym_batch_wait": ([C.c_void_p, C.c_uint64, C.c_int64, C.c_void_p], C.c_int),
     "sym_server_stats_get": ([C.c_void_p, C.c_void_p], C.c_int),
     "sym_server_destroy": ([C.c_void_p], C.c_int),
@@ -450,6 +459,34 @@ class SymTensor:
         self.order, self.n = order, n
         self.device = idx.device
         self._info = None
+
+    def save_image(self, host: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Relocatable image of the tensor in (pinned) host memory (sym_tensor_save); synchronises the stream."""
+        nb = lib().sym_tensor_image_bytes(self.handle)
+        if host is None:
+            host = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        check(lib().sym_tensor_save(self.handle, C.c_void_p(host.data_ptr()), host.numel(), _stream(stream)),
+              "sym_tensor_save")
+        (stream or torch.cuda.current_stream()).synchronize()
+        return host
+
+    @classmethod
+    def from_image(cls, host: torch.Tensor, device=None, stream=None) -> "SymTensor":
+        """A tensor rebuilt from an image (sym_tensor_load) into a fresh device arena."""
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        nb = lib().sym_tensor_load_bytes(C.c_void_p(host.data_ptr()))
+        if nb == 0:
+            raise SymError(-1, "sym_tensor_load_bytes")
+        X = cls.__new__(cls)
+        X.arena = _scratch(nb, dev)
+        h = C.c_void_p()
+        check(lib().sym_tensor_load(C.c_void_p(host.data_ptr()), _ptr(X.arena), X.arena.numel(), _stream(stream),
+                                    C.byref(h)), "sym_tensor_load")
+        X.handle = h
+        X._info = None
+        inf = X.info()
+        X.order, X.n, X.device = inf["order"], inf["n"], dev
+        return X
 
     @staticmethod
     def create_ws_bytes(order, n, nnz) -> int:
@@ -896,9 +933,10 @@ class Server:
     """Continuous-batching MTTKRP server (sym_server_create / sym_batch_submit / sym_batch_poll)."""
 
     def __init__(self, max_slots=8, max_rank=64, hbm_budget_bytes=120 << 30, small_nnz=1_000_000,
-                 wait_limit_s=30.0, device=None):
+                 wait_limit_s=30.0, device=None, coalesce_small=False, pool_bytes=0):
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
-        self.cfg = ServerCfg(max_slots, max_rank, hbm_budget_bytes, 0, small_nnz, int(wait_limit_s * 1e9))
+        self.cfg = ServerCfg(max_slots, max_rank, hbm_budget_bytes, int(coalesce_small), small_nnz,
+                             int(wait_limit_s * 1e9), int(pool_bytes))
         self.arena = _scratch(lib().sym_server_arena_bytes(C.byref(self.cfg)), dev)
         h = C.c_void_p()
         check(lib().sym_server_create(C.byref(self.cfg), _ptr(self.arena), self.arena.numel(), dev.index,
@@ -912,6 +950,23 @@ class Server:
         t = C.c_uint64(0)
         check(lib().sym_batch_submit(self.handle, C.byref(req), C.byref(t)), "sym_batch_submit")
         self._keep[t.value] = (X, B, M)
+        return t.value
+
+    def register(self, image: torch.Tensor) -> int:
+        """Registers a tensor image (SymTensor.save_image); the server keeps it resident when needed."""
+        tid = C.c_uint64(0)
+        check(lib().sym_server_register(self.handle, C.c_void_p(image.data_ptr()), C.byref(tid)),
+              "sym_server_register")
+        self._keep[("image", tid.value)] = image
+        return tid.value
+
+    def submit_registered(self, tid: int, B, M, residual=False, tag=0) -> int:
+        req = Request(None, B.data_ptr(), _dtype_code(B), B.shape[1], B.stride(0), M.data_ptr(), M.stride(0),
+                      int(residual), tag)
+        t = C.c_uint64(0)
+        check(lib().sym_batch_submit_registered(self.handle, tid, C.byref(req), C.byref(t)),
+              "sym_batch_submit_registered")
+        self._keep[t.value] = (B, M)
         return t.value
 
     def poll(self, ticket: int):

@@ -298,18 +298,17 @@ sym_tensor_s tensor_part(const sym_tensor_s* X, int64_t first, int64_t count) {
 
 sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
     if (!c) return SYM_E_INVALID;
-    if (c->strict_kernel < 0 || c->strict_kernel > 5) return SYM_E_INVALID;
+    if (c->strict_kernel < 0 || c->strict_kernel > 4) return SYM_E_INVALID;
     if (c->entries_per_warp < 0 || c->entries_per_warp % 32 != 0 || c->entries_per_warp > (1 << 24))
         return SYM_E_INVALID;
     if (c->entries_per_warp == 0 && c->strict_kernel != SYM_MTTKRP_PIPELINED) return SYM_E_INVALID;
-    const int max_threads = c->strict_kernel == SYM_MTTKRP_HOT ? 1024 : 512;
-    if (c->threads_per_cta < 64 || c->threads_per_cta > max_threads || c->threads_per_cta % 32) return SYM_E_INVALID;
+    if (c->threads_per_cta < 64 || c->threads_per_cta > 512 || c->threads_per_cta % 32) return SYM_E_INVALID;
     if (c->ctas_per_sm < 1 || c->ctas_per_sm > 8) return SYM_E_INVALID;
     if (c->strict_smem_kb < 0 || c->strict_smem_kb > 220 || c->diag_smem_kb < 0 || c->diag_smem_kb > 220)
         return SYM_E_INVALID;
     if (c->b_share_pct < 0 || c->b_share_pct > 100) return SYM_E_INVALID;
     if (c->leaf_index != 0 && c->leaf_index != 1) return SYM_E_INVALID;
-    const bool depth_field = c->strict_kernel == SYM_MTTKRP_HOT || c->strict_kernel == SYM_MTTKRP_LANE;
+    const bool depth_field = c->strict_kernel == SYM_MTTKRP_LANE;
     if (depth_field ? (c->vec_per_lane != 1 && c->vec_per_lane != 4) : (c->vec_per_lane != 1 && c->vec_per_lane != 2))
         return SYM_E_INVALID;
     if ((c->stream_hint != 0 && c->stream_hint != 1) || (c->l1_pref != 0 && c->l1_pref != 1)) return SYM_E_INVALID;
@@ -484,6 +483,16 @@ extern "C" sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype
     for (int chunk : {128, 256, 512})
         for (int thr : {128, 256}) cands.push_back({SYM_MTTKRP_STAGED, chunk, thr, 2, 0, 0, 0, 0, 1, 0, 0});
     for (int chunk : {128, 256}) cands.push_back({SYM_MTTKRP_PIPELINED, chunk, 256, 2, 0, 0, 0, 0, 1, 0, 0});
+    for (int depth : {1, 4}) {
+        if (depth == 4 && rank < 16) continue;
+        for (int chunk : {128, 256, 512}) {
+            cands.push_back({SYM_MTTKRP_LANE, chunk, 256, 2, 0, 0, 0, 0, depth, 1, 0});  // one pass
+            if (!X->rklo) continue;
+            for (int rc : {2, 4})  // two passes, unfactorised root pass of 64 rc entries per warp
+                cands.push_back({SYM_MTTKRP_LANE, chunk, 256, rc, 0, 0, 0, 1, depth, 1, 0});
+            cands.push_back({SYM_MTTKRP_LANE, chunk, 256, 2, 1, 0, 0, 1, depth, 1, 0});  // factorised root pass
+        }
+    }
     cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 0, 0, 0, 0, 1, 0, 0});
     cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 96, 0, 50, 0, 1, 0, 0});
     cands.push_back({SYM_MTTKRP_UNFACTORISED, 256, 256, 2, 0, 0, 0, 0, 1, 0, 0});

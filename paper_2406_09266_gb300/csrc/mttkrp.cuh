@@ -621,152 +621,6 @@ __global__ void __launch_bounds__(512) k_mttkrp_strict_pipe(
     }
 }
 
-// Persistent strict-stream kernel (SYM_MTTKRP_HOT): rows [0, HB) of B read
-// from a shared-memory copy, rows [0, H) of M accumulated in one, the leaf
-// factor rows of D consecutive entries requested together, and a choice of the
-// positions it updates:
-//   MODE 0: every position (leaf reductions per entry, fiber flushes above);
-//   MODE 1: all but the leaf (the leaf's rows are left to a MODE 2 pass);
-//   MODE 2: the root only, over the leaf index (tuples reversed and sorted, so
-//           the root is the LARGEST index of each tuple): row c_N receives
-//           (N-1)! times the sum over its subtree of v prod_{q<N} B[c_q],
-//           accumulated in registers along the root fiber.
-// MODE 1 over the canonical stream plus MODE 2 over the leaf index cover every
-// position exactly once with no per-entry reduction: the smallest indices
-// (the hottest rows under skewed distributions, where reductions would
-// contend) are roots or middle levels of the canonical order, and the largest
-// index of each tuple is the root of the second pass.  The per-entry work of
-// both passes is then one factor-row gather and one FMA row; the gathers of
-// the second pass are the small (hot) indices, which the shared-memory copy
-// of B serves.
-//
-// Work: the stream is cut into chunks of `chunk` entries and warp w of the
-// W warps of the grid takes chunks w, w + W, w + 2W, ...: every warp samples
-// every region of the stream, so regions whose entries cost more (short
-// fibers, contended rows) do not pile up on a few CTAs.  Fiber state is
-// flushed at the end of every chunk.  The shared copy of M is zeroed at start
-// and reduced into M once per CTA at the end.
-constexpr int hot_max_threads(int D) { return D >= 4 ? 768 : 1024; }
-
-template <int N, int KW, int L, bool BF16, int MODE, int D>
-__global__ void __launch_bounds__(hot_max_threads(D), 1) k_mttkrp_strict_hot(
-    const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
-    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
-    int64_t chunk, int H, int HB, int stream_hint) {
-    static_assert(D >= 1 && D <= L && L % D == 0, "prefetch depth divides the lanes per entry");
-    extern __shared__ float4 sink_mem[];
-    constexpr int LV = N - 1;
-    float* sm_m = reinterpret_cast<float*>(sink_mem);
-    float* sm_b = sm_m + (size_t)H * R;
-    const RowSink sink{sm_m, H, R, M, ldm};
-    const RowSource<BF16> src_b{sm_b, HB, R, B, ldb};
-    sink_zero(sm_m, H * R);
-    source_fill<BF16>(sm_b, HB, R, B, ldb);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int g = lane / L;
-    const int col = 4 * (lane % L);
-    const bool on = col < R;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-
-    for (int64_t start = gwarp * chunk; start < nnz; start += nwarps * chunk) {
-        const int64_t end = min(start + chunk, nnz);
-
-        int32_t cur[LV];
-        float4 Brow[LV], P[LV], T[LV];
-#pragma unroll
-        for (int q = 0; q < LV; ++q) {
-            cur[q] = -1;
-            Brow[q] = f4_zero();
-            P[q] = f4_zero();
-            T[q] = f4_zero();
-        }
-        bool have = false;
-        for (int64_t b0 = start; b0 < end; b0 += 32) {
-            const int64_t e = b0 + lane;
-            uint64_t mlo = 0, mhi = 0;
-            float mv = 0.f;
-            if (e < end) {
-                if (stream_hint) {
-                    mlo = __ldcs(klo + e);
-                    if (KW == 2) mhi = __ldcs(khi + e);
-                    mv = __ldcs(val + e);
-                } else {
-                    mlo = klo[e];
-                    if (KW == 2) mhi = khi[e];
-                    mv = val[e];
-                }
-            }
-            // entries of this group in this batch: b0 + g L + t, valid while t < nval
-            const int64_t left = end - (b0 + g * L);
-            const int nval = left <= 0 ? 0 : (left >= L ? L : (int)left);
-#pragma unroll 1
-            for (int t0 = 0; t0 < L; t0 += D) {
-                int32_t c[D][N];
-                float v[D];
-                float4 bl[D];
-#pragma unroll
-                for (int d = 0; d < D; ++d) {  // D leaf gathers in flight at once
-                    const int src = g * L + t0 + d;
-                    const uint64_t lo = __shfl_sync(0xffffffffu, mlo, src);
-                    const uint64_t hi = (KW == 2) ? __shfl_sync(0xffffffffu, mhi, src) : 0ull;
-                    v[d] = __shfl_sync(0xffffffffu, mv, src);
-                    decode_entry<N, KW>(lo, hi, bits, c[d]);
-                    bl[d] = (t0 + d < nval && on) ? src_b.get(c[d][N - 1], col) : f4_zero();
-                }
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    if (t0 + d >= nval || !on) continue;
-                    int dl = LV;
-#pragma unroll
-                    for (int q = LV - 1; q >= 0; --q)
-                        if (!have || c[d][q] != cur[q]) dl = q;
-                    if (dl < LV) {
-                        if (have) {
-#pragma unroll
-                            for (int q = LV - 1; q >= 0; --q) {
-                                if (q >= dl) {
-                                    if (MODE != 2 || q == 0) {
-                                        const float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
-                                        sink.add(cur[q], col, f4_scale(out, w));
-                                    }
-                                    if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
-                                    T[q] = f4_zero();
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int q = 0; q < LV; ++q) {
-                            if (q >= dl) {
-                                cur[q] = c[d][q];
-                                // the root row's own factor is not needed when only the root is flushed
-                                Brow[q] = (MODE != 2 || q > 0) ? src_b.get(c[d][q], col) : f4_zero();
-                                if (MODE != 2) P[q] = (q > 0) ? f4_mul(P[q - 1], Brow[q]) : Brow[q];
-                            }
-                        }
-                        have = true;
-                    }
-                    T[LV - 1] = f4_fmas(bl[d], v[d], T[LV - 1]);
-                    if (MODE == 0) sink.add(c[d][N - 1], col, f4_scale(P[LV - 1], w * v[d]));
-                }
-            }
-        }
-        if (have && on) {
-#pragma unroll
-            for (int q = LV - 1; q >= 0; --q) {
-                if (MODE != 2 || q == 0) {
-                    const float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
-                    sink.add(cur[q], col, f4_scale(out, w));
-                }
-                if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
-            }
-        }
-    }
-    __syncthreads();
-    sink_flush(sm_m, H, R, M, ldm);
-}
-
 // Strict-stream kernel with lane-parallel decoding (SYM_MTTKRP_LANE).
 //
 // The other strict kernels have all L lanes of a group shuffle, decode and
@@ -780,9 +634,15 @@ __global__ void __launch_bounds__(hot_max_threads(D), 1) k_mttkrp_strict_hot(
 // of the upper levels are broadcast only when a fiber changes.
 //
 // Work: warp w takes entries [w chunk, (w + 1) chunk); its G = 32 / L groups
-// split that range into G contiguous parts.  MODE as for the hot kernel:
-// 0 every position, 1 all but the leaf, 2 the root only (over the leaf index).
-// D leaf rows are requested before the D entries are processed.
+// split that range into G contiguous parts.  The positions it updates:
+//   MODE 0: every position (leaf reductions per entry, fiber flushes above);
+//   MODE 1: all but the leaf (the leaf's rows are left to a root-only pass);
+//   MODE 2: the root only, over the leaf index (tuples reversed and sorted, so
+//           the root is the LARGEST index of each tuple).
+// MODE 1 over the canonical stream plus a root-only pass over the leaf index
+// cover every position exactly once with no per-entry reduction.  D leaf rows
+// are requested before the D entries are processed, and each batch's keys one
+// batch ahead.
 template <int N, int KW, int L, bool BF16, int MODE, int D>
 __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
@@ -816,23 +676,32 @@ __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
         T[q] = f4_zero();
     }
     bool have = false;
-    for (int b = 0; b < nb; ++b) {
-        // ---- lane-parallel decode: this lane's entry and its first changed level
-        const int64_t e = gs + (int64_t)b * L + sl;
-        const bool valid = e < ge;
-        uint64_t lo = 0, hi = 0;
-        float v = 0.f;
-        if (valid) {
+    // the next batch's keys are requested one batch ahead, so the stream's DRAM latency overlaps the work
+    auto fetch = [&](int bb, uint64_t& flo, uint64_t& fhi, float& fv) {
+        const int64_t fe = gs + (int64_t)bb * L + sl;
+        flo = 0;
+        fhi = 0;
+        fv = 0.f;
+        if (bb < nb && fe < ge) {
             if (stream_hint) {
-                lo = __ldcs(klo + e);
-                if (KW == 2) hi = __ldcs(khi + e);
-                v = __ldcs(val + e);
+                flo = __ldcs(klo + fe);
+                if (KW == 2) fhi = __ldcs(khi + fe);
+                fv = __ldcs(val + fe);
             } else {
-                lo = klo[e];
-                if (KW == 2) hi = khi[e];
-                v = val[e];
+                flo = klo[fe];
+                if (KW == 2) fhi = khi[fe];
+                fv = val[fe];
             }
         }
+    };
+    uint64_t nlo, nhi;
+    float nv;
+    fetch(0, nlo, nhi, nv);
+    for (int b = 0; b < nb; ++b) {
+        // ---- lane-parallel decode: this lane's entry and its first changed level
+        const uint64_t lo = nlo, hi = nhi;
+        const float v = nv;
+        fetch(b + 1, nlo, nhi, nv);
         int32_t c[N];
         decode_entry<N, KW>(lo, hi, bits, c);
         int d = LV;
@@ -862,7 +731,7 @@ __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
             }
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                if (gs + (int64_t)b * L + t0 + k >= ge) break;  // group-uniform
+                if (gs + (int64_t)b * L + t0 + k >= ge) continue;  // group-uniform
                 const int dt = (int)(pk[k] & 7u);
                 if (dt < LV) {
                     if (have && on) {
@@ -905,6 +774,94 @@ __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
             if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
         }
     }
+}
+
+// Root-only pass over the leaf index, unfactorised below the root (the second
+// pass of the two-pass schedule).  Over the leaf index (tuples reversed and
+// sorted) the root c_1 of each entry is the largest index of the canonical
+// tuple; row c_1 receives (N-1)! times the sum over its root fiber of
+// v prod_{q>1} B[c_q], accumulated in registers and reduced once per fiber.
+// Below the root no fiber is tracked: every entry multiplies its N - 1 rows
+// directly (the rows are the smallest indices of their tuples, the hottest rows
+// under a skewed distribution, so they come from L1).  Lanes decode one entry
+// each; the group then steps through them with one broadcast per row offset,
+// one for the value and one for the root change.
+template <int N, int KW, int L, bool BF16>
+__global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
+    const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
+    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
+    int64_t chunk, int stream_hint) {
+    static_assert(N >= 2 && N <= 5, "order");
+    constexpr int G = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L, sl = lane % L;
+    const int col = 4 * sl;
+    const bool on = col < R;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t ws = warp * chunk;
+    if (ws >= nnz) return;
+    const int64_t we = min(ws + chunk, nnz);
+    const int64_t sub = (we - ws + G - 1) / G;
+    const int64_t gs = min(ws + g * sub, we), ge = min(gs + sub, we);
+    const int nb = (int)((sub + L - 1) / L);
+
+    auto fetch = [&](int bb, uint64_t& flo, uint64_t& fhi, float& fv) {
+        const int64_t fe = gs + (int64_t)bb * L + sl;
+        flo = 0;
+        fhi = 0;
+        fv = 0.f;
+        if (bb < nb && fe < ge) {
+            if (stream_hint) {
+                flo = __ldcs(klo + fe);
+                if (KW == 2) fhi = __ldcs(khi + fe);
+                fv = __ldcs(val + fe);
+            } else {
+                flo = klo[fe];
+                if (KW == 2) fhi = khi[fe];
+                fv = val[fe];
+            }
+        }
+    };
+    int32_t root = -1, lastroot = -1;
+    float4 acc = f4_zero();
+    uint64_t nlo, nhi;
+    float nv;
+    fetch(0, nlo, nhi, nv);
+    for (int b = 0; b < nb; ++b) {
+        const uint64_t lo = nlo, hi = nhi;
+        const float v = nv;
+        fetch(b + 1, nlo, nhi, nv);
+        int32_t c[N];
+        decode_entry<N, KW>(lo, hi, bits, c);
+        const int32_t up = __shfl_up_sync(0xffffffffu, c[0], 1, L);
+        const int32_t prev = sl == 0 ? lastroot : up;
+        const int32_t newroot = (c[0] != prev || (b == 0 && sl == 0)) ? c[0] : -1;  // -1: same root as before
+        lastroot = __shfl_sync(0xffffffffu, c[0], g * L + L - 1);
+#pragma unroll 1
+        for (int t = 0; t < L; ++t) {
+            const int src = g * L + t;
+            const int32_t nr = __shfl_sync(0xffffffffu, newroot, src);
+            const float vt = __shfl_sync(0xffffffffu, v, src);
+            int32_t r[N - 1];
+#pragma unroll
+            for (int q = 1; q < N; ++q) r[q - 1] = __shfl_sync(0xffffffffu, c[q], src);
+            // Past the group's last entry the lanes skip the work but stay in the loop: every lane of the
+            // warp must reach each full-warp shuffle above, whatever its group's entry count.
+            if (gs + (int64_t)b * L + t >= ge) continue;
+            if (nr >= 0) {  // a new root fiber starts at this entry
+                if (root >= 0 && on) red_add_f4(M + (int64_t)root * ldm + col, f4_scale(acc, w));
+                root = nr;
+                acc = f4_zero();
+            }
+            if (on) {
+                float4 prod = load_row4<BF16>(B, r[0], ldb, col);
+#pragma unroll
+                for (int q = 1; q < N - 1; ++q) prod = f4_mul(prod, load_row4<BF16>(B, r[q], ldb, col));
+                acc = f4_fmas(prod, vt, acc);
+            }
+        }
+    }
+    if (root >= 0 && on) red_add_f4(M + (int64_t)root * ldm + col, f4_scale(acc, w));
 }
 
 // One entry per lane group, any equality pattern (the diagonal stream; with
@@ -992,48 +949,6 @@ inline SinkPlan plan_sink(int64_t n, int R, int kb, int b_share_pct) {
     return SinkPlan{H, HB, (size_t)(H + HB) * row};
 }
 
-template <int N, int KW, int L, bool BF16, int MODE, int D>
-sym_status launch_hot_md(unsigned grid, int threads, const SinkPlan& sp, const uint64_t* klo, const uint64_t* khi,
-                         const float* val, int64_t cnt, int bits, const void* B, int64_t ldb, int R, float* M,
-                         int64_t ldm, float w, int64_t chunk, int stream_hint, const char* name, cudaStream_t s) {
-    SYM_TRY(raise_smem_limit(k_mttkrp_strict_hot<N, KW, L, BF16, MODE, D>, sp.bytes));
-    threads = std::min(threads, hot_max_threads(D));
-    SYM_PROF(name, s);
-    k_mttkrp_strict_hot<N, KW, L, BF16, MODE, D><<<grid, threads, sp.bytes, s>>>(
-        klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w, chunk, sp.H, sp.HB, stream_hint);
-    SYM_CHECK_LAUNCH();
-    return SYM_OK;
-}
-
-// Prefetch depth: 4 leaf gathers in flight per lane group when the rank
-// spans at least 4 lanes (depth >= 4), else 1.
-template <int N, int KW, int L, bool BF16, int MODE>
-sym_status launch_hot_m(int depth, unsigned grid, int threads, const SinkPlan& sp, const uint64_t* klo,
-                        const uint64_t* khi, const float* val, int64_t cnt, int bits, const void* B, int64_t ldb,
-                        int R, float* M, int64_t ldm, float w, int64_t chunk, int stream_hint, const char* name,
-                        cudaStream_t s) {
-    if (depth >= 4 && L >= 4)
-        return launch_hot_md<N, KW, L, BF16, MODE, (L >= 4 ? 4 : 1)>(grid, threads, sp, klo, khi, val, cnt, bits, B,
-                                                                     ldb, R, M, ldm, w, chunk, stream_hint, name, s);
-    return launch_hot_md<N, KW, L, BF16, MODE, 1>(grid, threads, sp, klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
-                                                  chunk, stream_hint, name, s);
-}
-
-template <int N, int KW, int L, bool BF16>
-sym_status launch_hot(int mode, int depth, unsigned grid, int threads, const SinkPlan& sp, const uint64_t* klo,
-                      const uint64_t* khi, const float* val, int64_t cnt, int bits, const void* B, int64_t ldb, int R,
-                      float* M, int64_t ldm, float w, int64_t chunk, int stream_hint, const char* name,
-                      cudaStream_t s) {
-    switch (mode) {
-        case 0: return launch_hot_m<N, KW, L, BF16, 0>(depth, grid, threads, sp, klo, khi, val, cnt, bits, B, ldb, R,
-                                                       M, ldm, w, chunk, stream_hint, name, s);
-        case 1: return launch_hot_m<N, KW, L, BF16, 1>(depth, grid, threads, sp, klo, khi, val, cnt, bits, B, ldb, R,
-                                                       M, ldm, w, chunk, stream_hint, name, s);
-        default: return launch_hot_m<N, KW, L, BF16, 2>(depth, grid, threads, sp, klo, khi, val, cnt, bits, B, ldb,
-                                                        R, M, ldm, w, chunk, stream_hint, name, s);
-    }
-}
-
 template <int N, int KW, int L, bool BF16, int MODE>
 sym_status launch_lane_m(int depth, int64_t cnt, const uint64_t* klo, const uint64_t* khi, const float* val, int bits,
                          const void* B, int64_t ldb, int R, float* M, int64_t ldm, float w, int64_t chunk,
@@ -1107,25 +1022,6 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             k_mttkrp_strict_pipe<N, KW, L, BF16><<<grid, threads, sp.bytes, s>>>(
                 X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
                 std::max<int64_t>(0, cfg.entries_per_warp), sp.H, sp.HB);
-        } else if (cfg.strict_kernel == SYM_MTTKRP_HOT) {
-            // leaf_index = 1 with a leaf index: two passes (canonical stream without the leaf, then the
-            // leaf index for the root only); otherwise one pass over the canonical stream
-            const bool two = cfg.leaf_index != 0 && X->rklo != nullptr;
-            const SinkPlan sp = plan_sink(X->n, R, cfg.strict_smem_kb, cfg.b_share_pct);
-            const SinkPlan sp2 = plan_sink(X->n, R, cfg.strict_smem_kb, 100);  // root pass: rows of B only
-            const int hthreads = std::max(64, std::min(1024, (int)cfg.threads_per_cta)) / 32 * 32;
-            const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
-            const unsigned grid = (unsigned)std::max<int64_t>(
-                1, std::min<int64_t>((int64_t)sms * std::max(1, (int)cfg.ctas_per_sm), (ns + chunk - 1) / chunk));
-            const int depth = cfg.vec_per_lane;  // leaf gathers in flight per lane group (1 or 4)
-            sym_status hs = launch_hot<N, KW, L, BF16>(two ? 1 : 0, depth, grid, hthreads, sp, X->klo, X->khi, X->val,
-                                                       ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                                                       cfg.stream_hint, "mttkrp_strict", s);
-            if (hs == SYM_OK && two)
-                hs = launch_hot<N, KW, L, BF16>(2, depth, grid, hthreads, sp2, X->rklo, X->rkhi, X->rval, ns, X->bits,
-                                                B, ldb, R, M, ldm, (float)fact[N - 1], chunk, cfg.stream_hint,
-                                                "mttkrp_strict_leaf", s);
-            if (hs != SYM_OK) return hs;
         } else if (cfg.strict_kernel == SYM_MTTKRP_LANE && X->n <= (1 << 29)) {  // leaf row << 3 fits 32 bits
             // leaf_index = 1 with a leaf index: the canonical stream for every position but the leaf, then
             // the leaf index for its root; otherwise one pass over the canonical stream
@@ -1137,10 +1033,21 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
                                 : launch_lane_m<N, KW, L, BF16, 0>(cfg.vec_per_lane, ns, X->klo, X->khi, X->val,
                                                                    X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
                                                                    chunk, cfg.stream_hint, "mttkrp_strict", s);
-            if (ls == SYM_OK && two)
-                ls = launch_lane_m<N, KW, L, BF16, 2>(cfg.vec_per_lane, ns, X->rklo, X->rkhi, X->rval, X->bits, B, ldb,
-                                                      R, M, ldm, (float)fact[N - 1], chunk, cfg.stream_hint,
-                                                      "mttkrp_strict_leaf", s);
+            if (ls == SYM_OK && two) {
+                if (cfg.strict_smem_kb == 0) {  // root pass unfactorised below the root
+                    const int64_t rchunk = cfg.ctas_per_sm > 0 ? 64LL * cfg.ctas_per_sm : 256;
+                    const int64_t warps = (ns + rchunk - 1) / rchunk;
+                    SYM_PROF("mttkrp_strict_leaf", s);
+                    k_mttkrp_rootpass<N, KW, L, BF16><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(
+                        X->rklo, X->rkhi, X->rval, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], rchunk,
+                        cfg.stream_hint);
+                    ls = cuda_status(cudaGetLastError());
+                } else {
+                    ls = launch_lane_m<N, KW, L, BF16, 2>(cfg.vec_per_lane, ns, X->rklo, X->rkhi, X->rval, X->bits,
+                                                          B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
+                                                          cfg.stream_hint, "mttkrp_strict_leaf", s);
+                }
+            }
             if (ls != SYM_OK) return ls;
         } else if (cfg.strict_kernel == SYM_MTTKRP_STAGED) {
             const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;

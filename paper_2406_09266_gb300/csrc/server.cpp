@@ -7,13 +7,30 @@
 // its slot's stream, and polls completion events.  Requests that arrive while
 // others run are admitted as soon as room frees up, so their kernels overlap
 // on the device; small requests go to high-priority streams so they are not
-// stuck behind large ones.  Each response carries the FP64 CP-fit residual when
-// asked for, and host steady-clock timestamps for submit, admission and
-// completion.  Nothing here waits on the device without a bound: the scheduler
-// only queries events, and destroy drains with a time limit.
+// stuck behind large ones.  With coalesce_small, the small requests admitted
+// in one scheduler pass share one slot: they run back to back on its stream
+// with one completion event (a grouped launch), so a burst of small requests
+// does not take every slot.  Each response carries the FP64 CP-fit residual
+// when asked for, and host steady-clock timestamps for submit, admission and
+// completion.
+//
+// Registered tensors: a caller may hand the server the host image of a tensor
+// (sym_tensor_save) instead of a resident tensor.  The server keeps such
+// tensors in a device pool carved from its arena: a request for a tensor that
+// is not resident loads it (one host-to-device copy of its canonical arrays,
+// on the request's stream, before the kernels); when the pool is full, the
+// least recently used resident tensors that no request in flight uses are
+// dropped (the host image is the master copy, so nothing is copied back).  The
+// pool and the factors / outputs of the requests in flight together stay
+// within the HBM budget.
+//
+// Nothing here waits on the device without a bound: the scheduler only queries
+// events, and destroy drains with a time limit.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -27,15 +44,30 @@
 
 namespace {
 
+constexpr int kMaxGroup = 16;  // requests in one grouped launch
+
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
         .count();
 }
 
+// A registered tensor: its host image and, while resident, its pool range.
+struct Entry {
+    const void* image = nullptr;
+    size_t bytes = 0;      // device bytes when loaded
+    bool resident = false;
+    size_t off = 0;        // pool offset while resident
+    sym_tensor_s* X = nullptr;  // handle into the pool while resident
+    cudaEvent_t ready = nullptr;  // recorded after the load
+    int inuse = 0;         // requests in flight on it
+    uint64_t last_use = 0;
+};
+
 struct Pending {
     uint64_t ticket;
     sym_request r;
+    int64_t reg = -1;  // registered tensor index, or -1 (r.X is a resident tensor)
     size_t bytes;
     uint64_t t_submit;
     bool small;
@@ -46,19 +78,23 @@ struct Slot {
     cudaEvent_t done = nullptr;
     bool high = false;
     bool busy = false;
-    Pending req{};
+    std::vector<Pending> reqs;  // one request, or a group of small ones
     uint64_t t_admit = 0;
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    double* res_dev = nullptr;
-    double* res_host = nullptr;  // pinned
+    double* res_dev = nullptr;   // kMaxGroup residuals
+    double* res_host = nullptr;  // pinned, kMaxGroup
     sym_status launch_status = SYM_OK;
 };
 
-size_t request_bytes(const sym_request& r) {
-    const sym_tensor_s* X = r.X;
+size_t factor_bytes(const sym_request& r, int64_t n) {
     const size_t esz = r.bdt == SYM_BF16 ? 2 : 4;
-    return X->info.arena_used + (size_t)X->n * (size_t)r.ldb * esz + (size_t)X->n * (size_t)r.ldm * 4;
+    return (size_t)n * (size_t)r.ldb * esz + (size_t)n * (size_t)r.ldm * 4;
+}
+
+size_t slot_bytes(const sym_server_cfg* cfg) {
+    return symgpu::align_up(symgpu::residual_ws_bytes(cfg->max_rank), 256) +
+           symgpu::align_up(sizeof(double) * kMaxGroup, 256);
 }
 
 }  // namespace
@@ -79,14 +115,89 @@ struct sym_server_s {
     std::thread th;
     sym_server_stats stats{};
     int64_t inflight = 0;
+    // registered tensors and their device pool
+    char* pool = nullptr;
+    size_t pool_bytes = 0;
+    std::map<size_t, size_t> free_ranges;  // offset -> size, coalesced
+    std::vector<Entry> entries;
+    uint64_t tick = 0;
+    size_t resident_bytes = 0;
 
     void run();
     void finish(Slot& s, sym_status st);
     void launch(Slot& s);
     void release();
+    bool pool_alloc(size_t bytes, size_t* off);
+    void pool_free(size_t off, size_t bytes);
+    bool make_resident(Entry& E, cudaStream_t s, sym_status* err);
 };
 
-// Streams, events and pinned buffers of the slots (host-side resources only).
+bool sym_server_s::pool_alloc(size_t bytes, size_t* off) {
+    for (auto it = free_ranges.begin(); it != free_ranges.end(); ++it) {
+        if (it->second < bytes) continue;
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t at = it->first + bytes;
+        free_ranges.erase(it);
+        if (rest) free_ranges[at] = rest;
+        return true;
+    }
+    return false;
+}
+
+void sym_server_s::pool_free(size_t off, size_t bytes) {
+    auto it = free_ranges.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_ranges.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        free_ranges.erase(nx);
+    }
+    if (it != free_ranges.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            free_ranges.erase(it);
+        }
+    }
+}
+
+// Called with mu held.  Loads E into the pool (evicting least recently used
+// idle entries as needed) with its copies on stream s; false when the pool
+// cannot make room now (every resident entry is in use).
+bool sym_server_s::make_resident(Entry& E, cudaStream_t s, sym_status* err) {
+    *err = SYM_OK;
+    size_t off = 0;
+    while (!pool_alloc(E.bytes, &off)) {
+        Entry* victim = nullptr;
+        for (auto& c : entries)
+            if (c.resident && c.inuse == 0 && (!victim || c.last_use < victim->last_use)) victim = &c;
+        if (!victim) return false;
+        pool_free(victim->off, victim->bytes);
+        sym_tensor_destroy(victim->X);
+        victim->X = nullptr;
+        victim->resident = false;
+        resident_bytes -= victim->bytes;
+        stats.evictions += 1;
+    }
+    sym_tensor X = nullptr;
+    sym_status st = sym_tensor_load(E.image, pool + off, E.bytes, reinterpret_cast<sym_stream_t>(s), &X);
+    if (st == SYM_OK) st = symgpu::cuda_status(cudaEventRecord(E.ready, s));
+    if (st != SYM_OK) {
+        if (X) sym_tensor_destroy(X);
+        pool_free(off, E.bytes);
+        *err = st;
+        return true;  // admitted, fails at launch
+    }
+    E.X = X;
+    E.off = off;
+    E.resident = true;
+    resident_bytes += E.bytes;
+    stats.loads += 1;
+    stats.peak_resident_bytes = std::max<int64_t>(stats.peak_resident_bytes, (int64_t)resident_bytes);
+    return true;
+}
+
+// Streams, events and pinned buffers of the slots and of the registered tensors.
 void sym_server_s::release() {
     for (auto& s : slots) {
         if (s.stream) cudaStreamDestroy(s.stream);
@@ -96,37 +207,59 @@ void sym_server_s::release() {
         s.done = nullptr;
         s.res_host = nullptr;
     }
+    for (auto& e : entries) {
+        if (e.X) sym_tensor_destroy(e.X);
+        if (e.ready) cudaEventDestroy(e.ready);
+        e.X = nullptr;
+        e.ready = nullptr;
+    }
 }
 
 void sym_server_s::finish(Slot& s, sym_status st) {
-    sym_result res{};
-    res.status = st;
-    res.residual = (st == SYM_OK && s.req.r.want_residual) ? *s.res_host : 0.0;
-    res.user_tag = s.req.r.user_tag;
-    res.t_submit_ns = s.req.t_submit;
-    res.t_admit_ns = s.t_admit;
-    res.t_done_ns = now_ns();
+    const uint64_t t_done = now_ns();
     {
         std::lock_guard<std::mutex> lk(mu);
-        done[s.req.ticket] = res;
-        live.erase(s.req.ticket);
-        inflight_bytes -= s.req.bytes;
-        inflight -= 1;
-        stats.completed += 1;
+        for (size_t k = 0; k < s.reqs.size(); ++k) {
+            const Pending& p = s.reqs[k];
+            sym_result res{};
+            res.status = st;
+            res.residual = (st == SYM_OK && p.r.want_residual) ? s.res_host[k] : 0.0;
+            res.user_tag = p.r.user_tag;
+            res.t_submit_ns = p.t_submit;
+            res.t_admit_ns = s.t_admit;
+            res.t_done_ns = t_done;
+            done[p.ticket] = res;
+            live.erase(p.ticket);
+            inflight_bytes -= p.bytes;
+            inflight -= 1;
+            stats.completed += 1;
+            if (p.reg >= 0) entries[(size_t)p.reg].inuse -= 1;
+        }
     }
+    s.reqs.clear();
     s.busy = false;
     cv_done.notify_all();
 }
 
 void sym_server_s::launch(Slot& s) {
     using namespace symgpu;
-    const sym_request& r = s.req.r;
-    const bool bf16 = r.bdt == SYM_BF16;
-    sym_status st = mttkrp_core(r.X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.stream);
-    if (st == SYM_OK && r.want_residual) {
-        st = residual_launch(r.X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.res_dev, s.ws, s.ws_bytes, s.stream);
-        if (st == SYM_OK)
-            st = cuda_status(cudaMemcpyAsync(s.res_host, s.res_dev, sizeof(double), cudaMemcpyDeviceToHost, s.stream));
+    sym_status st = s.launch_status;
+    for (size_t k = 0; k < s.reqs.size() && st == SYM_OK; ++k) {
+        const sym_request& r = s.reqs[k].r;
+        const bool bf16 = r.bdt == SYM_BF16;
+        const sym_tensor_s* X = r.X;
+        if (s.reqs[k].reg >= 0) {
+            Entry& E = entries[(size_t)s.reqs[k].reg];
+            X = E.X;
+            st = cuda_status(cudaStreamWaitEvent(s.stream, E.ready, 0));  // its load may run on another slot
+        }
+        if (st == SYM_OK) st = mttkrp_core(X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.stream);
+        if (st == SYM_OK && r.want_residual) {
+            st = residual_launch(X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.res_dev + k, s.ws, s.ws_bytes, s.stream);
+            if (st == SYM_OK)
+                st = cuda_status(
+                    cudaMemcpyAsync(s.res_host + k, s.res_dev + k, sizeof(double), cudaMemcpyDeviceToHost, s.stream));
+        }
     }
     if (st == SYM_OK) st = cuda_status(cudaEventRecord(s.done, s.stream));
     s.launch_status = st;
@@ -156,6 +289,7 @@ void sym_server_s::run() {
             std::unique_lock<std::mutex> lk(mu);
             if (stop && queue.empty() && inflight == 0) break;
             const uint64_t t = now_ns();
+            Slot* group = nullptr;  // the slot collecting this pass's small requests
             for (auto it = queue.begin(); it != queue.end();) {
                 if (inflight_bytes + it->bytes > cfg.hbm_budget_bytes) {
                     // head blocked on budget: later requests may pass it for a while
@@ -163,41 +297,59 @@ void sym_server_s::run() {
                     ++it;
                     continue;
                 }
-                Slot* pick = nullptr;
-                for (auto& s : slots)  // small -> prefer high priority; large -> prefer low
-                    if (!s.busy && s.high == it->small) {
-                        pick = &s;
-                        break;
-                    }
-                if (!pick)
-                    for (auto& s : slots)
-                        if (!s.busy) {
+                const bool join = cfg.coalesce_small && it->small && group && (int)group->reqs.size() < kMaxGroup;
+                Slot* pick = join ? group : nullptr;
+                if (!pick) {
+                    for (auto& s : slots)  // small -> prefer high priority; large -> prefer low
+                        if (!s.busy && s.high == it->small) {
                             pick = &s;
                             break;
                         }
+                    if (!pick)
+                        for (auto& s : slots)
+                            if (!s.busy) {
+                                pick = &s;
+                                break;
+                            }
+                }
                 if (!pick) break;
-                pick->busy = true;
-                pick->req = *it;
-                pick->t_admit = t;
+                if (!pick->busy) pick->launch_status = SYM_OK;
+                if (it->reg >= 0) {
+                    Entry& E = entries[(size_t)it->reg];
+                    if (!E.resident) {
+                        sym_status err = SYM_OK;
+                        if (!make_resident(E, pick->stream, &err)) {
+                            ++it;  // no room in the pool yet: later requests may pass
+                            continue;
+                        }
+                        if (err != SYM_OK) pick->launch_status = err;
+                    }
+                    E.inuse += 1;
+                    E.last_use = ++tick;
+                }
+                if (!pick->busy) {
+                    pick->busy = true;
+                    pick->t_admit = t;
+                    to_launch.push_back(pick);
+                    stats.launches += 1;
+                    if (cfg.coalesce_small && it->small) group = pick;
+                } else if ((int)pick->reqs.size() == 1) {
+                    stats.grouped_launches += 1;  // the slot's first request now leads a group
+                }
+                pick->reqs.push_back(*it);
                 inflight_bytes += it->bytes;
                 inflight += 1;
                 stats.admitted += 1;
                 stats.peak_inflight = std::max<int64_t>(stats.peak_inflight, inflight);
-                stats.peak_bytes = std::max<int64_t>(stats.peak_bytes, (int64_t)inflight_bytes);
-                to_launch.push_back(pick);
+                stats.peak_bytes = std::max<int64_t>(stats.peak_bytes, (int64_t)(inflight_bytes + resident_bytes));
                 it = queue.erase(it);
             }
             if (to_launch.empty() && !progressed) {
                 if (inflight == 0)
-                    cv_sched.wait_for(lk, std::chrono::milliseconds(20),
-                                      [&] { return stop || !queue.empty(); });
+                    cv_sched.wait_for(lk, std::chrono::milliseconds(20), [&] { return stop || !queue.empty(); });
             }
         }
-        for (Slot* s : to_launch) {
-            launch(*s);
-            std::lock_guard<std::mutex> lk(mu);
-            stats.launches += 1;
-        }
+        for (Slot* s : to_launch) launch(*s);
         if (to_launch.empty() && !progressed) std::this_thread::sleep_for(std::chrono::microseconds(10));
     }
     bool self_release;
@@ -215,8 +367,7 @@ using namespace symgpu;
 
 extern "C" size_t sym_server_arena_bytes(const sym_server_cfg* cfg) {
     if (!cfg || cfg->max_slots < 1 || cfg->max_rank < 4) return 0;
-    const size_t per = align_up(residual_ws_bytes(cfg->max_rank), 256) + 256;
-    return per * (size_t)cfg->max_slots;
+    return slot_bytes(cfg) * (size_t)cfg->max_slots + align_up(cfg->pool_bytes, 256);
 }
 
 extern "C" sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, size_t arena_bytes, int device,
@@ -226,6 +377,7 @@ extern "C" sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, 
     if (!cfg || cfg->max_slots < 1 || cfg->max_slots > 256 || cfg->max_rank < 4 || cfg->max_rank > 128 ||
         cfg->max_rank % 4 || cfg->hbm_budget_bytes == 0)
         return SYM_E_INVALID;
+    if (cfg->pool_bytes > cfg->hbm_budget_bytes) return SYM_E_BUDGET;
     if (!arena || !aligned(arena, 256)) return SYM_E_INVALID;
     if (arena_bytes < sym_server_arena_bytes(cfg)) return SYM_E_NOMEM;
     sym_server_s* S = new (std::nothrow) sym_server_s();
@@ -237,39 +389,71 @@ extern "C" sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, 
     int lo = 0, hi = 0;
     if (st == SYM_OK) st = cuda_status(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     S->slots.resize((size_t)cfg->max_slots);
-    const size_t per = align_up(residual_ws_bytes(cfg->max_rank), 256) + 256;
+    const size_t per = slot_bytes(cfg);
     for (int k = 0; k < cfg->max_slots && st == SYM_OK; ++k) {
         Slot& s = S->slots[(size_t)k];
         s.high = k < (cfg->max_slots + 1) / 2;
         st = cuda_status(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, s.high ? hi : lo));
         if (st == SYM_OK) st = cuda_status(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
-        if (st == SYM_OK) st = cuda_status(cudaHostAlloc((void**)&s.res_host, sizeof(double), cudaHostAllocDefault));
+        if (st == SYM_OK)
+            st = cuda_status(cudaHostAlloc((void**)&s.res_host, sizeof(double) * kMaxGroup, cudaHostAllocDefault));
         char* base = static_cast<char*>(arena) + per * (size_t)k;
         s.res_dev = reinterpret_cast<double*>(base);
-        s.ws = base + 256;
-        s.ws_bytes = per - 256;
+        s.ws = base + align_up(sizeof(double) * kMaxGroup, 256);
+        s.ws_bytes = per - align_up(sizeof(double) * kMaxGroup, 256);
     }
+    S->pool = static_cast<char*>(arena) + per * (size_t)cfg->max_slots;
+    S->pool_bytes = align_up(cfg->pool_bytes, 256);
+    if (S->pool_bytes) S->free_ranges[0] = S->pool_bytes;
     if (st != SYM_OK) {
-        for (auto& s : S->slots) {
-            if (s.stream) cudaStreamDestroy(s.stream);
-            if (s.done) cudaEventDestroy(s.done);
-            if (s.res_host) cudaFreeHost(s.res_host);
-        }
+        S->release();
         delete S;
         return st;
     }
     try {
         S->th = std::thread([S] { S->run(); });
     } catch (...) {
-        for (auto& s : S->slots) {
-            cudaStreamDestroy(s.stream);
-            cudaEventDestroy(s.done);
-            cudaFreeHost(s.res_host);
-        }
+        S->release();
         delete S;
         return SYM_E_NOMEM;
     }
     *out = S;
+    return SYM_OK;
+}
+
+extern "C" sym_status sym_server_register(sym_server S, const void* image, uint64_t* id) {
+    if (!S || !image || !id) return SYM_E_INVALID;
+    const size_t bytes = sym_tensor_load_bytes(image);
+    if (bytes == 0) return SYM_E_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return SYM_E_INVALID;
+    if (align_up(bytes, 256) > S->pool_bytes) return SYM_E_BUDGET;  // could never be resident
+    Entry e;
+    e.image = image;
+    e.bytes = align_up(bytes, 256);
+    if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) return SYM_E_CUDA;
+    S->entries.push_back(e);
+    *id = (uint64_t)(S->entries.size() - 1);
+    return SYM_OK;
+}
+
+static sym_status enqueue(sym_server S, const sym_request& r, int64_t reg, int64_t n, int64_t nnz, size_t tensor_bytes,
+                          uint64_t* ticket) {
+    const size_t bytes = tensor_bytes + factor_bytes(r, n);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) return SYM_E_INVALID;
+        if (bytes + (reg >= 0 ? S->pool_bytes : 0) > S->cfg.hbm_budget_bytes) {
+            S->stats.rejected += 1;
+            return SYM_E_BUDGET;
+        }
+        Pending p{S->next_ticket++, r, reg, bytes, now_ns(), nnz <= S->cfg.small_nnz};
+        S->queue.push_back(p);
+        S->live.insert(p.ticket);
+        S->stats.submitted += 1;
+        *ticket = p.ticket;
+    }
+    S->cv_sched.notify_one();
     return SYM_OK;
 }
 
@@ -279,22 +463,31 @@ extern "C" sym_status sym_batch_submit(sym_server S, const sym_request* req, uin
     if (validate_mttkrp_args(req->X, req->B, req->bdt, req->rank, req->ldb, req->M, req->ldm) != SYM_OK)
         return SYM_E_BADREQ;
     if (req->rank > S->cfg.max_rank) return SYM_E_BADREQ;
-    const size_t bytes = request_bytes(*req);
+    return enqueue(S, *req, -1, req->X->n, req->X->nnz, req->X->info.arena_used, ticket);
+}
+
+extern "C" sym_status sym_batch_submit_registered(sym_server S, uint64_t id, const sym_request* req,
+                                                  uint64_t* ticket) {
+    if (!S || !req || !ticket) return SYM_E_INVALID;
+    int64_t n = 0, nnz = 0;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (S->stop) return SYM_E_INVALID;
-        if (bytes > S->cfg.hbm_budget_bytes) {
-            S->stats.rejected += 1;
-            return SYM_E_BUDGET;
-        }
-        Pending p{S->next_ticket++, *req, bytes, now_ns(), req->X->nnz <= S->cfg.small_nnz};
-        S->queue.push_back(p);
-        S->live.insert(p.ticket);
-        S->stats.submitted += 1;
-        *ticket = p.ticket;
+        if (id >= S->entries.size()) return SYM_E_NOTFOUND;
+        // the header fields the checks need, without touching the device
+        const size_t lb = sym_tensor_load_bytes(S->entries[(size_t)id].image);
+        if (lb == 0) return SYM_E_BADREQ;
+        sym_tensor_info_t inf;
+        if (sym_tensor_image_info(S->entries[(size_t)id].image, &inf) != SYM_OK) return SYM_E_BADREQ;
+        n = inf.n;
+        nnz = inf.nnz;
     }
-    S->cv_sched.notify_one();
-    return SYM_OK;
+    if (!req->B || !req->M || (req->bdt != SYM_F32 && req->bdt != SYM_BF16)) return SYM_E_BADREQ;
+    if (req->rank < 4 || req->rank > 128 || req->rank % 4 || req->rank > S->cfg.max_rank) return SYM_E_BADREQ;
+    if (req->ldb < req->rank || req->ldm < req->rank || req->ldb % 4 || req->ldm % 4) return SYM_E_BADREQ;
+    if (!aligned(req->B, req->bdt == SYM_BF16 ? 8 : 16) || !aligned(req->M, 16)) return SYM_E_BADREQ;
+    sym_request r = *req;
+    r.X = nullptr;
+    return enqueue(S, r, (int64_t)id, n, nnz, 0, ticket);
 }
 
 extern "C" sym_status sym_batch_poll(sym_server S, uint64_t ticket, sym_result* out) {
@@ -341,6 +534,7 @@ extern "C" sym_status sym_server_stats_get(sym_server S, sym_server_stats* out) 
     if (!S || !out) return SYM_E_INVALID;
     std::lock_guard<std::mutex> lk(S->mu);
     *out = S->stats;
+    out->resident_bytes = (int64_t)S->resident_bytes;
     return SYM_OK;
 }
 

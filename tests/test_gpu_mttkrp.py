@@ -238,68 +238,10 @@ def test_cpfit_good_fit_cancellation():
     assert abs(float(res.item()) - want) <= TOL_F32 * ab
 
 
-HOT_CONFIGS = [
-    # (threads, ctas_per_sm, smem_kb, b_share, chunk, leaf_index)
-    (1024, 1, 200, 25, 256, 1),
-    (512, 1, 128, 0, 128, 1),
-    (256, 2, 96, 50, 32, 1),
-    (512, 1, 64, 100, 512, 0),   # only rows of B on chip
-    (128, 4, 0, 0, 64, 1),       # no shared memory: every row in L2
-    (1024, 1, 200, 0, 1024, 0),
-]
-
-
-@pytest.mark.parametrize("k", range(len(HOT_CONFIGS)))
-@pytest.mark.parametrize("case", ["zipf3_r64", "zipf3_r12_bf16", "unif2_r4", "unif4_r32", "unif5_r16_all_on_chip",
-                                  "unif3_two_word_keys"])
-def test_mttkrp_hot_kernel(k, case):
-    """The persistent hot-row kernel: rows of M and B below H / HB on chip, chunks from a per-CTA counter,
-    with and without the leaf index (smallest index of each tuple as the leaf)."""
-    sg = need_gpu()
-    thr, cps, kb, bs, chunk, leaf = HOT_CONFIGS[k]
-    bf16 = case.endswith("bf16")
-    if case.startswith("zipf3"):
-        T, R = synth.tensor3_zipf(3000, 80000, 14), (64 if case == "zipf3_r64" else 12)
-    elif case == "unif2_r4":
-        T, R = synth.tensor_uniform(2, 700, 9000, 15), 4
-    elif case == "unif4_r32":
-        T, R = synth.tensor_uniform(4, 80, 30001, 16), 32
-    elif case == "unif5_r16_all_on_chip":
-        T, R = synth.tensor_uniform(5, 20, 8003, 17), 16
-    else:
-        T, R = synth.tensor_uniform(3, 5_000_000, 20000, 18), 16   # 3 x 23 bits: two-word keys
-    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
-    if leaf and T.order >= 3:
-        X.add_leaf_index()
-    X.set_config(strict_kernel=sg.MTTKRP_HOT, entries_per_warp=chunk, threads_per_cta=thr, ctas_per_sm=cps,
-                 strict_smem_kb=kb, b_share_pct=bs, leaf_index=leaf, stream_hint=1)
-    Bt, B32, Bused = factor(T.n, R, 5, bf16)
-    M = host(X.mttkrp(Bt))
-    cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
-    ref, ra = oracle.mttkrp_enum(T.order, T.n, cidx, cval, Bused.astype(np.float64))
-    e = oracle.componentwise_error(M, ref, ra)
-    assert e <= TOL_F32, e
-    if bf16:
-        ref32, ra32 = oracle.mttkrp_enum(T.order, T.n, cidx, cval, B32.astype(np.float64))
-        assert oracle.componentwise_error(M, ref32, ra32) <= TOL_BF16
-
-
-def test_mttkrp_hot_kernel_rejects_bad_config():
-    sg = need_gpu()
-    T = synth.tensor_uniform(3, 50, 500, 1)
-    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
-    for bad in (dict(threads_per_cta=2048), dict(entries_per_warp=0), dict(strict_smem_kb=300),
-                dict(entries_per_warp=48)):
-        cfg = dict(strict_kernel=sg.MTTKRP_HOT, entries_per_warp=256, threads_per_cta=512, ctas_per_sm=1,
-                   strict_smem_kb=64)
-        cfg.update(bad)
-        with pytest.raises(sg.SymError):
-            X.set_config(**cfg)
-
-
 LANE_CONFIGS = [
-    # (chunk, depth, leaf_index)
-    (256, 1, 1), (512, 4, 1), (32, 1, 0), (96, 4, 0), (1024, 1, 0), (64, 4, 1),
+    # (chunk, depth, leaf_index, root pass: 0 unfactorised / 1 factorised, root-pass chunk / 64)
+    (256, 1, 1, 0, 2), (512, 4, 1, 0, 8), (32, 1, 0, 0, 1), (96, 4, 0, 0, 1), (1024, 1, 0, 0, 1), (64, 4, 1, 1, 1),
+    (128, 1, 1, 1, 1), (64, 1, 1, 0, 1),
 ]
 
 
@@ -308,10 +250,11 @@ LANE_CONFIGS = [
                                   "unif3_two_word_keys", "zipf3_r128"])
 def test_mttkrp_lane_kernel(k, case):
     """Lane-parallel decoding (each lane decodes one entry and finds its first changed fiber level), one pass
-    or two passes (canonical stream without the leaf, leaf index for the root), 1 or 4 leaf gathers in flight,
-    chunks that split fibers between warps and between the groups of a warp."""
+    or two passes (canonical stream without the leaf, then the leaf index for the root, factorised or
+    unfactorised below it), 1 or 4 leaf gathers in flight, chunks that split fibers between warps and between
+    the groups of a warp, and ragged entry counts (the groups of the last warp hold different numbers)."""
     sg = need_gpu()
-    chunk, depth, leaf = LANE_CONFIGS[k]
+    chunk, depth, leaf, factorised_root, rchunk = LANE_CONFIGS[k]
     bf16 = case.endswith("bf16")
     if case.startswith("zipf3"):
         R = {"zipf3_r64": 64, "zipf3_r12_bf16": 12, "zipf3_r128": 128}[case]
@@ -328,7 +271,7 @@ def test_mttkrp_lane_kernel(k, case):
     if leaf and T.order >= 3:
         X.add_leaf_index()
     X.set_config(strict_kernel=sg.MTTKRP_LANE, entries_per_warp=chunk, threads_per_cta=256, leaf_index=leaf,
-                 vec_per_lane=depth, stream_hint=1)
+                 vec_per_lane=depth, stream_hint=1, strict_smem_kb=factorised_root, ctas_per_sm=rchunk)
     Bt, B32, Bused = factor(T.n, R, 6, bf16)
     M = host(X.mttkrp(Bt))
     cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
@@ -338,3 +281,14 @@ def test_mttkrp_lane_kernel(k, case):
     if bf16:
         ref32, ra32 = oracle.mttkrp_enum(T.order, T.n, cidx, cval, B32.astype(np.float64))
         assert oracle.componentwise_error(M, ref32, ra32) <= TOL_BF16
+
+
+def test_mttkrp_lane_kernel_rejects_bad_config():
+    sg = need_gpu()
+    T = synth.tensor_uniform(3, 50, 500, 1)
+    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
+    for bad in (dict(vec_per_lane=2), dict(entries_per_warp=0), dict(entries_per_warp=48), dict(strict_kernel=5)):
+        cfg = dict(strict_kernel=sg.MTTKRP_LANE, entries_per_warp=256, threads_per_cta=256, leaf_index=1)
+        cfg.update(bad)
+        with pytest.raises(sg.SymError):
+            X.set_config(**cfg)

@@ -28,7 +28,7 @@ def cuts(total, K, seed):
 
 @pytest.mark.parametrize("K", [2, 3, 7])
 @pytest.mark.parametrize("case", ["zipf3_r32", "unif4_r16", "unif5_r8_diag", "unif2_r4"])
-@pytest.mark.parametrize("kernel", ["plain", "hot"])
+@pytest.mark.parametrize("kernel", ["plain", "lane"])
 def test_mttkrp_entry_partition(K, case, kernel):
     sg = need_gpu()
     if case == "zipf3_r32":
@@ -40,9 +40,9 @@ def test_mttkrp_entry_partition(K, case, kernel):
     else:
         T, R = synth.tensor_uniform(2, 500, 6000, 24), 4
     X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
-    if kernel == "hot":
-        X.set_config(strict_kernel=sg.MTTKRP_HOT, entries_per_warp=64, threads_per_cta=512, ctas_per_sm=1,
-                     strict_smem_kb=64, b_share_pct=25, leaf_index=0)
+    if kernel == "lane":
+        X.set_config(strict_kernel=sg.MTTKRP_LANE, entries_per_warp=64, threads_per_cta=256, leaf_index=1,
+                     vec_per_lane=4 if R >= 16 else 1)
     info = X.info()
     Bt, B32, _ = factor(T.n, R, 7)
     c = cuts(info["nnz"], K, 100 + K)

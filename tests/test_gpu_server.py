@@ -119,3 +119,97 @@ def test_poll_until_done():
     with pytest.raises(sg.SymError):
         S.poll(t)         # results are handed out once
     S.close()
+
+
+def test_registered_tensors_evicted_and_reloaded():
+    """Registered tensors live in a pool smaller than all of them together: requests cycling through them
+    force loads and least-recently-used evictions; every result equals the tensor's own MTTKRP and the oracle."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    P = pool(sg, [(3, 500, 30000), (4, 80, 20000), (5, 25, 8000), (3, 900, 40000), (4, 120, 25000)], seed=31)
+    images = [X.save_image() for _, X in P]
+    sizes = [X.info()["arena_used"] for _, X in P]
+    pool_bytes = int(max(sizes) * 2.2)          # room for about two tensors at once
+    S = sg.Server(max_slots=4, max_rank=32, hbm_budget_bytes=pool_bytes + (64 << 20), pool_bytes=pool_bytes)
+    ids = [S.register(img) for img in images]
+    reqs = []
+    for k in range(20):
+        j = (k * 3) % len(P)            # revisits tensors after others pushed them out
+        T, X = P[j]
+        R = (8, 16, 32)[k % 3]
+        Bt, B32, Bused = factor(T.n, R, 200 + k, bf16=(k % 4 == 1))
+        M = torch.empty((T.n, R), device="cuda")
+        reqs.append((S.submit_registered(ids[j], Bt, M, residual=True, tag=k), T, X, Bt, Bused, M))
+    for t, T, X, Bt, Bused, M in reqs:
+        r = S.wait(t, 60)
+        assert r["status"] == 0
+        cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
+        ref, ra = oracle.mttkrp_enum(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+        assert oracle.componentwise_error(host(M), ref, ra) <= TOL_F32
+        want, ab, _ = oracle.cpfit(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+        assert abs(r["residual"] - want) / ab <= TOL_F32
+    st = S.stats()
+    assert st["completed"] == 20 and st["loads"] > len(P) and st["evictions"] > 0
+    assert st["peak_resident_bytes"] <= pool_bytes and st["peak_bytes"] <= pool_bytes + (64 << 20)
+    # a tensor larger than the whole pool is refused at registration
+    big_pool = sg.Server(max_slots=2, max_rank=16, hbm_budget_bytes=1 << 30, pool_bytes=4096)
+    with pytest.raises(sg.SymError) as e:
+        big_pool.register(images[0])
+    assert e.value.code == -6
+    big_pool.close()
+    with pytest.raises(sg.SymError) as e:
+        S.submit_registered(999, Bt, M)
+    assert e.value.code == -11
+    S.close()
+
+
+def test_small_requests_grouped_launches():
+    """coalesce_small: small requests admitted together share one slot (grouped launch); results unchanged."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    P = pool(sg, [(3, 200, 3000), (4, 40, 2000), (5, 15, 1500)], seed=41)
+    S = sg.Server(max_slots=2, max_rank=16, small_nnz=100_000, coalesce_small=True)
+    reqs = []
+    for k in range(40):
+        T, X = P[k % 3]
+        Bt, B32, Bused = factor(T.n, 16, 300 + k)
+        M = torch.empty((T.n, 16), device="cuda")
+        reqs.append((S.submit(X, Bt, M, residual=True, tag=k), T, Bused, M))
+    for t, T, Bused, M in reqs:
+        r = S.wait(t, 60)
+        assert r["status"] == 0
+        cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
+        ref, ra = oracle.mttkrp_enum(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+        assert oracle.componentwise_error(host(M), ref, ra) <= TOL_F32
+        want, ab, _ = oracle.cpfit(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+        assert abs(r["residual"] - want) / ab <= TOL_F32
+    st = S.stats()
+    assert st["completed"] == 40 and st["launches"] < 40 and st["grouped_launches"] >= 1
+    S.close()
+
+
+def test_destroy_timeout_keeps_buffers_valid():
+    """A drain limit that runs out: destroy returns SYM_E_TIMEOUT while work is in flight; the caller keeps the
+    buffers until the device is done, and the results are still right."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    T = synth.tensor_uniform(3, 3000, 400_000, 51)
+    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
+    S = sg.Server(max_slots=2, max_rank=64, wait_limit_s=1e-9)
+    B = dev(synth.factor_normal(T.n, 64, 51))
+    Ms = [torch.empty((T.n, 64), device="cuda") for _ in range(6)]
+    for M in Ms:
+        S.submit(X, B, M)
+    import time
+    t0 = time.time()
+    while S.stats()["admitted"] < 1 and time.time() - t0 < 10:
+        time.sleep(1e-4)
+    code = sg.lib().sym_server_destroy(S.handle)
+    S.handle = None
+    assert code in (0, -7)     # -7 when work was still in flight at the limit
+    torch.cuda.synchronize()
+    time.sleep(0.2)            # the scheduler thread finishes and releases the server's own resources
+    ref = X.mttkrp(B)
+    torch.cuda.synchronize()
+    # requests that were admitted before the limit ran to completion; queued ones were dropped
+    assert any(float((M - ref).abs().max()) <= 1e-4 * float(ref.abs().max()) for M in Ms)
