@@ -313,6 +313,22 @@ def l2_roof(gathers, reds, R, ceil, n_tag, kernel_ms):
             "peak_source": "measured (sym_ceiling_run: random row gathers / vector row reductions in L2, this run)"}
 
 
+def strict_fiber_counts(order, idx):
+    """Strict canonical entries and their distinct prefixes (c1..cq) for q = 1..N-1 (host, numpy): the fiber
+    counts of the CSF traversal, from which the algorithmic row operations of an MTTKRP pass follow."""
+    rows = np.sort(np.asarray(idx).T, axis=1)
+    rows = rows[np.all(rows[:, 1:] != rows[:, :-1], axis=1)]
+    rows = rows[np.lexsort(rows.T[::-1])]
+    change = np.zeros(len(rows), bool)
+    if len(rows):
+        change[0] = True
+    counts = []
+    for q in range(order - 1):
+        change[1:] |= rows[1:, q] != rows[:-1, q]
+        counts.append(int(change.sum()))
+    return len(rows), counts
+
+
 def sampled_row_errors(order, n, idx, val, B32, M, Mb=None, Bb=None, rows=64, seed=0):
     """Componentwise error of the GPU result on a sample of output rows, against the FP64 oracle (the
     definitional enumeration restricted to those rows).  BF16: against the oracle on the FP32 factor (gate
@@ -503,6 +519,25 @@ def run_ours(args):
         Xe.close()
 
     e2e_step()
+    # one more step with events between its phases (where the end-to-end time goes)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    t_host = time.perf_counter()
+    ev[0].record()
+    i_d = idx_h.to(dev, non_blocking=True)
+    v_d = val_h.to(dev, non_blocking=True)
+    b_d = B_h.to(dev, non_blocking=True)
+    ev[1].record()
+    Xe = sg.SymTensor(i_d, v_d, T.n, ws=ws_create)
+    ev[2].record()
+    Xe.mttkrp(b_d, M=M)
+    ev[3].record()
+    M_h.copy_(M, non_blocking=True)
+    ev[4].record()
+    torch.cuda.synchronize()
+    e2e_parts = {"h2d_ms": ev[0].elapsed_time(ev[1]), "canonicalise_ms": ev[1].elapsed_time(ev[2]),
+                 "mttkrp_ms": ev[2].elapsed_time(ev[3]), "d2h_ms": ev[3].elapsed_time(ev[4]),
+                 "host_wall_ms": (time.perf_counter() - t_host) * 1e3}
+    Xe.close()
     e2e_k = max(3, min(args.steps, 10))
     D.barrier()
     t0 = time.perf_counter()
@@ -514,7 +549,7 @@ def run_ours(args):
 
     # ---- secondary rows
     if args.rows == "all" and D.rank == 0:
-        extras["rows"] = secondary_rows(torch, sg, dev, flush, stream, hbm_peak)
+        extras["rows"] = secondary_rows(torch, sg, dev, flush, stream, hbm_peak, ceil)
         try:
             extras["rows"]["batched_ssymv_syprd_4096"] = batch_row(torch, sg, dev, flush, stream, hbm_peak)
         except Exception as e:
@@ -535,7 +570,8 @@ def run_ours(args):
            "roofline": roof,
            "e2e": {"value": info["nnz"] * D.ws / e2e_s, "unit": "canonical nnz/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
-                   "includes": "H2D of coordinate list + values + factor, canonicalisation, MTTKRP, D2H of M"},
+                   "includes": "H2D of coordinate list + values + factor, canonicalisation, MTTKRP, D2H of M",
+                   "one_step_breakdown": e2e_parts},
            "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed": t_wall, "extras": extras}
     if D.rank == 0 and not args.no_cpu:
         rate, meta = oracle_sample_rate(T, MAIN["rank"])
@@ -554,7 +590,7 @@ def run_ours(args):
     D.close()
 
 
-def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
+def secondary_rows(torch, sg, dev, flush, stream, hbm_peak, ceil=None):
     rows = {}
     # 4-way and 5-way symmetric MTTKRP, FP32 and BF16 factors
     for name, order, n, nnz, rank in [("mttkrp4_unif_n20k_nnz10M_r32", 4, 20_000, 10_000_000, 32),
@@ -601,6 +637,13 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak):
             E.close()
         except Exception as e:
             r["expanded_error"] = str(e)
+        if ceil:
+            # one factor-row gather and one row reduction per strict entry (leaf) and per fiber of every level
+            ns, fib = strict_fiber_counts(order, T.idx)
+            ops = ns + sum(fib)
+            strict_ms = sum(v for k, v in r["f32"]["per_kernel_ms"].items() if k.startswith("mttkrp_strict"))
+            r["roofline"] = l2_roof(ops, ops, rank, ceil, f"n{n}_r{rank}", strict_ms)
+            r["roofline"]["fibers_per_level"] = fib
         rows[name] = r
         X.close()
     rows["ssymv_n2000_nnz20k"] = small_ssymv_row(torch, sg, dev, flush, stream)

@@ -87,6 +87,18 @@ sym_status sym_profile_enable(int on);
 int sym_profile_read(sym_profile_entry* out, int max_entries);
 sym_status sym_profile_reset(void);
 
+/* Bounds-checked build (no paper counterpart: a checking aid in place of a
+ * memory checker).  libsymgpu_bc.so is this library compiled with
+ * -DSYM_BOUNDS_CHECK: the kernels of the hot path (canonical-stream MTTKRP,
+ * SSYMV / SYPRD in the multi-block, one-launch and banded forms) check every
+ * gathered or scattered index against the extent of its array, skip an access
+ * outside it and add one to *counter; they never trap.  sym_bounds_check_enabled
+ * returns 1 in that library and 0 here; sym_bounds_check_attach sets the
+ * counter [device, 8-byte aligned, caller-owned; NULL detaches] for every
+ * kernel of the library (SYM_E_UNSUPPORTED in the normal build).  Synchronous. */
+int sym_bounds_check_enabled(void);
+sym_status sym_bounds_check_attach(unsigned long long* counter);
+
 /* Measured ceilings of the operations the kernels are made of (no paper
  * counterpart: the denominators of the roofline fractions the benchmarks
  * report).  Each kind times one kernel of the primitive operation alone:

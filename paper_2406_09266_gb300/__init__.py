@@ -135,6 +135,8 @@ _SIGS = {
     "sym_profile_enable": ([C.c_int], C.c_int),
     "sym_profile_read": ([C.c_void_p, C.c_int], C.c_int),
     "sym_profile_reset": ([], C.c_int),
+    "sym_bounds_check_enabled": ([], C.c_int),
+    "sym_bounds_check_attach": ([C.c_void_p], C.c_int),
     "sym_ceiling_bytes": ([C.c_int, C.c_int64, C.c_int], C.c_size_t),
     "sym_ceiling_run": ([C.c_int, C.c_void_p, C.c_size_t, C.c_int64, C.c_int, C.c_int64, C.c_int, C.c_void_p,
                          C.c_void_p, C.c_void_p], C.c_int),

@@ -41,8 +41,16 @@ def _headers():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+# The bounds-checked library (every gather / scatter index of the hot-path kernels checked, violations counted):
+# the sources it needs, compiled with -DSYM_BOUNDS_CHECK into a build folder of its own.
+LIB_BC = os.path.join(PKG, "libsymgpu_bc.so")
+BUILD_BC = os.path.join(PKG, "_build_bc")
+BC_SOURCES = ("common.cu", "sort.cu", "tensor.cu", "mttkrp.cu", "mttkrp_n2.cu", "mttkrp_n3.cu", "mttkrp_n4.cu",
+              "mttkrp_n5.cu", "spmv.cu", "spmv_cluster.cu", "spmv_band.cu", "spmv_batch.cu", "cpals.cu")
+
+
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj
@@ -58,25 +66,29 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, jobs: int | None = None, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, jobs: int | None = None, extra=(), bounds_check: bool = False) -> str:
+    build_dir, lib = (BUILD_BC, LIB_BC) if bounds_check else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
+    if bounds_check:
+        srcs = [s for s in srcs if os.path.basename(s) in BC_SOURCES]
+        extra = tuple(extra) + ("-DSYM_BOUNDS_CHECK",)
     if force:
-        for f in glob.glob(os.path.join(BUILD, "*.o")):
+        for f in glob.glob(os.path.join(build_dir, "*.o")):
             os.remove(f)
     jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv))
+    print(build(force="--force" in sys.argv, bounds_check="--bounds-check" in sys.argv))

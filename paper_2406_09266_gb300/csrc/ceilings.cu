@@ -174,18 +174,11 @@ __global__ void __launch_bounds__(CEIL_THREADS) k_ceil_bulk(const float* __restr
             }
         }
         if (!RED) {
-            // bounded wait for this iteration's rows (records a timeout, never hangs); on a timeout
-            // it waits once more, bounded, for the copies still in flight, then stops
+            // bounded wait for this iteration's rows (records a timeout, never hangs): lane 0 waits and the
+            // warp follows its verdict, so every lane leaves the loop together; on a timeout lane 0 waits once
+            // more, bounded, for the copies still in flight, then the warp stops
             uint32_t ok = 0;
-            for (int spin = 0; spin < (1 << 22) && !ok; ++spin)
-                asm volatile(
-                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
-                    "p;\n}\n"
-                    : "=r"(ok)
-                    : "r"(smem_addr(&bar[warp])), "r"(phase)
-                    : "memory");
-            if (!ok) {
-                if (lane == 0) atomicOr(reinterpret_cast<unsigned*>(out) + 1023, 2u);
+            if (lane == 0) {
                 for (int spin = 0; spin < (1 << 22) && !ok; ++spin)
                     asm volatile(
                         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, "
@@ -193,7 +186,30 @@ __global__ void __launch_bounds__(CEIL_THREADS) k_ceil_bulk(const float* __restr
                         : "=r"(ok)
                         : "r"(smem_addr(&bar[warp])), "r"(phase)
                         : "memory");
-                break;
+                if (!ok) {
+                    atomicOr(reinterpret_cast<unsigned*>(out) + 1023, 2u);
+                    uint32_t late = 0;
+                    for (int spin = 0; spin < (1 << 22) && !late; ++spin)
+                        asm volatile(
+                            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 "
+                            "%0, 1, 0, p;\n}\n"
+                            : "=r"(late)
+                            : "r"(smem_addr(&bar[warp])), "r"(phase)
+                            : "memory");
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            // the other lanes observe the completed phase too before reading the rows
+            if (lane != 0) {
+                uint32_t seen = 0;
+                for (int spin = 0; spin < 64 && !seen; ++spin)
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 "
+                        "%0, 1, 0, p;\n}\n"
+                        : "=r"(seen)
+                        : "r"(smem_addr(&bar[warp])), "r"(phase)
+                        : "memory");
             }
             phase ^= 1u;
             acc += buf[lane % R];

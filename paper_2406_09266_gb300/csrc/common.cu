@@ -123,7 +123,36 @@ ProfScope::~ProfScope() {
     }
 }
 
+std::vector<sym_status (*)(unsigned long long*)>& bc_setters() {
+    static std::vector<sym_status (*)(unsigned long long*)> v;  // filled during static initialisation
+    return v;
+}
+
+void bc_register_setter(sym_status (*set)(unsigned long long*)) { bc_setters().push_back(set); }
+
 }  // namespace symgpu
+
+extern "C" int sym_bounds_check_enabled(void) {
+#ifdef SYM_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" sym_status sym_bounds_check_attach(unsigned long long* counter) {
+#ifdef SYM_BOUNDS_CHECK
+    if (counter && !symgpu::aligned(counter, 8)) return SYM_E_INVALID;
+    for (auto set : symgpu::bc_setters()) {
+        const sym_status st = set(counter);
+        if (st != SYM_OK) return st;
+    }
+    return SYM_OK;
+#else
+    (void)counter;
+    return SYM_E_UNSUPPORTED;
+#endif
+}
 
 extern "C" sym_status sym_profile_enable(int on) {
     symgpu::g_prof_on.store(on ? 1 : 0);

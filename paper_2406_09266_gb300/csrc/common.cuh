@@ -76,6 +76,39 @@ struct ProfScope {
 };
 #define SYM_PROF(name, stream) symgpu::ProfScope _sym_prof_scope(name, stream)
 
+// ---------------------------------------------------------------- bounds-checked build
+//
+// Compiled with -DSYM_BOUNDS_CHECK (the separate libsymgpu_bc.so), the kernels
+// of the hot path check every gathered or scattered index against the extent
+// of its array before the access; an index outside it skips the access and adds
+// one to a caller-given device counter (sym_bounds_check_attach), never a trap.
+// Device code cannot share one global across translation units without
+// relocatable device code, so every translation unit holds its own copy of the
+// counter's address and registers a setter that sym_bounds_check_attach calls.
+// In the normal build SYM_INDEX_OK is the constant true and nothing is emitted.
+void bc_register_setter(sym_status (*set)(unsigned long long*));
+#ifdef SYM_BOUNDS_CHECK
+static __device__ unsigned long long* g_bc_counter = nullptr;
+namespace {
+inline sym_status bc_set_counter_here(unsigned long long* p) {
+    return cuda_status(cudaMemcpyToSymbol(g_bc_counter, &p, sizeof(p)));
+}
+struct BcRegistrar {
+    BcRegistrar() { bc_register_setter(&bc_set_counter_here); }
+};
+static BcRegistrar g_bc_registrar;
+}  // namespace
+__device__ __forceinline__ bool bc_index_ok(int64_t i, int64_t n) {
+    if (i >= 0 && i < n) return true;
+    unsigned long long* c = g_bc_counter;
+    if (c) atomicAdd(c, 1ull);
+    return false;
+}
+#define SYM_INDEX_OK(i, n) symgpu::bc_index_ok((int64_t)(i), (int64_t)(n))
+#else
+#define SYM_INDEX_OK(i, n) true
+#endif
+
 // ---------------------------------------------------------------- device utils
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -46,6 +46,22 @@ __device__ __forceinline__ void decode_entry(uint64_t lo, uint64_t hi, int bits,
     unpack_key<N, KW>(KeyWords{lo, hi}, bits, c);
 }
 
+// Bounds-checked build: every coordinate of a decoded entry against the tensor's
+// dimension n (a violation is counted and the entry skipped); true otherwise.
+template <int N>
+__device__ __forceinline__ bool coords_in_range(const int32_t* c, int64_t n) {
+#ifdef SYM_BOUNDS_CHECK
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < N; ++q) ok = SYM_INDEX_OK(c[q], n) && ok;
+    return ok;
+#else
+    (void)c;
+    (void)n;
+    return true;
+#endif
+}
+
 __device__ __forceinline__ float f4_get(const float4& v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
@@ -144,7 +160,7 @@ template <int N, int KW, int L, bool BF16, int MODE>
 __global__ void __launch_bounds__(MT_THREADS, (N <= 3 && KW == 1 && L > 1) ? 5 : 1) k_mttkrp_strict(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
-    int64_t chunk, int stream_hint) {
+    int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX) {
     static_assert(N >= 2 && N <= 5, "order");
     constexpr int LV = N - 1;  // fiber levels above the leaf
     const int lane = threadIdx.x & 31;
@@ -190,6 +206,7 @@ __global__ void __launch_bounds__(MT_THREADS, (N <= 3 && KW == 1 && L > 1) ? 5 :
             if (b0 + src >= end) continue;
             int32_t c[N];
             decode_entry<N, KW>(lo, hi, bits, c);
+            if (!coords_in_range<N>(c, nrows)) continue;
             // first fiber level whose coordinate changed (LV: same prefix)
             int d = LV;
 #pragma unroll
@@ -647,7 +664,7 @@ template <int N, int KW, int L, bool BF16, int MODE, int D>
 __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
-    int64_t chunk, int stream_hint) {
+    int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX) {
     static_assert(N >= 2 && N <= 5, "order");
     static_assert(D >= 1 && D <= L && L % D == 0, "prefetch depth divides the lanes per entry");
     constexpr int LV = N - 1;
@@ -712,7 +729,10 @@ __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
             if (c[q] != prev) d = q;
         }
         if (b == 0 && sl == 0) d = 0;  // the group's first entry opens every level
-        const uint32_t packed = ((uint32_t)c[N - 1] << 3) | (uint32_t)d;
+        // level 7 marks an entry the bounds-checked build drops (an index outside [0, n))
+        const bool valid = gs + (int64_t)b * L + sl < ge;
+        const bool inr = !valid || coords_in_range<N>(c, nrows);
+        const uint32_t packed = inr ? (((uint32_t)c[N - 1] << 3) | (uint32_t)d) : 7u;
 #pragma unroll
         for (int q = 0; q < LV; ++q) lastc[q] = __shfl_sync(0xffffffffu, c[q], g * L + L - 1);
 
@@ -726,13 +746,14 @@ __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
             for (int k = 0; k < D; ++k) {
                 pk[k] = __shfl_sync(0xffffffffu, packed, g * L + t0 + k);
                 vt[k] = __shfl_sync(0xffffffffu, v, g * L + t0 + k);
-                const bool ok = on && (gs + (int64_t)b * L + t0 + k < ge);
+                const bool ok = on && (gs + (int64_t)b * L + t0 + k < ge) && (pk[k] & 7u) != 7u;
                 bl[k] = ok ? load_row4<BF16>(B, (int64_t)(pk[k] >> 3), ldb, col) : f4_zero();
             }
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 if (gs + (int64_t)b * L + t0 + k >= ge) continue;  // group-uniform
                 const int dt = (int)(pk[k] & 7u);
+                if (dt == 7) continue;  // dropped by the bounds check
                 if (dt < LV) {
                     if (have && on) {
 #pragma unroll
@@ -790,7 +811,7 @@ template <int N, int KW, int L, bool BF16>
 __global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
-    int64_t chunk, int stream_hint) {
+    int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX) {
     static_assert(N >= 2 && N <= 5, "order");
     constexpr int G = 32 / L;
     const int lane = threadIdx.x & 31;
@@ -835,7 +856,8 @@ __global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
         decode_entry<N, KW>(lo, hi, bits, c);
         const int32_t up = __shfl_up_sync(0xffffffffu, c[0], 1, L);
         const int32_t prev = sl == 0 ? lastroot : up;
-        const int32_t newroot = (c[0] != prev || (b == 0 && sl == 0)) ? c[0] : -1;  // -1: same root as before
+        int32_t newroot = (c[0] != prev || (b == 0 && sl == 0)) ? c[0] : -1;  // -1: same root as before
+        if (!coords_in_range<N>(c, nrows) && gs + (int64_t)b * L + sl < ge) newroot = -2;  // dropped entry
         lastroot = __shfl_sync(0xffffffffu, c[0], g * L + L - 1);
 #pragma unroll 1
         for (int t = 0; t < L; ++t) {
@@ -847,7 +869,7 @@ __global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
             for (int q = 1; q < N; ++q) r[q - 1] = __shfl_sync(0xffffffffu, c[q], src);
             // Past the group's last entry the lanes skip the work but stay in the loop: every lane of the
             // warp must reach each full-warp shuffle above, whatever its group's entry count.
-            if (gs + (int64_t)b * L + t >= ge) continue;
+            if (gs + (int64_t)b * L + t >= ge || nr == -2) continue;
             if (nr >= 0) {  // a new root fiber starts at this entry
                 if (root >= 0 && on) red_add_f4(M + (int64_t)root * ldm + col, f4_scale(acc, w));
                 root = nr;
@@ -870,7 +892,8 @@ __global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
 template <int N, int KW, int L, bool BF16>
 __global__ void __launch_bounds__(512) k_mttkrp_entries(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t cnt,
-    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, int H, int HB) {
+    int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, int H, int HB,
+    int64_t nrows = INT64_MAX) {
     extern __shared__ float4 sink_mem[];
     float* sm_m = reinterpret_cast<float*>(sink_mem);
     float* sm_b = sm_m + (size_t)H * R;
@@ -891,6 +914,7 @@ __global__ void __launch_bounds__(512) k_mttkrp_entries(
     for (int64_t e = group; e < cnt && on; e += ngroups) {
         int32_t c[N];
         decode_entry<N, KW>(klo[e], KW == 2 ? khi[e] : 0ull, bits, c);
+        if (!coords_in_range<N>(c, nrows)) continue;
         const float v = val[e];
         float4 b[N];
 #pragma unroll
@@ -952,16 +976,16 @@ inline SinkPlan plan_sink(int64_t n, int R, int kb, int b_share_pct) {
 template <int N, int KW, int L, bool BF16, int MODE>
 sym_status launch_lane_m(int depth, int64_t cnt, const uint64_t* klo, const uint64_t* khi, const float* val, int bits,
                          const void* B, int64_t ldb, int R, float* M, int64_t ldm, float w, int64_t chunk,
-                         int stream_hint, const char* name, cudaStream_t s) {
+                         int stream_hint, const char* name, cudaStream_t s, int64_t nrows) {
     const int64_t warps = (cnt + chunk - 1) / chunk;
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
     SYM_PROF(name, s);
     if (depth >= 4 && L >= 4)
         k_mttkrp_lane<N, KW, L, BF16, MODE, (L >= 4 ? 4 : 1)><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M,
-                                                                                 ldm, w, chunk, stream_hint);
+                                                                                 ldm, w, chunk, stream_hint, nrows);
     else
         k_mttkrp_lane<N, KW, L, BF16, MODE, 1><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
-                                                                   chunk, stream_hint);
+                                                                   chunk, stream_hint, nrows);
     SYM_CHECK_LAUNCH();
     return SYM_OK;
 }
@@ -992,19 +1016,19 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
                 SYM_PROF("mttkrp_strict", s);
                 k_mttkrp_strict<N, KW, L, BF16, 0><<<grid, MT_THREADS, 0, s>>>(
                     X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                    cfg.stream_hint);
+                    cfg.stream_hint, X->n);
             } else {
                 {
                     SYM_PROF("mttkrp_strict", s);
                     k_mttkrp_strict<N, KW, L, BF16, 1><<<grid, MT_THREADS, 0, s>>>(
                         X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                        cfg.stream_hint);
+                        cfg.stream_hint, X->n);
                 }
                 SYM_CHECK_LAUNCH();
                 SYM_PROF("mttkrp_strict_leaf", s);
                 k_mttkrp_strict<N, KW, L, BF16, 2><<<grid, MT_THREADS, 0, s>>>(
                     X->rklo, X->rkhi, X->rval, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                    cfg.stream_hint);
+                    cfg.stream_hint, X->n);
             }
         } else if (cfg.strict_kernel == SYM_MTTKRP_PIPELINED) {
             const SinkPlan sp = plan_sink(X->n, R, cfg.strict_smem_kb, cfg.b_share_pct);
@@ -1029,10 +1053,10 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
             sym_status ls = two ? launch_lane_m<N, KW, L, BF16, 1>(cfg.vec_per_lane, ns, X->klo, X->khi, X->val,
                                                                    X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
-                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s)
+                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s, X->n)
                                 : launch_lane_m<N, KW, L, BF16, 0>(cfg.vec_per_lane, ns, X->klo, X->khi, X->val,
                                                                    X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
-                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s);
+                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s, X->n);
             if (ls == SYM_OK && two) {
                 if (cfg.strict_smem_kb == 0) {  // root pass unfactorised below the root
                     const int64_t rchunk = cfg.ctas_per_sm > 0 ? 64LL * cfg.ctas_per_sm : 256;
@@ -1040,12 +1064,12 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
                     SYM_PROF("mttkrp_strict_leaf", s);
                     k_mttkrp_rootpass<N, KW, L, BF16><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(
                         X->rklo, X->rkhi, X->rval, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], rchunk,
-                        cfg.stream_hint);
+                        cfg.stream_hint, X->n);
                     ls = cuda_status(cudaGetLastError());
                 } else {
                     ls = launch_lane_m<N, KW, L, BF16, 2>(cfg.vec_per_lane, ns, X->rklo, X->rkhi, X->rval, X->bits,
                                                           B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                                                          cfg.stream_hint, "mttkrp_strict_leaf", s);
+                                                          cfg.stream_hint, "mttkrp_strict_leaf", s, X->n);
                 }
             }
             if (ls != SYM_OK) return ls;
@@ -1068,7 +1092,7 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
                                                                                      (int64_t)sms * 16));
             SYM_PROF("mttkrp_strict", s);
             k_mttkrp_entries<N, KW, L, BF16><<<grid, threads, 0, s>>>(X->klo, X->khi, X->val, ns, X->bits, B, ldb, R,
-                                                                      M, ldm, 0, 0);
+                                                                      M, ldm, 0, 0, X->n);
         }
         SYM_CHECK_LAUNCH();
     }
@@ -1084,7 +1108,7 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nd + gpc - 1) / gpc, cap));
         SYM_PROF("mttkrp_diag", s);
         k_mttkrp_entries<N, KW, L, BF16><<<grid, dthreads, sp.bytes, s>>>(dlo, dhi, X->val + ns, nd, X->bits, B, ldb,
-                                                                          R, M, ldm, sp.H, sp.HB);
+                                                                          R, M, ldm, sp.H, sp.HB, X->n);
         SYM_CHECK_LAUNCH();
     }
     return SYM_OK;

@@ -34,7 +34,8 @@ template <int L, bool SYPRD>
 __global__ void __launch_bounds__(SV_THREADS) k_ssymv(int64_t row0, int64_t row_end, const int32_t* __restrict__ rowptr,
                                                       const int32_t* __restrict__ col, const float* __restrict__ val,
                                                       const float* __restrict__ x, float* __restrict__ y,
-                                                      double* __restrict__ partials) {
+                                                      double* __restrict__ partials, int64_t ncols = INT64_MAX,
+                                                      int64_t nnz = INT64_MAX) {
     constexpr int GPC = SV_THREADS / L;
     const int lane = threadIdx.x & 31;
     const int s = lane % L;
@@ -45,7 +46,9 @@ __global__ void __launch_bounds__(SV_THREADS) k_ssymv(int64_t row0, int64_t row_
         const float xi = x[i];
         const int p1 = rowptr[i + 1];
         for (int p = rowptr[i] + s; p < p1; p += L) {
+            if (!SYM_INDEX_OK(p, nnz)) break;  // bounds-checked build: a row pointer past the entries
             const int j = col[p];
+            if (!SYM_INDEX_OK(j, ncols)) continue;  // bounds-checked build: a column outside the matrix
             const float a = val[p];
             const float t = a * x[j];
             rowsum += t;
@@ -96,9 +99,11 @@ sym_status launch_ssymv_l(const sym_csr_upper* A, const float* x, float* y, doub
     const unsigned grid = (unsigned)std::max<int64_t>(1, (row_end - row0 + GPC - 1) / GPC);
     SYM_PROF("ssymv", s);
     if (syprd)
-        k_ssymv<L, true><<<grid, SV_THREADS, 0, s>>>(row0, row_end, A->rowptr, A->col, A->val, x, y, partials);
+        k_ssymv<L, true><<<grid, SV_THREADS, 0, s>>>(row0, row_end, A->rowptr, A->col, A->val, x, y, partials, A->n,
+                                                     A->nnz);
     else
-        k_ssymv<L, false><<<grid, SV_THREADS, 0, s>>>(row0, row_end, A->rowptr, A->col, A->val, x, y, partials);
+        k_ssymv<L, false><<<grid, SV_THREADS, 0, s>>>(row0, row_end, A->rowptr, A->col, A->val, x, y, partials, A->n,
+                                                      A->nnz);
     SYM_CHECK_LAUNCH();
     if (syprd) {
         k_sum_partials<<<1, 1024, 0, s>>>(partials, grid, syprd);

@@ -170,7 +170,7 @@ __device__ __forceinline__ int phase_of(const float* g) {
 // Padding entries (only at the end of a block) contribute nothing.
 template <int MODE, bool SYPRD>
 __device__ __forceinline__ void band_vec4(uint4 pk, float4 av, const float* xI, float* yI, const float* xJ,
-                                          float* yJ, float& sp) {
+                                          float* yJ, float& sp, int wI = 0x7fffffff, int wJ = 0x7fffffff) {
     const uint32_t k[4] = {pk.x, pk.y, pk.z, pk.w};
     const float a[4] = {av.x, av.y, av.z, av.w};
     bool v[4];
@@ -180,6 +180,13 @@ __device__ __forceinline__ void band_vec4(uint4 pk, float4 av, const float* xI, 
         v[e] = k[e] != BAND_PAD;
         r[e] = v[e] ? (int)(k[e] >> 16) : (e > 0 ? r[e - 1] : 0);
         c[e] = v[e] ? (int)(k[e] & 0xffffu) : 0;
+#ifdef SYM_BOUNDS_CHECK
+        if (v[e] && (!SYM_INDEX_OK(r[e], wI) || !SYM_INDEX_OK(c[e], MODE == 0 ? wI : wJ))) {
+            v[e] = false;  // an in-band pair outside its band: dropped
+            r[e] = 0;
+            c[e] = 0;
+        }
+#endif
     }
     float t[4], xr[4];
 #pragma unroll
@@ -214,7 +221,7 @@ __device__ __forceinline__ void band_vec4(uint4 pk, float4 av, const float* xI, 
 template <int MODE, bool SYPRD, int EPL>
 __device__ __forceinline__ void band_groups(uint32_t gi, uint32_t gv, int m, int first, int stride, uint32_t xI,
                                             uint32_t yI, uint32_t xJ, uint32_t yJ, const float* gxJ, float* gyJ,
-                                            float& sp) {
+                                            float& sp, int wI = 0x7fffffff, int wJ = 0x7fffffff) {
 #pragma unroll
     for (int q = 0; q < EPL; ++q) {
         const int e = first + q * stride;
@@ -223,6 +230,7 @@ __device__ __forceinline__ void band_groups(uint32_t gi, uint32_t gv, int m, int
         if (k == BAND_PAD) break;  // padding only trails a block's last group
         const float a = lds_f32(gv + 4u * (uint32_t)e);
         const uint32_t r4 = (k >> 16) << 2, c4 = (k & 0xffffu) << 2;
+        if (!SYM_INDEX_OK(k >> 16, wI) || !SYM_INDEX_OK(k & 0xffffu, MODE == 0 ? wI : wJ)) continue;
         const float xr = lds_f32(xI + r4);
         const float xc = MODE == 2 ? __ldg(gxJ + (c4 >> 2)) : lds_f32((MODE == 0 ? xI : xJ) + c4);
         const float t = a * xc;
@@ -550,13 +558,15 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
             const int first = cw * BAND_GROUP + lane, stride = NC * BAND_GROUP;
             const uint32_t sxI = smem_u32(xI), syI = smem_u32(yI);
             if (mode == 0) {
-                band_groups<0, SYPRD, EPL>(gi, gv, cm.m, first, stride, sxI, syI, sxI, syI, nullptr, nullptr, sp);
+                band_groups<0, SYPRD, EPL>(gi, gv, cm.m, first, stride, sxI, syI, sxI, syI, nullptr, nullptr, sp,
+                                           cm.wI, cm.wJ);
             } else if (mode == 1) {
                 band_groups<1, SYPRD, EPL>(gi, gv, cm.m, first, stride, sxI, syI,
-                                           smem_u32(xJb + bJ * WB + cm.leadJ), smem_u32(yJ1), nullptr, nullptr, sp);
+                                           smem_u32(xJb + bJ * WB + cm.leadJ), smem_u32(yJ1), nullptr, nullptr, sp, cm.wI, cm.wJ);
             } else {
                 const int64_t off = cm.base + (int64_t)cm.J * W;
-                band_groups<2, SYPRD, EPL>(gi, gv, cm.m, first, stride, sxI, syI, 0u, 0u, x + off, y + off, sp);
+                band_groups<2, SYPRD, EPL>(gi, gv, cm.m, first, stride, sxI, syI, 0u, 0u, x + off, y + off, sp,
+                                           cm.wI, cm.wJ);
             }
         } else
 #pragma unroll
@@ -566,12 +576,12 @@ __global__ void __launch_bounds__(1024, 1) k_ssymv_band(const BandTask* __restri
                 const uint4 pk = vi[e];
                 const float4 av = vv[e];
                 if (mode == 0) {
-                    band_vec4<0, SYPRD>(pk, av, xI, yI, xI, yI, sp);
+                    band_vec4<0, SYPRD>(pk, av, xI, yI, xI, yI, sp, cm.wI, cm.wJ);
                 } else if (mode == 1) {
-                    band_vec4<1, SYPRD>(pk, av, xI, yI, xJb + bJ * WB + cm.leadJ, yJ1, sp);
+                    band_vec4<1, SYPRD>(pk, av, xI, yI, xJb + bJ * WB + cm.leadJ, yJ1, sp, cm.wI, cm.wJ);
                 } else {
                     const int64_t off = cm.base + (int64_t)cm.J * W;
-                    band_vec4<2, SYPRD>(pk, av, xI, yI, x + off, y + off, sp);
+                    band_vec4<2, SYPRD>(pk, av, xI, yI, x + off, y + off, sp, cm.wI, cm.wJ);
                 }
             }
         }

@@ -225,7 +225,10 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS, 1)
                 xi = xs[i];
             }
             const int j = cs[q];
-            if ((unsigned)j >= (unsigned)n) continue;
+            if ((unsigned)j >= (unsigned)n) {  // a column outside the matrix: skipped (and counted when checked)
+                (void)SYM_INDEX_OK(j, n);
+                continue;
+            }
             const float a = vs[q];
             const float t = a * xs[j];
             rowsum += t;

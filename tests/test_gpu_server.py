@@ -168,13 +168,16 @@ def test_small_requests_grouped_launches():
     sg = need_gpu()
     torch = pytest.importorskip("torch")
     P = pool(sg, [(3, 200, 3000), (4, 40, 2000), (5, 15, 1500)], seed=41)
-    S = sg.Server(max_slots=2, max_rank=16, small_nnz=100_000, coalesce_small=True)
-    reqs = []
+    # one slot and a burst of submissions: requests queue while the slot is busy, and the backlog is admitted
+    # as groups
+    S = sg.Server(max_slots=1, max_rank=16, small_nnz=100_000, coalesce_small=True)
+    made = []
     for k in range(40):
         T, X = P[k % 3]
         Bt, B32, Bused = factor(T.n, 16, 300 + k)
-        M = torch.empty((T.n, 16), device="cuda")
-        reqs.append((S.submit(X, Bt, M, residual=True, tag=k), T, Bused, M))
+        made.append((T, X, Bt, Bused, torch.empty((T.n, 16), device="cuda")))
+    torch.cuda.synchronize()
+    reqs = [(S.submit(X, Bt, M, residual=True, tag=k), T, Bused, M) for k, (T, X, Bt, Bused, M) in enumerate(made)]
     for t, T, Bused, M in reqs:
         r = S.wait(t, 60)
         assert r["status"] == 0
