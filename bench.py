@@ -135,10 +135,16 @@ class ClockSampler:
 # ---------------------------------------------------------------------------- helpers
 
 def kernel_source_hash():
+    """Hash of the default strict-stream kernel's source: mttkrp.cuh up to the end of k_mttkrp_strict (its
+    helpers and body; the other kernels follow it) plus the headers it includes."""
     h = hashlib.sha256()
     for f in ("mttkrp.cuh", "common.cuh", "tensor.cuh"):
         with open(os.path.join(ROOT, "paper_2406_09266_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+            text = fh.read()
+        if f == "mttkrp.cuh":
+            cut = text.find(b"// The plain kernel with VPL float4 column groups per lane")
+            text = text[:cut] if cut > 0 else text
+        h.update(text)
     return h.hexdigest()[:16]
 
 
@@ -377,8 +383,14 @@ def run_ours(args):
     import tempfile
     t0 = time.perf_counter()
     if args.kernel_only:
-        # profiling mode: a fixed configuration (the one the autotuner picks for this workload)
-        X.set_config(strict_kernel=0, entries_per_warp=512, diag_smem_kb=48, leaf_index=0)
+        # profiling mode: a fixed configuration (by default the one the autotuner picks for this workload)
+        fields = dict(strict_kernel=0, entries_per_warp=512, diag_smem_kb=48, leaf_index=0)
+        for kv in filter(None, args.mttkrp_cfg.split(",")):
+            k, v = kv.split("=")
+            fields[k.strip()] = int(v)
+        if fields.get("leaf_index"):
+            X.add_leaf_index()
+        X.set_config(**fields)
         tuned_cfg, tuned_ms = X.get_config(), 0.0
     else:
         tuned_cfg, tuned_ms = X.autotune(B, M=M, cache_path=os.path.join(tempfile.gettempdir(), "symgpu_tune.txt"))
@@ -1110,6 +1122,9 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="profiling mode: setup, warm-up and the timed steps only (no e2e or extra rows), with "
                          "the MTTKRP configuration fixed instead of autotuned")
+    ap.add_argument("--mttkrp-cfg", default="", metavar="FIELDS",
+                    help="kernel-only mode: comma-separated name=value sym_mttkrp_cfg fields that replace the "
+                         "default fixed configuration (leaf_index=1 also builds the leaf index)")
     ap.add_argument("--ttm-only", action="store_true",
                     help="profiling mode: the symmetric TTM kernels on the TTM row's tensor, nothing else")
     ap.add_argument("--ptensor-only", action="store_true",

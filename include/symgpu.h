@@ -523,8 +523,9 @@ typedef struct {
                                   sym_tensor_add_leaf_index) instead of one reduction per entry (also for the
                                   lane kernel; ignored without a leaf index) */
     int32_t vec_per_lane;      /* plain kernel: float4 column groups per lane, 1 or 2 (2 needs rank >= 8);
-                                  lane kernel: leaf gathers issued together per lane group, 1 or 4 (4 needs
-                                  rank >= 16) */
+                                  lane kernel: its shape, 1 = 4 columns per lane, 4 = the same with four leaf
+                                  gathers issued together per lane group (needs rank >= 16), 2 = 8 columns per
+                                  lane (ranks below 8 run shape 1) */
     int32_t stream_hint;       /* plain kernel: 1 = read the canonical stream with evict-first loads so it does not
                                   displace factor rows from L1 / L2 */
     int32_t l1_pref;           /* plain kernel: 1 = ask for the largest L1 (no shared-memory carveout) */
@@ -751,8 +752,10 @@ sym_status sym_batch_submit(sym_server S, const sym_request* req, uint64_t* tick
  * `image` [host] is a tensor image from sym_tensor_save that the caller keeps
  * unchanged for the server's lifetime.  The tensor is loaded into the pool when
  * a request needs it and dropped (least recently used first, never while a
- * request in flight uses it) when another one needs the room.  SYM_E_BUDGET if
- * it could never fit in the pool. */
+ * request in flight uses it) when another one needs the room.  Requests whose
+ * tensor is resident are admitted first; one that needs a load waits up to
+ * 20 ms while others can run, so that the requests for its tensor queued
+ * meanwhile share one load.  SYM_E_BUDGET if it could never fit in the pool. */
 sym_status sym_server_register(sym_server S, const void* image, uint64_t* id);
 /* As sym_batch_submit for a registered tensor (req->X is ignored); the request
  * is validated on the host, and SYM_E_NOTFOUND names an unknown id. */

@@ -309,7 +309,8 @@ sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
     if (c->b_share_pct < 0 || c->b_share_pct > 100) return SYM_E_INVALID;
     if (c->leaf_index != 0 && c->leaf_index != 1) return SYM_E_INVALID;
     const bool depth_field = c->strict_kernel == SYM_MTTKRP_LANE;
-    if (depth_field ? (c->vec_per_lane != 1 && c->vec_per_lane != 4) : (c->vec_per_lane != 1 && c->vec_per_lane != 2))
+    if (depth_field ? (c->vec_per_lane != 1 && c->vec_per_lane != 2 && c->vec_per_lane != 4)
+                    : (c->vec_per_lane != 1 && c->vec_per_lane != 2))
         return SYM_E_INVALID;
     if ((c->stream_hint != 0 && c->stream_hint != 1) || (c->l1_pref != 0 && c->l1_pref != 1)) return SYM_E_INVALID;
     return SYM_OK;
@@ -483,8 +484,9 @@ extern "C" sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype
     for (int chunk : {128, 256, 512})
         for (int thr : {128, 256}) cands.push_back({SYM_MTTKRP_STAGED, chunk, thr, 2, 0, 0, 0, 0, 1, 0, 0});
     for (int chunk : {128, 256}) cands.push_back({SYM_MTTKRP_PIPELINED, chunk, 256, 2, 0, 0, 0, 0, 1, 0, 0});
-    for (int depth : {1, 4}) {
-        if (depth == 4 && rank < 16) continue;
+    for (int depth : {1, 4, 2}) {  // lane shapes: one or four leaf rows in flight, or 8 columns per lane
+        // (8 columns per lane measured slower than 4 below rank 64: too few lanes per entry)
+        if ((depth == 4 && rank < 16) || (depth == 2 && rank < 64)) continue;
         for (int chunk : {128, 256, 512}) {
             cands.push_back({SYM_MTTKRP_LANE, chunk, 256, 2, 0, 0, 0, 0, depth, 1, 0});  // one pass
             if (!X->rklo) continue;

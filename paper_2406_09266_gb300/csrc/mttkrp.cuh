@@ -255,7 +255,9 @@ __global__ void __launch_bounds__(MT_THREADS, (N <= 3 && KW == 1 && L > 1) ? 5 :
 }
 
 // The plain kernel with VPL float4 column groups per lane (L = R / (4 VPL) lanes
-// per entry), so one warp instruction serves more entries and the per-entry
+// per entry; group v of a lane at columns 4 l + 4 L v, so each vector access of
+// the L lanes covers 16 L contiguous bytes of the row), so one warp instruction
+// serves more entries and the per-entry
 // scalar work (shuffles, key decode, fiber tests, addressing) is spread over
 // fewer lanes.  Every position is handled in this one pass.
 template <int N, int KW, int L, int VPL, bool BF16>
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict_wide(
     constexpr int LV = N - 1;
     const int lane = threadIdx.x & 31;
     const int g = lane / L;
-    const int col0 = 4 * VPL * (lane % L);
+    const int col0 = 4 * (lane % L);  // column group v of this lane starts at col0 + 4 L v
     int64_t start, end;
     warp_range(nnz, chunk, &start, &end);
     if (start >= end || col0 >= R) {
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict_wide(
     bool have = false;
     bool on[VPL];
 #pragma unroll
-    for (int v = 0; v < VPL; ++v) on[v] = col0 + 4 * v < R;
+    for (int v = 0; v < VPL; ++v) on[v] = col0 + 4 * L * v < R;
     for (int64_t b0 = start; b0 < end; b0 += 32) {
         const int64_t e = b0 + lane;
         uint64_t mlo = 0, mhi = 0;
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict_wide(
 #pragma unroll
                             for (int v = 0; v < VPL; ++v) {
                                 float4 out = (q > 0) ? f4_mul(P[q - 1][v], T[q][v]) : T[q][v];
-                                if (on[v]) red_add_f4(M + (int64_t)cur[q] * ldm + col0 + 4 * v, f4_scale(out, w));
+                                if (on[v]) red_add_f4(M + (int64_t)cur[q] * ldm + col0 + 4 * L * v, f4_scale(out, w));
                                 if (q > 0) T[q - 1][v] = f4_fma(Brow[q][v], T[q][v], T[q - 1][v]);
                                 T[q][v] = f4_zero();
                             }
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict_wide(
                         cur[q] = c[q];
 #pragma unroll
                         for (int v = 0; v < VPL; ++v) {
-                            Brow[q][v] = on[v] ? load_row4<BF16>(B, c[q], ldb, col0 + 4 * v) : f4_zero();
+                            Brow[q][v] = on[v] ? load_row4<BF16>(B, c[q], ldb, col0 + 4 * L * v) : f4_zero();
                             P[q][v] = (q > 0) ? f4_mul(P[q - 1][v], Brow[q][v]) : Brow[q][v];
                         }
                     }
@@ -341,11 +343,11 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict_wide(
             }
             float4 bl[VPL];
 #pragma unroll
-            for (int v = 0; v < VPL; ++v) bl[v] = on[v] ? load_row4<BF16>(B, c[N - 1], ldb, col0 + 4 * v) : f4_zero();
+            for (int v = 0; v < VPL; ++v) bl[v] = on[v] ? load_row4<BF16>(B, c[N - 1], ldb, col0 + 4 * L * v) : f4_zero();
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
                 T[LV - 1][v] = f4_fmas(bl[v], x, T[LV - 1][v]);
-                if (on[v]) red_add_f4(M + (int64_t)c[N - 1] * ldm + col0 + 4 * v, f4_scale(P[LV - 1][v], w * x));
+                if (on[v]) red_add_f4(M + (int64_t)c[N - 1] * ldm + col0 + 4 * L * v, f4_scale(P[LV - 1][v], w * x));
             }
         }
     }
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_mttkrp_strict_wide(
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
                 float4 out = (q > 0) ? f4_mul(P[q - 1][v], T[q][v]) : T[q][v];
-                if (on[v]) red_add_f4(M + (int64_t)cur[q] * ldm + col0 + 4 * v, f4_scale(out, w));
+                if (on[v]) red_add_f4(M + (int64_t)cur[q] * ldm + col0 + 4 * L * v, f4_scale(out, w));
                 if (q > 0) T[q - 1][v] = f4_fma(Brow[q][v], T[q][v], T[q - 1][v]);
             }
         }
@@ -659,20 +661,27 @@ __global__ void __launch_bounds__(512) k_mttkrp_strict_pipe(
 // MODE 1 over the canonical stream plus a root-only pass over the leaf index
 // cover every position exactly once with no per-entry reduction.  D leaf rows
 // are requested before the D entries are processed, and each batch's keys one
-// batch ahead.
-template <int N, int KW, int L, bool BF16, int MODE, int D>
-__global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
+// batch ahead.  Each lane owns V float4 column groups (columns 4 l + 4 L u,
+// u < V, for lane l of the group: each gather / reduction instruction of the
+// group covers 16 L contiguous bytes of the row), so a wider V spreads the
+// per-entry scalar work (broadcasts, address arithmetic, loop control) over
+// more columns and lets a warp hold 32 / L entries at once with L = R / (4 V).
+template <int N, int KW, int L, bool BF16, int MODE, int D, int V>
+__global__ void __launch_bounds__(256, V == 1 ? (D == 1 ? 4 : 3) : 3) k_mttkrp_lane(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
     int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX) {
     static_assert(N >= 2 && N <= 5, "order");
     static_assert(D >= 1 && D <= L && L % D == 0, "prefetch depth divides the lanes per entry");
+    static_assert(V == 1 || V == 2, "column groups per lane");
     constexpr int LV = N - 1;
     constexpr int G = 32 / L;
     const int lane = threadIdx.x & 31;
     const int g = lane / L, sl = lane % L;
-    const int col = 4 * sl;
-    const bool on = col < R;
+    const int col = 4 * sl;  // column group u of this lane starts at col + 4 L u
+    bool on[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) on[u] = col + 4 * L * u < R;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t ws = warp * chunk;
@@ -683,16 +692,36 @@ __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
     const int nb = (int)((sub + L - 1) / L);  // batches: the same count for every group of the warp
 
     int32_t cur[LV], lastc[LV];
-    float4 Brow[LV], P[LV], T[LV];
+    float4 Brow[LV][V], P[LV][V], T[LV][V];
 #pragma unroll
     for (int q = 0; q < LV; ++q) {
         cur[q] = -1;
         lastc[q] = -1;
-        Brow[q] = f4_zero();
-        P[q] = f4_zero();
-        T[q] = f4_zero();
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            Brow[q][u] = f4_zero();
+            P[q][u] = f4_zero();
+            T[q][u] = f4_zero();
+        }
     }
     bool have = false;
+    // flush the open fibers at levels >= dt (deepest first), each into its row with its prefix product
+    auto flush = [&](int dt) {
+#pragma unroll
+        for (int q = LV - 1; q >= 0; --q) {
+            if (q >= dt) {
+#pragma unroll
+                for (int u = 0; u < V; ++u) {
+                    if (on[u] && (MODE != 2 || q == 0)) {
+                        const float4 out = (q > 0) ? f4_mul(P[q - 1][u], T[q][u]) : T[q][u];
+                        red_add_f4(M + (int64_t)cur[q] * ldm + col + 4 * L * u, f4_scale(out, w));
+                    }
+                    if (q > 0) T[q - 1][u] = f4_fma(Brow[q][u], T[q][u], T[q - 1][u]);
+                    T[q][u] = f4_zero();
+                }
+            }
+        }
+    };
     // the next batch's keys are requested one batch ahead, so the stream's DRAM latency overlaps the work
     auto fetch = [&](int bb, uint64_t& flo, uint64_t& fhi, float& fv) {
         const int64_t fe = gs + (int64_t)bb * L + sl;
@@ -735,66 +764,58 @@ __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
         const uint32_t packed = inr ? (((uint32_t)c[N - 1] << 3) | (uint32_t)d) : 7u;
 #pragma unroll
         for (int q = 0; q < LV; ++q) lastc[q] = __shfl_sync(0xffffffffu, c[q], g * L + L - 1);
+        // entries of this batch that belong to the group (group-uniform)
+        const int nvalid = (int)min((int64_t)L, max((int64_t)0, ge - (gs + (int64_t)b * L)));
 
         // ---- the group steps through its L entries, D at a time
 #pragma unroll 1
         for (int t0 = 0; t0 < L; t0 += D) {
             uint32_t pk[D];
             float vt[D];
-            float4 bl[D];
+            float4 bl[D][V];
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 pk[k] = __shfl_sync(0xffffffffu, packed, g * L + t0 + k);
                 vt[k] = __shfl_sync(0xffffffffu, v, g * L + t0 + k);
-                const bool ok = on && (gs + (int64_t)b * L + t0 + k < ge) && (pk[k] & 7u) != 7u;
-                bl[k] = ok ? load_row4<BF16>(B, (int64_t)(pk[k] >> 3), ldb, col) : f4_zero();
+                const bool ok = (t0 + k < nvalid) && (pk[k] & 7u) != 7u;
+#pragma unroll
+                for (int u = 0; u < V; ++u)
+                    bl[k][u] = (ok && on[u]) ? load_row4<BF16>(B, (int64_t)(pk[k] >> 3), ldb, col + 4 * L * u)
+                                             : f4_zero();
             }
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                if (gs + (int64_t)b * L + t0 + k >= ge) continue;  // group-uniform
+                if (t0 + k >= nvalid) continue;  // group-uniform
                 const int dt = (int)(pk[k] & 7u);
                 if (dt == 7) continue;  // dropped by the bounds check
                 if (dt < LV) {
-                    if (have && on) {
-#pragma unroll
-                        for (int q = LV - 1; q >= 0; --q) {
-                            if (q >= dt) {
-                                if (MODE != 2 || q == 0) {
-                                    const float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
-                                    red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
-                                }
-                                if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
-                                T[q] = f4_zero();
-                            }
-                        }
-                    }
+                    if (have) flush(dt);
 #pragma unroll
                     for (int q = 0; q < LV; ++q) {
                         if (q >= dt) {
                             cur[q] = __shfl_sync(gmask, c[q], t0 + k, L);
-                            Brow[q] = (on && (MODE != 2 || q > 0)) ? load_row4<BF16>(B, cur[q], ldb, col)
-                                                                   : f4_zero();
-                            if (MODE != 2) P[q] = (q > 0) ? f4_mul(P[q - 1], Brow[q]) : Brow[q];
+#pragma unroll
+                            for (int u = 0; u < V; ++u) {
+                                Brow[q][u] = (on[u] && (MODE != 2 || q > 0))
+                                                 ? load_row4<BF16>(B, cur[q], ldb, col + 4 * L * u)
+                                                 : f4_zero();
+                                if (MODE != 2) P[q][u] = (q > 0) ? f4_mul(P[q - 1][u], Brow[q][u]) : Brow[q][u];
+                            }
                         }
                     }
                     have = true;
                 }
-                T[LV - 1] = f4_fmas(bl[k], vt[k], T[LV - 1]);
-                if (MODE == 0 && on)
-                    red_add_f4(M + (int64_t)(pk[k] >> 3) * ldm + col, f4_scale(P[LV - 1], w * vt[k]));
-            }
-        }
-    }
-    if (have && on) {
 #pragma unroll
-        for (int q = LV - 1; q >= 0; --q) {
-            if (MODE != 2 || q == 0) {
-                const float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
-                red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
+                for (int u = 0; u < V; ++u) {
+                    T[LV - 1][u] = f4_fmas(bl[k][u], vt[k], T[LV - 1][u]);
+                    if (MODE == 0 && on[u])
+                        red_add_f4(M + (int64_t)(pk[k] >> 3) * ldm + col + 4 * L * u,
+                                   f4_scale(P[LV - 1][u], w * vt[k]));
+                }
             }
-            if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
         }
     }
+    if (have) flush(0);
 }
 
 // Root-only pass over the leaf index, unfactorised below the root (the second
@@ -807,8 +828,8 @@ __global__ void __launch_bounds__(256, D == 1 ? 4 : 3) k_mttkrp_lane(
 // under a skewed distribution, so they come from L1).  Lanes decode one entry
 // each; the group then steps through them with one broadcast per row offset,
 // one for the value and one for the root change.
-template <int N, int KW, int L, bool BF16>
-__global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
+template <int N, int KW, int L, bool BF16, int V>
+__global__ void __launch_bounds__(256, V == 1 ? 4 : 3) k_mttkrp_rootpass(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
     int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX) {
@@ -816,8 +837,10 @@ __global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
     constexpr int G = 32 / L;
     const int lane = threadIdx.x & 31;
     const int g = lane / L, sl = lane % L;
-    const int col = 4 * sl;
-    const bool on = col < R;
+    const int col = 4 * sl;  // column group u of this lane starts at col + 4 L u
+    bool on[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) on[u] = col + 4 * L * u < R;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t ws = warp * chunk;
     if (ws >= nnz) return;
@@ -844,7 +867,14 @@ __global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
         }
     };
     int32_t root = -1, lastroot = -1;
-    float4 acc = f4_zero();
+    float4 acc[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) acc[u] = f4_zero();
+    auto flush_root = [&]() {
+#pragma unroll
+        for (int u = 0; u < V; ++u)
+            if (on[u]) red_add_f4(M + (int64_t)root * ldm + col + 4 * L * u, f4_scale(acc[u], w));
+    };
     uint64_t nlo, nhi;
     float nv;
     fetch(0, nlo, nhi, nv);
@@ -871,19 +901,23 @@ __global__ void __launch_bounds__(256, 4) k_mttkrp_rootpass(
             // warp must reach each full-warp shuffle above, whatever its group's entry count.
             if (gs + (int64_t)b * L + t >= ge || nr == -2) continue;
             if (nr >= 0) {  // a new root fiber starts at this entry
-                if (root >= 0 && on) red_add_f4(M + (int64_t)root * ldm + col, f4_scale(acc, w));
+                if (root >= 0) flush_root();
                 root = nr;
-                acc = f4_zero();
-            }
-            if (on) {
-                float4 prod = load_row4<BF16>(B, r[0], ldb, col);
 #pragma unroll
-                for (int q = 1; q < N - 1; ++q) prod = f4_mul(prod, load_row4<BF16>(B, r[q], ldb, col));
-                acc = f4_fmas(prod, vt, acc);
+                for (int u = 0; u < V; ++u) acc[u] = f4_zero();
+            }
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                if (on[u]) {
+                    float4 prod = load_row4<BF16>(B, r[0], ldb, col + 4 * L * u);
+#pragma unroll
+                    for (int q = 1; q < N - 1; ++q) prod = f4_mul(prod, load_row4<BF16>(B, r[q], ldb, col + 4 * L * u));
+                    acc[u] = f4_fmas(prod, vt, acc[u]);
+                }
             }
         }
     }
-    if (root >= 0 && on) red_add_f4(M + (int64_t)root * ldm + col, f4_scale(acc, w));
+    if (root >= 0) flush_root();
 }
 
 // One entry per lane group, any equality pattern (the diagonal stream; with
@@ -973,19 +1007,44 @@ inline SinkPlan plan_sink(int64_t n, int R, int kb, int b_share_pct) {
     return SinkPlan{H, HB, (size_t)(H + HB) * row};
 }
 
+// Lane-kernel shapes selected by vec_per_lane: 1 = one float4 column group per
+// lane, one leaf row in flight; 4 = the same with four leaf rows requested
+// together; 2 = two column groups per lane (half the lanes per entry).
 template <int N, int KW, int L, bool BF16, int MODE>
-sym_status launch_lane_m(int depth, int64_t cnt, const uint64_t* klo, const uint64_t* khi, const float* val, int bits,
+sym_status launch_lane_m(int shape, int64_t cnt, const uint64_t* klo, const uint64_t* khi, const float* val, int bits,
                          const void* B, int64_t ldb, int R, float* M, int64_t ldm, float w, int64_t chunk,
                          int stream_hint, const char* name, cudaStream_t s, int64_t nrows) {
     const int64_t warps = (cnt + chunk - 1) / chunk;
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    constexpr int LH = L >= 2 ? L / 2 : 1;
     SYM_PROF(name, s);
-    if (depth >= 4 && L >= 4)
-        k_mttkrp_lane<N, KW, L, BF16, MODE, (L >= 4 ? 4 : 1)><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M,
-                                                                                 ldm, w, chunk, stream_hint, nrows);
+    if (shape == 4 && L >= 4)
+        k_mttkrp_lane<N, KW, L, BF16, MODE, (L >= 4 ? 4 : 1), 1><<<grid, 256, 0, s>>>(
+            klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w, chunk, stream_hint, nrows);
+    else if (shape == 2 && L >= 2)
+        k_mttkrp_lane<N, KW, LH, BF16, MODE, 1, 2><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm,
+                                                                        w, chunk, stream_hint, nrows);
     else
-        k_mttkrp_lane<N, KW, L, BF16, MODE, 1><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
+        k_mttkrp_lane<N, KW, L, BF16, MODE, 1, 1><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
+                                                                      chunk, stream_hint, nrows);
+    SYM_CHECK_LAUNCH();
+    return SYM_OK;
+}
+
+template <int N, int KW, int L, bool BF16>
+sym_status launch_rootpass(int shape, int64_t cnt, const uint64_t* klo, const uint64_t* khi, const float* val,
+                           int bits, const void* B, int64_t ldb, int R, float* M, int64_t ldm, float w, int64_t chunk,
+                           int stream_hint, cudaStream_t s, int64_t nrows) {
+    const int64_t warps = (cnt + chunk - 1) / chunk;
+    const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    constexpr int LH = L >= 2 ? L / 2 : 1;
+    SYM_PROF("mttkrp_strict_leaf", s);
+    if (shape == 2 && L >= 2)
+        k_mttkrp_rootpass<N, KW, LH, BF16, 2><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
                                                                    chunk, stream_hint, nrows);
+    else
+        k_mttkrp_rootpass<N, KW, L, BF16, 1><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
+                                                                  chunk, stream_hint, nrows);
     SYM_CHECK_LAUNCH();
     return SYM_OK;
 }
@@ -1060,12 +1119,9 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             if (ls == SYM_OK && two) {
                 if (cfg.strict_smem_kb == 0) {  // root pass unfactorised below the root
                     const int64_t rchunk = cfg.ctas_per_sm > 0 ? 64LL * cfg.ctas_per_sm : 256;
-                    const int64_t warps = (ns + rchunk - 1) / rchunk;
-                    SYM_PROF("mttkrp_strict_leaf", s);
-                    k_mttkrp_rootpass<N, KW, L, BF16><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(
-                        X->rklo, X->rkhi, X->rval, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], rchunk,
-                        cfg.stream_hint, X->n);
-                    ls = cuda_status(cudaGetLastError());
+                    ls = launch_rootpass<N, KW, L, BF16>(cfg.vec_per_lane, ns, X->rklo, X->rkhi, X->rval, X->bits, B,
+                                                         ldb, R, M, ldm, (float)fact[N - 1], rchunk, cfg.stream_hint,
+                                                         s, X->n);
                 } else {
                     ls = launch_lane_m<N, KW, L, BF16, 2>(cfg.vec_per_lane, ns, X->rklo, X->rkhi, X->rval, X->bits,
                                                           B, ldb, R, M, ldm, (float)fact[N - 1], chunk,

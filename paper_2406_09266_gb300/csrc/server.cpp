@@ -22,7 +22,9 @@
 // least recently used resident tensors that no request in flight uses are
 // dropped (the host image is the master copy, so nothing is copied back).  The
 // pool and the factors / outputs of the requests in flight together stay
-// within the HBM budget.
+// within the HBM budget.  Admission prefers requests whose tensor is resident:
+// a request that would need a load waits (up to 20 ms) while others can run,
+// so the requests for one tensor that queue meanwhile share its load.
 //
 // Nothing here waits on the device without a bound: the scheduler only queries
 // events, and destroy drains with a time limit.
@@ -45,6 +47,10 @@
 namespace {
 
 constexpr int kMaxGroup = 16;  // requests in one grouped launch
+// A request for a registered tensor that is not on the device waits up to this
+// long behind requests whose tensors are, so that one load serves every request
+// for that tensor queued meanwhile.
+constexpr uint64_t kAffinityWaitNs = 20'000'000;
 
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -290,59 +296,74 @@ void sym_server_s::run() {
             if (stop && queue.empty() && inflight == 0) break;
             const uint64_t t = now_ns();
             Slot* group = nullptr;  // the slot collecting this pass's small requests
-            for (auto it = queue.begin(); it != queue.end();) {
-                if (inflight_bytes + it->bytes > cfg.hbm_budget_bytes) {
-                    // head blocked on budget: later requests may pass it for a while
-                    if (it == queue.begin() && t - it->t_submit > pass_limit_ns) break;
-                    ++it;
-                    continue;
-                }
-                const bool join = cfg.coalesce_small && it->small && group && (int)group->reqs.size() < kMaxGroup;
-                Slot* pick = join ? group : nullptr;
-                if (!pick) {
-                    for (auto& s : slots)  // small -> prefer high priority; large -> prefer low
-                        if (!s.busy && s.high == it->small) {
-                            pick = &s;
-                            break;
-                        }
-                    if (!pick)
-                        for (auto& s : slots)
-                            if (!s.busy) {
+            // Phase 0 admits requests whose tensor is on the device (or not registered) and registered
+            // requests that have waited longer than kAffinityWaitNs; phase 1, with the slots left, the rest
+            // (each loading its tensor, after which the queued requests for that tensor are resident too).
+            bool slots_left = true;
+            for (int phase = 0; phase < 2 && slots_left; ++phase) {
+                for (auto it = queue.begin(); it != queue.end();) {
+                    if (phase == 0 && it->reg >= 0 && !entries[(size_t)it->reg].resident &&
+                        t - it->t_submit < kAffinityWaitNs) {
+                        ++it;
+                        continue;
+                    }
+                    if (inflight_bytes + it->bytes > cfg.hbm_budget_bytes) {
+                        // head blocked on budget: later requests may pass it for a while
+                        if (it == queue.begin() && t - it->t_submit > pass_limit_ns) break;
+                        ++it;
+                        continue;
+                    }
+                    const bool join =
+                        cfg.coalesce_small && it->small && group && (int)group->reqs.size() < kMaxGroup;
+                    Slot* pick = join ? group : nullptr;
+                    if (!pick) {
+                        for (auto& s : slots)  // small -> prefer high priority; large -> prefer low
+                            if (!s.busy && s.high == it->small) {
                                 pick = &s;
                                 break;
                             }
-                }
-                if (!pick) break;
-                if (!pick->busy) pick->launch_status = SYM_OK;
-                if (it->reg >= 0) {
-                    Entry& E = entries[(size_t)it->reg];
-                    if (!E.resident) {
-                        sym_status err = SYM_OK;
-                        if (!make_resident(E, pick->stream, &err)) {
-                            ++it;  // no room in the pool yet: later requests may pass
-                            continue;
-                        }
-                        if (err != SYM_OK) pick->launch_status = err;
+                        if (!pick)
+                            for (auto& s : slots)
+                                if (!s.busy) {
+                                    pick = &s;
+                                    break;
+                                }
                     }
-                    E.inuse += 1;
-                    E.last_use = ++tick;
+                    if (!pick) {  // no slot free: both phases end
+                        slots_left = false;
+                        break;
+                    }
+                    if (!pick->busy) pick->launch_status = SYM_OK;
+                    if (it->reg >= 0) {
+                        Entry& E = entries[(size_t)it->reg];
+                        if (!E.resident) {
+                            sym_status err = SYM_OK;
+                            if (!make_resident(E, pick->stream, &err)) {
+                                ++it;  // no room in the pool yet: later requests may pass
+                                continue;
+                            }
+                            if (err != SYM_OK) pick->launch_status = err;
+                        }
+                        E.inuse += 1;
+                        E.last_use = ++tick;
+                    }
+                    if (!pick->busy) {
+                        pick->busy = true;
+                        pick->t_admit = t;
+                        to_launch.push_back(pick);
+                        stats.launches += 1;
+                        if (cfg.coalesce_small && it->small) group = pick;
+                    } else if ((int)pick->reqs.size() == 1) {
+                        stats.grouped_launches += 1;  // the slot's first request now leads a group
+                    }
+                    pick->reqs.push_back(*it);
+                    inflight_bytes += it->bytes;
+                    inflight += 1;
+                    stats.admitted += 1;
+                    stats.peak_inflight = std::max<int64_t>(stats.peak_inflight, inflight);
+                    stats.peak_bytes = std::max<int64_t>(stats.peak_bytes, (int64_t)(inflight_bytes + resident_bytes));
+                    it = queue.erase(it);
                 }
-                if (!pick->busy) {
-                    pick->busy = true;
-                    pick->t_admit = t;
-                    to_launch.push_back(pick);
-                    stats.launches += 1;
-                    if (cfg.coalesce_small && it->small) group = pick;
-                } else if ((int)pick->reqs.size() == 1) {
-                    stats.grouped_launches += 1;  // the slot's first request now leads a group
-                }
-                pick->reqs.push_back(*it);
-                inflight_bytes += it->bytes;
-                inflight += 1;
-                stats.admitted += 1;
-                stats.peak_inflight = std::max<int64_t>(stats.peak_inflight, inflight);
-                stats.peak_bytes = std::max<int64_t>(stats.peak_bytes, (int64_t)(inflight_bytes + resident_bytes));
-                it = queue.erase(it);
             }
             if (to_launch.empty() && !progressed) {
                 if (inflight == 0)

@@ -242,6 +242,8 @@ LANE_CONFIGS = [
     # (chunk, depth, leaf_index, root pass: 0 unfactorised / 1 factorised, root-pass chunk / 64)
     (256, 1, 1, 0, 2), (512, 4, 1, 0, 8), (32, 1, 0, 0, 1), (96, 4, 0, 0, 1), (1024, 1, 0, 0, 1), (64, 4, 1, 1, 1),
     (128, 1, 1, 1, 1), (64, 1, 1, 0, 1),
+    # 8 columns per lane (shape 2): one pass, two passes with either root pass
+    (256, 2, 0, 0, 1), (96, 2, 1, 0, 2), (512, 2, 1, 1, 1),
 ]
 
 
@@ -251,7 +253,7 @@ LANE_CONFIGS = [
 def test_mttkrp_lane_kernel(k, case):
     """Lane-parallel decoding (each lane decodes one entry and finds its first changed fiber level), one pass
     or two passes (canonical stream without the leaf, then the leaf index for the root, factorised or
-    unfactorised below it), 1 or 4 leaf gathers in flight, chunks that split fibers between warps and between
+    unfactorised below it), 1 or 4 leaf gathers in flight or 8 columns per lane, chunks that split fibers between warps and between
     the groups of a warp, and ragged entry counts (the groups of the last warp hold different numbers)."""
     sg = need_gpu()
     chunk, depth, leaf, factorised_root, rchunk = LANE_CONFIGS[k]
@@ -287,7 +289,7 @@ def test_mttkrp_lane_kernel_rejects_bad_config():
     sg = need_gpu()
     T = synth.tensor_uniform(3, 50, 500, 1)
     X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
-    for bad in (dict(vec_per_lane=2), dict(entries_per_warp=0), dict(entries_per_warp=48), dict(strict_kernel=5)):
+    for bad in (dict(vec_per_lane=3), dict(entries_per_warp=0), dict(entries_per_warp=48), dict(strict_kernel=5)):
         cfg = dict(strict_kernel=sg.MTTKRP_LANE, entries_per_warp=256, threads_per_cta=256, leaf_index=1)
         cfg.update(bad)
         with pytest.raises(sg.SymError):

@@ -149,7 +149,7 @@ def test_registered_tensors_evicted_and_reloaded():
         want, ab, _ = oracle.cpfit(T.order, T.n, cidx, cval, Bused.astype(np.float64))
         assert abs(r["residual"] - want) / ab <= TOL_F32
     st = S.stats()
-    assert st["completed"] == 20 and st["loads"] > len(P) and st["evictions"] > 0
+    assert st["completed"] == 20 and st["loads"] >= len(P) and st["evictions"] >= len(P) - 2
     assert st["peak_resident_bytes"] <= pool_bytes and st["peak_bytes"] <= pool_bytes + (64 << 20)
     # a tensor larger than the whole pool is refused at registration
     big_pool = sg.Server(max_slots=2, max_rank=16, hbm_budget_bytes=1 << 30, pool_bytes=4096)
@@ -160,6 +160,40 @@ def test_registered_tensors_evicted_and_reloaded():
     with pytest.raises(sg.SymError) as e:
         S.submit_registered(999, Bt, M)
     assert e.value.code == -11
+    S.close()
+
+
+def test_registered_requests_share_loads():
+    """A pool with room for one of two registered tensors and a burst of requests alternating between them:
+    admission takes the requests for the resident tensor first, so the queued requests for the other share
+    one load instead of one load each (first-come order would load for every request)."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    P = pool(sg, [(3, 600, 40000), (4, 90, 30000)], seed=51)
+    images = [X.save_image() for _, X in P]
+    sizes = [X.info()["arena_used"] for _, X in P]
+    pool_bytes = int(max(sizes) * 1.5)
+    S = sg.Server(max_slots=1, max_rank=16, hbm_budget_bytes=pool_bytes + (64 << 20), pool_bytes=pool_bytes)
+    ids = [S.register(img) for img in images]
+    made = []
+    for k in range(16):
+        T, X = P[k % 2]
+        Bt, B32, Bused = factor(T.n, 16, 500 + k)
+        made.append((k % 2, T, Bt, Bused, torch.empty((T.n, 16), device="cuda")))
+    torch.cuda.synchronize()
+    reqs = [(S.submit_registered(ids[j], Bt, M, residual=True, tag=k), T, Bused, M)
+            for k, (j, T, Bt, Bused, M) in enumerate(made)]
+    for t, T, Bused, M in reqs:
+        r = S.wait(t, 60)
+        assert r["status"] == 0
+        cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
+        ref, ra = oracle.mttkrp_enum(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+        assert oracle.componentwise_error(host(M), ref, ra) <= TOL_F32
+        want, ab, _ = oracle.cpfit(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+        assert abs(r["residual"] - want) / ab <= TOL_F32
+    st = S.stats()
+    assert st["completed"] == 16 and 2 <= st["loads"] <= 6, st
+    assert st["peak_resident_bytes"] <= pool_bytes
     S.close()
 
 
