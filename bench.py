@@ -134,26 +134,46 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------- helpers
 
-def kernel_source_hash():
-    """Hash of the default strict-stream kernel's source: mttkrp.cuh up to the end of k_mttkrp_strict (its
-    helpers and body; the other kernels follow it) plus the headers it includes."""
+def kernel_source_hash(plain_only=True):
+    """Hash of a strict-stream kernel's source.  plain_only: mttkrp.cuh up to the end of k_mttkrp_strict (its
+    helpers and body; the other kernels follow it), else all of mttkrp.cuh; plus the headers it includes."""
     h = hashlib.sha256()
     for f in ("mttkrp.cuh", "common.cuh", "tensor.cuh"):
         with open(os.path.join(ROOT, "paper_2406_09266_gb300", "csrc", f), "rb") as fh:
             text = fh.read()
-        if f == "mttkrp.cuh":
+        if f == "mttkrp.cuh" and plain_only:
             cut = text.find(b"// The plain kernel with VPL float4 column groups per lane")
             text = text[:cut] if cut > 0 else text
         h.update(text)
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
+def strict_variant(cfg, rank=64, order=3):
+    """(kernel name for the bench line, key of its DRAM-traffic record, whether the plain-kernel source hash
+    applies) of the strict-stream kernel a configuration runs (one-word keys, FP32 factor)."""
+    k, epw, leaf, shape = cfg["strict_kernel"], cfg["entries_per_warp"], cfg["leaf_index"], cfg["vec_per_lane"]
+    lanes = max(1, rank // 4)
+    if k == 0:
+        mode = 1 if leaf else 0
+        if shape == 2 and not leaf:
+            return (f"k_mttkrp_strict_wide<{order},1,{lanes // 2},2,f32> ({epw} entries/warp)", f"plain_wide_c{epw}",
+                    False)
+        return f"k_mttkrp_strict<{order},1,{lanes},f32,MODE{mode}> ({epw} entries/warp)", f"plain_m{mode}_c{epw}", True
+    if k == 4:
+        mode = 1 if leaf else 0
+        d, v = (4, 1) if shape == 4 else (1, shape)
+        return (f"k_mttkrp_lane<{order},1,{lanes // v},f32,MODE{mode},D{d},V{v}> ({epw} entries/warp)",
+                f"lane_m{mode}_d{d}_v{v}_c{epw}", False)
+    name = {1: "k_mttkrp_strict_pipe", 2: "k_mttkrp_entries", 3: "k_mttkrp_strict_staged"}.get(k, "?")
+    return f"{name}<{order},1,{lanes},f32> ({epw} entries/warp)", f"k{k}_c{epw}", False
+
+
+def recorded_traffic(kernel: str, workload: str, plain_only=True):
     """DRAM bytes per launch recorded in profiles/ for this kernel source, else None."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    want = kernel_source_hash()
+    want = kernel_source_hash(plain_only)
     with open(p) as f:
         for ln in f:
             m = re.match(r"\s*(\S+)\s+(\S+)\s+src=(\w+)\s+dram_bytes_per_launch=(\d+)", ln)
@@ -428,13 +448,16 @@ def run_ours(args):
     # The kernel's binding roof is L2, not HBM: per strict entry it gathers the leaf's factor row and reduces
     # into the leaf's output row (R floats each), and per (c1, c2) fiber and per c1 fiber one more of each.
     # Those algorithmic row operations, at the measured random-row ceilings of this GPU, give the ceiling time.
+    # With the leaf index (two passes) this launch is the first pass: no leaf reductions.
     ceil = measure_ceilings(sg) if D.rank == 0 and not args.kernel_only else None
+    kname, tkey, plain_src = strict_variant(tuned_cfg, MAIN["rank"])
     if ceil is not None:
         rows_ops = info["nnz_strict"] + info["l2_fibers"] + info["root_fibers"]
-        roof = l2_roof(rows_ops, rows_ops, MAIN["rank"], ceil, "n100000_r64", per_launch_ms)
+        reds = rows_ops - (info["nnz_strict"] if tuned_cfg["leaf_index"] else 0)
+        roof = l2_roof(rows_ops, reds, MAIN["rank"], ceil, "n100000_r64", per_launch_ms)
     else:
         roof = {"bound": "l2", "achieved": None, "peak": None, "unit": "GB/s", "frac": None}
-    roof.update({"kernel": "k_mttkrp_strict<3,1,16,f32>", "traffic": recorded_traffic("mttkrp_strict", WORKLOAD_NAME),
+    roof.update({"kernel": kname, "traffic": recorded_traffic("mttkrp_strict:" + tkey, WORKLOAD_NAME, plain_src),
                  "launch_ms": per_launch_ms,
                  "share_of_step": strict_ms / max(sum(v[1] for v in prof.values()), 1e-12),
                  "hbm": {"algorithmic_bytes_per_launch": alg_bytes, "achieved_gbs": achieved, "peak_gbs": hbm_peak,
@@ -656,6 +679,9 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak, ceil=None):
             strict_ms = sum(v for k, v in r["f32"]["per_kernel_ms"].items() if k.startswith("mttkrp_strict"))
             r["roofline"] = l2_roof(ops, ops, rank, ceil, f"n{n}_r{rank}", strict_ms)
             r["roofline"]["fibers_per_level"] = fib
+            r["roofline"]["kernel"] = strict_variant(r["f32"]["mttkrp_config"], rank, order)[0]
+            r["roofline"]["model"] = ("one-pass row operations (a gather and a reduction per strict entry and per "
+                                      "fiber) against the strict-stream time of the tuned configuration")
         rows[name] = r
         X.close()
     rows["ssymv_n2000_nnz20k"] = small_ssymv_row(torch, sg, dev, flush, stream)
@@ -912,13 +938,15 @@ def batch_row(torch, sg, dev, flush, stream, hbm_peak, count=4096, per_row=16, s
     return out
 
 
-def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=4):
+def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=4, affinity_s=1.0):
     """Poisson arrivals of MTTKRP requests; continuous batching vs one launch per request (FP32).
 
     Run 1: the tensors are resident (created by the caller) under the 120 GB budget; small requests are
     grouped.  Run 2: the same trace over registered tensor images with a device pool smaller than the set, so
     the server loads tensors on demand and evicts the least recently used ones (host images are the master
-    copy).  Latency is t_done - t_arrival (host steady clock); 'steady' statistics use the second half of the
+    copy); requests for resident tensors go first, a request needing a load waits up to `affinity_s`.  A
+    request whose factor an earlier request used declares it unchanged (residual=2): the server reuses that
+    factor's cached Gram matrix for the residual.  Latency is t_done - t_arrival (host steady clock); 'steady' statistics use the second half of the
     trace only."""
     import threading
     st = synth.Stream(seed, tag=77)
@@ -949,6 +977,12 @@ def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=
     rsel = np.array(ranks)[(st.uniform(requests) * 4).astype(np.int64)]
     dts = np.where(st.uniform(requests) < 0.5, "bf16", "f32")
     work_nnz = float(sum(pool[w].nnz for w in which))
+    # residual=2 once a factor has been used by an earlier request of the trace (its Gram matrix may be reused)
+    seen, res_flag = set(), []
+    for i in range(requests):
+        key = (int(which[i]), int(rsel[i]), str(dts[i]))
+        res_flag.append(2 if key in seen else True)
+        seen.add(key)
     # one output buffer per (tensor, rank), shared by that pair's requests: the trace is timed, not checked (the
     # results of the serving paths are checked in the tests)
     outs = {(k, R): torch.empty((pool[k].n, R), device=dev) for k in range(pool_size) for R in ranks}
@@ -997,7 +1031,7 @@ def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=
     # run 1: resident tensors, 120 GB budget, small requests grouped
     S = sg.Server(max_slots=8, max_rank=64, hbm_budget_bytes=120 << 30, small_nnz=1_000_000, coalesce_small=True)
     cb = serve(S, lambda S_, i: S_.submit(pool[which[i]], facs[(int(which[i]), int(rsel[i]), dts[i])],
-                                          outs[(int(which[i]), int(rsel[i]))], residual=True, tag=i))
+                                          outs[(int(which[i]), int(rsel[i]))], residual=res_flag[i], tag=i))
     cb["server_stats"] = S.stats()
     S.close()
     # run 2: registered images, device pool at 60 % of the images' total: loads and LRU evictions
@@ -1005,14 +1039,15 @@ def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=
     image_bytes = sum(int(sg.lib().sym_tensor_load_bytes(sg.C.c_void_p(im.data_ptr()))) for im in images)
     pool_bytes = int(image_bytes * 0.6)
     S = sg.Server(max_slots=8, max_rank=64, hbm_budget_bytes=pool_bytes + (16 << 30), small_nnz=1_000_000,
-                  coalesce_small=True, pool_bytes=pool_bytes)
+                  coalesce_small=True, pool_bytes=pool_bytes, affinity_wait_s=affinity_s)
     ids = [S.register(im) for im in images]
     ev = serve(S, lambda S_, i: S_.submit_registered(ids[which[i]], facs[(int(which[i]), int(rsel[i]), dts[i])],
-                                                    outs[(int(which[i]), int(rsel[i]))], residual=True, tag=i))
+                                                    outs[(int(which[i]), int(rsel[i]))], residual=res_flag[i], tag=i))
     ev["server_stats"] = S.stats()
     ev["pool_bytes"] = pool_bytes
     ev["registered_image_bytes"] = image_bytes
     ev["hbm_budget_bytes"] = pool_bytes + (16 << 30)
+    ev["affinity_wait_ms"] = affinity_s * 1e3
     S.close()
     del images
     # plain: one launch per request on one stream, FP32 factors, in arrival order (first 4,000 requests)

@@ -714,7 +714,9 @@ typedef struct {
     int64_t ldb;
     float* M;            /* [device] output, n x rank, row stride ldm; caller keeps it alive until done */
     int64_t ldm;
-    int32_t want_residual;
+    int32_t want_residual; /* 0: none; 1: the FP64 CP-fit residual; 2: the same, and B (same pointer, rank, ldb,
+                              type and n) is unchanged since an earlier request to this server, so the Gram
+                              matrix B^T B the server computed then may be reused (it keeps the 512 most recent) */
     uint64_t user_tag;
 } sym_request;
 
@@ -736,6 +738,8 @@ typedef struct {
     int64_t small_nnz;         /* "small": at most this many canonical entries (also picks high-priority slots) */
     int64_t wait_limit_ns;     /* bound used by sym_server_destroy's drain */
     size_t pool_bytes;         /* device pool for registered tensors (part of the arena and of the budget) */
+    int64_t affinity_wait_ns;  /* a request whose registered tensor is not resident waits up to this long while
+                                  requests for resident tensors are admitted first (0: first come, first served) */
 } sym_server_cfg;
 
 /* Device scratch the server needs (per-slot residual workspaces, then the
@@ -754,8 +758,9 @@ sym_status sym_batch_submit(sym_server S, const sym_request* req, uint64_t* tick
  * a request needs it and dropped (least recently used first, never while a
  * request in flight uses it) when another one needs the room.  Requests whose
  * tensor is resident are admitted first; one that needs a load waits up to
- * 20 ms while others can run, so that the requests for its tensor queued
- * meanwhile share one load.  SYM_E_BUDGET if it could never fit in the pool. */
+ * cfg.affinity_wait_ns while others can run, so that the requests for its
+ * tensor queued meanwhile share one load.  SYM_E_BUDGET if it could never fit
+ * in the pool. */
 sym_status sym_server_register(sym_server S, const void* image, uint64_t* id);
 /* As sym_batch_submit for a registered tensor (req->X is ignored); the request
  * is validated on the host, and SYM_E_NOTFOUND names an unknown id. */
@@ -773,6 +778,7 @@ typedef struct {
     int64_t loads;             /* registered tensors brought into the pool */
     int64_t evictions;         /* registered tensors dropped from the pool to make room */
     int64_t peak_resident_bytes, resident_bytes;
+    int64_t gram_hits;         /* residuals that reused a cached Gram matrix (want_residual 2) */
 } sym_server_stats;
 sym_status sym_server_stats_get(sym_server S, sym_server_stats* out);
 /* Drains queued and in-flight work (bounded by cfg.wait_limit_ns), stops the

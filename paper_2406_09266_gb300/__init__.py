@@ -96,14 +96,15 @@ class Result(C.Structure):
 class ServerCfg(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_rank", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
                 ("coalesce_small", C.c_int32), ("small_nnz", C.c_int64), ("wait_limit_ns", C.c_int64),
-                ("pool_bytes", C.c_size_t)]
+                ("pool_bytes", C.c_size_t), ("affinity_wait_ns", C.c_int64)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
                 ("rejected", C.c_int64), ("launches", C.c_int64), ("grouped_launches", C.c_int64),
                 ("peak_inflight", C.c_int64), ("peak_bytes", C.c_int64), ("loads", C.c_int64),
-                ("evictions", C.c_int64), ("peak_resident_bytes", C.c_int64), ("resident_bytes", C.c_int64)]
+                ("evictions", C.c_int64), ("peak_resident_bytes", C.c_int64), ("resident_bytes", C.c_int64),
+                ("gram_hits", C.c_int64)]
 
 
 class MttkrpCfg(C.Structure):
@@ -935,10 +936,10 @@ class Server:
     """Continuous-batching MTTKRP server (sym_server_create / sym_batch_submit / sym_batch_poll)."""
 
     def __init__(self, max_slots=8, max_rank=64, hbm_budget_bytes=120 << 30, small_nnz=1_000_000,
-                 wait_limit_s=30.0, device=None, coalesce_small=False, pool_bytes=0):
+                 wait_limit_s=30.0, device=None, coalesce_small=False, pool_bytes=0, affinity_wait_s=0.02):
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.cfg = ServerCfg(max_slots, max_rank, hbm_budget_bytes, int(coalesce_small), small_nnz,
-                             int(wait_limit_s * 1e9), int(pool_bytes))
+                             int(wait_limit_s * 1e9), int(pool_bytes), int(affinity_wait_s * 1e9))
         self.arena = _scratch(lib().sym_server_arena_bytes(C.byref(self.cfg)), dev)
         h = C.c_void_p()
         check(lib().sym_server_create(C.byref(self.cfg), _ptr(self.arena), self.arena.numel(), dev.index,
@@ -947,6 +948,8 @@ class Server:
         self._keep = {}
 
     def submit(self, X: SymTensor, B, M, residual=False, tag=0) -> int:
+        """Queues M = MTTKRP(X, B).  residual: False, True (FP64 CP-fit residual), or 2 (the residual, with B
+        unchanged since an earlier request to this server: its cached Gram matrix may be reused)."""
         req = Request(X.handle.value, B.data_ptr(), _dtype_code(B), B.shape[1], B.stride(0), M.data_ptr(),
                       M.stride(0), int(residual), tag)
         t = C.c_uint64(0)

@@ -193,6 +193,12 @@ struct NullCarver {
 
 sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, const float* M,
                            int64_t ldm, double* residual, void* ws, size_t ws_bytes, cudaStream_t s) {
+    return residual_launch_gram(X, B, bf16, R, ldb, M, ldm, residual, ws, ws_bytes, nullptr, nullptr, s);
+}
+
+sym_status residual_launch_gram(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, const float* M,
+                                int64_t ldm, double* residual, void* ws, size_t ws_bytes, const double* G_in,
+                                double* G_out, cudaStream_t s) {
     Carver c(ws, ws_bytes);
     ResidualWs w = layout_residual(c, R);
     if (!w.G || !w.xm) return SYM_E_NOMEM;
@@ -202,13 +208,17 @@ sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int 
     const int64_t rows_per_cta = GRAM_ROWS_PER_CTA;
     const unsigned grid = (unsigned)std::max<int64_t>(1, (X->n + rows_per_cta - 1) / rows_per_cta);
     const size_t smem = sizeof(float) * GRAM_ROWS * R;
-    {
+    const double* G = G_in;
+    if (!G) {  // G = B^T B, into the caller's buffer or the workspace
+        double* Gw = G_out ? G_out : w.G;
+        if (G_out) SYM_CUDA(cudaMemsetAsync(G_out, 0, sizeof(double) * (size_t)R * (R + 1) / 2, s));
         SYM_PROF("cpfit_gram", s);
         if (bf16)
-            k_gram<true><<<grid, threads, smem, s>>>(B, X->n, ldb, R, w.G, rows_per_cta);
+            k_gram<true><<<grid, threads, smem, s>>>(B, X->n, ldb, R, Gw, rows_per_cta);
         else
-            k_gram<false><<<grid, threads, smem, s>>>(B, X->n, ldb, R, w.G, rows_per_cta);
+            k_gram<false><<<grid, threads, smem, s>>>(B, X->n, ldb, R, Gw, rows_per_cta);
         SYM_CHECK_LAUNCH();
+        G = Gw;
     }
     const unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(4 * sms, (X->n * R + 255) / 256));
     {
@@ -219,7 +229,7 @@ sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int 
             k_dot_bm<false><<<g2, 256, 0, s>>>(B, ldb, M, ldm, X->n, R, w.xm);
         SYM_CHECK_LAUNCH();
     }
-    k_residual_final<<<1, 256, 0, s>>>(w.G, R, X->order, w.xm, X->info.normsq, residual);
+    k_residual_final<<<1, 256, 0, s>>>(G, R, X->order, w.xm, X->info.normsq, residual);
     SYM_CHECK_LAUNCH();
     return SYM_OK;
 }

@@ -32,6 +32,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 
 #include "common.cuh"
@@ -148,6 +149,37 @@ __device__ __forceinline__ void warp_range(int64_t nnz, int64_t chunk, int64_t* 
     }
 }
 
+// Final root flush of a CTA's lane groups, combined in shared memory.  Under a
+// skewed distribution a few root fibers hold a large share of the entries
+// (Zipf(1.2): the hottest root 22 % of the 3-way stream), so every warp in
+// their span ends inside them and would reduce its root sum into the same
+// output row.  Instead each group leaves (root, its R-float sum) in shared
+// memory; the first group of every run of equal roots (CTA order) adds the run
+// and issues one row reduction.  Every thread of the CTA must call this (it
+// holds a barrier); `valid` is false for a group with nothing to flush.
+template <int L>
+__device__ __forceinline__ void cta_root_flush(int32_t root, float4 v, bool valid, bool on, float* M, int64_t ldm,
+                                               int col, float w) {
+    __shared__ int32_t s_root[MT_THREADS / L];
+    __shared__ float4 s_vec[MT_THREADS];
+    const int gid = (int)threadIdx.x / L, sl = (int)threadIdx.x % L;
+    const int ng = (int)blockDim.x / L;
+    if (sl == 0) s_root[gid] = valid ? root : -1;
+    s_vec[threadIdx.x] = v;
+    __syncthreads();
+    if (valid && (gid == 0 || s_root[gid - 1] != root)) {
+        float4 acc = v;
+        for (int k = gid + 1; k < ng && s_root[k] == root; ++k) {
+            const float4 o = s_vec[k * L + sl];
+            acc.x += o.x;
+            acc.y += o.y;
+            acc.z += o.z;
+            acc.w += o.w;
+        }
+        if (on) red_add_f4(M + (int64_t)root * ldm + col, f4_scale(acc, w));
+    }
+}
+
 // CSF-factorised strict-stream kernel, no shared memory, one entry at a time
 // per lane group (the simplest form).
 //   MODE 0: every position (fiber flushes for c_1..c_{N-1}, a reduction per
@@ -169,7 +201,7 @@ __global__ void __launch_bounds__(MT_THREADS, (N <= 3 && KW == 1 && L > 1) ? 5 :
     const bool on = col < R;
     int64_t start, end;
     warp_range(nnz, chunk, &start, &end);
-    if (start >= end) return;
+    // a warp past the end still reaches the CTA's final root flush (a barrier)
 
     int32_t cur[LV];
     float4 Brow[LV], P[LV], T[LV];
@@ -244,14 +276,15 @@ __global__ void __launch_bounds__(MT_THREADS, (N <= 3 && KW == 1 && L > 1) ? 5 :
     }
     if (have && on) {
 #pragma unroll
-        for (int q = LV - 1; q >= 0; --q) {
-            if (MODE != 2 || q == 0) {
-                float4 out = (q > 0) ? f4_mul(P[q - 1], T[q]) : T[q];
+        for (int q = LV - 1; q >= 1; --q) {
+            if (MODE != 2) {
+                const float4 out = f4_mul(P[q - 1], T[q]);
                 red_add_f4(M + (int64_t)cur[q] * ldm + col, f4_scale(out, w));
             }
-            if (q > 0) T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
+            T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
         }
     }
+    cta_root_flush<L>(cur[0], T[0], have, on, M, ldm, col, w);
 }
 
 // The plain kernel with VPL float4 column groups per lane (L = R / (4 VPL) lanes
@@ -684,8 +717,8 @@ __global__ void __launch_bounds__(256, V == 1 ? (D == 1 ? 4 : 3) : 3) k_mttkrp_l
     for (int u = 0; u < V; ++u) on[u] = col + 4 * L * u < R;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t ws = warp * chunk;
-    if (ws >= nnz) return;
+    // a warp past the end runs no batch but still reaches the CTA's final root flush (a barrier)
+    const int64_t ws = min(warp * chunk, nnz);
     const int64_t we = min(ws + chunk, nnz);
     const int64_t sub = (we - ws + G - 1) / G;
     const int64_t gs = min(ws + g * sub, we), ge = min(gs + sub, we);
@@ -705,11 +738,11 @@ __global__ void __launch_bounds__(256, V == 1 ? (D == 1 ? 4 : 3) : 3) k_mttkrp_l
         }
     }
     bool have = false;
-    // flush the open fibers at levels >= dt (deepest first), each into its row with its prefix product
-    auto flush = [&](int dt) {
+    // flush the open fibers at levels >= max(dt, qmin) (deepest first), each into its row with its prefix product
+    auto flush = [&](int dt, int qmin) {
 #pragma unroll
         for (int q = LV - 1; q >= 0; --q) {
-            if (q >= dt) {
+            if (q >= dt && q >= qmin) {
 #pragma unroll
                 for (int u = 0; u < V; ++u) {
                     if (on[u] && (MODE != 2 || q == 0)) {
@@ -789,7 +822,7 @@ __global__ void __launch_bounds__(256, V == 1 ? (D == 1 ? 4 : 3) : 3) k_mttkrp_l
                 const int dt = (int)(pk[k] & 7u);
                 if (dt == 7) continue;  // dropped by the bounds check
                 if (dt < LV) {
-                    if (have) flush(dt);
+                    if (have) flush(dt, 0);
 #pragma unroll
                     for (int q = 0; q < LV; ++q) {
                         if (q >= dt) {
@@ -815,7 +848,13 @@ __global__ void __launch_bounds__(256, V == 1 ? (D == 1 ? 4 : 3) : 3) k_mttkrp_l
             }
         }
     }
-    if (have) flush(0);
+    // levels below the root as usual; the root through the CTA's combined flush
+    if (have) flush(0, 1);
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+        if (u > 0) __syncthreads();  // the previous column group's shared slots are read
+        cta_root_flush<L>(cur[0], T[0][u], have, on[u], M, ldm, col + 4 * L * u, w);
+    }
 }
 
 // Root-only pass over the leaf index, unfactorised below the root (the second
@@ -992,6 +1031,27 @@ __global__ void __launch_bounds__(512) k_mttkrp_entries(
 
 // ---------------------------------------------------------------- launch
 
+// Smallest shared-memory carveout (percent of the SM's maximum) that holds the
+// static shared memory of `kernel` for as many CTAs of MT_THREADS threads as
+// an SM can run (plus the 1 KB the hardware reserves per CTA); the rest of
+// the unified L1 / shared memory stays L1.
+template <typename K>
+int l1_carveout_pct(K kernel) {
+    static std::atomic<int> pct{-1};  // per kernel instantiation; every device of the process is a GB300
+    if (pct.load() < 0) {
+        cudaFuncAttributes fa{};
+        int smem_sm = 0;
+        if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, current_device()) !=
+                cudaSuccess ||
+            smem_sm <= 0)
+            return (int)cudaSharedmemCarveoutDefault;
+        const size_t need = (size_t)(2048 / MT_THREADS) * (fa.sharedSizeBytes + 1024);
+        pct.store((int)std::min<size_t>(100, (need * 100 + (size_t)smem_sm - 1) / (size_t)smem_sm));
+    }
+    return pct.load();
+}
+
 // Hot-row sizing within a shared-memory budget: rows of M (H) and of B (HB).
 struct SinkPlan {
     int H;
@@ -1063,10 +1123,12 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             const unsigned grid = (unsigned)((warps * 32 + MT_THREADS - 1) / MT_THREADS);
             const bool leaf_pass = cfg.leaf_index != 0 && X->rklo != nullptr;
             constexpr int L2 = L / 2;   // lanes per entry with 8 columns per lane
-            // carveout preference: all of the unified L1 / shared memory as L1, or the driver default
+            // carveout preference: as much of the unified L1 / shared memory as L1 as leaves room for the
+            // kernel's static shared memory (its final root flush) in every CTA an SM can hold, or the default
             SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_strict<N, KW, L, BF16, 0>,
                                           cudaFuncAttributePreferredSharedMemoryCarveout,
-                                          cfg.l1_pref ? 0 : (int)cudaSharedmemCarveoutDefault));
+                                          cfg.l1_pref ? l1_carveout_pct(k_mttkrp_strict<N, KW, L, BF16, 0>)
+                                                      : (int)cudaSharedmemCarveoutDefault));
             if (!leaf_pass && cfg.vec_per_lane == 2 && L2 >= 1) {
                 SYM_PROF("mttkrp_strict", s);
                 k_mttkrp_strict_wide<N, KW, (L2 >= 1 ? L2 : 1), 2, BF16><<<grid, MT_THREADS, 0, s>>>(
@@ -1209,6 +1271,11 @@ sym_status mttkrp_core(const sym_tensor_s* X, const void* B, bool bf16, int R, i
                        cudaStream_t s);
 sym_status residual_launch(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, const float* M,
                            int64_t ldm, double* residual, void* ws, size_t ws_bytes, cudaStream_t s);
+// The same with the Gram matrix B^T B (packed upper triangle, FP64) taken from G_in when given (not
+// recomputed), else computed into G_out when given (kept for later calls), else into the workspace.
+sym_status residual_launch_gram(const sym_tensor_s* X, const void* B, bool bf16, int R, int64_t ldb, const float* M,
+                                int64_t ldm, double* residual, void* ws, size_t ws_bytes, const double* G_in,
+                                double* G_out, cudaStream_t s);
 size_t residual_ws_bytes(int R);
 // G (packed upper triangle r <= s, FP64, overwritten) = B^T B.
 sym_status gram_launch(int64_t n, const void* B, bool bf16, int R, int64_t ldb, double* G, cudaStream_t s);

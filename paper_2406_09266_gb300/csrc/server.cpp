@@ -23,8 +23,11 @@
 // dropped (the host image is the master copy, so nothing is copied back).  The
 // pool and the factors / outputs of the requests in flight together stay
 // within the HBM budget.  Admission prefers requests whose tensor is resident:
-// a request that would need a load waits (up to 20 ms) while others can run,
-// so the requests for one tensor that queue meanwhile share its load.
+// a request that would need a load waits (up to cfg.affinity_wait_ns) while
+// others can run, so the requests for one tensor that queue meanwhile share
+// its load.  A request may declare its factor unchanged since an earlier
+// request (want_residual 2): the residual then reuses the Gram matrix B^T B
+// cached from that request instead of recomputing it.
 //
 // Nothing here waits on the device without a bound: the scheduler only queries
 // events, and destroy drains with a time limit.
@@ -47,10 +50,7 @@
 namespace {
 
 constexpr int kMaxGroup = 16;  // requests in one grouped launch
-// A request for a registered tensor that is not on the device waits up to this
-// long behind requests whose tensors are, so that one load serves every request
-// for that tensor queued meanwhile.
-constexpr uint64_t kAffinityWaitNs = 20'000'000;
+constexpr int kGramSlots = 512;  // cached Gram matrices (B^T B) of recently used factors
 
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -77,6 +77,24 @@ struct Pending {
     size_t bytes;
     uint64_t t_submit;
     bool small;
+    int gram = -1;     // Gram cache slot the request reads or fills, or -1
+};
+
+// The Gram matrix of one factor (identified by its device pointer, shape,
+// stride and type), kept for requests that declare the factor unchanged.
+struct GramSlot {
+    const void* B = nullptr;
+    int64_t n = 0, ldb = 0;
+    int32_t rank = 0;
+    sym_dtype bdt = SYM_F32;
+    double* G = nullptr;          // packed upper triangle, FP64 (server arena)
+    cudaEvent_t ready = nullptr;  // recorded after it is computed
+    bool valid = false;
+    int inuse = 0;                // requests in flight reading or filling it
+    uint64_t last_use = 0;
+    bool same(const sym_request& r, int64_t nn) const {
+        return valid && B == r.B && n == nn && ldb == r.ldb && rank == r.rank && bdt == r.bdt;
+    }
 };
 
 struct Slot {
@@ -101,6 +119,10 @@ size_t factor_bytes(const sym_request& r, int64_t n) {
 size_t slot_bytes(const sym_server_cfg* cfg) {
     return symgpu::align_up(symgpu::residual_ws_bytes(cfg->max_rank), 256) +
            symgpu::align_up(sizeof(double) * kMaxGroup, 256);
+}
+
+size_t gram_bytes(const sym_server_cfg* cfg) {
+    return symgpu::align_up(sizeof(double) * (size_t)cfg->max_rank * (cfg->max_rank + 1) / 2, 256);
 }
 
 }  // namespace
@@ -128,6 +150,8 @@ struct sym_server_s {
     std::vector<Entry> entries;
     uint64_t tick = 0;
     size_t resident_bytes = 0;
+    GramSlot grams[kGramSlots];  // touched by the scheduler thread only
+    uint64_t gram_tick = 0;
 
     void run();
     void finish(Slot& s, sym_status st);
@@ -219,6 +243,10 @@ void sym_server_s::release() {
         e.X = nullptr;
         e.ready = nullptr;
     }
+    for (auto& g : grams) {
+        if (g.ready) cudaEventDestroy(g.ready);
+        g.ready = nullptr;
+    }
 }
 
 void sym_server_s::finish(Slot& s, sym_status st) {
@@ -240,6 +268,7 @@ void sym_server_s::finish(Slot& s, sym_status st) {
             inflight -= 1;
             stats.completed += 1;
             if (p.reg >= 0) entries[(size_t)p.reg].inuse -= 1;
+            if (p.gram >= 0) grams[p.gram].inuse -= 1;
         }
     }
     s.reqs.clear();
@@ -261,7 +290,46 @@ void sym_server_s::launch(Slot& s) {
         }
         if (st == SYM_OK) st = mttkrp_core(X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.stream);
         if (st == SYM_OK && r.want_residual) {
-            st = residual_launch(X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.res_dev + k, s.ws, s.ws_bytes, s.stream);
+            // Gram of the factor: reused when the request declares the factor unchanged (want_residual 2) and
+            // the cache holds it, else computed into an idle cache slot (the least recently used one)
+            const double* G_in = nullptr;
+            double* G_out = nullptr;
+            int gi = -1;
+            for (int g = 0; g < kGramSlots && gi < 0; ++g)
+                if (grams[g].same(r, X->n)) gi = g;
+            if (gi >= 0 && r.want_residual == 2) {
+                st = cuda_status(cudaStreamWaitEvent(s.stream, grams[gi].ready, 0));
+                G_in = grams[gi].G;
+                stats.gram_hits += 1;
+            } else {
+                if (gi >= 0 && grams[gi].inuse > 0) {  // stale copy still read: retire it, fill another slot
+                    grams[gi].valid = false;
+                    gi = -1;
+                }
+                if (gi < 0)
+                    for (int g = 0; g < kGramSlots; ++g)
+                        if (grams[g].inuse == 0 && (gi < 0 || grams[g].last_use < grams[gi].last_use)) gi = g;
+                if (gi >= 0) {
+                    GramSlot& G = grams[gi];
+                    G.B = r.B;
+                    G.n = X->n;
+                    G.ldb = r.ldb;
+                    G.rank = r.rank;
+                    G.bdt = r.bdt;
+                    G.valid = true;
+                    G_out = G.G;
+                }
+            }
+            if (gi >= 0) {
+                grams[gi].inuse += 1;
+                grams[gi].last_use = ++gram_tick;
+                s.reqs[k].gram = gi;
+            }
+            if (st == SYM_OK)
+                st = residual_launch_gram(X, r.B, bf16, r.rank, r.ldb, r.M, r.ldm, s.res_dev + k, s.ws, s.ws_bytes,
+                                          G_in, G_out, s.stream);
+            if (st == SYM_OK && G_out) st = cuda_status(cudaEventRecord(grams[gi].ready, s.stream));
+            if (st != SYM_OK && G_out) grams[gi].valid = false;
             if (st == SYM_OK)
                 st = cuda_status(
                     cudaMemcpyAsync(s.res_host + k, s.res_dev + k, sizeof(double), cudaMemcpyDeviceToHost, s.stream));
@@ -297,13 +365,14 @@ void sym_server_s::run() {
             const uint64_t t = now_ns();
             Slot* group = nullptr;  // the slot collecting this pass's small requests
             // Phase 0 admits requests whose tensor is on the device (or not registered) and registered
-            // requests that have waited longer than kAffinityWaitNs; phase 1, with the slots left, the rest
-            // (each loading its tensor, after which the queued requests for that tensor are resident too).
+            // requests that have waited longer than cfg.affinity_wait_ns; phase 1, with the slots left, the
+            // rest (each loading its tensor, after which the queued requests for that tensor are resident too).
+            const uint64_t affinity_ns = (uint64_t)std::max<int64_t>(0, cfg.affinity_wait_ns);
             bool slots_left = true;
             for (int phase = 0; phase < 2 && slots_left; ++phase) {
                 for (auto it = queue.begin(); it != queue.end();) {
                     if (phase == 0 && it->reg >= 0 && !entries[(size_t)it->reg].resident &&
-                        t - it->t_submit < kAffinityWaitNs) {
+                        t - it->t_submit < affinity_ns) {
                         ++it;
                         continue;
                     }
@@ -388,7 +457,7 @@ using namespace symgpu;
 
 extern "C" size_t sym_server_arena_bytes(const sym_server_cfg* cfg) {
     if (!cfg || cfg->max_slots < 1 || cfg->max_rank < 4) return 0;
-    return slot_bytes(cfg) * (size_t)cfg->max_slots + align_up(cfg->pool_bytes, 256);
+    return slot_bytes(cfg) * (size_t)cfg->max_slots + gram_bytes(cfg) * kGramSlots + align_up(cfg->pool_bytes, 256);
 }
 
 extern "C" sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, size_t arena_bytes, int device,
@@ -396,7 +465,7 @@ extern "C" sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, 
     if (!out) return SYM_E_INVALID;
     *out = nullptr;
     if (!cfg || cfg->max_slots < 1 || cfg->max_slots > 256 || cfg->max_rank < 4 || cfg->max_rank > 128 ||
-        cfg->max_rank % 4 || cfg->hbm_budget_bytes == 0)
+        cfg->max_rank % 4 || cfg->hbm_budget_bytes == 0 || cfg->affinity_wait_ns < 0)
         return SYM_E_INVALID;
     if (cfg->pool_bytes > cfg->hbm_budget_bytes) return SYM_E_BUDGET;
     if (!arena || !aligned(arena, 256)) return SYM_E_INVALID;
@@ -423,7 +492,12 @@ extern "C" sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, 
         s.ws = base + align_up(sizeof(double) * kMaxGroup, 256);
         s.ws_bytes = per - align_up(sizeof(double) * kMaxGroup, 256);
     }
-    S->pool = static_cast<char*>(arena) + per * (size_t)cfg->max_slots;
+    char* gram_base = static_cast<char*>(arena) + per * (size_t)cfg->max_slots;
+    for (int g = 0; g < kGramSlots && st == SYM_OK; ++g) {
+        S->grams[g].G = reinterpret_cast<double*>(gram_base + gram_bytes(cfg) * (size_t)g);
+        st = cuda_status(cudaEventCreateWithFlags(&S->grams[g].ready, cudaEventDisableTiming));
+    }
+    S->pool = gram_base + gram_bytes(cfg) * kGramSlots;
     S->pool_bytes = align_up(cfg->pool_bytes, 256);
     if (S->pool_bytes) S->free_ranges[0] = S->pool_bytes;
     if (st != SYM_OK) {
@@ -483,7 +557,7 @@ extern "C" sym_status sym_batch_submit(sym_server S, const sym_request* req, uin
     if (!req->X) return SYM_E_BADREQ;
     if (validate_mttkrp_args(req->X, req->B, req->bdt, req->rank, req->ldb, req->M, req->ldm) != SYM_OK)
         return SYM_E_BADREQ;
-    if (req->rank > S->cfg.max_rank) return SYM_E_BADREQ;
+    if (req->rank > S->cfg.max_rank || req->want_residual < 0 || req->want_residual > 2) return SYM_E_BADREQ;
     return enqueue(S, *req, -1, req->X->n, req->X->nnz, req->X->info.arena_used, ticket);
 }
 
@@ -503,6 +577,7 @@ extern "C" sym_status sym_batch_submit_registered(sym_server S, uint64_t id, con
         nnz = inf.nnz;
     }
     if (!req->B || !req->M || (req->bdt != SYM_F32 && req->bdt != SYM_BF16)) return SYM_E_BADREQ;
+    if (req->want_residual < 0 || req->want_residual > 2) return SYM_E_BADREQ;
     if (req->rank < 4 || req->rank > 128 || req->rank % 4 || req->rank > S->cfg.max_rank) return SYM_E_BADREQ;
     if (req->ldb < req->rank || req->ldm < req->rank || req->ldb % 4 || req->ldm % 4) return SYM_E_BADREQ;
     if (!aligned(req->B, req->bdt == SYM_BF16 ? 8 : 16) || !aligned(req->M, 16)) return SYM_E_BADREQ;

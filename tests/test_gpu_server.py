@@ -94,6 +94,9 @@ def test_bad_requests_and_unknown_tickets():
     with pytest.raises(sg.SymError) as e:      # rank not a multiple of 4
         S.submit(X, torch.zeros((100, 6), device="cuda"), torch.zeros((100, 6), device="cuda"))
     assert e.value.code == -9
+    with pytest.raises(sg.SymError) as e:      # want_residual outside 0..2
+        S.submit(X, dev(synth.factor_normal(100, 16, 2)), torch.empty((100, 16), device="cuda"), residual=3)
+    assert e.value.code == -9
     good = S.submit(X, dev(synth.factor_normal(100, 16, 2)), torch.empty((100, 16), device="cuda"))
     assert S.wait(good, 30)["status"] == 0
     with pytest.raises(sg.SymError) as e:
@@ -194,6 +197,52 @@ def test_registered_requests_share_loads():
     st = S.stats()
     assert st["completed"] == 16 and 2 <= st["loads"] <= 6, st
     assert st["peak_resident_bytes"] <= pool_bytes
+    S.close()
+
+
+def test_cached_gram_reused_and_refreshed():
+    """residual=2 declares the factor unchanged since an earlier request: the residual reuses the Gram matrix
+    cached then (gram_hits counts it) and still equals the oracle's.  Overwriting the factor in place and
+    submitting with residual=True recomputes it; later residual=2 requests see the new factor."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    P = pool(sg, [(3, 400, 20000), (4, 60, 9000)], seed=71)
+    S = sg.Server(max_slots=3, max_rank=32)
+    facs = []
+    for k, (T, X) in enumerate(P):
+        Bt, B32, Bused = factor(T.n, 16, 700 + k, bf16=(k == 1))
+        facs.append([T, X, Bt, Bused])
+
+    def run(flags):
+        outs = []
+        for j, flag in flags:
+            T, X, Bt, Bused = facs[j]
+            M = torch.empty((T.n, 16), device="cuda")
+            outs.append((S.submit(X, Bt, M, residual=flag), j, M, Bused.copy()))
+        for t, j, M, Bused in outs:
+            r = S.wait(t, 60)
+            assert r["status"] == 0
+            T = facs[j][0]
+            cidx, cval = oracle.canonicalize(T.order, T.n, T.idx, T.val)
+            ref, ra = oracle.mttkrp_enum(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+            assert oracle.componentwise_error(host(M), ref, ra) <= TOL_F32
+            want, ab, _ = oracle.cpfit(T.order, T.n, cidx, cval, Bused.astype(np.float64))
+            assert abs(r["residual"] - want) / ab <= TOL_F32
+
+    run([(0, True), (1, True)])
+    run([(0, 2), (1, 2), (0, 2), (1, 2)])
+    hits = S.stats()["gram_hits"]
+    assert hits == 4
+    # the factor changes in place: the caller says so (residual=True), the cache is refreshed
+    T, X, Bt, _ = facs[0]
+    torch.manual_seed(5)
+    newB = torch.randn(Bt.shape, device="cuda") / 4.0
+    Bt.copy_(newB.to(Bt.dtype))
+    torch.cuda.synchronize()
+    facs[0][3] = host(Bt.float()).astype(np.float32)
+    run([(0, True)])
+    run([(0, 2), (0, 2)])
+    assert S.stats()["gram_hits"] == hits + 2
     S.close()
 
 
