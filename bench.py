@@ -152,18 +152,20 @@ def strict_variant(cfg, rank=64, order=3):
     """(kernel name for the bench line, key of its DRAM-traffic record, whether the plain-kernel source hash
     applies) of the strict-stream kernel a configuration runs (one-word keys, FP32 factor)."""
     k, epw, leaf, shape = cfg["strict_kernel"], cfg["entries_per_warp"], cfg["leaf_index"], cfg["vec_per_lane"]
+    rc = cfg.get("root_combine", 1)
     lanes = max(1, rank // 4)
     if k == 0:
         mode = 1 if leaf else 0
         if shape == 2 and not leaf:
             return (f"k_mttkrp_strict_wide<{order},1,{lanes // 2},2,f32> ({epw} entries/warp)", f"plain_wide_c{epw}",
                     False)
-        return f"k_mttkrp_strict<{order},1,{lanes},f32,MODE{mode}> ({epw} entries/warp)", f"plain_m{mode}_c{epw}", True
+        return (f"k_mttkrp_strict<{order},1,{lanes},f32,MODE{mode}> ({epw} entries/warp, root combine {rc})",
+                f"plain_m{mode}_c{epw}_r{rc}", True)
     if k == 4:
         mode = 1 if leaf else 0
         d, v = (4, 1) if shape == 4 else (1, shape)
-        return (f"k_mttkrp_lane<{order},1,{lanes // v},f32,MODE{mode},D{d},V{v}> ({epw} entries/warp)",
-                f"lane_m{mode}_d{d}_v{v}_c{epw}", False)
+        return (f"k_mttkrp_lane<{order},1,{lanes // v},f32,MODE{mode},D{d},V{v}> ({epw} entries/warp, root combine "
+                f"{rc})", f"lane_m{mode}_d{d}_v{v}_c{epw}_r{rc}", False)
     name = {1: "k_mttkrp_strict_pipe", 2: "k_mttkrp_entries", 3: "k_mttkrp_strict_staged"}.get(k, "?")
     return f"{name}<{order},1,{lanes},f32> ({epw} entries/warp)", f"k{k}_c{epw}", False
 
@@ -573,11 +575,14 @@ def run_ours(args):
                  "mttkrp_ms": ev[2].elapsed_time(ev[3]), "d2h_ms": ev[3].elapsed_time(ev[4]),
                  "host_wall_ms": (time.perf_counter() - t_host) * 1e3}
     Xe.close()
-    e2e_k = max(3, min(args.steps, 10))
+    e2e_k = max(5, min(args.steps, 20))
     D.barrier()
     t0 = time.perf_counter()
+    e2e_steps = []
     for _ in range(e2e_k):
+        t1 = time.perf_counter()
         e2e_step()
+        e2e_steps.append((time.perf_counter() - t1) * 1e3)
     e2e_s = D.max((time.perf_counter() - t0) / e2e_k)
     h2d = idx_h.numel() * 4 + val_h.numel() * 4 + B_h.numel() * 4
     d2h = M_h.numel() * 4
@@ -606,7 +611,9 @@ def run_ours(args):
            "e2e": {"value": info["nnz"] * D.ws / e2e_s, "unit": "canonical nnz/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
                    "includes": "H2D of coordinate list + values + factor, canonicalisation, MTTKRP, D2H of M",
-                   "one_step_breakdown": e2e_parts},
+                   "one_step_breakdown": e2e_parts, "steps": e2e_k,
+                   "step_ms": {"p50": float(np.median(e2e_steps)), "min": float(min(e2e_steps)),
+                               "max": float(max(e2e_steps))}},
            "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed": t_wall, "extras": extras}
     if D.rank == 0 and not args.no_cpu:
         rate, meta = oracle_sample_rate(T, MAIN["rank"])

@@ -529,6 +529,9 @@ typedef struct {
     int32_t stream_hint;       /* plain kernel: 1 = read the canonical stream with evict-first loads so it does not
                                   displace factor rows from L1 / L2 */
     int32_t l1_pref;           /* plain kernel: 1 = ask for the largest L1 (no shared-memory carveout) */
+    int32_t root_combine;      /* plain and lane kernels: 1 = a CTA merges its lane groups' final root sums in
+                                  shared memory and reduces each root once (pays off when a few roots hold a
+                                  large share of the entries), 0 = one reduction per lane group */
 } sym_mttkrp_cfg;
 sym_status sym_mttkrp_default_config(sym_mttkrp_cfg* out);
 sym_status sym_mttkrp_set_config(sym_tensor X, const sym_mttkrp_cfg* cfg);

@@ -111,7 +111,7 @@ class MttkrpCfg(C.Structure):
     _fields_ = [("strict_kernel", C.c_int32), ("entries_per_warp", C.c_int32), ("threads_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("strict_smem_kb", C.c_int32), ("diag_smem_kb", C.c_int32),
                 ("b_share_pct", C.c_int32), ("leaf_index", C.c_int32), ("vec_per_lane", C.c_int32),
-                ("stream_hint", C.c_int32), ("l1_pref", C.c_int32)]
+                ("stream_hint", C.c_int32), ("l1_pref", C.c_int32), ("root_combine", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -522,9 +522,9 @@ class SymTensor:
 
     def set_config(self, strict_kernel=MTTKRP_PLAIN, entries_per_warp=256, threads_per_cta=256, ctas_per_sm=2,
                    strict_smem_kb=0, diag_smem_kb=96, b_share_pct=0, leaf_index=1, vec_per_lane=1, stream_hint=0,
-                   l1_pref=0):
+                   l1_pref=0, root_combine=1):
         cfg = MttkrpCfg(strict_kernel, entries_per_warp, threads_per_cta, ctas_per_sm, strict_smem_kb, diag_smem_kb,
-                        b_share_pct, leaf_index, vec_per_lane, stream_hint, l1_pref)
+                        b_share_pct, leaf_index, vec_per_lane, stream_hint, l1_pref, root_combine)
         check(lib().sym_mttkrp_set_config(self.handle, C.byref(cfg)), "sym_mttkrp_set_config")
 
     def add_leaf_index(self, stream=None):

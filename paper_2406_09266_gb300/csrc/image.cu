@@ -16,7 +16,7 @@
 namespace symgpu {
 namespace {
 
-constexpr uint64_t kImageMagic = 0x31474d4953594d53ull;  // "SMYSIMG1" read as little-endian bytes
+constexpr uint64_t kImageMagic = 0x32474d4953594d53ull;  // "SMYSIMG2" read as little-endian bytes
 constexpr size_t kHeaderBytes = 1024;
 
 struct ImageHeader {

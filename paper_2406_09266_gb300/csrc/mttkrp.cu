@@ -323,6 +323,7 @@ sym_status validate_mttkrp_cfg(const sym_mttkrp_cfg* c) {
                     : (c->vec_per_lane != 1 && c->vec_per_lane != 2))
         return SYM_E_INVALID;
     if ((c->stream_hint != 0 && c->stream_hint != 1) || (c->l1_pref != 0 && c->l1_pref != 1)) return SYM_E_INVALID;
+    if (c->root_combine != 0 && c->root_combine != 1) return SYM_E_INVALID;
     return SYM_OK;
 }
 
@@ -335,7 +336,7 @@ std::string tune_key(const sym_tensor_s* X, int rank, sym_dtype bdt) {
     for (auto& ch : name)
         if (ch == ' ') ch = '_';
     char buf[320];
-    snprintf(buf, sizeof(buf), "mttkrp2|%s|N%d|n%lld|nnz%lld|strict%lld|R%d|%s|leaf%d", name.c_str(), X->order,
+    snprintf(buf, sizeof(buf), "mttkrp3|%s|N%d|n%lld|nnz%lld|strict%lld|R%d|%s|leaf%d", name.c_str(), X->order,
              (long long)X->n, (long long)X->nnz, (long long)X->nnz_strict, rank, bdt == SYM_BF16 ? "bf16" : "f32",
              X->rklo ? 1 : 0);
     return buf;
@@ -351,9 +352,9 @@ bool tune_lookup(const char* path, const std::string& key, sym_mttkrp_cfg* cfg, 
         char k[400];
         sym_mttkrp_cfg c;
         float t;
-        if (sscanf(line, "%399s %d %d %d %d %d %d %d %d %d %d %d %f", k, &c.strict_kernel, &c.entries_per_warp,
+        if (sscanf(line, "%399s %d %d %d %d %d %d %d %d %d %d %d %d %f", k, &c.strict_kernel, &c.entries_per_warp,
                    &c.threads_per_cta, &c.ctas_per_sm, &c.strict_smem_kb, &c.diag_smem_kb, &c.b_share_pct,
-                   &c.leaf_index, &c.vec_per_lane, &c.stream_hint, &c.l1_pref, &t) == 13 &&
+                   &c.leaf_index, &c.vec_per_lane, &c.stream_hint, &c.l1_pref, &c.root_combine, &t) == 14 &&
             key == k && validate_mttkrp_cfg(&c) == SYM_OK) {
             *cfg = c;
             *ms = t;
@@ -368,9 +369,9 @@ void tune_store(const char* path, const std::string& key, const sym_mttkrp_cfg& 
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %.6f\n", key.c_str(), c.strict_kernel, c.entries_per_warp,
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %.6f\n", key.c_str(), c.strict_kernel, c.entries_per_warp,
             c.threads_per_cta, c.ctas_per_sm, c.strict_smem_kb, c.diag_smem_kb, c.b_share_pct, c.leaf_index,
-            c.vec_per_lane, c.stream_hint, c.l1_pref, ms);
+            c.vec_per_lane, c.stream_hint, c.l1_pref, c.root_combine, ms);
     fclose(f);
 }
 
@@ -431,7 +432,7 @@ extern "C" sym_status sym_mttkrp_range(sym_tensor X, const void* B, sym_dtype bd
 
 extern "C" sym_status sym_mttkrp_default_config(sym_mttkrp_cfg* out) {
     if (!out) return SYM_E_INVALID;
-    *out = sym_mttkrp_cfg{SYM_MTTKRP_PLAIN, 256, 256, 2, 0, 96, 0, 1, 1, 0, 0};
+    *out = sym_mttkrp_cfg{SYM_MTTKRP_PLAIN, 256, 256, 2, 0, 96, 0, 1, 1, 0, 0, 1};
     return SYM_OK;
 }
 
@@ -487,27 +488,36 @@ extern "C" sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype
         if (leaf && !X->rklo) continue;
         for (int chunk : {128, 256, 512})
             for (int sh : {0, 1})
-                for (int l1 : {0, 1}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, leaf, 1, sh, l1});
+                for (int l1 : {0, 1}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, leaf, 1, sh, l1, 1});
     }
     if (rank >= 8)
-        for (int chunk : {256, 512}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, 0, 2, 0, 0});
+        for (int chunk : {256, 512}) cands.push_back({SYM_MTTKRP_PLAIN, chunk, 256, 2, 0, 0, 0, 0, 2, 0, 0, 1});
     for (int chunk : {128, 256, 512})
-        for (int thr : {128, 256}) cands.push_back({SYM_MTTKRP_STAGED, chunk, thr, 2, 0, 0, 0, 0, 1, 0, 0});
-    for (int chunk : {128, 256}) cands.push_back({SYM_MTTKRP_PIPELINED, chunk, 256, 2, 0, 0, 0, 0, 1, 0, 0});
+        for (int thr : {128, 256}) cands.push_back({SYM_MTTKRP_STAGED, chunk, thr, 2, 0, 0, 0, 0, 1, 0, 0, 1});
+    for (int chunk : {128, 256}) cands.push_back({SYM_MTTKRP_PIPELINED, chunk, 256, 2, 0, 0, 0, 0, 1, 0, 0, 1});
     for (int depth : {1, 4, 2}) {  // lane shapes: one or four leaf rows in flight, or 8 columns per lane
         // (8 columns per lane measured slower than 4 below rank 64: too few lanes per entry)
         if ((depth == 4 && rank < 16) || (depth == 2 && rank < 64)) continue;
         for (int chunk : {128, 256, 512}) {
-            cands.push_back({SYM_MTTKRP_LANE, chunk, 256, 2, 0, 0, 0, 0, depth, 1, 0});  // one pass
+            cands.push_back({SYM_MTTKRP_LANE, chunk, 256, 2, 0, 0, 0, 0, depth, 1, 0, 1});  // one pass
             if (!X->rklo) continue;
             for (int rc : {2, 4})  // two passes, unfactorised root pass of 64 rc entries per warp
-                cands.push_back({SYM_MTTKRP_LANE, chunk, 256, rc, 0, 0, 0, 1, depth, 1, 0});
-            cands.push_back({SYM_MTTKRP_LANE, chunk, 256, 2, 1, 0, 0, 1, depth, 1, 0});  // factorised root pass
+                cands.push_back({SYM_MTTKRP_LANE, chunk, 256, rc, 0, 0, 0, 1, depth, 1, 0, 1});
+            cands.push_back({SYM_MTTKRP_LANE, chunk, 256, 2, 1, 0, 0, 1, depth, 1, 0, 1});  // factorised root pass
         }
     }
-    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 0, 0, 0, 0, 1, 0, 0});
-    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 96, 0, 50, 0, 1, 0, 0});
-    cands.push_back({SYM_MTTKRP_UNFACTORISED, 256, 256, 2, 0, 0, 0, 0, 1, 0, 0});
+    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 0, 0, 0, 0, 1, 0, 0, 1});
+    cands.push_back({SYM_MTTKRP_PIPELINED, 0, 512, 2, 96, 0, 50, 0, 1, 0, 0, 1});
+    cands.push_back({SYM_MTTKRP_UNFACTORISED, 256, 256, 2, 0, 0, 0, 0, 1, 0, 0, 1});
+    {  // the plain and lane kernels also without the combined root flush
+        const size_t base = cands.size();
+        for (size_t k = 0; k < base; ++k)
+            if (cands[k].strict_kernel == SYM_MTTKRP_PLAIN || cands[k].strict_kernel == SYM_MTTKRP_LANE) {
+                sym_mttkrp_cfg c = cands[k];
+                c.root_combine = 0;
+                cands.push_back(c);
+            }
+    }
     cudaEvent_t e0, e1;
     SYM_CUDA(cudaEventCreate(&e0));
     SYM_CUDA(cudaEventCreate(&e1));

@@ -153,31 +153,61 @@ __device__ __forceinline__ void warp_range(int64_t nnz, int64_t chunk, int64_t* 
 // skewed distribution a few root fibers hold a large share of the entries
 // (Zipf(1.2): the hottest root 22 % of the 3-way stream), so every warp in
 // their span ends inside them and would reduce its root sum into the same
-// output row.  Instead each group leaves (root, its R-float sum) in shared
-// memory; the first group of every run of equal roots (CTA order) adds the run
-// and issues one row reduction.  Every thread of the CTA must call this (it
-// holds a barrier); `valid` is false for a group with nothing to flush.
+// output row.  Instead the groups' (root, R-float sum) pairs are merged by a
+// pairwise tree in shared memory: at distance d, group g (a multiple of 2d)
+// absorbs group g + d when both hold the same root (or g holds none), and
+// otherwise group g + d reduces its own sum into its row.  Every sum is added
+// exactly once; a CTA whose groups all end in one root issues one reduction.
+// Every thread of the CTA must call this (it holds barriers); `valid` is false
+// for a group with nothing to flush.
+// Its shared memory is dynamic (root_flush_smem bytes, given at launch only
+// when the flush is combined), so a kernel launched without it keeps the whole
+// unified L1 / shared memory as L1.
+template <int L>
+constexpr size_t root_flush_smem() {
+    return sizeof(float4) * MT_THREADS + sizeof(int32_t) * (MT_THREADS / L);
+}
+
 template <int L>
 __device__ __forceinline__ void cta_root_flush(int32_t root, float4 v, bool valid, bool on, float* M, int64_t ldm,
                                                int col, float w) {
-    __shared__ int32_t s_root[MT_THREADS / L];
-    __shared__ float4 s_vec[MT_THREADS];
+    extern __shared__ __align__(16) unsigned char root_flush_dyn[];
+    float4* s_vec = reinterpret_cast<float4*>(root_flush_dyn);                       // MT_THREADS
+    int32_t* s_root = reinterpret_cast<int32_t*>(root_flush_dyn + sizeof(float4) * MT_THREADS);  // MT_THREADS / L
     const int gid = (int)threadIdx.x / L, sl = (int)threadIdx.x % L;
     const int ng = (int)blockDim.x / L;
-    if (sl == 0) s_root[gid] = valid ? root : -1;
-    s_vec[threadIdx.x] = v;
+    int32_t rg = valid ? root : -1;
+    float4 acc = valid ? v : f4_zero();
+    if (sl == 0) s_root[gid] = rg;
+    s_vec[threadIdx.x] = acc;
     __syncthreads();
-    if (valid && (gid == 0 || s_root[gid - 1] != root)) {
-        float4 acc = v;
-        for (int k = gid + 1; k < ng && s_root[k] == root; ++k) {
-            const float4 o = s_vec[k * L + sl];
-            acc.x += o.x;
-            acc.y += o.y;
-            acc.z += o.z;
-            acc.w += o.w;
+    for (int d = 1; d < ng; d <<= 1) {
+        const bool lead = (gid % (2 * d)) == 0 && gid + d < ng;
+        if (lead) {
+            const int32_t rp = s_root[gid + d];
+            const float4 vp = s_vec[(gid + d) * L + sl];
+            if (rp >= 0) {
+                if (rp == rg) {
+                    acc.x += vp.x;
+                    acc.y += vp.y;
+                    acc.z += vp.z;
+                    acc.w += vp.w;
+                } else if (rg < 0) {
+                    rg = rp;
+                    acc = vp;
+                } else if (on) {
+                    red_add_f4(M + (int64_t)rp * ldm + col, f4_scale(vp, w));
+                }
+            }
         }
-        if (on) red_add_f4(M + (int64_t)root * ldm + col, f4_scale(acc, w));
+        __syncthreads();
+        if (lead) {
+            if (sl == 0) s_root[gid] = rg;
+            s_vec[threadIdx.x] = acc;
+        }
+        __syncthreads();
     }
+    if (gid == 0 && rg >= 0 && on) red_add_f4(M + (int64_t)rg * ldm + col, f4_scale(acc, w));
 }
 
 // CSF-factorised strict-stream kernel, no shared memory, one entry at a time
@@ -192,7 +222,7 @@ template <int N, int KW, int L, bool BF16, int MODE>
 __global__ void __launch_bounds__(MT_THREADS, (N <= 3 && KW == 1 && L > 1) ? 5 : 1) k_mttkrp_strict(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
-    int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX) {
+    int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX, int combine = 1) {
     static_assert(N >= 2 && N <= 5, "order");
     constexpr int LV = N - 1;  // fiber levels above the leaf
     const int lane = threadIdx.x & 31;
@@ -284,7 +314,10 @@ __global__ void __launch_bounds__(MT_THREADS, (N <= 3 && KW == 1 && L > 1) ? 5 :
             T[q - 1] = f4_fma(Brow[q], T[q], T[q - 1]);
         }
     }
-    cta_root_flush<L>(cur[0], T[0], have, on, M, ldm, col, w);
+    if (combine)  // uniform over the grid: every thread of the CTA reaches the barriers or none does
+        cta_root_flush<L>(cur[0], T[0], have, on, M, ldm, col, w);
+    else if (have && on)
+        red_add_f4(M + (int64_t)cur[0] * ldm + col, f4_scale(T[0], w));
 }
 
 // The plain kernel with VPL float4 column groups per lane (L = R / (4 VPL) lanes
@@ -703,7 +736,7 @@ template <int N, int KW, int L, bool BF16, int MODE, int D, int V>
 __global__ void __launch_bounds__(256, V == 1 ? (D == 1 ? 4 : 3) : 3) k_mttkrp_lane(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const float* __restrict__ val, int64_t nnz,
     int bits, const void* __restrict__ B, int64_t ldb, int R, float* __restrict__ M, int64_t ldm, float w,
-    int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX) {
+    int64_t chunk, int stream_hint, int64_t nrows = INT64_MAX, int combine = 1) {
     static_assert(N >= 2 && N <= 5, "order");
     static_assert(D >= 1 && D <= L && L % D == 0, "prefetch depth divides the lanes per entry");
     static_assert(V == 1 || V == 2, "column groups per lane");
@@ -852,8 +885,12 @@ __global__ void __launch_bounds__(256, V == 1 ? (D == 1 ? 4 : 3) : 3) k_mttkrp_l
     if (have) flush(0, 1);
 #pragma unroll
     for (int u = 0; u < V; ++u) {
-        if (u > 0) __syncthreads();  // the previous column group's shared slots are read
-        cta_root_flush<L>(cur[0], T[0][u], have, on[u], M, ldm, col + 4 * L * u, w);
+        if (combine) {  // uniform over the grid
+            if (u > 0) __syncthreads();  // the previous column group's shared slots are read
+            cta_root_flush<L>(cur[0], T[0][u], have, on[u], M, ldm, col + 4 * L * u, w);
+        } else if (have && on[u]) {
+            red_add_f4(M + (int64_t)cur[0] * ldm + col + 4 * L * u, f4_scale(T[0][u], w));
+        }
     }
 }
 
@@ -1031,25 +1068,22 @@ __global__ void __launch_bounds__(512) k_mttkrp_entries(
 
 // ---------------------------------------------------------------- launch
 
-// Smallest shared-memory carveout (percent of the SM's maximum) that holds the
-// static shared memory of `kernel` for as many CTAs of MT_THREADS threads as
-// an SM can run (plus the 1 KB the hardware reserves per CTA); the rest of
-// the unified L1 / shared memory stays L1.
-template <typename K>
-int l1_carveout_pct(K kernel) {
-    static std::atomic<int> pct{-1};  // per kernel instantiation; every device of the process is a GB300
-    if (pct.load() < 0) {
-        cudaFuncAttributes fa{};
-        int smem_sm = 0;
-        if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess ||
-            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, current_device()) !=
-                cudaSuccess ||
-            smem_sm <= 0)
+// Smallest shared-memory carveout (percent of the SM's maximum) that holds
+// `smem` bytes of shared memory for as many CTAs of MT_THREADS threads as an
+// SM can run (plus the 1 KB the hardware reserves per CTA); the rest of the
+// unified L1 / shared memory stays L1.  0 when the kernel takes none.
+inline int l1_carveout_pct(size_t smem) {
+    if (smem == 0) return 0;
+    static std::atomic<int> smem_sm{0};  // every device of the process is a GB300
+    if (smem_sm.load() <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, current_device()) != cudaSuccess ||
+            v <= 0)
             return (int)cudaSharedmemCarveoutDefault;
-        const size_t need = (size_t)(2048 / MT_THREADS) * (fa.sharedSizeBytes + 1024);
-        pct.store((int)std::min<size_t>(100, (need * 100 + (size_t)smem_sm - 1) / (size_t)smem_sm));
+        smem_sm.store(v);
     }
-    return pct.load();
+    const size_t need = (size_t)(2048 / MT_THREADS) * (smem + 1024);
+    return (int)std::min<size_t>(100, (need * 100 + (size_t)smem_sm.load() - 1) / (size_t)smem_sm.load());
 }
 
 // Hot-row sizing within a shared-memory budget: rows of M (H) and of B (HB).
@@ -1073,20 +1107,21 @@ inline SinkPlan plan_sink(int64_t n, int R, int kb, int b_share_pct) {
 template <int N, int KW, int L, bool BF16, int MODE>
 sym_status launch_lane_m(int shape, int64_t cnt, const uint64_t* klo, const uint64_t* khi, const float* val, int bits,
                          const void* B, int64_t ldb, int R, float* M, int64_t ldm, float w, int64_t chunk,
-                         int stream_hint, const char* name, cudaStream_t s, int64_t nrows) {
+                         int stream_hint, const char* name, cudaStream_t s, int64_t nrows, int combine) {
     const int64_t warps = (cnt + chunk - 1) / chunk;
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
     constexpr int LH = L >= 2 ? L / 2 : 1;
+    const size_t rf = combine ? root_flush_smem<L>() : 0, rfh = combine ? root_flush_smem<LH>() : 0;
     SYM_PROF(name, s);
     if (shape == 4 && L >= 4)
-        k_mttkrp_lane<N, KW, L, BF16, MODE, (L >= 4 ? 4 : 1), 1><<<grid, 256, 0, s>>>(
-            klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w, chunk, stream_hint, nrows);
+        k_mttkrp_lane<N, KW, L, BF16, MODE, (L >= 4 ? 4 : 1), 1><<<grid, 256, rf, s>>>(
+            klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w, chunk, stream_hint, nrows, combine);
     else if (shape == 2 && L >= 2)
-        k_mttkrp_lane<N, KW, LH, BF16, MODE, 1, 2><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm,
-                                                                        w, chunk, stream_hint, nrows);
+        k_mttkrp_lane<N, KW, LH, BF16, MODE, 1, 2><<<grid, 256, rfh, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm,
+                                                                        w, chunk, stream_hint, nrows, combine);
     else
-        k_mttkrp_lane<N, KW, L, BF16, MODE, 1, 1><<<grid, 256, 0, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
-                                                                      chunk, stream_hint, nrows);
+        k_mttkrp_lane<N, KW, L, BF16, MODE, 1, 1><<<grid, 256, rf, s>>>(klo, khi, val, cnt, bits, B, ldb, R, M, ldm, w,
+                                                                      chunk, stream_hint, nrows, combine);
     SYM_CHECK_LAUNCH();
     return SYM_OK;
 }
@@ -1124,32 +1159,32 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             const bool leaf_pass = cfg.leaf_index != 0 && X->rklo != nullptr;
             constexpr int L2 = L / 2;   // lanes per entry with 8 columns per lane
             // carveout preference: as much of the unified L1 / shared memory as L1 as leaves room for the
-            // kernel's static shared memory (its final root flush) in every CTA an SM can hold, or the default
+            // combined root flush's shared memory in every CTA an SM can hold, or the driver default
+            const size_t rf_smem = cfg.root_combine ? root_flush_smem<L>() : 0;
             SYM_CUDA(cudaFuncSetAttribute(k_mttkrp_strict<N, KW, L, BF16, 0>,
                                           cudaFuncAttributePreferredSharedMemoryCarveout,
-                                          cfg.l1_pref ? l1_carveout_pct(k_mttkrp_strict<N, KW, L, BF16, 0>)
-                                                      : (int)cudaSharedmemCarveoutDefault));
+                                          cfg.l1_pref ? l1_carveout_pct(rf_smem) : (int)cudaSharedmemCarveoutDefault));
             if (!leaf_pass && cfg.vec_per_lane == 2 && L2 >= 1) {
                 SYM_PROF("mttkrp_strict", s);
                 k_mttkrp_strict_wide<N, KW, (L2 >= 1 ? L2 : 1), 2, BF16><<<grid, MT_THREADS, 0, s>>>(
                     X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk);
             } else if (!leaf_pass) {
                 SYM_PROF("mttkrp_strict", s);
-                k_mttkrp_strict<N, KW, L, BF16, 0><<<grid, MT_THREADS, 0, s>>>(
+                k_mttkrp_strict<N, KW, L, BF16, 0><<<grid, MT_THREADS, rf_smem, s>>>(
                     X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                    cfg.stream_hint, X->n);
+                    cfg.stream_hint, X->n, cfg.root_combine);
             } else {
                 {
                     SYM_PROF("mttkrp_strict", s);
-                    k_mttkrp_strict<N, KW, L, BF16, 1><<<grid, MT_THREADS, 0, s>>>(
+                    k_mttkrp_strict<N, KW, L, BF16, 1><<<grid, MT_THREADS, rf_smem, s>>>(
                         X->klo, X->khi, X->val, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                        cfg.stream_hint, X->n);
+                        cfg.stream_hint, X->n, cfg.root_combine);
                 }
                 SYM_CHECK_LAUNCH();
                 SYM_PROF("mttkrp_strict_leaf", s);
-                k_mttkrp_strict<N, KW, L, BF16, 2><<<grid, MT_THREADS, 0, s>>>(
+                k_mttkrp_strict<N, KW, L, BF16, 2><<<grid, MT_THREADS, rf_smem, s>>>(
                     X->rklo, X->rkhi, X->rval, ns, X->bits, B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                    cfg.stream_hint, X->n);
+                    cfg.stream_hint, X->n, cfg.root_combine);
             }
         } else if (cfg.strict_kernel == SYM_MTTKRP_PIPELINED) {
             const SinkPlan sp = plan_sink(X->n, R, cfg.strict_smem_kb, cfg.b_share_pct);
@@ -1174,10 +1209,10 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
             const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
             sym_status ls = two ? launch_lane_m<N, KW, L, BF16, 1>(cfg.vec_per_lane, ns, X->klo, X->khi, X->val,
                                                                    X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
-                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s, X->n)
+                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s, X->n, cfg.root_combine)
                                 : launch_lane_m<N, KW, L, BF16, 0>(cfg.vec_per_lane, ns, X->klo, X->khi, X->val,
                                                                    X->bits, B, ldb, R, M, ldm, (float)fact[N - 1],
-                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s, X->n);
+                                                                   chunk, cfg.stream_hint, "mttkrp_strict", s, X->n, cfg.root_combine);
             if (ls == SYM_OK && two) {
                 if (cfg.strict_smem_kb == 0) {  // root pass unfactorised below the root
                     const int64_t rchunk = cfg.ctas_per_sm > 0 ? 64LL * cfg.ctas_per_sm : 256;
@@ -1187,7 +1222,7 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
                 } else {
                     ls = launch_lane_m<N, KW, L, BF16, 2>(cfg.vec_per_lane, ns, X->rklo, X->rkhi, X->rval, X->bits,
                                                           B, ldb, R, M, ldm, (float)fact[N - 1], chunk,
-                                                          cfg.stream_hint, "mttkrp_strict_leaf", s, X->n);
+                                                          cfg.stream_hint, "mttkrp_strict_leaf", s, X->n, cfg.root_combine);
                 }
             }
             if (ls != SYM_OK) return ls;

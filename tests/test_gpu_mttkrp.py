@@ -83,6 +83,11 @@ CONFIGS = [
     dict(strict_kernel=3, entries_per_warp=32, threads_per_cta=64, leaf_index=0, diag_smem_kb=0),
     dict(strict_kernel=3, entries_per_warp=1024, threads_per_cta=512, leaf_index=0),
     dict(strict_kernel=0, entries_per_warp=512, leaf_index=0, stream_hint=1, l1_pref=1),
+    # one root reduction per lane group instead of the CTA's combined root flush
+    dict(strict_kernel=0, entries_per_warp=128, leaf_index=0, root_combine=0),
+    dict(strict_kernel=0, entries_per_warp=256, leaf_index=1, root_combine=0),
+    dict(strict_kernel=4, entries_per_warp=256, leaf_index=0, vec_per_lane=4, root_combine=0),
+    dict(strict_kernel=4, entries_per_warp=64, leaf_index=1, vec_per_lane=1, root_combine=0),
 ]
 
 
@@ -289,7 +294,8 @@ def test_mttkrp_lane_kernel_rejects_bad_config():
     sg = need_gpu()
     T = synth.tensor_uniform(3, 50, 500, 1)
     X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
-    for bad in (dict(vec_per_lane=3), dict(entries_per_warp=0), dict(entries_per_warp=48), dict(strict_kernel=5)):
+    for bad in (dict(vec_per_lane=3), dict(entries_per_warp=0), dict(entries_per_warp=48), dict(strict_kernel=5),
+                dict(root_combine=2)):
         cfg = dict(strict_kernel=sg.MTTKRP_LANE, entries_per_warp=256, threads_per_cta=256, leaf_index=1)
         cfg.update(bad)
         with pytest.raises(sg.SymError):
