@@ -373,10 +373,14 @@ sym_status sym_tensor_create_bytes(int order, int64_t n, int64_t nnz, size_t* ar
  *      indices distinct) and the DIAGONAL stream (some index repeated);
  *   5. exact counts are taken (per equality pattern, full-tensor nonzeros,
  *      fibers) and ||X||^2 over the full tensor is summed in FP64.
- * idx [device]: order rows of nnz int32, row q at idx + q*ld_idx, any position
- * order per tuple.  val [device]: nnz floats.  Order 2..5, 1 <= n < 2^31,
- * order * ceil(log2 n) <= 128.  Synchronises `stream` (it reads back counts).
- * On error no tensor is created. */
+ * idx [device, or page-locked host memory the device can address (cudaHostAlloc
+ * / cudaHostRegister): order rows of nnz int32, row q at idx + q*ld_idx, any
+ * position order per tuple.  It is read once, by the packing kernel, so a
+ * host coordinate list crosses the host link inside that kernel instead of in
+ * a separate copy; pageable host memory is refused with SYM_E_INVALID].
+ * val [device]: nnz floats (read out of order after the sort).  Order 2..5,
+ * 1 <= n < 2^31, order * ceil(log2 n) <= 128.  Synchronises `stream` (it reads
+ * back counts).  On error no tensor is created. */
 sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const int32_t* idx, int64_t ld_idx,
                              const float* val, sym_dup_policy dup, void* arena, size_t arena_bytes,
                              void* ws, size_t ws_bytes, sym_stream_t stream, sym_tensor* out);

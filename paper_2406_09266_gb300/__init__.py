@@ -443,24 +443,27 @@ class SymTensor:
 
     def __init__(self, idx: torch.Tensor, val: torch.Tensor, n: int, dup: int = DUP_ERROR, stream=None,
                  ws: torch.Tensor | None = None):
-        if idx.dim() != 2 or idx.dtype != torch.int32 or not idx.is_cuda:
-            raise TypeError("idx must be a (order, nnz) int32 CUDA tensor")
+        if idx.dim() != 2 or idx.dtype != torch.int32 or not (idx.is_cuda or idx.is_pinned()):
+            raise TypeError("idx must be a (order, nnz) int32 CUDA tensor or pinned host tensor")
         if val.dtype != torch.float32 or not val.is_cuda:
             raise TypeError("val must be a float32 CUDA tensor")
         order, nnz = idx.shape
-        idx = idx.contiguous()
+        if idx.is_cuda:
+            idx = idx.contiguous()
+        elif not idx.is_contiguous():
+            raise TypeError("a pinned host idx must be contiguous")
         ab, wb = C.c_size_t(0), C.c_size_t(0)
         check(lib().sym_tensor_create_bytes(order, n, nnz, C.byref(ab), C.byref(wb)), "sym_tensor_create_bytes")
-        self.arena = _scratch(ab.value, idx.device)
+        self.arena = _scratch(ab.value, val.device)
         if ws is None or ws.numel() < wb.value:
-            ws = _scratch(wb.value, idx.device)
+            ws = _scratch(wb.value, val.device)
         h = C.c_void_p()
         check(lib().sym_tensor_create(order, n, nnz, _ptr(idx), max(nnz, 1), _ptr(val.contiguous()), dup,
                                       _ptr(self.arena), self.arena.numel(), _ptr(ws), ws.numel(), _stream(stream),
                                       C.byref(h)), "sym_tensor_create")
         self.handle = h
         self.order, self.n = order, n
-        self.device = idx.device
+        self.device = val.device
         self._info = None
 
     def save_image(self, host: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -755,12 +758,15 @@ class PTensor:
     `parts`, part p's indices in [0, dims[p]); symmetric under permutations inside each part."""
 
     def __init__(self, idx: torch.Tensor, val: torch.Tensor, parts, dims, dup: int = DUP_ERROR, stream=None):
-        if idx.dim() != 2 or idx.dtype != torch.int32 or not idx.is_cuda:
-            raise TypeError("idx must be a (order, nnz) int32 CUDA tensor")
+        if idx.dim() != 2 or idx.dtype != torch.int32 or not (idx.is_cuda or idx.is_pinned()):
+            raise TypeError("idx must be a (order, nnz) int32 CUDA tensor or pinned host tensor")
         if val.dtype != torch.float32 or not val.is_cuda:
             raise TypeError("val must be a float32 CUDA tensor")
         order, nnz = idx.shape
-        idx = idx.contiguous()
+        if idx.is_cuda:
+            idx = idx.contiguous()
+        elif not idx.is_contiguous():
+            raise TypeError("a pinned host idx must be contiguous")
         self._part = (C.c_int32 * len(parts))(*[int(p) for p in parts])
         self._dim = (C.c_int64 * len(dims))(*[int(d) for d in dims])
         ab, wb = C.c_size_t(0), C.c_size_t(0)

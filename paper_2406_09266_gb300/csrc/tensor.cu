@@ -462,6 +462,22 @@ extern "C" sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const
     if (st != SYM_OK) return st;
     if (nnz > 0 && (!idx || !val || ld_idx < nnz)) return SYM_E_INVALID;
     if (dup != SYM_DUP_ERROR && dup != SYM_DUP_KEEP_EQUAL) return SYM_E_INVALID;
+    if (nnz > 0) {
+        // idx may be page-locked host memory (read in place by the packing kernel through its device
+        // address); val must be device memory (gathered in sorted order later)
+        cudaPointerAttributes ai{}, av{};
+        if (cudaPointerGetAttributes(&ai, idx) != cudaSuccess || cudaPointerGetAttributes(&av, val) != cudaSuccess) {
+            cudaGetLastError();
+            return SYM_E_INVALID;
+        }
+        if (av.type != cudaMemoryTypeDevice && av.type != cudaMemoryTypeManaged) return SYM_E_INVALID;
+        if (ai.type == cudaMemoryTypeHost) {
+            if (!ai.devicePointer) return SYM_E_INVALID;
+            idx = static_cast<const int32_t*>(ai.devicePointer);
+        } else if (ai.type != cudaMemoryTypeDevice && ai.type != cudaMemoryTypeManaged) {
+            return SYM_E_INVALID;
+        }
+    }
     if (!arena || !ws || !aligned(arena, 256) || !aligned(ws, 256)) return SYM_E_INVALID;
     if (arena_bytes < need_a || ws_bytes < need_w) return SYM_E_NOMEM;
     const int bits = bits_for(n);

@@ -36,6 +36,38 @@ def test_canonical_bitexact(order, n, nnz, recipe):
     assert info["key_bits"] * order > 64 or n < 70_000
 
 
+@pytest.mark.parametrize("order,n,nnz,recipe", [CASES[2], CASES[5]])
+def test_canonical_from_pinned_host_coordinates(order, n, nnz, recipe):
+    """The coordinate list may stay in page-locked host memory (read in place by the packing kernel): the
+    canonical form and the counts equal the oracle's bit for bit; pageable host memory is refused."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    T = synth.tensor3_zipf(n, nnz, 3) if recipe == "zipf" else synth.tensor_uniform(order, n, nnz, 3)
+    idx_h = torch.from_numpy(np.ascontiguousarray(T.idx)).pin_memory()
+    X = sg.SymTensor(idx_h, dev(T.val), n)
+    cidx, cval = oracle.canonicalize(order, n, T.idx, T.val)
+    want_idx, want_val, n_strict = canonical_split(order, cidx, cval)
+    gi, gv = X.export()
+    assert np.array_equal(host(gi), want_idx)
+    assert np.array_equal(host(gv).view(np.uint32), want_val.view(np.uint32))
+    info = X.info()
+    assert info["nnz"] == cval.shape[0] and info["nnz_strict"] == n_strict
+    assert info["expanded_nnz"] == oracle.counts(order, cidx, cval)["expanded"]
+    # pageable host memory cannot be read by the device: refused before any launch
+    C = sg.C
+    idx_p = torch.from_numpy(np.ascontiguousarray(T.idx))
+    ab, wb = C.c_size_t(0), C.c_size_t(0)
+    assert sg.lib().sym_tensor_create_bytes(order, n, nnz, C.byref(ab), C.byref(wb)) == 0
+    arena = torch.empty(ab.value, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(wb.value, dtype=torch.uint8, device="cuda")
+    val_d = dev(T.val)
+    out = C.c_void_p()
+    rc = sg.lib().sym_tensor_create(order, n, nnz, C.c_void_p(idx_p.data_ptr()), nnz, C.c_void_p(val_d.data_ptr()),
+                                    0, C.c_void_p(arena.data_ptr()), arena.numel(), C.c_void_p(ws.data_ptr()),
+                                    ws.numel(), None, C.byref(out))
+    assert rc == -1 and not out.value   # SYM_E_INVALID, no tensor
+
+
 def test_ragged_tail_and_tiles():
     """Sizes around the radix-sort tile (2048) and scan tile (4096) boundaries."""
     sg = need_gpu()
