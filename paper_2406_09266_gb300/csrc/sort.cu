@@ -86,6 +86,22 @@ sym_status scan_impl(const T* in, T* out, int64_t n, void* ws, cudaStream_t s) {
     return SYM_OK;
 }
 
+// Two-level exclusive scan for the radix count arrays: per-tile exclusive
+// prefixes in `out` and the exclusive scan of the tile totals in `sums`, so a
+// consumer reads out[i] + sums[i / SCAN_TILE] and no pass adds the tile
+// offsets back into `out`.  Needs at most SCAN_TILE tiles (false otherwise).
+bool scan_two_level_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums, cudaStream_t s) {
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (n <= 0 || tiles > SCAN_TILE) return false;
+    k_scan_tiles<uint32_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, sums);
+    k_scan_tiles<uint32_t><<<1, SCAN_THREADS, 0, s>>>(sums, sums, tiles, (uint32_t*)nullptr);
+    return true;
+}
+
+__device__ __forceinline__ uint32_t count_offset(const uint32_t* offsets, const uint32_t* tile_sums, int64_t i) {
+    return offsets[i] + (tile_sums ? tile_sums[i / SCAN_TILE] : 0u);
+}
+
 // ---------------------------------------------------------------- radix sort
 
 constexpr int RADIX_BITS = 8;
@@ -129,7 +145,7 @@ template <int KW>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi, const uint32_t* __restrict__ pay,
     uint64_t* __restrict__ olo, uint64_t* __restrict__ ohi, uint32_t* __restrict__ opay, int64_t n, int shift,
-    const uint32_t* __restrict__ offsets, int64_t ntiles) {
+    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ tile_sums, int64_t ntiles) {
     __shared__ uint32_t cnt[RS_WARPS][RADIX];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < RS_WARPS * RADIX; t += RS_THREADS) (&cnt[0][0])[t] = 0;
@@ -156,7 +172,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     __syncthreads();
     // per digit: exclusive offsets across warps, seeded with the global offset
     for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) {
-        uint32_t run = offsets[(int64_t)d * ntiles + blockIdx.x];
+        uint32_t run = count_offset(offsets, tile_sums, (int64_t)d * ntiles + blockIdx.x);
 #pragma unroll
         for (int ww = 0; ww < RS_WARPS; ++ww) {
             uint32_t c = cnt[ww][d];
@@ -191,6 +207,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
                                                                      uint64_t* __restrict__ olo,
                                                                      uint32_t* __restrict__ opay, int64_t n, int shift,
                                                                      const uint32_t* __restrict__ offsets,
+                                                                     const uint32_t* __restrict__ tile_sums,
                                                                      int64_t ntiles) {
     static_assert(RS_THREADS == RADIX, "one thread per digit in the tile scan");
     __shared__ uint32_t cnt[RS_WARPS][RADIX];
@@ -231,7 +248,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
         __syncthreads();
         uint32_t start = incl - tot;
         for (int k = 0; k < w; ++k) start += wsum[k];
-        gbase[d] = offsets[(int64_t)d * ntiles + blockIdx.x] - start;
+        gbase[d] = count_offset(offsets, tile_sums, (int64_t)d * ntiles + blockIdx.x) - start;
         uint32_t run = start;
 #pragma unroll
         for (int ww = 0; ww < RS_WARPS; ++ww) {
@@ -313,14 +330,22 @@ sym_status radix_sort_pairs(int kw, uint64_t* klo, uint64_t* khi, uint32_t* pay,
             k_radix_hist<1><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(a_lo, a_hi, n, shift, counts, ntiles);
         }
         SYM_CHECK_LAUNCH();
-        sym_status st = exclusive_scan_u32(counts, offs, nc, sws, s);
-        if (st != SYM_OK) return st;
+        // digit offsets: two-level (tile prefixes + scanned tile sums, read together by the scatter) when the
+        // count array has at most SCAN_TILE tiles, else a full scan
+        const uint32_t* tsums = static_cast<const uint32_t*>(sws);
+        if (scan_two_level_u32(counts, offs, nc, static_cast<uint32_t*>(sws), s)) {
+            SYM_CHECK_LAUNCH();
+        } else {
+            tsums = nullptr;
+            sym_status st = exclusive_scan_u32(counts, offs, nc, sws, s);
+            if (st != SYM_OK) return st;
+        }
         if (kw == 2) {
             k_radix_scatter<2><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(a_lo, a_hi, a_p, b_lo, b_hi, b_p, n, shift,
-                                                                      offs, ntiles);
+                                                                      offs, tsums, ntiles);
         } else {
             k_radix_scatter_staged<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(a_lo, a_p, b_lo, b_p, n, shift, offs,
-                                                                         ntiles);
+                                                                         tsums, ntiles);
         }
         SYM_CHECK_LAUNCH();
         uint64_t* t = a_lo; a_lo = b_lo; b_lo = t;
