@@ -550,12 +550,17 @@ def run_ours(args):
     del X
     torch.cuda.empty_cache()
 
-    # The coordinate list stays in pinned host memory: the packing kernel reads it over the host link in
-    # place (sym_tensor_create accepts page-locked host coordinates); values and factor are copied.
+    # The coordinate list and the values stay in pinned host memory: sym_tensor_create reads the coordinates
+    # in place (packing kernel) and copies the values on a stream of its own while the keys are sorted; the
+    # factor's copy runs on a side stream meanwhile.
+    side = torch.cuda.Stream()
+
     def e2e_step():
-        v_d = val_h.to(dev, non_blocking=True)
-        b_d = B_h.to(dev, non_blocking=True)
-        Xe = sg.SymTensor(idx_h, v_d, T.n, ws=ws_create)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            b_d = B_h.to(dev, non_blocking=True)
+        Xe = sg.SymTensor(idx_h, val_h, T.n, ws=ws_create)
+        torch.cuda.current_stream().wait_stream(side)
         Xe.mttkrp(b_d, M=M)
         M_h.copy_(M, non_blocking=True)
         torch.cuda.synchronize()
@@ -563,23 +568,25 @@ def run_ours(args):
 
     e2e_step()
     # one more step with events between its phases (where the end-to-end time goes)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     t_host = time.perf_counter()
     ev[0].record()
-    v_d = val_h.to(dev, non_blocking=True)
-    b_d = B_h.to(dev, non_blocking=True)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        b_d = B_h.to(dev, non_blocking=True)
+    Xe = sg.SymTensor(idx_h, val_h, T.n, ws=ws_create)
     ev[1].record()
-    Xe = sg.SymTensor(idx_h, v_d, T.n, ws=ws_create)
-    ev[2].record()
+    torch.cuda.current_stream().wait_stream(side)
     Xe.mttkrp(b_d, M=M)
-    ev[3].record()
+    ev[2].record()
     M_h.copy_(M, non_blocking=True)
-    ev[4].record()
+    ev[3].record()
     torch.cuda.synchronize()
-    e2e_parts = {"h2d_values_factor_ms": ev[0].elapsed_time(ev[1]),
-                 "canonicalise_with_coordinate_read_ms": ev[1].elapsed_time(ev[2]),
-                 "mttkrp_ms": ev[2].elapsed_time(ev[3]), "d2h_ms": ev[3].elapsed_time(ev[4]),
-                 "host_wall_ms": (time.perf_counter() - t_host) * 1e3}
+    e2e_parts = {"create_from_host_ms": ev[0].elapsed_time(ev[1]),
+                 "mttkrp_ms": ev[1].elapsed_time(ev[2]), "d2h_ms": ev[2].elapsed_time(ev[3]),
+                 "host_wall_ms": (time.perf_counter() - t_host) * 1e3,
+                 "note": "create_from_host: coordinates read in place, values copied during the sort, the "
+                         "factor's copy overlapped on a side stream"}
     Xe.close()
     e2e_k = max(5, min(args.steps, 20))
     D.barrier()
@@ -617,7 +624,8 @@ def run_ours(args):
            "e2e": {"value": info["nnz"] * D.ws / e2e_s, "unit": "canonical nnz/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
                    "includes": "coordinate list read from pinned host memory by the packing kernel, H2D of "
-                               "values + factor, canonicalisation, MTTKRP, D2H of M",
+                               "values (during the sort) and factor (side stream), canonicalisation, MTTKRP, "
+                               "D2H of M",
                    "one_step_breakdown": e2e_parts, "steps": e2e_k,
                    "step_ms": {"p50": float(np.median(e2e_steps)), "min": float(min(e2e_steps)),
                                "max": float(max(e2e_steps))}},

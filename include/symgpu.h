@@ -378,9 +378,11 @@ sym_status sym_tensor_create_bytes(int order, int64_t n, int64_t nnz, size_t* ar
  * position order per tuple.  It is read once, by the packing kernel, so a
  * host coordinate list crosses the host link inside that kernel instead of in
  * a separate copy; pageable host memory is refused with SYM_E_INVALID].
- * val [device]: nnz floats (read out of order after the sort).  Order 2..5,
- * 1 <= n < 2^31, order * ceil(log2 n) <= 128.  Synchronises `stream` (it reads
- * back counts).  On error no tensor is created. */
+ * val [device, or page-locked host memory]: nnz floats, read out of order after
+ * the sort; host values are copied into the workspace on a stream of the call's
+ * own while the keys are packed and sorted, so the copy overlaps the sort.
+ * Order 2..5, 1 <= n < 2^31, order * ceil(log2 n) <= 128.  Synchronises
+ * `stream` (it reads back counts).  On error no tensor is created. */
 sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const int32_t* idx, int64_t ld_idx,
                              const float* val, sym_dup_policy dup, void* arena, size_t arena_bytes,
                              void* ws, size_t ws_bytes, sym_stream_t stream, sym_tensor* out);

@@ -445,8 +445,12 @@ class SymTensor:
                  ws: torch.Tensor | None = None):
         if idx.dim() != 2 or idx.dtype != torch.int32 or not (idx.is_cuda or idx.is_pinned()):
             raise TypeError("idx must be a (order, nnz) int32 CUDA tensor or pinned host tensor")
-        if val.dtype != torch.float32 or not val.is_cuda:
-            raise TypeError("val must be a float32 CUDA tensor")
+        if val.dtype != torch.float32 or not (val.is_cuda or val.is_pinned()):
+            raise TypeError("val must be a float32 CUDA tensor or pinned host tensor")
+        if not val.is_cuda and not val.is_contiguous():
+            raise TypeError("a pinned host val must be contiguous")
+        dev = val.device if val.is_cuda else (idx.device if idx.is_cuda else
+                                              torch.device("cuda", torch.cuda.current_device()))
         order, nnz = idx.shape
         if idx.is_cuda:
             idx = idx.contiguous()
@@ -454,16 +458,17 @@ class SymTensor:
             raise TypeError("a pinned host idx must be contiguous")
         ab, wb = C.c_size_t(0), C.c_size_t(0)
         check(lib().sym_tensor_create_bytes(order, n, nnz, C.byref(ab), C.byref(wb)), "sym_tensor_create_bytes")
-        self.arena = _scratch(ab.value, val.device)
+        self.arena = _scratch(ab.value, dev)
         if ws is None or ws.numel() < wb.value:
-            ws = _scratch(wb.value, val.device)
+            ws = _scratch(wb.value, dev)
         h = C.c_void_p()
-        check(lib().sym_tensor_create(order, n, nnz, _ptr(idx), max(nnz, 1), _ptr(val.contiguous()), dup,
-                                      _ptr(self.arena), self.arena.numel(), _ptr(ws), ws.numel(), _stream(stream),
-                                      C.byref(h)), "sym_tensor_create")
+        check(lib().sym_tensor_create(order, n, nnz, _ptr(idx), max(nnz, 1),
+                                      _ptr(val.contiguous() if val.is_cuda else val), dup, _ptr(self.arena),
+                                      self.arena.numel(), _ptr(ws), ws.numel(), _stream(stream), C.byref(h)),
+              "sym_tensor_create")
         self.handle = h
         self.order, self.n = order, n
-        self.device = val.device
+        self.device = dev
         self._info = None
 
     def save_image(self, host: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -760,8 +765,12 @@ class PTensor:
     def __init__(self, idx: torch.Tensor, val: torch.Tensor, parts, dims, dup: int = DUP_ERROR, stream=None):
         if idx.dim() != 2 or idx.dtype != torch.int32 or not (idx.is_cuda or idx.is_pinned()):
             raise TypeError("idx must be a (order, nnz) int32 CUDA tensor or pinned host tensor")
-        if val.dtype != torch.float32 or not val.is_cuda:
-            raise TypeError("val must be a float32 CUDA tensor")
+        if val.dtype != torch.float32 or not (val.is_cuda or val.is_pinned()):
+            raise TypeError("val must be a float32 CUDA tensor or pinned host tensor")
+        if not val.is_cuda and not val.is_contiguous():
+            raise TypeError("a pinned host val must be contiguous")
+        dev = val.device if val.is_cuda else (idx.device if idx.is_cuda else
+                                              torch.device("cuda", torch.cuda.current_device()))
         order, nnz = idx.shape
         if idx.is_cuda:
             idx = idx.contiguous()

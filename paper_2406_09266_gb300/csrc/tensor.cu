@@ -67,31 +67,51 @@ __device__ __forceinline__ int distinct_perms(const int32_t* c) {
     return fact[N] / den;
 }
 
+// Each thread packs PACK_EPT entries, CT apart, with all their coordinate loads
+// issued before any is used: when the coordinate list is read in place from
+// host memory over the host link, the extra loads in flight hide its latency.
+constexpr int PACK_EPT = 4;
+
 template <int N, int KW>
-__global__ void k_pack(const int32_t* __restrict__ idx, int64_t ld, const float* __restrict__ val, int64_t nnz,
-                       int64_t n, int bits, uint64_t* __restrict__ klo, uint64_t* __restrict__ khi,
-                       uint32_t* __restrict__ pay, DevCounters* cnt) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool bad = false;
-    if (e < nnz) {
-        int32_t c[N];
+__global__ void __launch_bounds__(CT) k_pack(const int32_t* __restrict__ idx, int64_t ld, int64_t nnz, int64_t n,
+                                             int bits, uint64_t* __restrict__ klo, uint64_t* __restrict__ khi,
+                                             uint32_t* __restrict__ pay, DevCounters* cnt) {
+    const int64_t e0 = (int64_t)blockIdx.x * (CT * PACK_EPT) + threadIdx.x;
+    int32_t c[PACK_EPT][N];
+#pragma unroll
+    for (int u = 0; u < PACK_EPT; ++u) {
+        const int64_t e = e0 + (int64_t)u * CT;
+#pragma unroll
+        for (int q = 0; q < N; ++q) c[u][q] = e < nnz ? idx[(int64_t)q * ld + e] : 0;
+    }
+    int bad = 0;
+#pragma unroll
+    for (int u = 0; u < PACK_EPT; ++u) {
+        const int64_t e = e0 + (int64_t)u * CT;
+        if (e >= nnz) continue;
+        bool out = false;
 #pragma unroll
         for (int q = 0; q < N; ++q) {
-            c[q] = idx[(int64_t)q * ld + e];
-            if (c[q] < 0 || c[q] >= n) {
-                bad = true;
-                c[q] = 0;
+            if (c[u][q] < 0 || c[u][q] >= n) {
+                out = true;
+                c[u][q] = 0;
             }
         }
-        sort_small<N>(c);
-        KeyWords k = pack_key<N, KW>(c, bits);
+        bad += out ? 1 : 0;
+        sort_small<N>(c[u]);
+        KeyWords k = pack_key<N, KW>(c[u], bits);
         klo[e] = k.lo;
         if (KW == 2) khi[e] = k.hi;
         pay[e] = (uint32_t)e;
     }
-    unsigned m = __ballot_sync(0xffffffffu, bad);
-    if (m && (threadIdx.x & 31) == 0) atomicAdd(&cnt->range_bad, (unsigned long long)__popc(m));
-    (void)val;
+    // entries with an out-of-range coordinate (each counted once)
+    unsigned m = __ballot_sync(0xffffffffu, bad != 0);
+    if (m) {
+        int tot = bad;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&cnt->range_bad, (unsigned long long)tot);
+    }
 }
 
 // Marks kept entries (first of each equal-key run), classifies them and takes
@@ -358,7 +378,7 @@ struct CreatePlan {
 template <typename C>
 void layout_ws(C& c, int64_t nnz, int kw, uint64_t** lo0, uint64_t** hi0, uint32_t** p0, uint64_t** lo1,
                uint64_t** hi1, uint32_t** p1, uint32_t** fs, uint32_t** fd, uint32_t** ps, uint32_t** pd,
-               DevCounters** cnt, void** radix, void** scan) {
+               DevCounters** cnt, void** radix, void** scan, float** vcopy) {
     size_t m = nnz > 0 ? (size_t)nnz : 1;
     *lo0 = c.template take<uint64_t>(m);
     *hi0 = kw == 2 ? c.template take<uint64_t>(m) : nullptr;
@@ -373,6 +393,7 @@ void layout_ws(C& c, int64_t nnz, int kw, uint64_t** lo0, uint64_t** hi0, uint32
     *cnt = c.template take<DevCounters>(1);
     *radix = c.template take<char>(radix_ws_bytes((int64_t)m, kw));
     *scan = c.template take<char>(scan_ws_bytes((int64_t)m));
+    *vcopy = c.template take<float>(m);  // device copy of values given in host memory
 }
 
 struct NullCarver {
@@ -392,23 +413,49 @@ void layout_arena(C& c, int64_t nnz, int kw, uint64_t** lo, uint64_t** hi, float
     *val = c.template take<float>(m);
 }
 
+// Copy of host values issued on a side stream once the keys are packed.
+struct SideCopy {
+    cudaStream_t side = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
+    const float* host = nullptr;
+    float* dev = nullptr;
+    size_t bytes = 0;
+    sym_status issue(cudaStream_t s) {  // after the packing kernel on s
+        if (!side) return SYM_OK;
+        SYM_CUDA(cudaEventRecord(start, s));
+        SYM_CUDA(cudaStreamWaitEvent(side, start, 0));
+        SYM_CUDA(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, side));
+        SYM_CUDA(cudaEventRecord(done, side));
+        return SYM_OK;
+    }
+    ~SideCopy() {
+        if (side) cudaStreamSynchronize(side);  // on every path the copy into the workspace has landed
+        if (start) cudaEventDestroy(start);
+        if (done) cudaEventDestroy(done);
+        if (side) cudaStreamDestroy(side);
+    }
+};
+
 template <int N>
 sym_status launch_create_kernels(int kw, const int32_t* idx, int64_t ld, const float* val, int64_t nnz, int64_t n,
                                  int bits, int policy, uint64_t* lo0, uint64_t* hi0, uint32_t* p0, uint64_t* lo1,
                                  uint64_t* hi1, uint32_t* p1, uint32_t* fs, uint32_t* fd, uint32_t* ps,
                                  uint32_t* pd, DevCounters* cnt, void* radix, void* scan, uint64_t* out_lo,
-                                 uint64_t* out_hi, float* out_val, cudaStream_t s) {
+                                 uint64_t* out_hi, float* out_val, SideCopy& vals, cudaStream_t s) {
     unsigned g = (unsigned)((nnz + CT - 1) / CT);
+    const unsigned gp = (unsigned)((nnz + CT * PACK_EPT - 1) / (CT * PACK_EPT));
     if (kw == 1)
-        k_pack<N, 1><<<g, CT, 0, s>>>(idx, ld, val, nnz, n, bits, lo0, hi0, p0, cnt);
+        k_pack<N, 1><<<gp, CT, 0, s>>>(idx, ld, nnz, n, bits, lo0, hi0, p0, cnt);
     else
-        k_pack<N, 2><<<g, CT, 0, s>>>(idx, ld, val, nnz, n, bits, lo0, hi0, p0, cnt);
+        k_pack<N, 2><<<gp, CT, 0, s>>>(idx, ld, nnz, n, bits, lo0, hi0, p0, cnt);
     SYM_CHECK_LAUNCH();
+    SYM_TRY(vals.issue(s));
     uint64_t *slo, *shi;
     uint32_t* sp;
     sym_status st = radix_sort_pairs(kw, lo0, hi0, p0, lo1, hi1, p1, nnz, N * bits, radix, s, &slo, &shi, &sp);
     if (st != SYM_OK) return st;
     const unsigned gm = (unsigned)std::min<int64_t>((int64_t)g, (int64_t)sm_count() * 8);
+    if (vals.done) SYM_CUDA(cudaStreamWaitEvent(s, vals.done, 0));  // values copied during the sort
     if (kw == 1)
         k_mark<N, 1><<<gm, CT, 0, s>>>(slo, shi, sp, val, nnz, bits, policy, fs, fd, cnt);
     else
@@ -446,7 +493,8 @@ extern "C" sym_status sym_tensor_create_bytes(int order, int64_t n, int64_t nnz,
     uint32_t *p0, *p1, *fs, *fd, *ps, *pd;
     DevCounters* c;
     void *r, *sc;
-    layout_ws(w, nnz, kw, &l0, &h0, &p0, &l1, &h1, &p1, &fs, &fd, &ps, &pd, &c, &r, &sc);
+    float* vc;
+    layout_ws(w, nnz, kw, &l0, &h0, &p0, &l1, &h1, &p1, &fs, &fd, &ps, &pd, &c, &r, &sc, &vc);
     if (arena_bytes) *arena_bytes = a.s.used;
     if (ws_bytes) *ws_bytes = w.s.used;
     return SYM_OK;
@@ -462,15 +510,20 @@ extern "C" sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const
     if (st != SYM_OK) return st;
     if (nnz > 0 && (!idx || !val || ld_idx < nnz)) return SYM_E_INVALID;
     if (dup != SYM_DUP_ERROR && dup != SYM_DUP_KEEP_EQUAL) return SYM_E_INVALID;
+    bool val_host = false;
     if (nnz > 0) {
         // idx may be page-locked host memory (read in place by the packing kernel through its device
-        // address); val must be device memory (gathered in sorted order later)
+        // address); val may be device memory or page-locked host memory (copied during the sort)
         cudaPointerAttributes ai{}, av{};
         if (cudaPointerGetAttributes(&ai, idx) != cudaSuccess || cudaPointerGetAttributes(&av, val) != cudaSuccess) {
             cudaGetLastError();
             return SYM_E_INVALID;
         }
-        if (av.type != cudaMemoryTypeDevice && av.type != cudaMemoryTypeManaged) return SYM_E_INVALID;
+        if (av.type == cudaMemoryTypeHost) {
+            val_host = true;  // page-locked: copied into the workspace on a side stream during the sort
+        } else if (av.type != cudaMemoryTypeDevice && av.type != cudaMemoryTypeManaged) {
+            return SYM_E_INVALID;
+        }
         if (ai.type == cudaMemoryTypeHost) {
             if (!ai.devicePointer) return SYM_E_INVALID;
             idx = static_cast<const int32_t*>(ai.devicePointer);
@@ -492,14 +545,29 @@ extern "C" sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const
     uint32_t *p0, *p1, *fs, *fd, *ps, *pd;
     DevCounters* cnt;
     void *radix, *scan;
-    layout_ws(W, nnz, kw, &l0, &h0, &p0, &l1, &h1, &p1, &fs, &fd, &ps, &pd, &cnt, &radix, &scan);
+    float* vcopy;
+    layout_ws(W, nnz, kw, &l0, &h0, &p0, &l1, &h1, &p1, &fs, &fd, &ps, &pd, &cnt, &radix, &scan, &vcopy);
     SYM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(DevCounters), s));
+    // Values in page-locked host memory cross the host link on a side stream while the keys are sorted
+    // (after the packing kernel, which reads the coordinates over the same link); the first kernel that
+    // reads them waits for the copy.  The side stream and events live for this call only (it synchronises
+    // `s`, which waits for them, before returning).
+    SideCopy sc;
+    if (val_host) {
+        SYM_CUDA(cudaStreamCreateWithFlags(&sc.side, cudaStreamNonBlocking));
+        SYM_CUDA(cudaEventCreateWithFlags(&sc.start, cudaEventDisableTiming));
+        SYM_CUDA(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming));
+        sc.host = val;
+        sc.dev = vcopy;
+        sc.bytes = (size_t)nnz * sizeof(float);
+        val = vcopy;
+    }
     if (nnz > 0) {
         switch (order) {
-            case 2: st = launch_create_kernels<2>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, s); break;
-            case 3: st = launch_create_kernels<3>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, s); break;
-            case 4: st = launch_create_kernels<4>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, s); break;
-            default: st = launch_create_kernels<5>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, s); break;
+            case 2: st = launch_create_kernels<2>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, sc, s); break;
+            case 3: st = launch_create_kernels<3>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, sc, s); break;
+            case 4: st = launch_create_kernels<4>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, sc, s); break;
+            default: st = launch_create_kernels<5>(kw, idx, ld_idx, val, nnz, n, bits, dup, l0, h0, p0, l1, h1, p1, fs, fd, ps, pd, cnt, radix, scan, out_lo, out_hi, out_val, sc, s); break;
         }
         if (st != SYM_OK) return st;
     }

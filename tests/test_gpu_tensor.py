@@ -38,21 +38,24 @@ def test_canonical_bitexact(order, n, nnz, recipe):
 
 @pytest.mark.parametrize("order,n,nnz,recipe", [CASES[2], CASES[5]])
 def test_canonical_from_pinned_host_coordinates(order, n, nnz, recipe):
-    """The coordinate list may stay in page-locked host memory (read in place by the packing kernel): the
-    canonical form and the counts equal the oracle's bit for bit; pageable host memory is refused."""
+    """The coordinate list (and the values) may stay in page-locked host memory (the coordinates read in place
+    by the packing kernel, the values copied during the sort): the canonical form and the counts equal the
+    oracle's bit for bit; pageable host memory is refused."""
     sg = need_gpu()
     torch = pytest.importorskip("torch")
     T = synth.tensor3_zipf(n, nnz, 3) if recipe == "zipf" else synth.tensor_uniform(order, n, nnz, 3)
     idx_h = torch.from_numpy(np.ascontiguousarray(T.idx)).pin_memory()
-    X = sg.SymTensor(idx_h, dev(T.val), n)
+    val_h = torch.from_numpy(np.ascontiguousarray(T.val)).pin_memory()
     cidx, cval = oracle.canonicalize(order, n, T.idx, T.val)
     want_idx, want_val, n_strict = canonical_split(order, cidx, cval)
-    gi, gv = X.export()
-    assert np.array_equal(host(gi), want_idx)
-    assert np.array_equal(host(gv).view(np.uint32), want_val.view(np.uint32))
-    info = X.info()
-    assert info["nnz"] == cval.shape[0] and info["nnz_strict"] == n_strict
-    assert info["expanded_nnz"] == oracle.counts(order, cidx, cval)["expanded"]
+    # host coordinates with device values, then host coordinates and host values (copied during the sort)
+    for X in (sg.SymTensor(idx_h, dev(T.val), n), sg.SymTensor(idx_h, val_h, n)):
+        gi, gv = X.export()
+        assert np.array_equal(host(gi), want_idx)
+        assert np.array_equal(host(gv).view(np.uint32), want_val.view(np.uint32))
+        info = X.info()
+        assert info["nnz"] == cval.shape[0] and info["nnz_strict"] == n_strict
+        assert info["expanded_nnz"] == oracle.counts(order, cidx, cval)["expanded"]
     # pageable host memory cannot be read by the device: refused before any launch
     C = sg.C
     idx_p = torch.from_numpy(np.ascontiguousarray(T.idx))
