@@ -130,10 +130,16 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint64_t* __res
     for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) h[d] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    for (int k = threadIdx.x; k < RS_TILE; k += RS_THREADS) {
-        int64_t i = base + k;
-        if (i < n) atomicAdd(&h[digit_of<KW>(klo, khi, i, shift)], 1u);
+    // every key of the thread is requested before the first count is taken
+    unsigned dg[RS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
+        dg[r] = i < n ? digit_of<KW>(klo, khi, i, shift) : 0xffffu;
     }
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r)
+        if (dg[r] != 0xffffu) atomicAdd(&h[dg[r]], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) counts[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
@@ -216,6 +222,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
     __shared__ uint64_t s_lo[RS_TILE];
     __shared__ uint32_t s_pl[RS_TILE];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // this thread's digit offset, requested first so its latency overlaps the tile's loads
+    const uint32_t goff = count_offset(offsets, tile_sums, (int64_t)threadIdx.x * ntiles + blockIdx.x);
     for (int t = threadIdx.x; t < RS_WARPS * RADIX; t += RS_THREADS) (&cnt[0][0])[t] = 0;
     __syncthreads();
     const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
@@ -229,11 +237,28 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
         if (i < n) {
             lo[r] = klo[i];
             pl[r] = pay[i];
-            dg[r] = (unsigned)((lo[r] >> shift) & (RADIX - 1));
-            atomicAdd(&cnt[w][dg[r]], 1u);
-        } else {
-            dg[r] = 0xffffu;  // sentinel group, never placed
         }
+    }
+    // Per-warp multisplit without atomics: in each round the lanes holding one
+    // digit find each other (match), the first of them advances the warp's count
+    // of that digit and hands the old count to the others; an item's offset in
+    // its warp's run of the digit is that count plus its rank among the lanes
+    // (input order, so the sort stays stable).
+    const unsigned ltmask = lanemask_lt();
+    uint32_t off[RS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
+        dg[r] = i < n ? (unsigned)((lo[r] >> shift) & (RADIX - 1)) : 0xffffu;  // 0xffff: no item, never placed
+        const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == leader && dg[r] != 0xffffu) {
+            base = cnt[w][dg[r]];
+            cnt[w][dg[r]] = base + (uint32_t)__popc(peers);
+        }
+        off[r] = __shfl_sync(0xffffffffu, base, leader) + (uint32_t)__popc(peers & ltmask);
+        __syncwarp();  // the count update is seen by the next round's leaders
     }
     __syncthreads();
     // Thread d: the digit's count in the tile, its start in the tile (exclusive
@@ -248,7 +273,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
         __syncthreads();
         uint32_t start = incl - tot;
         for (int k = 0; k < w; ++k) start += wsum[k];
-        gbase[d] = count_offset(offsets, tile_sums, (int64_t)d * ntiles + blockIdx.x) - start;
+        gbase[d] = goff - start;
         uint32_t run = start;
 #pragma unroll
         for (int ww = 0; ww < RS_WARPS; ++ww) {
@@ -258,19 +283,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
         }
     }
     __syncthreads();
-    const unsigned ltmask = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
-        const unsigned rank = __popc(peers & ltmask);
         if (dg[r] != 0xffffu) {
-            const uint32_t p = cnt[w][dg[r]] + rank;
+            const uint32_t p = cnt[w][dg[r]] + off[r];
             s_lo[p] = lo[r];
             s_pl[p] = pl[r];
         }
-        __syncwarp();
-        if (dg[r] != 0xffffu && rank == 0) cnt[w][dg[r]] += __popc(peers);
-        __syncwarp();
     }
     __syncthreads();
     const int m = n - tbase < RS_TILE ? (int)(n - tbase) : RS_TILE;
