@@ -208,7 +208,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
 // k_radix_scatter place the tile in digit order in shared memory first, then
 // consecutive threads write consecutive output positions of each digit's run
 // (coalesced stores instead of one scattered 8-byte store per item).
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint64_t* __restrict__ klo,
+#ifndef SYM_RS_MIN_BLOCKS
+#define SYM_RS_MIN_BLOCKS 1  // CTAs per SM the staged scatter is compiled for (register budget)
+#endif
+__global__ void __launch_bounds__(RS_THREADS, SYM_RS_MIN_BLOCKS) k_radix_scatter_staged(const uint64_t* __restrict__ klo,
                                                                      const uint32_t* __restrict__ pay,
                                                                      uint64_t* __restrict__ olo,
                                                                      uint32_t* __restrict__ opay, int64_t n, int shift,
@@ -230,10 +233,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
     const int64_t wbase = tbase + (int64_t)w * (32 * RS_ROUNDS);
     uint64_t lo[RS_ROUNDS];
     uint32_t pl[RS_ROUNDS];
-    unsigned dg[RS_ROUNDS];
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
         int64_t i = wbase + r * 32 + lane;
+        lo[r] = 0;
+        pl[r] = 0;
         if (i < n) {
             lo[r] = klo[i];
             pl[r] = pay[i];
@@ -244,20 +248,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
     // of that digit and hands the old count to the others; an item's offset in
     // its warp's run of the digit is that count plus its rank among the lanes
     // (input order, so the sort stays stable).
+    // (offsets are below 256, the warp's item count: four to a register)
     const unsigned ltmask = lanemask_lt();
-    uint32_t off[RS_ROUNDS];
+    uint32_t off[RS_ROUNDS / 4] = {};
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
         const int64_t i = wbase + r * 32 + lane;
-        dg[r] = i < n ? (unsigned)((lo[r] >> shift) & (RADIX - 1)) : 0xffffu;  // 0xffff: no item, never placed
-        const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+        const unsigned dg = i < n ? (unsigned)((lo[r] >> shift) & (RADIX - 1)) : 0xffffu;  // 0xffff: no item
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
-        if (lane == leader && dg[r] != 0xffffu) {
-            base = cnt[w][dg[r]];
-            cnt[w][dg[r]] = base + (uint32_t)__popc(peers);
+        if (lane == leader && dg != 0xffffu) {
+            base = cnt[w][dg];
+            cnt[w][dg] = base + (uint32_t)__popc(peers);
         }
-        off[r] = __shfl_sync(0xffffffffu, base, leader) + (uint32_t)__popc(peers & ltmask);
+        const uint32_t o = __shfl_sync(0xffffffffu, base, leader) + (uint32_t)__popc(peers & ltmask);
+        off[r / 4] |= (o & 0xffu) << (8 * (r % 4));
         __syncwarp();  // the count update is seen by the next round's leaders
     }
     __syncthreads();
@@ -285,8 +291,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter_staged(const uint6
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        if (dg[r] != 0xffffu) {
-            const uint32_t p = cnt[w][dg[r]] + off[r];
+        if (wbase + r * 32 + lane < n) {
+            const unsigned dg = (unsigned)((lo[r] >> shift) & (RADIX - 1));
+            const uint32_t p = cnt[w][dg] + ((off[r / 4] >> (8 * (r % 4))) & 0xffu);
             s_lo[p] = lo[r];
             s_pl[p] = pl[r];
         }
