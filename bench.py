@@ -960,7 +960,7 @@ def batch_row(torch, sg, dev, flush, stream, hbm_peak, count=4096, per_row=16, s
     return out
 
 
-def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=4, affinity_s=1.0):
+def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=4, affinity_s=1.0, pool_frac=0.6):
     """Poisson arrivals of MTTKRP requests; continuous batching vs one launch per request (FP32).
 
     Run 1: the tensors are resident (created by the caller) under the 120 GB budget; small requests are
@@ -1059,7 +1059,7 @@ def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=
     # run 2: registered images, device pool at 60 % of the images' total: loads and LRU evictions
     images = [X.save_image() for X in pool]
     image_bytes = sum(int(sg.lib().sym_tensor_load_bytes(sg.C.c_void_p(im.data_ptr()))) for im in images)
-    pool_bytes = int(image_bytes * 0.6)
+    pool_bytes = int(image_bytes * pool_frac)
     S = sg.Server(max_slots=8, max_rank=64, hbm_budget_bytes=pool_bytes + (16 << 30), small_nnz=1_000_000,
                   coalesce_small=True, pool_bytes=pool_bytes, affinity_wait_s=affinity_s)
     ids = [S.register(im) for im in images]
