@@ -17,10 +17,12 @@
 // Registered tensors: a caller may hand the server the host image of a tensor
 // (sym_tensor_save) instead of a resident tensor.  The server keeps such
 // tensors in a device pool carved from its arena: a request for a tensor that
-// is not resident loads it (one host-to-device copy of its canonical arrays,
-// on the request's stream, before the kernels); when the pool is full, the
+// is not resident loads it (one host-to-device copy of its canonical arrays);
+// when the pool is full, the
 // least recently used resident tensors that no request in flight uses are
-// dropped (the host image is the master copy, so nothing is copied back).  The
+// dropped (the host image is the master copy, so nothing is copied back).
+// Loads run on a stream of their own (at most two at a time) and take no
+// slot: a request is admitted once its tensor's copy has landed.  The
 // pool and the factors / outputs of the requests in flight together stay
 // within the HBM budget.  Admission prefers requests whose tensor is resident:
 // a request that would need a load waits (up to cfg.affinity_wait_ns) while
@@ -30,7 +32,9 @@
 // cached from that request instead of recomputing it.
 //
 // Nothing here waits on the device without a bound: the scheduler only queries
-// events, and destroy drains with a time limit.
+// events, and destroy drains with a time limit (releasing the server then
+// waits for the load stream's last copy, a host-to-device copy that ends by
+// itself).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -51,6 +55,7 @@ namespace {
 
 constexpr int kMaxGroup = 16;  // requests in one grouped launch
 constexpr int kGramSlots = 512;  // cached Gram matrices (B^T B) of recently used factors
+constexpr int kMaxLoads = 2;     // registered-tensor loads in flight at once
 
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -67,6 +72,7 @@ struct Entry {
     sym_tensor_s* X = nullptr;  // handle into the pool while resident
     cudaEvent_t ready = nullptr;  // recorded after the load
     int inuse = 0;         // requests in flight on it
+    bool loading = false;  // its copy into the pool is in flight (on the load stream)
     uint64_t last_use = 0;
 };
 
@@ -152,6 +158,8 @@ struct sym_server_s {
     size_t resident_bytes = 0;
     GramSlot grams[kGramSlots];  // touched by the scheduler thread only
     uint64_t gram_tick = 0;
+    cudaStream_t load_stream = nullptr;  // copies of registered tensors into the pool
+    int loads_in_flight = 0;
 
     void run();
     void finish(Slot& s, sym_status st);
@@ -160,6 +168,7 @@ struct sym_server_s {
     bool pool_alloc(size_t bytes, size_t* off);
     void pool_free(size_t off, size_t bytes);
     bool make_resident(Entry& E, cudaStream_t s, sym_status* err);
+    void fail_queued(std::deque<Pending>::iterator& it, sym_status st);
 };
 
 bool sym_server_s::pool_alloc(size_t bytes, size_t* off) {
@@ -200,7 +209,7 @@ bool sym_server_s::make_resident(Entry& E, cudaStream_t s, sym_status* err) {
     while (!pool_alloc(E.bytes, &off)) {
         Entry* victim = nullptr;
         for (auto& c : entries)
-            if (c.resident && c.inuse == 0 && (!victim || c.last_use < victim->last_use)) victim = &c;
+            if (c.resident && c.inuse == 0 && !c.loading && (!victim || c.last_use < victim->last_use)) victim = &c;
         if (!victim) return false;
         pool_free(victim->off, victim->bytes);
         sym_tensor_destroy(victim->X);
@@ -227,8 +236,29 @@ bool sym_server_s::make_resident(Entry& E, cudaStream_t s, sym_status* err) {
     return true;
 }
 
+// Called with mu held: a queued request that can never run (its tensor failed
+// to load) completes with that status; `it` moves to the next request.
+void sym_server_s::fail_queued(std::deque<Pending>::iterator& it, sym_status st) {
+    sym_result res{};
+    res.status = st;
+    res.user_tag = it->r.user_tag;
+    res.t_submit_ns = it->t_submit;
+    res.t_admit_ns = res.t_done_ns = now_ns();
+    done[it->ticket] = res;
+    live.erase(it->ticket);
+    stats.admitted += 1;
+    stats.completed += 1;
+    it = queue.erase(it);
+    cv_done.notify_all();
+}
+
 // Streams, events and pinned buffers of the slots and of the registered tensors.
 void sym_server_s::release() {
+    if (load_stream) {
+        cudaStreamSynchronize(load_stream);  // no copy into the caller's arena is left in flight
+        cudaStreamDestroy(load_stream);
+        load_stream = nullptr;
+    }
     for (auto& s : slots) {
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.done) cudaEventDestroy(s.done);
@@ -368,6 +398,14 @@ void sym_server_s::run() {
             // requests that have waited longer than cfg.affinity_wait_ns; phase 1, with the slots left, the
             // rest (each loading its tensor, after which the queued requests for that tensor are resident too).
             const uint64_t affinity_ns = (uint64_t)std::max<int64_t>(0, cfg.affinity_wait_ns);
+            if (loads_in_flight > 0)  // loads that have landed make their tensors admissible
+                for (auto& E : entries)
+                    if (E.loading && cudaEventQuery(E.ready) != cudaErrorNotReady) {
+                        cudaGetLastError();
+                        E.loading = false;
+                        --loads_in_flight;
+                        progressed = true;
+                    }
             bool slots_left = true;
             for (int phase = 0; phase < 2 && slots_left; ++phase) {
                 for (auto it = queue.begin(); it != queue.end();) {
@@ -381,6 +419,30 @@ void sym_server_s::run() {
                         if (it == queue.begin() && t - it->t_submit > pass_limit_ns) break;
                         ++it;
                         continue;
+                    }
+                    if (it->reg >= 0) {
+                        // A tensor that is not resident is loaded on the load stream without taking a slot; its
+                        // requests are admitted once the copy has landed, so slots keep serving resident work.
+                        Entry& E = entries[(size_t)it->reg];
+                        if (E.loading) {
+                            ++it;
+                            continue;
+                        }
+                        if (!E.resident) {
+                            if (loads_in_flight < kMaxLoads) {
+                                sym_status err = SYM_OK;
+                                if (make_resident(E, load_stream, &err)) {  // false: no room in the pool yet
+                                    if (err != SYM_OK) {
+                                        fail_queued(it, err);
+                                        continue;
+                                    }
+                                    E.loading = true;
+                                    ++loads_in_flight;
+                                }
+                            }
+                            ++it;
+                            continue;
+                        }
                     }
                     const bool join =
                         cfg.coalesce_small && it->small && group && (int)group->reqs.size() < kMaxGroup;
@@ -403,16 +465,8 @@ void sym_server_s::run() {
                         break;
                     }
                     if (!pick->busy) pick->launch_status = SYM_OK;
-                    if (it->reg >= 0) {
+                    if (it->reg >= 0) {  // resident and loaded (checked above)
                         Entry& E = entries[(size_t)it->reg];
-                        if (!E.resident) {
-                            sym_status err = SYM_OK;
-                            if (!make_resident(E, pick->stream, &err)) {
-                                ++it;  // no room in the pool yet: later requests may pass
-                                continue;
-                            }
-                            if (err != SYM_OK) pick->launch_status = err;
-                        }
                         E.inuse += 1;
                         E.last_use = ++tick;
                     }
@@ -434,8 +488,27 @@ void sym_server_s::run() {
                     it = queue.erase(it);
                 }
             }
+            // Loads need no slot: requests that have waited out the affinity wait get their tensor's load
+            // started even while every slot is busy.
+            for (auto it = queue.begin(); it != queue.end() && loads_in_flight < kMaxLoads;) {
+                if (it->reg >= 0 && t - it->t_submit >= affinity_ns) {
+                    Entry& E = entries[(size_t)it->reg];
+                    if (!E.resident && !E.loading) {
+                        sym_status err = SYM_OK;
+                        if (make_resident(E, load_stream, &err)) {
+                            if (err != SYM_OK) {
+                                fail_queued(it, err);
+                                continue;
+                            }
+                            E.loading = true;
+                            ++loads_in_flight;
+                        }
+                    }
+                }
+                ++it;
+            }
             if (to_launch.empty() && !progressed) {
-                if (inflight == 0)
+                if (inflight == 0 && loads_in_flight == 0)
                     cv_sched.wait_for(lk, std::chrono::milliseconds(20), [&] { return stop || !queue.empty(); });
             }
         }
@@ -492,6 +565,7 @@ extern "C" sym_status sym_server_create(const sym_server_cfg* cfg, void* arena, 
         s.ws = base + align_up(sizeof(double) * kMaxGroup, 256);
         s.ws_bytes = per - align_up(sizeof(double) * kMaxGroup, 256);
     }
+    if (st == SYM_OK) st = cuda_status(cudaStreamCreateWithPriority(&S->load_stream, cudaStreamNonBlocking, lo));
     char* gram_base = static_cast<char*>(arena) + per * (size_t)cfg->max_slots;
     for (int g = 0; g < kGramSlots && st == SYM_OK; ++g) {
         S->grams[g].G = reinterpret_cast<double*>(gram_base + gram_bytes(cfg) * (size_t)g);
