@@ -552,6 +552,15 @@ sym_status sym_mttkrp_set_chunk(sym_tensor X, int entries_per_warp);
 sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
                                int64_t ldm, const char* cache_path, sym_stream_t stream, sym_mttkrp_cfg* best,
                                float* best_ms);
+/* The same with every timed run preceded by a rewrite of flush [device,
+ * flush_bytes, caller-owned scratch, overwritten; make it larger than L2], so
+ * the candidates are compared with cold caches, as a caller that runs other
+ * work between calls sees them (a small tensor that fits in L2 otherwise
+ * favours configurations that re-read it).  flush NULL with flush_bytes 0 is
+ * sym_mttkrp_autotune; cache entries of the two are kept apart. */
+sym_status sym_mttkrp_autotune_cold(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb, float* M,
+                                    int64_t ldm, void* flush, size_t flush_bytes, const char* cache_path,
+                                    sym_stream_t stream, sym_mttkrp_cfg* best, float* best_ms);
 
 /* One symmetric CP-ALS update of the shared factor (the decomposition the
  * symmetric MTTKRP serves, Sec. 5.2.6):

@@ -196,6 +196,8 @@ _SIGS = {
     "sym_mttkrp_get_config": ([C.c_void_p, C.c_void_p], C.c_int),
     "sym_mttkrp_autotune": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_char_p,
                              C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_mttkrp_autotune_cold": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64,
+                                  C.c_void_p, C.c_size_t, C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sym_cp_als_workspace_bytes": ([C.c_void_p, C.c_int], C.c_size_t),
     "sym_cp_als_step": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                          C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
@@ -550,15 +552,24 @@ class SymTensor:
         check(lib().sym_mttkrp_get_config(self.handle, C.byref(cfg)), "sym_mttkrp_get_config")
         return cfg.as_dict()
 
-    def autotune(self, B: torch.Tensor, M: torch.Tensor | None = None, cache_path: str | None = None, stream=None):
-        """Times kernel configurations for these operands; keeps the fastest. Returns (config dict, ms)."""
+    def autotune(self, B: torch.Tensor, M: torch.Tensor | None = None, cache_path: str | None = None, stream=None,
+                 flush: torch.Tensor | None = None):
+        """Times kernel configurations for these operands; keeps the fastest. Returns (config dict, ms).
+        flush: a device buffer larger than L2, rewritten before every timed run (cold-cache comparison)."""
         rank = B.shape[1]
         if M is None:
             M = torch.empty((self.n, rank), dtype=torch.float32, device=B.device)
         best, ms = MttkrpCfg(), C.c_float(0)
-        check(lib().sym_mttkrp_autotune(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(M), M.stride(0),
-                                        cache_path.encode() if cache_path else None, _stream(stream), C.byref(best),
-                                        C.byref(ms)), "sym_mttkrp_autotune")
+        path = cache_path.encode() if cache_path else None
+        if flush is None:
+            check(lib().sym_mttkrp_autotune(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(M),
+                                            M.stride(0), path, _stream(stream), C.byref(best), C.byref(ms)),
+                  "sym_mttkrp_autotune")
+        else:
+            check(lib().sym_mttkrp_autotune_cold(self.handle, _ptr(B), _dtype_code(B), rank, B.stride(0), _ptr(M),
+                                                 M.stride(0), _ptr(flush), flush.numel() * flush.element_size(),
+                                                 path, _stream(stream), C.byref(best), C.byref(ms)),
+                  "sym_mttkrp_autotune_cold")
         return best.as_dict(), ms.value
 
     def mttkrp_workspace(self, rank: int, bdt: int = F32, residual: bool = True) -> torch.Tensor:

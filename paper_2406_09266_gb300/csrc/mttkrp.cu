@@ -470,9 +470,17 @@ extern "C" sym_status sym_mttkrp_set_chunk(sym_tensor X, int entries_per_warp) {
 extern "C" sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb,
                                           float* M, int64_t ldm, const char* cache_path, sym_stream_t stream,
                                           sym_mttkrp_cfg* best, float* best_ms) {
+    return sym_mttkrp_autotune_cold(X, B, bdt, rank, ldb, M, ldm, nullptr, 0, cache_path, stream, best, best_ms);
+}
+
+extern "C" sym_status sym_mttkrp_autotune_cold(sym_tensor X, const void* B, sym_dtype bdt, int rank, int64_t ldb,
+                                               float* M, int64_t ldm, void* flush, size_t flush_bytes,
+                                               const char* cache_path, sym_stream_t stream, sym_mttkrp_cfg* best,
+                                               float* best_ms) {
     sym_status st = validate_mttkrp_args(X, B, bdt, rank, ldb, M, ldm);
     if (st != SYM_OK) return st;
-    const std::string key = tune_key(X, rank, bdt);
+    if ((flush == nullptr) != (flush_bytes == 0)) return SYM_E_INVALID;
+    const std::string key = tune_key(X, rank, bdt) + (flush ? "|cold" : "|warm");
     sym_mttkrp_cfg found;
     float found_ms = 0.f;
     if (tune_lookup(cache_path, key, &found, &found_ms)) {
@@ -525,6 +533,8 @@ extern "C" sym_status sym_mttkrp_autotune(sym_tensor X, const void* B, sym_dtype
         if (mttkrp_core_cfg(X, B, bf16, rank, ldb, M, ldm, c, s) != SYM_OK) return false;  // warm-up
         float tot = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
+            // cold: the caller's buffer (larger than L2) is rewritten before each timed run
+            if (flush && cudaMemsetAsync(flush, rep + 1, flush_bytes, s) != cudaSuccess) return false;
             cudaEventRecord(e0, s);
             if (mttkrp_core_cfg(X, B, bf16, rank, ldb, M, ldm, c, s) != SYM_OK) return false;
             cudaEventRecord(e1, s);

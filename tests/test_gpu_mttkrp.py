@@ -140,6 +140,31 @@ def test_mttkrp_autotune_and_cache(tmp_path):
     assert oracle.componentwise_error(host(X2.mttkrp(B)), ref, ra) <= TOL_F32
 
 
+def test_mttkrp_autotune_cold_caches(tmp_path):
+    """Cold-cache tuning (a caller buffer larger than L2 rewritten before every timed run): a valid choice, kept
+    apart from warm entries in the cache file, and the tuned kernel still matches the oracle."""
+    sg = need_gpu()
+    torch = pytest.importorskip("torch")
+    T = synth.tensor_uniform(4, 60, 20000, 19)
+    X = sg.SymTensor(dev(T.idx), dev(T.val), T.n)
+    B = dev(synth.factor_normal(T.n, 16, 19))
+    cache = str(tmp_path / "mt.txt")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cfg, ms = X.autotune(B, cache_path=cache, flush=flush)
+    assert ms > 0 and X.get_config() == cfg
+    X.autotune(B, cache_path=cache)                     # a warm entry of its own, not the cold one's
+    lines = open(cache).read().split("\n")
+    assert sum("|cold " in ln for ln in lines) == 1 and sum("|warm " in ln for ln in lines) == 1
+    X.set_config(**cfg)
+    cidx, cval = oracle.canonicalize(4, T.n, T.idx, T.val)
+    ref, ra = oracle.mttkrp_enum(4, T.n, cidx, cval, synth.factor_normal(T.n, 16, 19).astype(np.float64))
+    assert oracle.componentwise_error(host(X.mttkrp(B)), ref, ra) <= TOL_F32
+    M = torch.empty((T.n, 16), device="cuda")
+    rc = sg.lib().sym_mttkrp_autotune_cold(X.handle, sg.C.c_void_p(B.data_ptr()), 0, 16, 16,
+                                           sg.C.c_void_p(M.data_ptr()), 16, None, 64, None, None, None, None)
+    assert rc == -1   # a flush size without a flush buffer
+
+
 def test_mttkrp_zipf_hot_rows():
     sg = need_gpu()
     T = synth.tensor3_zipf(5000, 200_000, 8)
