@@ -665,7 +665,17 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak, ceil=None):
         for tag, Bt in (("f32", torch.from_numpy(B32).to(dev)),
                         ("bf16", torch.from_numpy(synth.bf16_rne(B32).view(np.int16)).to(dev).view(torch.bfloat16))):
             M = torch.empty((n, rank), dtype=torch.float32, device=dev)
-            cfg, _ = X.autotune(Bt, M=M, cache_path=tune_cache, flush=flush)
+            cfg, tune_ms = X.autotune(Bt, M=M, cache_path=tune_cache, flush=flush)
+            # the tuner's pick against the plain kernel (128 entries per warp), both timed as the row is
+            plain = dict(strict_kernel=0, entries_per_warp=128, leaf_index=0, l1_pref=1, stream_hint=1,
+                         root_combine=1, diag_smem_kb=cfg["diag_smem_kb"])
+            X.set_config(**plain)
+            t_plain = float(np.mean(timed_steps(torch, lambda: X.mttkrp(Bt, M=M), 5, flush, stream)))
+            X.set_config(**cfg)
+            t_tuned = float(np.mean(timed_steps(torch, lambda: X.mttkrp(Bt, M=M), 5, flush, stream)))
+            if t_plain < t_tuned:
+                X.set_config(**plain)
+                cfg = X.get_config()
             for _ in range(3):
                 X.mttkrp(Bt, M=M)
             sg.profile_reset()
@@ -675,7 +685,8 @@ def secondary_rows(torch, sg, dev, flush, stream, hbm_peak, ceil=None):
             prof = sg.profile_read()
             ms = float(np.mean(t))
             r[tag] = {"ms": ms, "canonical_nnz_per_s": info["nnz"] / (ms * 1e-3), "mttkrp_config": cfg,
-                      "per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()}}
+                      "per_kernel_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()},
+                      "selection": {"autotune_ms": tune_ms, "tuned_ms": t_tuned, "plain_128_ms": t_plain}}
             X.mttkrp(Bt, M=M)
             res[tag] = M.cpu().numpy()
         try:
