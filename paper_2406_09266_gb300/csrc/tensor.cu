@@ -514,10 +514,15 @@ extern "C" sym_status sym_tensor_create(int order, int64_t n, int64_t nnz, const
     if (nnz > 0) {
         // idx may be page-locked host memory (read in place by the packing kernel through its device
         // address); val may be device memory or page-locked host memory (copied during the sort)
+        // (a pointer the runtime cannot classify, e.g. some virtual-memory mappings, is taken as device memory)
         cudaPointerAttributes ai{}, av{};
-        if (cudaPointerGetAttributes(&ai, idx) != cudaSuccess || cudaPointerGetAttributes(&av, val) != cudaSuccess) {
+        if (cudaPointerGetAttributes(&ai, idx) != cudaSuccess) {
             cudaGetLastError();
-            return SYM_E_INVALID;
+            ai.type = cudaMemoryTypeDevice;
+        }
+        if (cudaPointerGetAttributes(&av, val) != cudaSuccess) {
+            cudaGetLastError();
+            av.type = cudaMemoryTypeDevice;
         }
         if (av.type == cudaMemoryTypeHost) {
             val_host = true;  // page-locked: copied into the workspace on a side stream during the sort
