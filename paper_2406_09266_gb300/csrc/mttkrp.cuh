@@ -1068,6 +1068,18 @@ __global__ void __launch_bounds__(512) k_mttkrp_entries(
 
 // ---------------------------------------------------------------- launch
 
+// A second stream for the diagonal stream's kernel, so it runs beside the
+// strict stream's kernel instead of after it (the two add into M with
+// atomics, so their order does not matter).  Set for the calling host thread
+// by the public MTTKRP entry points; null elsewhere (the serving runtime
+// overlaps whole requests instead).
+struct SideLaunch {
+    cudaStream_t stream;
+    cudaEvent_t fork, join;
+};
+extern thread_local const SideLaunch* t_side_launch;
+const SideLaunch* side_launch_for_device(int device);  // per host thread and device; null on failure
+
 // Smallest shared-memory carveout (percent of the SM's maximum) that holds
 // `smem` bytes of shared memory for as many CTAs of MT_THREADS threads as an
 // SM can run (plus the 1 KB the hardware reserves per CTA); the rest of the
@@ -1151,6 +1163,13 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
     const int fact[6] = {1, 1, 2, 6, 24, 120};
     const int sms = sm_count();
     const int threads = std::max(64, std::min(512, (int)cfg.threads_per_cta)) / 32 * 32;
+    const SideLaunch* side = (ns > 0 && nd > 0) ? t_side_launch : nullptr;
+    cudaStream_t ds = s;  // the diagonal stream's kernel
+    if (side) {
+        SYM_CUDA(cudaEventRecord(side->fork, s));
+        SYM_CUDA(cudaStreamWaitEvent(side->stream, side->fork, 0));
+        ds = side->stream;
+    }
     if (ns > 0) {
         if (cfg.strict_kernel == SYM_MTTKRP_PLAIN) {
             const int64_t chunk = cfg.entries_per_warp > 0 ? cfg.entries_per_warp : 256;
@@ -1259,10 +1278,16 @@ sym_status launch_mttkrp_shape(const sym_tensor_s* X, const void* B, int R, int6
         const int64_t gpc = (dthreads / 32) * (32 / L);
         const int64_t cap = sp.bytes > 0 ? (int64_t)sms * (sp.bytes > 100 * 1024 ? 1 : 2) : (int64_t)sms * 16;
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nd + gpc - 1) / gpc, cap));
-        SYM_PROF("mttkrp_diag", s);
-        k_mttkrp_entries<N, KW, L, BF16><<<grid, dthreads, sp.bytes, s>>>(dlo, dhi, X->val + ns, nd, X->bits, B, ldb,
-                                                                          R, M, ldm, sp.H, sp.HB, X->n);
-        SYM_CHECK_LAUNCH();
+        {
+            SYM_PROF("mttkrp_diag", ds);
+            k_mttkrp_entries<N, KW, L, BF16><<<grid, dthreads, sp.bytes, ds>>>(dlo, dhi, X->val + ns, nd, X->bits, B,
+                                                                               ldb, R, M, ldm, sp.H, sp.HB, X->n);
+            SYM_CHECK_LAUNCH();
+        }
+        if (side) {
+            SYM_CUDA(cudaEventRecord(side->join, ds));
+            SYM_CUDA(cudaStreamWaitEvent(s, side->join, 0));
+        }
     }
     return SYM_OK;
 }
