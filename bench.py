@@ -347,6 +347,8 @@ def strict_fiber_counts(order, idx):
     rows = np.sort(np.asarray(idx).T, axis=1)
     rows = rows[np.all(rows[:, 1:] != rows[:, :-1], axis=1)]
     rows = rows[np.lexsort(rows.T[::-1])]
+    if len(rows) > 1:  # repeated tuples (any stored permutation of one entry) count once
+        rows = rows[np.concatenate(([True], np.any(rows[1:] != rows[:-1], axis=1)))]
     change = np.zeros(len(rows), bool)
     if len(rows):
         change[0] = True
