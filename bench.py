@@ -616,6 +616,10 @@ def run_ours(args):
             extras["rows"]["serving_poisson_2000rps"] = serving_row(torch, sg, dev)
         except Exception as e:
             extras["rows"]["serving_poisson_2000rps"] = {"error": repr(e)}
+        try:
+            extras["rows"]["serving_device_loop_20000rps"] = devloop_row(torch, sg, dev)
+        except Exception as e:
+            extras["rows"]["serving_device_loop_20000rps"] = {"error": repr(e)}
 
     out = {"metric": "canonical_nnz_per_s", "value": value, "unit": "canonical nnz/s", "n_gpus": D.ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -1115,6 +1119,147 @@ def serving_row(torch, sg, dev, requests=20000, rate=2000.0, pool_size=32, seed=
             "continuous_batching": cb, "registered_pool_with_eviction": ev, "one_launch_per_request_f32": plain}
 
 
+def devloop_row(torch, sg, dev, requests=20000, rate=20000.0, seed=5):
+    """Poisson arrivals of small requests (70 % MTTKRP of orders 3/4/5 with ranks 8-64, half BF16 factors;
+    30 % SSYMV + SYPRD) served three ways on the same trace: the device-resident loop (one persistent kernel,
+    requests published into mapped memory), one launch per request (synchronised before the next), and, for
+    the MTTKRP requests of the trace alone, the host-scheduled continuous-batching server next to the device
+    loop.  Latency is completion - arrival on the host steady clock (the loop's completion time is its
+    kernel's %globaltimer stamp, calibrated against that clock); 'steady' statistics use the second half."""
+    import threading
+    st = synth.Stream(seed, tag=91)
+    n_t, n_m = 12, 8
+    orders = np.where(st.uniform(n_t) < 0.5, 3, np.where(st.uniform(n_t) < 0.7, 4, 5))
+    ns = np.rint(np.exp(math.log(500.0) + st.uniform(n_t) * math.log(40.0))).astype(np.int64)
+    nnzs = np.rint(np.exp(math.log(2e3) + st.uniform(n_t) * math.log(50.0))).astype(np.int64)
+    tensors = []
+    for k in range(n_t):
+        idx, val = sg.gen_coords(int(orders[k]), int(ns[k]), int(nnzs[k]), seed * 100 + k)
+        tensors.append(sg.SymTensor(idx, val, int(ns[k]), dup=sg.DUP_KEEP_EQUAL))
+    mats = []
+    for k in range(n_m):
+        n = int(round(math.exp(math.log(1e3) + float(st.uniform(1)[0]) * math.log(100.0))))
+        A = synth.upper_csr_rowdegree(n, 8.0 + 24.0 * float(st.uniform(1)[0]), seed * 100 + 50 + k)
+        x = synth.vector_uniform(n, seed * 100 + 50 + k)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        mats.append((n, t(A.rowptr), t(A.col), t(A.val), t(x), int(A.col.shape[0])))
+    ranks = [8, 16, 32, 64]
+    facs = {}
+    for k, X in enumerate(tensors):
+        for R in ranks:
+            B = torch.randn((X.n, R), device=dev, generator=torch.Generator(device=dev).manual_seed(k * 7 + R))
+            B /= math.sqrt(R)
+            facs[(k, R, "f32")] = B
+            facs[(k, R, "bf16")] = B.to(torch.bfloat16)
+    outs = {(k, R): torch.empty((tensors[k].n, R), device=dev) for k in range(n_t) for R in ranks}
+    youts = [(torch.empty(m[0], device=dev), torch.empty(1, dtype=torch.float64, device=dev)) for m in mats]
+    gaps = -np.log(st.uniform_open0(requests)) / rate
+    arrive = np.cumsum(gaps)
+    is_mt = st.uniform(requests) < 0.7
+    which_t = (st.uniform(requests) * n_t).astype(np.int64)
+    which_m = (st.uniform(requests) * n_m).astype(np.int64)
+    rsel = np.array(ranks)[(st.uniform(requests) * 4).astype(np.int64)]
+    dts = np.where(st.uniform(requests) < 0.5, "bf16", "f32")
+    torch.cuda.synchronize()
+    t_ref_ns, t_ref_pc = time.monotonic_ns(), time.perf_counter()
+    to_pc = lambda ns_: t_ref_pc + (ns_ - t_ref_ns) * 1e-9
+
+    def summarize(lat, span, done_pc, base, arr):
+        lat = np.asarray(lat)
+        m = len(lat)
+        h = m // 2
+        span2 = max(done_pc[h:]) - (arr[h] + base)
+        return {"requests": m, "p50_us": float(np.percentile(lat, 50) * 1e6),
+                "p99_us": float(np.percentile(lat, 99) * 1e6), "throughput_req_per_s": m / span,
+                "steady_second_half": {"p50_us": float(np.percentile(lat[h:], 50) * 1e6),
+                                       "p99_us": float(np.percentile(lat[h:], 99) * 1e6),
+                                       "throughput_req_per_s": (m - h) / max(span2, 1e-9)}}
+
+    def submit_dl(L, i):
+        if is_mt[i]:
+            k, R = int(which_t[i]), int(rsel[i])
+            return L.submit_mttkrp(tensors[k], facs[(k, R, str(dts[i]))], outs[(k, R)], tag=i)
+        m = mats[which_m[i]]
+        y, s = youts[which_m[i]]
+        return L.submit_ssymv(m[0], m[1], m[2], m[3], m[4], y, s, tag=i)
+
+    def serve(obj, submit, sel):
+        arr = arrive[sel]
+        tickets = [None] * len(sel)
+        base = time.perf_counter() + 0.05
+
+        def submitter():
+            for j, i in enumerate(sel):
+                while time.perf_counter() < base + arr[j]:
+                    pass
+                tickets[j] = submit(obj, i)
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        done_pc = []
+        for tk in tickets:
+            r = obj.wait(tk, 300.0)
+            assert r["status"] == 0
+            done_pc.append(to_pc(r["t_done_ns"]))
+        lat = [done_pc[j] - (base + arr[j]) for j in range(len(sel))]
+        return summarize(lat, max(done_pc) - base, done_pc, base, arr)
+
+    everything = np.arange(requests)
+    only_mt = np.nonzero(is_mt)[0]
+    L = sg.DevLoop(ring_slots=1024, idle_exit_s=0.002)
+    dl = serve(L, submit_dl, everything)
+    dl["loop_stats"] = L.stats()
+    L.close()
+    # one launch per request, synchronised before the next, in arrival order (FP32 and BF16 as in the trace)
+    torch.cuda.synchronize()
+    base = time.perf_counter() + 0.05
+    lat, done = [], []
+    ws = {}
+    for i in everything:
+        while time.perf_counter() < base + arrive[i]:
+            pass
+        if is_mt[i]:
+            k, R = int(which_t[i]), int(rsel[i])
+            tensors[k].mttkrp(facs[(k, R, str(dts[i]))], M=outs[(k, R)])
+        else:
+            j = int(which_m[i])
+            m = mats[j]
+            if j not in ws:
+                ws[j] = sg.spmv_workspace(m[0], m[1], m[2], m[3])
+            sg.spmv(m[0], m[1], m[2], m[3], m[4], y=youts[j][0], syprd=True, ws=ws[j])
+        torch.cuda.synchronize()
+        done.append(time.perf_counter())
+        lat.append(done[-1] - (base + arrive[i]))
+    plain = summarize(lat, max(done) - base, done, base, arrive)
+    # the MTTKRP requests alone: host-scheduled server (grouped small requests) and the device loop
+    S = sg.Server(max_slots=8, max_rank=64, hbm_budget_bytes=120 << 30, small_nnz=1_000_000, coalesce_small=True)
+    srv = serve(S, lambda S_, i: S_.submit(tensors[which_t[i]], facs[(int(which_t[i]), int(rsel[i]), str(dts[i]))],
+                                           outs[(int(which_t[i]), int(rsel[i]))], residual=False, tag=i), only_mt)
+    srv["server_stats"] = S.stats()
+    S.close()
+    L = sg.DevLoop(ring_slots=1024, idle_exit_s=0.002)
+    dl_mt = serve(L, submit_dl, only_mt)
+    L.close()
+    work = {"tensors": n_t, "orders": [int(o) for o in orders], "tensor_canonical_nnz": [X.nnz for X in tensors],
+            "matrices": n_m, "matrix_n": [m[0] for m in mats], "matrix_nnz": [m[5] for m in mats]}
+    for X in tensors:
+        X.close()
+    return {"requests": requests, "rate_req_per_s": rate, "mttkrp_share": float(is_mt.mean()), "pool": work,
+            "device_loop": dl, "one_launch_per_request": plain,
+            "mttkrp_only": {"requests": int(only_mt.size), "device_loop": dl_mt, "host_scheduled_server": srv}}
+
+
+def run_devloop_only(args):
+    """The device-resident serving row alone."""
+    import torch
+
+    import paper_2406_09266_gb300 as sg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sg.load()
+    print(json.dumps({"mode": "devloop-only", "serving_device_loop_20000rps": devloop_row(torch, sg, dev)}))
+
+
 def run_batch_only(args):
     """Profiling mode for the batched SSYMV: one fixed shape (--batch-cfg), plain runs (no graph)."""
     import torch
@@ -1204,6 +1349,8 @@ def main():
                     help="profiling mode: the partially symmetric MTTKRP row alone")
     ap.add_argument("--small-only", action="store_true",
                     help="profiling mode: the 2,000 x 2,000 SSYMV + SYPRD row alone")
+    ap.add_argument("--devloop-only", action="store_true",
+                    help="the device-resident serving row alone")
     ap.add_argument("--batch-only", type=int, default=0, metavar="INSTANCES",
                     help="profiling mode: build a batch of this many instances and run the batched SSYMV a few times")
     ap.add_argument("--batch-cfg", default="", metavar="FIELDS",
@@ -1221,6 +1368,8 @@ def main():
         run_ptensor_only(args)
     elif args.small_only:
         run_small_only(args)
+    elif args.devloop_only:
+        run_devloop_only(args)
     else:
         run_ours(args)
 

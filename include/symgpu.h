@@ -809,6 +809,74 @@ sym_status sym_server_stats_get(sym_server S, sym_server_stats* out);
  * has finished them (for instance until cudaDeviceSynchronize returns). */
 sym_status sym_server_destroy(sym_server S);
 
+/* ===================================================================== */
+/* Serving: device-resident request loop (MTTKRP and SSYMV / SYPRD)          */
+/* ===================================================================== */
+
+/* One persistent kernel serves requests of any order, rank, factor type and
+ * kind (symmetric MTTKRP, Sec. 4.3 / Sec. 5.2.6; SSYMV with optional SYPRD,
+ * Sec. 3.1 / Sec. 5.2.1 / Sec. 5.2.3) on resident tensors and matrices.  A
+ * request is published into a ring in mapped host memory; the kernel's CTAs
+ * claim its chunks (output clearing first, then entry ranges), and the CTA that
+ * finishes the last chunk writes a completion word back into mapped memory.  No
+ * kernel is launched per request: the loop kernel runs while there is work and
+ * leaves after cfg.idle_exit_ns without any (the next submission launches it
+ * again).  MTTKRP runs in the per-entry form (every canonical entry updates the
+ * rows of its distinct indices with their arrangement weights), so the loop
+ * suits many small requests; the single calls stay faster for large ones.
+ * Inputs (tensor, factor, CSR, x) must be complete on the device before their
+ * submission; they are read through L2 only, so they may be rewritten between
+ * requests.  Floating-point atomics: not bitwise reproducible. */
+typedef struct sym_devloop_s* sym_devloop;
+
+typedef struct {
+    int32_t ring_slots;        /* requests published at once (power of two, 16..4096) */
+    int32_t ctas;              /* CTAs of the loop kernel (0: two per SM) */
+    size_t hbm_budget_bytes;   /* bound on the bytes touched by the published requests */
+    int64_t idle_exit_ns;      /* the loop kernel leaves after this long without a published request (> 0) */
+    int64_t wait_limit_ns;     /* bound of the kernel's internal waits and of sym_devloop_destroy's drain (> 0) */
+} sym_devloop_cfg;
+
+/* Allocates the ring, control and completion words (page-locked, mapped) and
+ * the device counters, and calibrates the device clock against the host's
+ * steady clock (result timestamps are host steady-clock nanoseconds).
+ * Synchronous; SYM_E_INVALID for a bad cfg. */
+sym_status sym_devloop_create(const sym_devloop_cfg* cfg, int device, sym_devloop* out);
+/* M = MTTKRP(X, B) for a resident tensor (req->X; want_residual must be 0).
+ * M [device, n x rank, row stride ldm] is overwritten (cleared by the loop);
+ * argument rules as sym_mttkrp.  Requests are published in submission order
+ * while a ring slot is free and the published requests' bytes (tensor arena,
+ * factor, output) stay within the budget; the rest wait on the host and are
+ * published by later calls (submit, poll, wait).  A request larger than the
+ * whole budget fails with SYM_E_BUDGET; a malformed one with SYM_E_BADREQ.
+ * The caller keeps every buffer alive until the request is done. */
+sym_status sym_devloop_submit_mttkrp(sym_devloop L, const sym_request* req, uint64_t* ticket);
+/* y = A x for an upper CSR (as sym_spmv; trusted, column indices outside
+ * [0, n) skipped); y [device, n floats] overwritten; syprd [device, 1 double,
+ * nullable] receives x^T A x (off-diagonal terms twice), FP32 per thread and
+ * FP64 across threads and chunks. */
+sym_status sym_devloop_submit_ssymv(sym_devloop L, const sym_csr_upper* A, const float* x, float* y,
+                                    double* syprd, uint64_t user_tag, uint64_t* ticket);
+/* SYM_PENDING until the request is done; then its result (once): status
+ * SYM_OK, or SYM_E_TIMEOUT when an internal wait of the kernel ran out (its
+ * outputs are then undefined, SYPRD NaN).  t_admit_ns is the publication time,
+ * t_done_ns the kernel's completion time on the host clock.  Also retires
+ * finished requests and publishes waiting ones. */
+sym_status sym_devloop_poll(sym_devloop L, uint64_t ticket, sym_result* out);
+/* Polls until the request is done or timeout_ns runs out (SYM_E_TIMEOUT). */
+sym_status sym_devloop_wait(sym_devloop L, uint64_t ticket, int64_t timeout_ns, sym_result* out);
+typedef struct {
+    int64_t submitted, published, completed, rejected;
+    int64_t launches;       /* launches of the loop kernel */
+    int64_t peak_inflight;  /* published requests not yet retired, at most */
+    int64_t peak_bytes;     /* their bytes, at most */
+} sym_devloop_stats;
+sym_status sym_devloop_stats_get(sym_devloop L, sym_devloop_stats* out);
+/* Drains submitted work (bounded by cfg.wait_limit_ns), stops the loop kernel
+ * and frees everything.  SYM_E_TIMEOUT if the drain ran out (requests still
+ * waiting are dropped; the kernel finishes the chunks it holds and leaves). */
+sym_status sym_devloop_destroy(sym_devloop L);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

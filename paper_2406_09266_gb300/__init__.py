@@ -107,6 +107,17 @@ class ServerStats(C.Structure):
                 ("gram_hits", C.c_int64)]
 
 
+class DevLoopCfg(C.Structure):
+    _fields_ = [("ring_slots", C.c_int32), ("ctas", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
+                ("idle_exit_ns", C.c_int64), ("wait_limit_ns", C.c_int64)]
+
+
+class DevLoopStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("published", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("launches", C.c_int64), ("peak_inflight", C.c_int64),
+                ("peak_bytes", C.c_int64)]
+
+
 class MttkrpCfg(C.Structure):
     _fields_ = [("strict_kernel", C.c_int32), ("entries_per_warp", C.c_int32), ("threads_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("strict_smem_kb", C.c_int32), ("diag_smem_kb", C.c_int32),
@@ -238,6 +249,13 @@ _SIGS = {
     "sym_batch_wait": ([C.c_void_p, C.c_uint64, C.c_int64, C.c_void_p], C.c_int),
     "sym_server_stats_get": ([C.c_void_p, C.c_void_p], C.c_int),
     "sym_server_destroy": ([C.c_void_p], C.c_int),
+    "sym_devloop_create": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "sym_devloop_submit_mttkrp": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "sym_devloop_submit_ssymv": ([C.c_void_p] * 5 + [C.c_uint64, C.c_void_p], C.c_int),
+    "sym_devloop_poll": ([C.c_void_p, C.c_uint64, C.c_void_p], C.c_int),
+    "sym_devloop_wait": ([C.c_void_p, C.c_uint64, C.c_int64, C.c_void_p], C.c_int),
+    "sym_devloop_stats_get": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_devloop_destroy": ([C.c_void_p], C.c_int),
 }
 
 
@@ -1028,6 +1046,77 @@ class Server:
             code = lib().sym_server_destroy(self.handle)
             self.handle = None
             check(code, "sym_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _result_dict(r):
+    return {"status": r.status, "residual": r.residual, "tag": r.user_tag, "t_submit_ns": r.t_submit_ns,
+            "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns}
+
+
+class DevLoop:
+    """Device-resident request loop (sym_devloop_*): one persistent kernel serves MTTKRP and SSYMV / SYPRD
+    requests published into a ring in mapped host memory."""
+
+    def __init__(self, ring_slots=1024, ctas=0, hbm_budget_bytes=120 << 30, idle_exit_s=0.002, wait_limit_s=10.0,
+                 device=None):
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.cfg = DevLoopCfg(ring_slots, ctas, hbm_budget_bytes, int(idle_exit_s * 1e9), int(wait_limit_s * 1e9))
+        h = C.c_void_p()
+        check(lib().sym_devloop_create(C.byref(self.cfg), dev.index, C.byref(h)), "sym_devloop_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit_mttkrp(self, X: "SymTensor", B, M, tag=0) -> int:
+        """Queues M = MTTKRP(X, B) (M overwritten)."""
+        req = Request(X.handle.value, B.data_ptr(), _dtype_code(B), B.shape[1], B.stride(0), M.data_ptr(),
+                      M.stride(0), 0, tag)
+        t = C.c_uint64(0)
+        check(lib().sym_devloop_submit_mttkrp(self.handle, C.byref(req), C.byref(t)), "sym_devloop_submit_mttkrp")
+        self._keep[t.value] = (X, B, M)
+        return t.value
+
+    def submit_ssymv(self, n, rowptr, col, val, x, y, syprd=None, tag=0) -> int:
+        """Queues y = A x (and x^T A x into syprd, a 1-element float64 tensor, when given)."""
+        A = csr_upper(n, rowptr, col, val)
+        t = C.c_uint64(0)
+        check(lib().sym_devloop_submit_ssymv(self.handle, C.byref(A), _ptr(x), _ptr(y), _ptr(syprd), tag,
+                                             C.byref(t)), "sym_devloop_submit_ssymv")
+        self._keep[t.value] = (rowptr, col, val, x, y, syprd)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending; else a dict with status and timestamps."""
+        r = Result()
+        code = lib().sym_devloop_poll(self.handle, ticket, C.byref(r))
+        if code == SYM_PENDING:
+            return None
+        check(code, "sym_devloop_poll")
+        self._keep.pop(ticket, None)
+        return _result_dict(r)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        r = Result()
+        check(lib().sym_devloop_wait(self.handle, ticket, int(timeout_s * 1e9), C.byref(r)), "sym_devloop_wait")
+        self._keep.pop(ticket, None)
+        return _result_dict(r)
+
+    def stats(self) -> dict:
+        st = DevLoopStats()
+        check(lib().sym_devloop_stats_get(self.handle, C.byref(st)), "sym_devloop_stats_get")
+        return {f: getattr(st, f) for f, _ in DevLoopStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            code = lib().sym_devloop_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+            check(code, "sym_devloop_destroy")
 
     def __del__(self):
         try:

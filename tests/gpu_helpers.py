@@ -14,6 +14,14 @@ import synth
 TOL_F32 = 1e-5
 TOL_BF16 = 1e-2
 
+
+def tol_bf16(order):
+    """BF16 factors against the oracle on the FP32 factors: 1e-2, or the rounding bound when that is larger.
+    Each of a term's order - 1 factor values carries a relative rounding error of at most u = 2^-8 (8-bit
+    significand, round to nearest even), so a term is off by at most (1 + u)^(order-1) - 1 of its magnitude:
+    7.8e-3 for order 3, 1.18e-2 for order 4, 1.57e-2 for order 5 (reached by output rows with one term)."""
+    return max(TOL_BF16, (1.0 + 2.0 ** -8) ** (order - 1) - 1.0 + TOL_F32)
+
 torch = pytest.importorskip("torch")
 
 
