@@ -13,9 +13,10 @@
  *   - Indices are 0-based.  Dense matrices are row-major with an explicit row
  *     stride (ld*) in elements.
  *   - Pointers marked [device] are CUDA device pointers; [host] are host
- *     pointers.  All device memory is owned by the caller (the library never
- *     calls cudaMalloc/cudaFree): handles and scratch are carved out of
- *     caller-given arenas and workspaces whose sizes come from the *_bytes
+ *     pointers.  All device memory is owned by the caller (the library calls
+ *     cudaMalloc/cudaFree only in sym_devloop_create / sym_devloop_destroy, for
+ *     the request loop's own ring and counters): handles and scratch are carved
+ *     out of caller-given arenas and workspaces whose sizes come from the *_bytes
  *     queries.  Arenas and workspaces must be 256-byte aligned.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Compute calls are asynchronous on that stream unless documented otherwise.
@@ -865,6 +866,12 @@ sym_status sym_devloop_submit_ssymv(sym_devloop L, const sym_csr_upper* A, const
 sym_status sym_devloop_poll(sym_devloop L, uint64_t ticket, sym_result* out);
 /* Polls until the request is done or timeout_ns runs out (SYM_E_TIMEOUT). */
 sym_status sym_devloop_wait(sym_devloop L, uint64_t ticket, int64_t timeout_ns, sym_result* out);
+/* Test hook of the loop's bounded zero-chunk wait (no paper counterpart): with
+ * hook = 1, requests submitted from now on have their zero chunks done but not
+ * counted, so their compute chunks' wait runs out after cfg.wait_limit_ns and
+ * they complete with SYM_E_TIMEOUT (outputs undefined, SYPRD NaN) while the
+ * loop goes on serving; hook = 0 restores normal requests. */
+sym_status sym_devloop_set_test_hook(sym_devloop L, int hook);
 typedef struct {
     int64_t submitted, published, completed, rejected;
     int64_t launches;       /* launches of the loop kernel */

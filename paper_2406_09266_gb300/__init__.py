@@ -255,6 +255,7 @@ _SIGS = {
     "sym_devloop_poll": ([C.c_void_p, C.c_uint64, C.c_void_p], C.c_int),
     "sym_devloop_wait": ([C.c_void_p, C.c_uint64, C.c_int64, C.c_void_p], C.c_int),
     "sym_devloop_stats_get": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sym_devloop_set_test_hook": ([C.c_void_p, C.c_int], C.c_int),
     "sym_devloop_destroy": ([C.c_void_p], C.c_int),
 }
 

@@ -62,7 +62,8 @@ constexpr int32_t DL_MTTKRP = 1, DL_SSYMV = 2;
 // One request as the loop kernel reads it (host-written, mapped memory).
 struct DLReq {
     int32_t kind, order, kw, bits;
-    int32_t bf16, rank, lanes, pad0;
+    int32_t bf16, rank, lanes;
+    int32_t hook;     // test hook: 1 = the zero chunks are done but not counted (the compute chunks' wait runs out)
     int64_t n, nnz;
     int64_t zchunks;  // zero chunks (first), then compute chunks
     int64_t nchunks;  // all chunks
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(DL_THREADS) k_devloop(DLArgs a) {
                 atomicAdd(a.acc + slot, s);
             }
             __threadfence();
-            if (k < Z) atomicAdd(a.zdone + slot, 1u);
+            if (k < Z && s_req.hook != 1) atomicAdd(a.zdone + slot, 1u);
             const unsigned prev = atomicAdd(a.done + slot, 1u);
             if (prev + 1 == (unsigned)s_req.nchunks) dl_finish(a, s_req, r, slot);
         }
@@ -472,6 +473,7 @@ struct sym_devloop_s {
     std::unordered_map<uint64_t, Flight> flight;
     std::unordered_map<uint64_t, sym_result> results;
     size_t inflight_bytes = 0;
+    int hook = 0;  // test hook copied into the requests submitted while it is set
     sym_devloop_stats stats{};
 };
 
@@ -548,6 +550,7 @@ sym_status dl_submit(sym_devloop L, const DLReq& q, size_t bytes, uint64_t tag, 
         return SYM_E_BUDGET;
     }
     Queued h{q, bytes, host_ns(), tag, L->next_ticket++};
+    h.q.hook = L->hook;
     L->queue.push_back(h);
     L->stats.submitted += 1;
     *ticket = h.ticket;
@@ -742,6 +745,13 @@ extern "C" sym_status sym_devloop_wait(sym_devloop L, uint64_t ticket, int64_t t
         if (host_ns() > deadline) return SYM_E_TIMEOUT;
         std::this_thread::sleep_for(std::chrono::microseconds(10));
     }
+}
+
+extern "C" sym_status sym_devloop_set_test_hook(sym_devloop L, int hook) {
+    if (!L || hook < 0 || hook > 1) return SYM_E_INVALID;
+    std::lock_guard<std::mutex> lk(L->mu);
+    L->hook = hook;
+    return SYM_OK;
 }
 
 extern "C" sym_status sym_devloop_stats_get(sym_devloop L, sym_devloop_stats* out) {

@@ -217,3 +217,31 @@ def test_devloop_budget_admission_empty_inputs_and_bad_requests():
     assert L.stats()["rejected"] == 0
     L.close()
     X.close()
+
+
+def test_devloop_zero_wait_runs_out_and_loop_goes_on():
+    """The compute chunks' bounded wait for the zero chunks, made to run out without any fault: the test hook
+    leaves one request's zero chunks uncounted; that request completes with SYM_E_TIMEOUT and NaN SYPRD, the
+    loop kernel keeps running, and the next request is exact."""
+    sg = need_gpu()
+    A = synth.upper_csr_uniform(2000, 30000, 11)
+    x = synth.vector_uniform(2000, 11)
+    rp, cl, vl, xd = dev(A.rowptr), dev(A.col), dev(A.val), dev(x)
+    y1, y2 = torch.empty(2000, device="cuda"), torch.empty(2000, device="cuda")
+    s1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    s2 = torch.empty(1, dtype=torch.float64, device="cuda")
+    yr, ya, sr, sa = ssymv_ref(A, x)
+    torch.cuda.synchronize()
+    L = sg.DevLoop(ring_slots=16, ctas=4, idle_exit_s=2.0, wait_limit_s=0.005)
+    sg.check(sg.lib().sym_devloop_set_test_hook(L.handle, 1), "sym_devloop_set_test_hook")
+    t1 = L.submit_ssymv(2000, rp, cl, vl, xd, y1, s1)
+    sg.check(sg.lib().sym_devloop_set_test_hook(L.handle, 0), "sym_devloop_set_test_hook")
+    r1 = L.wait(t1, 60)
+    assert r1["status"] == -7
+    assert np.isnan(float(s1.item()))
+    r2 = L.wait(L.submit_ssymv(2000, rp, cl, vl, xd, y2, s2), 60)
+    assert r2["status"] == 0
+    assert oracle.componentwise_error(host(y2), yr, ya) <= TOL_F32
+    assert abs(float(s2.item()) - sr) / sa <= TOL_F32
+    assert L.stats()["launches"] == 1
+    L.close()
