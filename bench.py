@@ -780,6 +780,22 @@ def small_ssymv_row(torch, sg, dev, flush, stream, n=2000, nnz=20000, seed=0, K=
         sg.bellman_step(n, rp, cl, vl, dd, y=yb)
     t = timed_steps(torch, lambda: sg.bellman_step(n, rp, cl, vl, dd, y=yb), K, flush, stream)
     row["bellman_ford_step_ms"] = float(np.mean(t))
+    try:
+        import oracle
+        x64 = x.astype(np.float64)
+        yr, ya = oracle.ssymv(n, A.rowptr, A.col, A.val, x64)
+        sr, sa = oracle.syprd(n, A.rowptr, A.col, A.val, x64)
+        y1, s1 = sg.spmv(n, rp, cl, vl, xd, syprd=True, ws=ws)
+        torch.cuda.synchronize()
+        bref = oracle.bellman(n, A.rowptr, A.col, A.val, np.abs(x).astype(np.float64))
+        row["error"] = {"ssymv_componentwise": oracle.componentwise_error(y1.cpu().numpy(), yr, ya),
+                        "syprd_relative": abs(float(s1.item()) - sr) / sa,
+                        "noalloc_graph_ssymv_componentwise": oracle.componentwise_error(y.cpu().numpy(), yr, ya),
+                        "noalloc_graph_syprd_relative": abs(float(s_out.item()) - sr) / sa,
+                        "bellman_ford_max_abs_diff": float(np.max(np.abs(yb.cpu().numpy().astype(np.float64) - bref))),
+                        "gate": "SSYMV / SYPRD <= 1e-5 (componentwise / relative to the sum of |terms|, FP64 oracle)"}
+    except Exception as e:
+        row["error"] = {"error": repr(e)}
     return row
 
 
@@ -813,6 +829,16 @@ def ptensor_row(torch, sg, dev, flush, stream, hbm_peak, parts=(2, 2), dims=(20_
                            "max_abs_diff_vs_expanded": float((Me - ref).abs().max())}
     E.close()
     X.close()
+    try:
+        import oracle
+        pc, pv = oracle.pcanonicalize(parts, dims, T.idx, T.val)
+        F64 = [f.cpu().numpy().astype(np.float64) for f in F]
+        for o in range(len(parts)):
+            rf, ra = oracle.pmttkrp_enum(parts, dims, pc, pv, F64, o)
+            out[f"part{o}"]["error"] = {"componentwise": oracle.componentwise_error(Ms[o].cpu().numpy(), rf, ra),
+                                        "gate": "<= 1e-5 componentwise (FP64 oracle, every row)"}
+    except Exception as e:
+        out["error"] = {"error": repr(e)}
     return out
 
 
@@ -847,6 +873,22 @@ def large_ssymv_row(torch, sg, dev, flush, stream, hbm_peak, n=1 << 21, per_row=
     tb = timed_steps(torch, lambda: sg.bellman_step(n, rp, cl, vl, d, y=yb), 10, flush, stream)
     out["bellman_ford_step_ms"] = float(np.mean(tb))
     out["bellman_ford_effective_gbs"] = alg / (out["bellman_ford_step_ms"] * 1e-3) / 1e9
+    try:
+        import oracle
+        y1, s1 = sg.spmv(n, rp, cl, vl, x, syprd=True, ws=ws)
+        torch.cuda.synchronize()
+        rp_h = rp.cpu().numpy().astype(np.int32)
+        cl_h = cl.cpu().numpy().astype(np.int32)
+        vl_h = vl.cpu().numpy().astype(np.float32)
+        x64 = x.cpu().numpy().astype(np.float64)
+        yr, ya = oracle.ssymv(n, rp_h, cl_h, vl_h, x64)
+        sr, sa = oracle.syprd(n, rp_h, cl_h, vl_h, x64)
+        out["error"] = {"ssymv_componentwise": oracle.componentwise_error(y1.cpu().numpy(), yr, ya),
+                        "syprd_relative": abs(float(s1.item()) - sr) / sa,
+                        "full_csr_componentwise": oracle.componentwise_error(yf.cpu().numpy(), yr, ya),
+                        "gate": "<= 1e-5 (componentwise / relative to the sum of |terms|, FP64 oracle, every row)"}
+    except Exception as e:
+        out["error"] = {"error": repr(e)}
     return out
 
 
@@ -892,6 +934,24 @@ def ttm_row(torch, sg, dev, flush, stream, hbm_peak, n=2000, nnz=5_000_000, rank
     out["max_abs_diff_full_vs_expanded"] = float((Cf - Ce).abs().max())
     E.close()
     X.close()
+    try:
+        # sampled output rows j against the FP64 oracle: C[j, :, :] of the full output and the packed
+        # positions j <= l of row j (at j n - j (j - 1) / 2 + (l - j))
+        import oracle
+        sel = np.unique(np.concatenate([[0, 1, n - 1], synth.Stream(seed, tag=93).randint(13, n)]))
+        cidx, cval = oracle.canonicalize(3, n, T.idx, T.val)
+        ref, ra = oracle.ttm_enum(3, n, cidx, cval, synth.factor_normal(n, rank, seed).astype(np.float64), rows=sel)
+        full = Cf[torch.from_numpy(sel).to(dev)].cpu().numpy()
+        Cph = Cp.cpu().numpy()
+        packed = np.concatenate([Cph[int(j) * n - int(j) * (int(j) - 1) // 2:][:n - int(j)] for j in sel])
+        out["error"] = {"rows_sampled": int(sel.size),
+                        "full_componentwise": oracle.componentwise_error(full, ref, ra),
+                        "packed_componentwise": oracle.componentwise_error(
+                            packed, np.concatenate([ref[s_, int(j):] for s_, j in enumerate(sel)]),
+                            np.concatenate([ra[s_, int(j):] for s_, j in enumerate(sel)])),
+                        "gate": "<= 1e-5 componentwise (FP64 oracle)"}
+    except Exception as e:
+        out["error"] = {"error": repr(e)}
     return out
 
 
