@@ -12,8 +12,11 @@ Also reported: the dominant kernel's roofline fraction from live per-kernel CUDA
 events, an end-to-end figure through the public API with host buffers
 (copies of the coordinate list and factor in, the result out, canonicalisation
 included), the FP64 CPU oracle on a bounded sample, the expanded non-symmetric
-baseline, the CP-fit residual cost, the 4-/5-way and SSYMV workloads, and the
-SM clocks sampled during the timed region.
+baseline, the CP-fit residual cost, the 4-/5-way, SSYMV, TTM, partial-symmetry and
+batched workloads (each with its error against the FP64 oracle), two serving traces
+(host-scheduled continuous batching at 2,000 req/s; the device-resident request loop
+at 20,000 req/s of small MTTKRP and SSYMV requests), and the SM clocks sampled
+during the timed region.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--rows main|all]
 """
