@@ -1,9 +1,9 @@
 """Helpers shared by the GPU parity tests (device transfer, oracle references, tolerances).
 
 Tolerances (componentwise error max |got - ref| / sum|terms|, ref and sum|terms|
-from the FP64 oracle): FP32 factors 1e-5; BF16 factors 1e-2 against the oracle
-on the original FP32 factors, and 1e-5 against the oracle on the BF16-rounded
-factors.
+from the FP64 oracle): FP32 factors 1e-5; BF16 factors 1e-5 against the oracle
+on the BF16-rounded factors, and 1e-2 against the oracle on the original FP32
+factors (tol_bf16: the BF16 rounding bound where that is larger, orders 4 and 5).
 """
 import numpy as np
 import pytest
